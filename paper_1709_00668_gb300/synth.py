@@ -1,0 +1,116 @@
+"""Seeded synthetic tensors shaped like the paper's planted workloads.
+
+This module is the one piece shared by the FP64 oracle's tests and the CUDA
+path's tests and benchmark.  It holds no arithmetic of the method itself: it
+only draws planted CP factors and noise (Section 5.1.1 of the paper: tensors
+built from known, randomly generated factors) and hands out the same bytes to
+both sides.
+
+Recipe (dense):
+    A, B, C  ~ U[0, 1) i.i.d., lambda = 1
+    X(i, j, k) = sum_r A(i, r) B(j, r) C(k, r) + eps,
+    eps ~ N(0, sigma^2), sigma = c * RMS(noiseless X over the full final tensor)
+Layout: slice-major, X[k, i, j] (k = time mode), i.e. element (i, j, k) sits at
+offset (k * I + i) * J + j.
+
+Optionally (`cond`), the factors are mixed toward a shared direction,
+a_r <- (1 - beta) u_r + beta u_0, with beta found by bisection so that the
+condition number of each factor Gram is about `cond` (values stay in [0, 1]).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+
+@dataclass
+class Planted:
+    X: torch.Tensor          # (K_total, I, J), slice-major, requested dtype
+    A: torch.Tensor          # (I, R) float64, planted
+    B: torch.Tensor          # (J, R)
+    C: torch.Tensor          # (K_total, R)
+    sigma: float             # noise standard deviation actually used
+
+    def slices(self, k0: int, k1: int) -> torch.Tensor:
+        return self.X[k0:k1]
+
+
+def _gen(seed: int, device) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def _mix_to_condition(U: torch.Tensor, target: float) -> torch.Tensor:
+    """Mix columns toward the first one until cond(U^T U) ~= target."""
+    if target is None or U.shape[1] < 2:
+        return U
+    u0 = U[:, :1]
+
+    def cond_of(beta: float) -> float:
+        M = (1.0 - beta) * U + beta * u0
+        ev = torch.linalg.eigvalsh(M.T @ M)
+        return float(ev[-1] / ev[0].clamp_min(1e-300))
+
+    lo, hi = 0.0, 0.999
+    if cond_of(lo) >= target:
+        return U
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if cond_of(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    beta = 0.5 * (lo + hi)
+    return (1.0 - beta) * U + beta * u0
+
+
+def planted_dense(I: int, J: int, K: int, R: int, *, noise: float = 0.01,
+                  seed: int = 0, dtype=torch.float32, device="cpu",
+                  cond: float | None = None, dist: str = "uniform") -> Planted:
+    """Planted rank-R dense tensor (K slices of I x J), seeded.
+
+    `dist` is "uniform" (U[0,1) factors, the paper's recipe) or "normal"
+    (N(0,1) factors, better conditioned; used by small pin tests).
+    The noiseless tensor is formed in float32 on CUDA devices (float64 on the
+    CPU), the noise in the same type; the result is cast to `dtype`.
+    """
+    dev = torch.device(device)
+    g = _gen(seed, dev)
+    draw = torch.rand if dist == "uniform" else torch.randn
+    A = draw(I, R, generator=g, device=dev, dtype=torch.float64)
+    B = draw(J, R, generator=g, device=dev, dtype=torch.float64)
+    C = draw(K, R, generator=g, device=dev, dtype=torch.float64)
+    if cond is not None:
+        A = _mix_to_condition(A, cond)
+        B = _mix_to_condition(B, cond)
+        C = _mix_to_condition(C, cond)
+    work = torch.float64 if dev.type == "cpu" else torch.float32
+    # noiseless X_(3) = C (A kr B)^T, slice by slice to bound memory
+    AB = (A[:, None, :] * B[None, :, :]).reshape(I * J, R).to(work)
+    X = torch.empty(K, I, J, dtype=work, device=dev)
+    step = max(1, (1 << 28) // max(1, I * J))
+    sumsq = 0.0
+    for k0 in range(0, K, step):
+        k1 = min(K, k0 + step)
+        blk = (C[k0:k1].to(work) @ AB.T).reshape(k1 - k0, I, J)
+        X[k0:k1] = blk
+        sumsq += float((blk.double() ** 2).sum())
+    rms = math.sqrt(sumsq / max(1, I * J * K))
+    sigma = float(noise) * rms
+    if sigma > 0:
+        for k0 in range(0, K, step):
+            k1 = min(K, k0 + step)
+            X[k0:k1] += sigma * torch.randn(k1 - k0, I, J, generator=g,
+                                             device=dev, dtype=work)
+    return Planted(X=X.to(dtype), A=A, B=B, C=C, sigma=sigma)
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> list[float]:
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    g = _gen(seed, "cpu")
+    gaps = torch.empty(n, dtype=torch.float64).exponential_(1.0, generator=g)
+    t = torch.cumsum(gaps / float(rate), 0)
+    return [float(x) for x in t]
