@@ -1,0 +1,198 @@
+/*
+ * sambaten.h -- C ABI of a GB300-native (sm_103a) batch-incremental CP update,
+ * after SamBaTen: "Sampling-based Batch Incremental Tensor Decomposition"
+ * (Gujral, Pasricha, Papalexakis; arxiv 1709.00668).
+ *
+ * The calls follow the paper's problem statement (Section 3.2): given a CP
+ * decomposition A, B, C, lambda of an I x J x K1 tensor and a batch of K2 new
+ * slices along the third (time) mode, return A, B and a C with K1 + K2 rows.
+ * One sbt_update runs Algorithm 1 once on the GPU: sample each mode by its
+ * measure of importance (Eq. 1), gather r summaries, CP-ALS each summary,
+ * normalise over the shared rows, match components (Lemma 1), project back and
+ * append the averaged new rows of C.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an sbt_status; SBT_OK is 0.  On any error a message
+ *     is available from sbt_last_error() (thread-local).
+ *   - Dense tensors are slice-major: element (i, j, k) of an I x J x K tensor
+ *     sits at data[(k * I + i) * J + j] (k is the time mode).
+ *   - Factor matrices are row-major n x R doubles: U[x * R + r].
+ *   - Input buffers are borrowed for the duration of the call and copied; the
+ *     caller keeps ownership.  on_device = 1 means the pointer is device memory
+ *     of the context's device, ordered on the context's CUDA stream.
+ *   - Output buffers are caller-owned host memory unless stated otherwise.
+ *   - R <= SBT_MAX_RANK, r <= SBT_MAX_REPS.
+ *   - Everything computes on the GPU; there is no CPU fallback.  A missing
+ *     GPU or a CUDA failure is reported as SBT_E_CUDA.
+ */
+#ifndef SAMBATEN_H
+#define SAMBATEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBT_MAX_RANK 32
+#define SBT_MAX_REPS 64
+
+typedef struct sbt_ctx sbt_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    SBT_OK = 0,
+    SBT_E_INVALID = 1,   /* bad argument (null pointer, out-of-range option) */
+    SBT_E_SHAPE = 2,     /* shape mismatch (I, J differ from init; K_new < 1) */
+    SBT_E_NOMEM = 3,     /* device allocation failed */
+    SBT_E_CUDA = 4,      /* CUDA runtime error or no usable device */
+    SBT_E_NONFINITE = 5, /* the new slices hold NaN or Inf; state unchanged */
+    SBT_E_RANGE = 6,     /* a fixed-point marginal would overflow 64 bits; state unchanged */
+    SBT_E_TIMEOUT = 7,   /* a bounded device wait gave up */
+    SBT_E_STATE = 8      /* call not valid in the context's current state */
+} sbt_status;
+
+typedef enum { SBT_F64 = 0, SBT_F32 = 1 } sbt_dtype; /* storage type of X */
+
+/* Arithmetic of the summary MTTKRP (the hot loop).  F64: float64 throughout
+ * (needs an F64 store).  F32: float32 values, float32 accumulation.  BF16:
+ * summary rounded to bfloat16 (nearest-even), float32 accumulation.  The R x R
+ * Cholesky factorisation, inversion, column norms and the fit stay float64 in
+ * every mode. */
+typedef enum { SBT_PREC_F64 = 0, SBT_PREC_F32 = 1, SBT_PREC_BF16 = 2 } sbt_prec;
+
+/* Update flags (sbt_update_stats.flags), OR-ed over repetitions. */
+#define SBT_FLAG_CHOL_REGULARIZED 1 /* a Gram Hadamard product was not positive definite */
+#define SBT_FLAG_ZERO_COLUMN 2      /* a factor column had zero norm */
+#define SBT_FLAG_SAMPLE_LT_RANK 4   /* a sample had fewer indices than R */
+
+typedef struct {
+    int32_t dtype;     /* sbt_dtype of data */
+    int32_t on_device; /* 1: data is device memory; 0: host memory */
+    int64_t I, J, K;   /* dense, slice-major */
+    const void *data;
+} sbt_tensor;
+
+typedef struct {
+    int32_t s_I, s_J, s_K; /* sampling factors: a sample keeps ceil(N/s) indices (Section 4.1) */
+    int32_t r;             /* repetitions (independent summaries per batch) */
+    double tol;            /* ALS stops when |fit - previous fit| < tol */
+    int32_t max_iters;     /* ALS iteration cap per summary */
+    int32_t max_iters_init;/* ALS iteration cap of sbt_init */
+    uint64_t seed;         /* Philox key (low and high words) */
+    uint32_t stream_id;    /* xor-ed into the Philox key's high word */
+    int32_t prec;          /* sbt_prec of the summary MTTKRP */
+    int32_t lambda_mode;   /* 0: keep lambda; 1: average with the summaries' estimate (Alg. 1 step 13) */
+    int32_t fixed_iters;   /* 1: ignore tol, run exactly max_iters iterations (parity mode) */
+    int64_t K_capacity;    /* slices the store is sized for up front (0: 2 * K0); grows on demand */
+    int64_t max_batch;     /* largest K_new sized up front (0: K0); grows on demand */
+    void *cuda_stream;     /* cudaStream_t for all device work; NULL: the legacy default stream */
+    int32_t check_every;   /* ALS convergence poll interval in iterations (0: 4) */
+} sbt_options;
+
+typedef struct {
+    int64_t K;                 /* slices held after the update */
+    int32_t r, R;
+    int32_t n_I, n_J, n_K;     /* sample sizes of the update */
+    int32_t flags;             /* SBT_FLAG_* */
+    int32_t iters[SBT_MAX_REPS];     /* ALS iterations per repetition */
+    double fit[SBT_MAX_REPS];        /* summary fit at the last ALS iteration */
+    double min_score[SBT_MAX_REPS];  /* smallest |G1|*|G2|*|G3| over matched pairs */
+    int32_t perm[SBT_MAX_REPS][SBT_MAX_RANK]; /* summary component -> old component */
+} sbt_update_stats;
+
+/* Library version string. */
+const char *sbt_version(void);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *sbt_last_error(void);
+
+/* Fill *opt with defaults: s = 2 in every mode, r = 4, tol = 1e-6, 50
+ * iterations (init: 50), seed 0, F32 MTTKRP, lambda kept. */
+sbt_status sbt_default_options(sbt_options *opt);
+
+/* Decompose X0 (I x J x K0) at rank R with CP-ALS on the GPU (Philox-uniform
+ * start), sort components by lambda, fix signs (sum A(:,r) >= 0, sum B(:,r)
+ * >= 0) and keep X0, the factors and the Eq. 1 marginals resident on the
+ * device.  This is the pre-existing decomposition of Section 3.2, (a). */
+sbt_status sbt_init(const sbt_tensor *X0, int32_t R, const sbt_options *opt, sbt_ctx **out);
+
+/* Same, but the pre-existing decomposition is given: lambda (R), A (I x R),
+ * B (J x R), C (K0 x R), host doubles, row-major.  No ALS runs. */
+sbt_status sbt_init_factors(const sbt_tensor *X0, int32_t R, const double *lambda,
+                            const double *A, const double *B, const double *C,
+                            const sbt_options *opt, sbt_ctx **out);
+
+/* Absorb K_new >= 1 new slices (I x J x K_new): Algorithm 1 once.  Sampling
+ * uses the marginals of the tensor before the update.  Transactional: on any
+ * error the factors, marginals and K are unchanged.  Returns after the GPU
+ * finished (one host synchronisation per call). */
+sbt_status sbt_update(sbt_ctx *ctx, const sbt_tensor *X_new);
+
+/* Copy the current model to host buffers (any may be NULL): lambda (R),
+ * A (I x R), B (J x R), C (K x R); *K_out receives K. */
+sbt_status sbt_factors(const sbt_ctx *ctx, double *lambda, double *A, double *B, double *C,
+                       int64_t *K_out);
+
+/* Fit of the full model against the full resident tensor:
+ * 1 - ||X - X_hat||_F / ||X||_F (Section 5.2, relative error = 1 - fit). */
+sbt_status sbt_fit(sbt_ctx *ctx, double *fit);
+
+/* Statistics of the last sbt_update. */
+sbt_status sbt_stats(const sbt_ctx *ctx, sbt_update_stats *st);
+
+/* Inspection of the last sbt_update (for parity checks): the sampled indices
+ * of repetition rep in mode (0: I_s, 1: J_s, 2: K_s over the old slices),
+ * ascending.  *n receives the count; at most cap are written. */
+sbt_status sbt_last_samples(const sbt_ctx *ctx, int32_t rep, int32_t mode, int32_t *out,
+                            int64_t cap, int64_t *n);
+
+/* The gathered summary of repetition rep as the values the ALS computed with
+ * (bfloat16 / float32 / float64, widened exactly to double), slice-major
+ * (Kp x n_I x n_J) with Kp = n_K + K_new; dims[3] receives (n_I, n_J, Kp). */
+sbt_status sbt_last_summary(const sbt_ctx *ctx, int32_t rep, double *out, int64_t cap,
+                            int64_t dims[3]);
+
+/* Summary factors of repetition rep after the shared-row normalisation
+ * (Alg. 1 step 6): lambda' (R), A' (n_I x R), B' (n_J x R), C' (Kp x R). */
+sbt_status sbt_last_summary_factors(const sbt_ctx *ctx, int32_t rep, double *lambda,
+                                    double *A, double *B, double *C);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+void sbt_destroy(sbt_ctx *ctx);
+
+/* ---- device-level operations (device pointers, ordered on `stream`) -------
+ * These run one kernel family on caller buffers and return without a host
+ * synchronisation unless stated.  Scratch is taken from the stream-ordered
+ * allocator (cudaMallocAsync) and returned before the call returns. */
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters: ctr (n x 4 uint32),
+ * out (n x 4 uint32); key = (key0, key1).  This is the counter-based
+ * generator behind the sampler and the ALS start values. */
+sbt_status sbt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
+                             int64_t n, void *stream);
+
+/* Weighted sampling without replacement of one mode (Section 4.1, Alg. 1
+ * step 3): draws n of the N indices with w[x] > 0, probability proportional
+ * to w (successive sampling through exponential keys), writes them ascending
+ * to out (device, n int32).  Philox key (lo32(seed), hi32(seed) ^ stream_id),
+ * counter (x, mode | rep << 4, batch, 1).  SBT_E_INVALID if n exceeds the
+ * number of positive weights (checked on the device; this call synchronises
+ * to report it). */
+sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64_t seed,
+                      uint32_t stream_id, int32_t mode, int32_t rep, uint32_t batch,
+                      int32_t *out, void *stream);
+
+/* MTTKRP of a dense slice-major tensor (K x I x J, row pitch ld >= J elements)
+ * for one mode (0: M = X_(1)(C kr B) -> I x R; 1: J x R; 2: K x R), the
+ * contraction inside every ALS step of Alg. 1 step 5.  dtype SBT_F64 or
+ * SBT_F32 applies to X, the factors A (I x R), B (J x R), C (K x R) and M. */
+sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
+                      const void *A, const void *B, const void *C, int32_t R, int32_t mode,
+                      void *M, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAMBATEN_H */

@@ -1,0 +1,859 @@
+// C ABI of libsambaten: context management and the per-batch pipeline of
+// Algorithm 1 (sample -> gather -> CP-ALS -> normalise/match -> project back ->
+// commit), all on one CUDA stream, one host synchronisation per update.
+#include "../../include/sambaten.h"
+#include "sbt_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace sbt;
+
+namespace {
+
+thread_local std::string g_err;
+
+sbt_status fail(sbt_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            return fail(e_ == cudaErrorMemoryAllocation ? SBT_E_NOMEM : SBT_E_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));          \
+        }                                                                             \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        sbt_status s_ = (expr);        \
+        if (s_ != SBT_OK) return s_;   \
+    } while (0)
+
+// device buffer that only grows
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~Buf() {
+        if (p) cudaFree(p);
+    }
+    sbt_status ensure(size_t bytes) {
+        if (bytes <= cap) return SBT_OK;
+        if (p) {
+            cudaFree(p);
+            p = nullptr;
+            cap = 0;
+        }
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(SBT_E_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+        }
+        cap = want;
+        return SBT_OK;
+    }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// host pinned buffer
+struct HBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~HBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    sbt_status ensure(size_t bytes) {
+        if (bytes <= cap) return SBT_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMallocHost(&p, std::max<size_t>(bytes, 256)) != cudaSuccess)
+            return fail(SBT_E_NOMEM, "cudaMallocHost failed");
+        cap = std::max<size_t>(bytes, 256);
+        return SBT_OK;
+    }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int round8(int64_t x) { return (int)((x + 7) / 8 * 8); }
+inline int esize_store(int dt) { return dt == SBT_F64 ? 8 : 4; }
+inline int esize_elem(int elem) { return elem == 0 ? 8 : (elem == 1 ? 4 : 2); }
+inline int esize_tf(int elem) { return elem == 0 ? 8 : 4; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct sbt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    sbt_options opt{};
+    int I = 0, J = 0, R = 0;
+    int64_t K = 0, Kcap = 0;
+    int sdtype = SBT_F32;
+    int lds = 0;
+    int S = 0;
+    int elem = 1;  // summary element: 0 f64, 1 f32, 2 bf16
+    uint32_t batch = 0;
+    int64_t npos[3] = {0, 0, 0};
+    // resident state
+    Buf store, A, B, C, lam, xa, xb, xc, dxa, dxb, xc_new, status;
+    HBuf h_status, h_poll, h_stats;
+    // workspace
+    Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
+    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging;
+    // last update
+    bool have_last = false;
+    int last_nI = 0, last_nJ = 0, last_nK = 0, last_Knew = 0, last_ldj = 0;
+    long long last_samp_stride = 0;
+    sbt_update_stats stats{};
+};
+
+// ---------------------------------------------------------------------------
+extern "C" const char *sbt_version(void) { return "sambaten-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char *sbt_last_error(void) { return g_err.c_str(); }
+
+extern "C" sbt_status sbt_default_options(sbt_options *o) {
+    if (!o) return fail(SBT_E_INVALID, "null options");
+    std::memset(o, 0, sizeof(*o));
+    o->s_I = o->s_J = o->s_K = 2;
+    o->r = 4;
+    o->tol = 1e-6;
+    o->max_iters = 50;
+    o->max_iters_init = 50;
+    o->seed = 0;
+    o->stream_id = 0;
+    o->prec = SBT_PREC_F32;
+    o->lambda_mode = 0;
+    o->fixed_iters = 0;
+    o->K_capacity = 0;
+    o->max_batch = 0;
+    o->cuda_stream = nullptr;
+    o->check_every = 4;
+    return SBT_OK;
+}
+
+static sbt_status check_options(const sbt_options *o, int R) {
+    if (!o) return fail(SBT_E_INVALID, "null options");
+    if (o->s_I < 1 || o->s_J < 1 || o->s_K < 1) return fail(SBT_E_INVALID, "sampling factors must be >= 1");
+    if (o->r < 1 || o->r > SBT_MAX_REPS) return fail(SBT_E_INVALID, "r out of range [1, SBT_MAX_REPS]");
+    if (R < 1 || R > SBT_MAX_RANK) return fail(SBT_E_INVALID, "R out of range [1, SBT_MAX_RANK]");
+    if (o->max_iters < 1 || o->max_iters_init < 1) return fail(SBT_E_INVALID, "iteration caps must be >= 1");
+    if (!(o->tol >= 0.0)) return fail(SBT_E_INVALID, "tol must be >= 0");
+    if (o->prec < SBT_PREC_F64 || o->prec > SBT_PREC_BF16) return fail(SBT_E_INVALID, "unknown precision");
+    if (o->lambda_mode != 0 && o->lambda_mode != 1) return fail(SBT_E_INVALID, "lambda_mode must be 0 or 1");
+    return SBT_OK;
+}
+
+static sbt_status check_tensor(const sbt_tensor *X) {
+    if (!X || !X->data) return fail(SBT_E_INVALID, "null tensor");
+    if (X->dtype != SBT_F64 && X->dtype != SBT_F32) return fail(SBT_E_INVALID, "unknown dtype");
+    if (X->I < 1 || X->J < 1 || X->K < 1) return fail(SBT_E_SHAPE, "tensor dimensions must be >= 1");
+    if (X->I > (1 << 30) || X->J > (1 << 30) || X->K > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
+    return SBT_OK;
+}
+
+// Move K_new slices (host or device) into the store at slice K0 and add their
+// marginals into (ma, mb, mc).
+static sbt_status append_slices(sbt_ctx *c, const sbt_tensor *X, int64_t K0, unsigned long long *ma,
+                                unsigned long long *mb, unsigned long long *mc) {
+    const size_t es = esize_store(c->sdtype);
+    char *dst = c->store.as<char>() + (size_t)K0 * c->I * c->lds * es;
+    const void *src = X->data;
+    int ldin = c->J;
+    if (!X->on_device) {
+        CK(cudaMemcpy2DAsync(dst, (size_t)c->lds * es, X->data, (size_t)c->J * es, (size_t)c->J * es,
+                             (size_t)X->K * c->I, cudaMemcpyHostToDevice, c->stream));
+        src = dst;
+        ldin = c->lds;
+    }
+    CK(launch_append(src, c->sdtype, X->K, c->I, c->J, ldin, dst, c->lds, c->S, ma, mb, mc,
+                     c->status.as<DevStatus>(), c->stream));
+    return SBT_OK;
+}
+
+static sbt_status read_status(sbt_ctx *c, DevStatus *out) {
+    CK(cudaMemcpyAsync(c->h_status.p, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = *c->h_status.as<DevStatus>();
+    return SBT_OK;
+}
+
+static sbt_status status_error(unsigned err) {
+    if (err & ERR_NONFINITE) return fail(SBT_E_NONFINITE, "non-finite value in the input slices");
+    if (err & ERR_RANGE) return fail(SBT_E_RANGE, "fixed-point marginal would overflow 64 bits");
+    if (err & ERR_SAMPLE) return fail(SBT_E_STATE, "sample size above the number of positive weights");
+    return SBT_OK;
+}
+
+// ALS descriptor over the ctx workspace for nrep summaries of shape n[3]
+static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
+                            const void *X, long long xrs, int max_iters) {
+    std::memset(&d, 0, sizeof(d));
+    d.nrep = nrep;
+    d.R = c->R;
+    d.n[0] = n[0];
+    d.n[1] = n[1];
+    d.n[2] = n[2];
+    d.ldj = ldj;
+    d.nK = nK;
+    d.elem = elem;
+    d.xrs = xrs;
+    d.X = X;
+    d.tol = c->opt.tol;
+    d.max_iters = max_iters;
+    d.fixed_iters = c->opt.fixed_iters;
+    choose_tiles(d, c->num_sms);
+    const int R = c->R;
+    const size_t tfs = esize_tf(elem);
+    const int nmax = std::max(n[0], std::max(n[1], n[2]));
+    for (int m = 0; m < 3; ++m) TRY(c->U[m].ensure((size_t)nrep * n[m] * R * tfs));
+    d.mrs = (long long)nmax * R;
+    TRY(c->M.ensure((size_t)nrep * d.mrs * 8));
+    d.prs = partial_elems(d);
+    TRY(c->part.ensure((size_t)nrep * d.prs * tfs));
+    TRY(c->G.ensure((size_t)nrep * 3 * R * R * 8));
+    TRY(c->lam_s.ensure((size_t)nrep * R * 8));
+    TRY(c->fit.ensure((size_t)nrep * 8));
+    TRY(c->fit_prev.ensure((size_t)nrep * 8));
+    TRY(c->normX2.ensure((size_t)nrep * 8));
+    TRY(c->iters.ensure((size_t)nrep * 4));
+    TRY(c->conv.ensure((size_t)nrep * 4));
+    TRY(c->flags.ensure((size_t)nrep * 4));
+    TRY(c->h_poll.ensure((size_t)nrep * 4));
+    for (int m = 0; m < 3; ++m) d.U[m] = c->U[m].p;
+    d.M = c->M.as<double>();
+    d.part = c->part.p;
+    d.G = c->G.as<double>();
+    d.lam = c->lam_s.as<double>();
+    d.fit = c->fit.as<double>();
+    d.fit_prev = c->fit_prev.as<double>();
+    d.normX2 = c->normX2.as<double>();
+    d.iters = c->iters.as<int>();
+    d.conv = c->conv.as<int>();
+    d.flags = c->flags.as<int>();
+    return SBT_OK;
+}
+
+// Run ALS iterations until every repetition converged (polled every
+// check_every iterations) or max_iters.
+static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters) {
+    const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
+    for (int it = 1; it <= max_iters; ++it) {
+        CK(launch_als_iteration(d, c->stream));
+        if (it == max_iters || (!c->opt.fixed_iters && it % every == 0)) {
+            CK(cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            const int *h = c->h_poll.as<int>();
+            bool all = true;
+            for (int q = 0; q < d.nrep; ++q) all = all && h[q];
+            if (all) break;
+        }
+    }
+    return SBT_OK;
+}
+
+static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const sbt_options *opt) {
+    TRY(check_tensor(X0));
+    TRY(check_options(opt, R));
+    if (opt->prec == SBT_PREC_F64 && X0->dtype != SBT_F64)
+        return fail(SBT_E_INVALID, "SBT_PREC_F64 needs a float64 store");
+    c->opt = *opt;
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->stream = (cudaStream_t)opt->cuda_stream;
+    c->I = (int)X0->I;
+    c->J = (int)X0->J;
+    c->R = R;
+    c->K = X0->K;
+    c->sdtype = X0->dtype;
+    c->lds = round8(c->J);
+    c->elem = opt->prec == SBT_PREC_F64 ? 0 : (opt->prec == SBT_PREC_F32 ? 1 : 2);
+    c->Kcap = std::max<int64_t>(opt->K_capacity > 0 ? opt->K_capacity : 2 * X0->K, X0->K + 1);
+    const size_t es = esize_store(c->sdtype);
+    TRY(c->store.ensure((size_t)c->Kcap * c->I * c->lds * es));
+    CK(cudaMemsetAsync(c->store.p, 0, (size_t)c->Kcap * c->I * c->lds * es, c->stream));
+    TRY(c->A.ensure((size_t)c->I * R * 8));
+    TRY(c->B.ensure((size_t)c->J * R * 8));
+    TRY(c->C.ensure((size_t)c->Kcap * R * 8));
+    TRY(c->lam.ensure((size_t)R * 8));
+    TRY(c->xa.ensure((size_t)c->I * 8));
+    TRY(c->xb.ensure((size_t)c->J * 8));
+    TRY(c->xc.ensure((size_t)c->Kcap * 8));
+    TRY(c->dxa.ensure((size_t)c->I * 8));
+    TRY(c->dxb.ensure((size_t)c->J * 8));
+    TRY(c->status.ensure(sizeof(DevStatus)));
+    TRY(c->h_status.ensure(sizeof(DevStatus)));
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
+    CK(cudaMemsetAsync(c->xa.p, 0, (size_t)c->I * 8, c->stream));
+    CK(cudaMemsetAsync(c->xb.p, 0, (size_t)c->J * 8, c->stream));
+    CK(cudaMemsetAsync(c->xc.p, 0, (size_t)c->Kcap * 8, c->stream));
+    // X0 into the store, then the shift S from max |x| (Eq. 1 fixed point)
+    const size_t sbytes = (size_t)X0->K * c->I * c->lds * es;
+    if (X0->on_device) {
+        CK(cudaMemcpy2DAsync(c->store.p, (size_t)c->lds * es, X0->data, (size_t)c->J * es, (size_t)c->J * es,
+                             (size_t)X0->K * c->I, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(cudaMemcpy2DAsync(c->store.p, (size_t)c->lds * es, X0->data, (size_t)c->J * es, (size_t)c->J * es,
+                             (size_t)X0->K * c->I, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(launch_absmax(c->store.p, c->sdtype, (long long)(sbytes / es), c->status.as<DevStatus>(), c->stream));
+    DevStatus hs;
+    TRY(read_status(c, &hs));
+    if (hs.err & ERR_NONFINITE) return fail(SBT_E_NONFINITE, "non-finite value in X0");
+    double M;
+    std::memcpy(&M, &hs.amax_bits, 8);
+    if (M == 0.0) {
+        c->S = 0;
+    } else {
+        int e2;
+        std::frexp(M * M, &e2);
+        c->S = 32 - e2;
+    }
+    CK(launch_append(c->store.p, c->sdtype, X0->K, c->I, c->J, c->lds, c->store.p, c->lds, c->S,
+                     c->xa.as<unsigned long long>(), c->xb.as<unsigned long long>(),
+                     c->xc.as<unsigned long long>(), c->status.as<DevStatus>(), c->stream));
+    TRY(read_status(c, &hs));
+    TRY(status_error(hs.err));
+    // positive-weight counts
+    std::vector<unsigned long long> h(std::max<int64_t>(std::max(c->I, c->J), X0->K));
+    const unsigned long long *src[3] = {c->xa.as<unsigned long long>(), c->xb.as<unsigned long long>(),
+                                        c->xc.as<unsigned long long>()};
+    const int64_t len[3] = {c->I, c->J, X0->K};
+    for (int m = 0; m < 3; ++m) {
+        CK(cudaMemcpy(h.data(), src[m], (size_t)len[m] * 8, cudaMemcpyDeviceToHost));
+        int64_t cnt = 0;
+        for (int64_t x = 0; x < len[m]; ++x) cnt += h[x] != 0;
+        c->npos[m] = cnt;
+    }
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_init(const sbt_tensor *X0, int32_t R, const sbt_options *opt, sbt_ctx **out) {
+    if (!out) return fail(SBT_E_INVALID, "null output pointer");
+    *out = nullptr;
+    sbt_ctx *c = new sbt_ctx();
+    sbt_status s = ctx_alloc(c, X0, R, opt);
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    // CP-ALS of X0 in the store's own precision (the identity summary)
+    AlsDesc d;
+    const int n[3] = {c->I, c->J, (int)c->K};
+    const int elem = c->sdtype == SBT_F64 ? 0 : 1;
+    s = setup_als(c, d, 1, n, c->lds, (int)c->K, elem, c->store.p, 0, opt->max_iters_init);
+    if (s == SBT_OK) s = c->rowsq.ensure((size_t)c->K * c->I * 8);
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    cudaError_t e = launch_rowsq(c->store.p, c->sdtype, c->K * c->I, c->J, c->lds, c->rowsq.as<double>(), c->stream);
+    if (e == cudaSuccess)
+        e = launch_als_prepare(d, nullptr, 0, (int)c->K, true, opt->seed, opt->stream_id, 0xFFFFFFFFu,
+                               c->rowsq.as<double>(), c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(SBT_E_CUDA, std::string("init ALS launch: ") + cudaGetErrorString(e));
+    }
+    s = run_als(c, d, opt->max_iters_init);
+    if (s == SBT_OK) {
+        e = launch_canonicalize(d, c->A.as<double>(), c->B.as<double>(), c->C.as<double>(), c->lam.as<double>(),
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = fail(SBT_E_CUDA, std::string("init canonicalize: ") + cudaGetErrorString(e));
+    }
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_init_factors(const sbt_tensor *X0, int32_t R, const double *lambda, const double *A,
+                                       const double *B, const double *C, const sbt_options *opt, sbt_ctx **out) {
+    if (!out) return fail(SBT_E_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!lambda || !A || !B || !C) return fail(SBT_E_INVALID, "null factor pointer");
+    sbt_ctx *c = new sbt_ctx();
+    sbt_status s = ctx_alloc(c, X0, R, opt);
+    if (s == SBT_OK) {
+        cudaError_t e = cudaMemcpy(c->A.p, A, (size_t)c->I * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->B.p, B, (size_t)c->J * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->C.p, C, (size_t)c->K * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->lam.p, lambda, (size_t)R * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(SBT_E_CUDA, std::string("factor upload: ") + cudaGetErrorString(e));
+    }
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SBT_OK;
+}
+
+// Grow the store (and C, x_c) to hold at least `need` slices.
+static sbt_status grow_store(sbt_ctx *c, int64_t need) {
+    if (need <= c->Kcap) return SBT_OK;
+    int64_t ncap = std::max<int64_t>(need, c->Kcap * 2);
+    const size_t es = esize_store(c->sdtype);
+    const size_t slice = (size_t)c->I * c->lds * es;
+    Buf ns, nC, nxc;
+    TRY(ns.ensure(ncap * slice));
+    TRY(nC.ensure((size_t)ncap * c->R * 8));
+    TRY(nxc.ensure((size_t)ncap * 8));
+    CK(cudaMemsetAsync(ns.p, 0, ncap * slice, c->stream));
+    CK(cudaMemsetAsync(nxc.p, 0, (size_t)ncap * 8, c->stream));
+    CK(cudaMemcpyAsync(ns.p, c->store.p, c->K * slice, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(nC.p, c->C.p, (size_t)c->K * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(nxc.p, c->xc.p, (size_t)c->K * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::swap(c->store.p, ns.p);
+    std::swap(c->store.cap, ns.cap);
+    std::swap(c->C.p, nC.p);
+    std::swap(c->C.cap, nC.cap);
+    std::swap(c->xc.p, nxc.p);
+    std::swap(c->xc.cap, nxc.cap);
+    c->Kcap = ncap;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    TRY(check_tensor(X));
+    if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
+    if (X->dtype != c->sdtype) return fail(SBT_E_INVALID, "dtype must match the initial tensor");
+    DeviceGuard dg(c->device);
+    const int R = c->R, r = c->opt.r;
+    const int K_new = (int)X->K;
+    const int64_t K_old = c->K;
+    TRY(grow_store(c, K_old + K_new));
+    // sample sizes (Section 4.1): ceil(N / s), clamped to the positive weights
+    const int nI = (int)std::min<int64_t>(ceil_div(c->I, c->opt.s_I), c->npos[0]);
+    const int nJ = (int)std::min<int64_t>(ceil_div(c->J, c->opt.s_J), c->npos[1]);
+    const int nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), c->npos[2]);
+    if (nI < 1 || nJ < 1 || nK < 1) return fail(SBT_E_STATE, "a mode has no positive weight to sample");
+    const int Kp = nK + K_new;
+    const int ldj = round8(nJ);
+    const long long samp_stride = std::max(nI, std::max(nJ, nK));
+    const long long key_stride = std::max<int64_t>(std::max(c->I, c->J), K_old);
+    TRY(c->samples.ensure((size_t)r * 3 * samp_stride * 4));
+    TRY(c->khi.ensure((size_t)r * 3 * key_stride * 8));
+    TRY(c->klo.ensure((size_t)r * 3 * key_stride * 8));
+    const long long xrs = (long long)Kp * nI * ldj;
+    TRY(c->Xs.ensure((size_t)r * xrs * esize_elem(c->elem)));
+    TRY(c->rowsq.ensure((size_t)r * Kp * nI * 8));
+    TRY(c->xc_new.ensure((size_t)K_new * 8));
+    // 1. append + marginal deltas
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
+    CK(cudaMemsetAsync(c->dxa.p, 0, (size_t)c->I * 8, c->stream));
+    CK(cudaMemsetAsync(c->dxb.p, 0, (size_t)c->J * 8, c->stream));
+    CK(cudaMemsetAsync(c->xc_new.p, 0, (size_t)K_new * 8, c->stream));
+    TRY(append_slices(c, X, K_old, c->dxa.as<unsigned long long>(), c->dxb.as<unsigned long long>(),
+                      c->xc_new.as<unsigned long long>()));
+    // 2. sampling from the marginals of the tensor before the update
+    SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.w[0] = c->xa.as<unsigned long long>();
+    sp.w[1] = c->xb.as<unsigned long long>();
+    sp.w[2] = c->xc.as<unsigned long long>();
+    sp.N[0] = c->I;
+    sp.N[1] = c->J;
+    sp.N[2] = (int)K_old;
+    sp.n[0] = nI;
+    sp.n[1] = nJ;
+    sp.n[2] = nK;
+    sp.mode_id[0] = 0;
+    sp.mode_id[1] = 1;
+    sp.mode_id[2] = 2;
+    sp.nmodes = 3;
+    sp.nrep = r;
+    sp.rep0 = 0;
+    sp.out = c->samples.as<int>();
+    sp.out_stride = samp_stride;
+    sp.khi = c->khi.as<unsigned long long>();
+    sp.klo = c->klo.as<unsigned long long>();
+    sp.key_stride = key_stride;
+    sp.seed = c->opt.seed;
+    sp.stream_id = c->opt.stream_id;
+    sp.batch = c->batch;
+    sp.status = c->status.as<DevStatus>();
+    CK(launch_sample(sp, c->stream));
+    // 3. gather the summaries
+    GatherParams g;
+    std::memset(&g, 0, sizeof(g));
+    g.store = c->store.p;
+    g.I = c->I;
+    g.lds = c->lds;
+    g.samples = c->samples.as<int>();
+    g.samp_stride = samp_stride;
+    g.nI = nI;
+    g.nJ = nJ;
+    g.nK = nK;
+    g.K_old = (int)K_old;
+    g.K_new = K_new;
+    g.nrep = r;
+    g.Xs = c->Xs.p;
+    g.ldj = ldj;
+    g.xrs = xrs;
+    g.rowsq = c->rowsq.as<double>();
+    CK(launch_gather(g, c->sdtype, c->elem, c->stream));
+    // 4. CP-ALS on the r summaries
+    AlsDesc d;
+    const int n[3] = {nI, nJ, Kp};
+    TRY(setup_als(c, d, r, n, ldj, nK, c->elem, c->Xs.p, xrs, c->opt.max_iters));
+    CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
+                          c->batch, c->rowsq.as<double>(), c->stream));
+    TRY(run_als(c, d, c->opt.max_iters));
+    // 5. normalise, match, project back; 6. commit
+    const int pmax = (int)samp_stride;
+    TRY(c->nu.ensure((size_t)r * 3 * R * 8));
+    TRY(c->cnew.ensure((size_t)r * K_new * R * 8));
+    TRY(c->prop.ensure((size_t)r * 3 * pmax * R * 8));
+    TRY(c->lam_est.ensure((size_t)r * R * 8));
+    TRY(c->perm.ensure((size_t)r * R * 4));
+    TRY(c->min_score.ensure((size_t)r * 8));
+    MergeDesc m;
+    std::memset(&m, 0, sizeof(m));
+    m.nrep = r;
+    m.R = R;
+    m.I = c->I;
+    m.J = c->J;
+    m.K_old = (int)K_old;
+    m.K_new = K_new;
+    m.nI = nI;
+    m.nJ = nJ;
+    m.nK = nK;
+    m.samples = c->samples.as<int>();
+    m.samp_stride = samp_stride;
+    for (int q = 0; q < 3; ++q) m.U[q] = c->U[q].p;
+    m.elem = c->elem == 0 ? 0 : 1;
+    m.lam_s = c->lam_s.as<double>();
+    m.A = c->A.as<double>();
+    m.B = c->B.as<double>();
+    m.C = c->C.as<double>();
+    m.lam = c->lam.as<double>();
+    m.nu = c->nu.as<double>();
+    m.cnew = c->cnew.as<double>();
+    m.prop = c->prop.as<double>();
+    m.pmax = pmax;
+    m.lam_est = c->lam_est.as<double>();
+    m.perm = c->perm.as<int>();
+    m.min_score = c->min_score.as<double>();
+    m.flags = c->flags.as<int>();
+    m.lambda_mode = c->opt.lambda_mode;
+    m.xa = c->xa.as<unsigned long long>();
+    m.xb = c->xb.as<unsigned long long>();
+    m.xc = c->xc.as<unsigned long long>();
+    m.dxa = c->dxa.as<unsigned long long>();
+    m.dxb = c->dxb.as<unsigned long long>();
+    m.xc_new = c->xc_new.as<unsigned long long>();
+    m.status = c->status.as<DevStatus>();
+    CK(launch_match(m, c->stream));
+    CK(launch_precommit(m, c->stream));
+    CK(launch_commit(m, c->stream));
+    // 7. one synchronisation: status and statistics
+    const size_t stat_bytes = sizeof(DevStatus) + (size_t)r * (4 + 8 + 8 + 4 + 4 * R);
+    TRY(c->h_stats.ensure(stat_bytes));
+    char *hb = c->h_stats.as<char>();
+    CK(cudaMemcpyAsync(hb, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    size_t off = sizeof(DevStatus);
+    CK(cudaMemcpyAsync(hb + off, d.iters, (size_t)r * 4, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 4;
+    CK(cudaMemcpyAsync(hb + off, d.fit, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 8;
+    CK(cudaMemcpyAsync(hb + off, m.min_score, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 8;
+    CK(cudaMemcpyAsync(hb + off, d.flags, (size_t)r * 4, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 4;
+    CK(cudaMemcpyAsync(hb + off, m.perm, (size_t)r * R * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    DevStatus hs;
+    std::memcpy(&hs, hb, sizeof(DevStatus));
+    if (hs.err) return status_error(hs.err);
+    // the update is committed
+    c->K = K_old + K_new;
+    c->batch += 1;
+    for (int q = 0; q < 3; ++q) c->npos[q] = (int64_t)hs.npos[q];
+    sbt_update_stats &st = c->stats;
+    std::memset(&st, 0, sizeof(st));
+    st.K = c->K;
+    st.r = r;
+    st.R = R;
+    st.n_I = nI;
+    st.n_J = nJ;
+    st.n_K = nK;
+    off = sizeof(DevStatus);
+    const int *it = (const int *)(hb + off);
+    off += (size_t)r * 4;
+    const double *ft = (const double *)(hb + off);
+    off += (size_t)r * 8;
+    const double *ms = (const double *)(hb + off);
+    off += (size_t)r * 8;
+    const int *fl = (const int *)(hb + off);
+    off += (size_t)r * 4;
+    const int *pm = (const int *)(hb + off);
+    for (int q = 0; q < r; ++q) {
+        st.iters[q] = it[q];
+        st.fit[q] = ft[q];
+        st.min_score[q] = ms[q];
+        st.flags |= fl[q];
+        for (int a = 0; a < R; ++a) st.perm[q][a] = pm[q * R + a];
+    }
+    c->have_last = true;
+    c->last_nI = nI;
+    c->last_nJ = nJ;
+    c->last_nK = nK;
+    c->last_Knew = K_new;
+    c->last_ldj = ldj;
+    c->last_samp_stride = samp_stride;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_factors(const sbt_ctx *c, double *lambda, double *A, double *B, double *C, int64_t *K_out) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    DeviceGuard dg(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    if (lambda) CK(cudaMemcpy(lambda, c->lam.p, (size_t)c->R * 8, cudaMemcpyDeviceToHost));
+    if (A) CK(cudaMemcpy(A, c->A.p, (size_t)c->I * c->R * 8, cudaMemcpyDeviceToHost));
+    if (B) CK(cudaMemcpy(B, c->B.p, (size_t)c->J * c->R * 8, cudaMemcpyDeviceToHost));
+    if (C) CK(cudaMemcpy(C, c->C.p, (size_t)c->K * c->R * 8, cudaMemcpyDeviceToHost));
+    if (K_out) *K_out = c->K;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_fit(sbt_ctx *c, double *fit) {
+    if (!c || !fit) return fail(SBT_E_INVALID, "null argument");
+    DeviceGuard dg(c->device);
+    const long long need = fit_scratch_doubles((int)c->K, c->I, c->J, c->R) + 2;
+    TRY(c->fitscr.ensure((size_t)need * 8));
+    double *scr = c->fitscr.as<double>();
+    CK(launch_full_fit(c->store.p, c->sdtype, (int)c->K, c->I, c->J, c->lds, c->A.as<double>(), c->B.as<double>(),
+                       c->C.as<double>(), c->lam.as<double>(), c->R, scr + need - 2, scr, c->stream));
+    double h[2];
+    CK(cudaMemcpyAsync(h, scr + need - 2, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *fit = h[1] > 0.0 ? 1.0 - std::sqrt(h[0]) / std::sqrt(h[1]) : 0.0;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_stats(const sbt_ctx *c, sbt_update_stats *st) {
+    if (!c || !st) return fail(SBT_E_INVALID, "null argument");
+    if (!c->have_last) return fail(SBT_E_STATE, "no update has run");
+    *st = c->stats;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_last_samples(const sbt_ctx *c, int32_t rep, int32_t mode, int32_t *out, int64_t cap,
+                                       int64_t *n) {
+    if (!c || !n) return fail(SBT_E_INVALID, "null argument");
+    if (!c->have_last) return fail(SBT_E_STATE, "no update has run");
+    if (rep < 0 || rep >= c->opt.r || mode < 0 || mode > 2) return fail(SBT_E_INVALID, "rep or mode out of range");
+    DeviceGuard dg(c->device);
+    const int cnt = mode == 0 ? c->last_nI : (mode == 1 ? c->last_nJ : c->last_nK);
+    *n = cnt;
+    if (out && cap > 0) {
+        const int64_t w = std::min<int64_t>(cap, cnt);
+        CK(cudaMemcpy(out, c->samples.as<int>() + (size_t)(rep * 3 + mode) * c->last_samp_stride, (size_t)w * 4,
+                      cudaMemcpyDeviceToHost));
+    }
+    return SBT_OK;
+}
+
+static inline float bf16_bits_to_float(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+extern "C" sbt_status sbt_last_summary(const sbt_ctx *c, int32_t rep, double *out, int64_t cap, int64_t dims[3]) {
+    if (!c || !dims) return fail(SBT_E_INVALID, "null argument");
+    if (!c->have_last) return fail(SBT_E_STATE, "no update has run");
+    if (rep < 0 || rep >= c->opt.r) return fail(SBT_E_INVALID, "rep out of range");
+    DeviceGuard dg(c->device);
+    const int nI = c->last_nI, nJ = c->last_nJ, Kp = c->last_nK + c->last_Knew, ldj = c->last_ldj;
+    dims[0] = nI;
+    dims[1] = nJ;
+    dims[2] = Kp;
+    const int64_t total = (int64_t)Kp * nI * nJ;
+    if (!out) return SBT_OK;
+    if (cap < total) return fail(SBT_E_INVALID, "output buffer too small");
+    const size_t es = esize_elem(c->elem);
+    const long long xrs = (long long)Kp * nI * ldj;
+    std::vector<unsigned char> h((size_t)xrs * es);
+    CK(cudaMemcpy(h.data(), c->Xs.as<unsigned char>() + (size_t)rep * xrs * es, (size_t)xrs * es,
+                  cudaMemcpyDeviceToHost));
+    for (int64_t row = 0; row < (int64_t)Kp * nI; ++row)
+        for (int jj = 0; jj < nJ; ++jj) {
+            const size_t idx = (size_t)row * ldj + jj;
+            double v;
+            if (c->elem == 0) std::memcpy(&v, &h[idx * 8], 8);
+            else if (c->elem == 1) {
+                float f;
+                std::memcpy(&f, &h[idx * 4], 4);
+                v = f;
+            } else {
+                uint16_t b;
+                std::memcpy(&b, &h[idx * 2], 2);
+                v = bf16_bits_to_float(b);
+            }
+            out[row * nJ + jj] = v;
+        }
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_last_summary_factors(const sbt_ctx *c, int32_t rep, double *lambda, double *A, double *B,
+                                               double *C) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    if (!c->have_last) return fail(SBT_E_STATE, "no update has run");
+    if (rep < 0 || rep >= c->opt.r) return fail(SBT_E_INVALID, "rep out of range");
+    DeviceGuard dg(c->device);
+    const int R = c->R;
+    const int n[3] = {c->last_nI, c->last_nJ, c->last_nK + c->last_Knew};
+    std::vector<double> nu(3 * R), ls(R);
+    CK(cudaMemcpy(nu.data(), c->nu.as<double>() + (size_t)rep * 3 * R, 3 * R * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ls.data(), c->lam_s.as<double>() + (size_t)rep * R, R * 8, cudaMemcpyDeviceToHost));
+    double *outs[3] = {A, B, C};
+    for (int q = 0; q < 3; ++q) {
+        if (!outs[q]) continue;
+        const size_t cnt = (size_t)n[q] * R;
+        if (c->elem == 0) {
+            CK(cudaMemcpy(outs[q], c->U[q].as<double>() + (size_t)rep * cnt, cnt * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f(cnt);
+            CK(cudaMemcpy(f.data(), c->U[q].as<float>() + (size_t)rep * cnt, cnt * 4, cudaMemcpyDeviceToHost));
+            for (size_t e = 0; e < cnt; ++e) outs[q][e] = f[e];
+        }
+        for (size_t e = 0; e < cnt; ++e) outs[q][e] /= nu[q * R + e % R];
+    }
+    if (lambda)
+        for (int a = 0; a < R; ++a) lambda[a] = ls[a] * nu[a] * nu[R + a] * nu[2 * R + a];
+    return SBT_OK;
+}
+
+extern "C" void sbt_destroy(sbt_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->stream);
+        delete c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// device-level operations
+extern "C" sbt_status sbt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out, int64_t n,
+                                        void *stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(SBT_E_INVALID, "bad arguments");
+    CK(launch_philox(ctr, make_uint2(key0, key1), out, n, (cudaStream_t)stream));
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64_t seed, uint32_t stream_id,
+                                 int32_t mode, int32_t rep, uint32_t batch, int32_t *out, void *stream) {
+    if (!w || !out || N < 1 || n < 0 || n > N || N > (1 << 30)) return fail(SBT_E_INVALID, "bad arguments");
+    if (mode < 0 || mode > 15 || rep < 0) return fail(SBT_E_INVALID, "mode or rep out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scr = nullptr;
+    const size_t bytes = (size_t)N * 16 + sizeof(DevStatus);
+    CK(cudaMallocAsync(&scr, bytes, st));
+    DevStatus *ds = (DevStatus *)((char *)scr + (size_t)N * 16);
+    cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.w[0] = (const unsigned long long *)w;
+    sp.N[0] = (int)N;
+    sp.n[0] = (int)n;
+    sp.mode_id[0] = mode;
+    sp.nmodes = 1;
+    sp.nrep = 1;
+    sp.rep0 = rep;
+    sp.out = out;
+    sp.out_stride = n;
+    sp.khi = (unsigned long long *)scr;
+    sp.klo = (unsigned long long *)scr + N;
+    sp.key_stride = N;
+    sp.seed = seed;
+    sp.stream_id = stream_id;
+    sp.batch = batch;
+    sp.status = ds;
+    if (e == cudaSuccess) e = launch_sample(sp, st);
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, &ds->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scr, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("sbt_sample: ") + cudaGetErrorString(e));
+    if (herr & ERR_SAMPLE) return fail(SBT_E_INVALID, "sample size above the number of positive weights");
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
+                                 const void *A, const void *B, const void *C, int32_t R, int32_t mode, void *M,
+                                 void *stream) {
+    if (!X || !A || !B || !C || !M) return fail(SBT_E_INVALID, "null pointer");
+    if (dtype != SBT_F64 && dtype != SBT_F32) return fail(SBT_E_INVALID, "dtype must be SBT_F64 or SBT_F32");
+    if (K < 1 || I < 1 || J < 1 || ld < J || ld % 8 != 0) return fail(SBT_E_SHAPE, "need K, I, J >= 1 and ld >= J, ld % 8 == 0");
+    if (((uintptr_t)X) % 16 != 0) return fail(SBT_E_INVALID, "X must be 16-byte aligned");
+    if (R < 1 || R > SBT_MAX_RANK || mode < 0 || mode > 2) return fail(SBT_E_INVALID, "R or mode out of range");
+    if (K > (1 << 30) || I > (1 << 30) || J > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AlsDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nrep = 1;
+    d.R = R;
+    d.n[0] = (int)I;
+    d.n[1] = (int)J;
+    d.n[2] = (int)K;
+    d.ldj = (int)ld;
+    d.nK = (int)K;
+    d.elem = dtype == SBT_F64 ? 0 : 1;
+    d.X = X;
+    d.xrs = 0;
+    d.U[0] = (void *)A;
+    d.U[1] = (void *)B;
+    d.U[2] = (void *)C;
+    choose_tiles(d, sms);
+    d.prs = partial_elems(d);
+    const int nmax = (int)std::max(I, std::max(J, K));
+    d.mrs = (long long)nmax * R;
+    const size_t tfs = dtype == SBT_F64 ? 8 : 4;
+    const size_t bytes = 256 + (size_t)d.prs * tfs + (size_t)d.mrs * 8 + 256;
+    char *scr = nullptr;
+    CK(cudaMallocAsync((void **)&scr, bytes, st));
+    d.conv = (int *)scr;
+    d.M = (double *)(scr + 256);
+    d.part = scr + 256 + (size_t)d.mrs * 8;
+    cudaError_t e = cudaMemsetAsync(scr, 0, 256, st);
+    if (e == cudaSuccess) e = launch_mttkrp_op(d, mode, M, st);
+    cudaError_t e2 = cudaFreeAsync(scr, st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("sbt_mttkrp: ") + cudaGetErrorString(e));
+    return SBT_OK;
+}

@@ -1,0 +1,478 @@
+// After the ALS: shared-row normalisation, matching (Lemma 1), project back,
+// commit of the averaged new rows; full-tensor fit; canonical order at init.
+#include "sbt_internal.cuh"
+
+#include <cmath>
+
+namespace sbt {
+
+// Maximum-weight perfect matching of an R x R score matrix (Hungarian method,
+// shortest augmenting paths with potentials; Kuhn 1955, Munkres 1957), single
+// thread.  perm[row] = column.  Ties resolve to the lower column index.
+__device__ void hungarian_max(const double *score, int ld, int R, int *perm) {
+    double u[33], v[33], minv[33];
+    int p[33], way[33];
+    bool used[33];
+    for (int j = 0; j <= R; ++j) {
+        u[j] = 0.0;
+        v[j] = 0.0;
+        p[j] = 0;
+        way[j] = 0;
+    }
+    for (int i = 1; i <= R; ++i) {
+        p[0] = i;
+        int j0 = 0;
+        for (int j = 0; j <= R; ++j) {
+            minv[j] = INFINITY;
+            used[j] = false;
+        }
+        // each pass marks one more column used, so at most R passes
+        for (int guard = 0; guard <= R; ++guard) {
+            used[j0] = true;
+            const int i0 = p[j0];
+            double delta = INFINITY;
+            int j1 = 0;
+            for (int j = 1; j <= R; ++j) {
+                if (used[j]) continue;
+                double sc = score[(i0 - 1) * ld + (j - 1)];
+                if (!isfinite(sc)) sc = 0.0;
+                const double cur = -sc - u[i0] - v[j];
+                if (cur < minv[j]) {
+                    minv[j] = cur;
+                    way[j] = j0;
+                }
+                if (minv[j] < delta) {
+                    delta = minv[j];
+                    j1 = j;
+                }
+            }
+            for (int j = 0; j <= R; ++j) {
+                if (used[j]) {
+                    u[p[j]] += delta;
+                    v[j] -= delta;
+                } else {
+                    minv[j] -= delta;
+                }
+            }
+            if (j1 == 0) break;  // no free column reachable (cannot happen for finite scores)
+            j0 = j1;
+            if (p[j0] == 0) break;
+        }
+        for (int guard = 0; guard <= R && j0; ++guard) {
+            const int j1 = way[j0];
+            p[j0] = p[j1];
+            j0 = j1;
+        }
+    }
+    // any column left unassigned is paired with the remaining rows in order
+    bool row_done[33];
+    for (int i = 0; i <= R; ++i) row_done[i] = false;
+    for (int j = 1; j <= R; ++j)
+        if (p[j] >= 1 && p[j] <= R && !row_done[p[j]]) row_done[p[j]] = true;
+        else p[j] = 0;
+    for (int j = 1; j <= R; ++j)
+        if (p[j] == 0)
+            for (int i = 1; i <= R; ++i)
+                if (!row_done[i]) {
+                    p[j] = i;
+                    row_done[i] = true;
+                    break;
+                }
+    for (int j = 1; j <= R; ++j) perm[p[j] - 1] = j - 1;
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per repetition.
+template <typename TF>
+__global__ void __launch_bounds__(256) k_match(MergeDesc m) {
+    const int rep = blockIdx.x;
+    const int R = m.R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Kp = m.nK + m.K_new;
+    const int n[3] = {m.nI, m.nJ, Kp};
+    const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
+    __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32];
+    __shared__ int perm[32];
+    __shared__ int zflag;
+    const TF *U[3];
+    const int *S[3];
+    const double *old[3] = {m.A, m.B, m.C};
+    for (int q = 0; q < 3; ++q) {
+        U[q] = (const TF *)m.U[q] + (long long)rep * n[q] * R;
+        S[q] = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
+    }
+    if (threadIdx.x == 0) zflag = 0;
+    __syncthreads();
+    // shared-row norms of the summary columns (Alg. 1 step 6) and of the anchors
+    for (int pr = warp; pr < 6 * R; pr += 8) {
+        const int which = pr / (3 * R), q = (pr / R) % 3, r = pr % R;
+        double a = 0.0;
+        for (int t = lane; t < nsh[q]; t += 32) {
+            double x = which == 0 ? (double)U[q][(long long)t * R + r] : old[q][(long long)S[q][t] * R + r];
+            a += x * x;
+        }
+        a = warp_sum(a);
+        if (lane == 0) {
+            double s = sqrt(a);
+            if (s == 0.0) {
+                s = 1.0;
+                if (which == 0) zflag = 1;
+            }
+            if (which == 0) nu[q][r] = s;
+            else Nn[q][r] = s;
+        }
+    }
+    __syncthreads();
+    // cosines Gamma_q(r', r) between unit summary and unit anchor columns
+    for (int tr = warp; tr < 3 * R * R; tr += 8) {
+        const int q = tr / (R * R), rp = (tr / R) % R, r = tr % R;
+        double a = 0.0;
+        for (int t = lane; t < nsh[q]; t += 32)
+            a += (double)U[q][(long long)t * R + rp] * old[q][(long long)S[q][t] * R + r];
+        a = warp_sum(a);
+        if (lane == 0) gam[q][rp][r] = a / (nu[q][rp] * Nn[q][r]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int rp = 0; rp < R; ++rp) {
+            lsp[rp] = m.lam_s[rep * R + rp] * nu[0][rp] * nu[1][rp] * nu[2][rp];
+            for (int r = 0; r < R; ++r)
+                score[rp * 32 + r] = fabs(gam[0][rp][r]) * fabs(gam[1][rp][r]) * fabs(gam[2][rp][r]);
+        }
+        hungarian_max(score, 32, R, perm);
+        double mn = INFINITY;
+        for (int rp = 0; rp < R; ++rp) {
+            mn = fmin(mn, score[rp * 32 + perm[rp]]);
+            m.perm[rep * R + rp] = perm[rp];
+        }
+        m.min_score[rep] = mn;
+        for (int q = 0; q < 3; ++q)
+            for (int r = 0; r < R; ++r) m.nu[(rep * 3 + q) * R + r] = nu[q][r];
+        for (int rp = 0; rp < R; ++rp) {
+            const int r = perm[rp];
+            const double den = Nn[0][r] * Nn[1][r] * Nn[2][r];
+            m.lam_est[rep * R + r] =
+                den != 0.0 ? lsp[rp] * gam[0][rp][r] * gam[1][rp][r] * gam[2][rp][r] / den : 0.0;
+        }
+        if (zflag) m.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
+    }
+    __syncthreads();
+    // least-squares scale of a summary column of mode q in the matched old scale
+    auto coef = [&](int q, int rp) -> double {
+        const int r = perm[rp];
+        double num = lsp[rp], den = m.lam[r];
+        for (int o = 0; o < 3; ++o)
+            if (o != q) {
+                num *= gam[o][rp][r];
+                den *= Nn[o][r];
+            }
+        return den != 0.0 ? num / den : 0.0;
+    };
+    // new rows of C (Alg. 1 step 9)
+    double *cn = m.cnew + (long long)rep * m.K_new * R;
+    for (int e = threadIdx.x; e < m.K_new * R; e += blockDim.x) {
+        const int k = e / R, rp = e % R;
+        const double u = (double)U[2][(long long)(m.nK + k) * R + rp] / nu[2][rp];
+        cn[(long long)k * R + perm[rp]] = coef(2, rp) * u;
+    }
+    // zero-entry proposals (Alg. 1 step 8)
+    for (int q = 0; q < 3; ++q) {
+        double *pp = m.prop + ((long long)rep * 3 + q) * m.pmax * R;
+        for (int e = threadIdx.x; e < nsh[q] * R; e += blockDim.x) {
+            const int t = e / R, rp = e % R, r = perm[rp];
+            double val = NAN;
+            if (old[q][(long long)S[q][t] * R + r] == 0.0)
+                val = coef(q, rp) * (double)U[q][(long long)t * R + rp] / nu[q][rp];
+            pp[(long long)t * R + r] = val;
+        }
+    }
+}
+
+cudaError_t launch_match(const MergeDesc &m, cudaStream_t st) {
+    if (m.elem == 0) k_match<double><<<m.nrep, 256, 0, st>>>(m);
+    else k_match<float><<<m.nrep, 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// overflow check of x_a + dx_a, x_b + dx_b (before anything is written)
+__global__ void k_precommit(MergeDesc m) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (e < m.I) bad = m.xa[e] + m.dxa[e] < m.xa[e];
+    else if (e < m.I + m.J) bad = m.xb[e - m.I] + m.dxb[e - m.I] < m.xb[e - m.I];
+    if (bad) atomicOr(&m.status->err, ERR_RANGE);
+}
+
+cudaError_t launch_precommit(const MergeDesc &m, cudaStream_t st) {
+    long long n = (long long)m.I + m.J;
+    k_precommit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+// lower_bound of x in ascending S[0..n)
+__device__ __forceinline__ int find_sorted(const int *S, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (S[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && S[lo] == x) ? lo : -1;
+}
+
+// Commit (Alg. 1 steps 8, 10, 12, 13): new rows of C = mean over repetitions;
+// exactly-zero old entries = mean of the proposing repetitions; lambda; fold
+// the marginal deltas.  Skipped entirely when the status word holds an error.
+__global__ void k_commit(MergeDesc m) {
+    if (m.status->err) return;
+    const int R = m.R;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nC = (long long)m.K_new * R;
+    const long long nA = (long long)m.I * R, nB = (long long)m.J * R, nCo = (long long)m.K_old * R;
+    if (e < nC) {
+        const int k = (int)(e / R), r = (int)(e % R);
+        double s = 0.0;
+        for (int q = 0; q < m.nrep; ++q) s += m.cnew[((long long)q * m.K_new + k) * R + r];
+        m.C[(long long)(m.K_old + k) * R + r] = s / m.nrep;
+        return;
+    }
+    e -= nC;
+    if (e < nA + nB + nCo) {
+        int q;
+        double *F;
+        int nsh;
+        if (e < nA) {
+            q = 0; F = m.A; nsh = m.nI;
+        } else if (e < nA + nB) {
+            e -= nA; q = 1; F = m.B; nsh = m.nJ;
+        } else {
+            e -= nA + nB; q = 2; F = m.C; nsh = m.nK;
+        }
+        if (F[e] != 0.0) return;
+        const int x = (int)(e / R), r = (int)(e % R);
+        double s = 0.0;
+        int c = 0;
+        for (int rep = 0; rep < m.nrep; ++rep) {
+            const int *S = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
+            const int t = find_sorted(S, nsh, x);
+            if (t < 0) continue;
+            const double v = m.prop[(((long long)rep * 3 + q) * m.pmax + t) * R + r];
+            if (!isnan(v)) {
+                s += v;
+                ++c;
+            }
+        }
+        if (c) F[e] = s / c;
+        return;
+    }
+    e -= nA + nB + nCo;
+    if (e < R) {
+        if (m.lambda_mode == 1) {
+            double s = 0.0;
+            for (int rep = 0; rep < m.nrep; ++rep) s += m.lam_est[rep * R + e];
+            m.lam[e] = 0.5 * (m.lam[e] + s / m.nrep);
+        }
+        return;
+    }
+    e -= R;
+    if (e < m.I) {
+        unsigned long long v = m.xa[e] + m.dxa[e];
+        m.xa[e] = v;
+        if (v) atomicAdd(&m.status->npos[0], 1ull);
+        return;
+    }
+    e -= m.I;
+    if (e < m.J) {
+        unsigned long long v = m.xb[e] + m.dxb[e];
+        m.xb[e] = v;
+        if (v) atomicAdd(&m.status->npos[1], 1ull);
+        return;
+    }
+    e -= m.J;
+    if (e < (long long)m.K_old + m.K_new) {
+        unsigned long long v = e < m.K_old ? m.xc[e] : m.xc_new[e - m.K_old];
+        if (e >= m.K_old) m.xc[e] = v;
+        if (v) atomicAdd(&m.status->npos[2], 1ull);
+    }
+}
+
+cudaError_t launch_commit(const MergeDesc &m, cudaStream_t st) {
+    const long long R = m.R;
+    long long n = (long long)m.K_new * R + (long long)m.I * R + (long long)m.J * R + (long long)m.K_old * R + R +
+                  m.I + m.J + m.K_old + m.K_new;
+    k_commit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Full-tensor fit: 1 - ||X - X_hat|| / ||X|| (Section 5.2).  A warp per row
+// (k, i): x_hat(j) = sum_r lambda_r A(i,r) C(k,r) B(j,r); residual squares and
+// squares accumulate per lane, then per CTA, then in fixed order.
+template <typename TS> struct FitAcc;
+template <> struct FitAcc<float> {
+    DF r{0.f, 0.f}, x{0.f, 0.f};
+    __device__ void add(float xv, float xh) {
+        float d = xv - xh;
+        r = df_add_sq(r, d);
+        x = df_add_sq(x, xv);
+    }
+    __device__ void total(double &rr, double &xx) {
+        rr = df_value(warp_df_sum(r));
+        xx = df_value(warp_df_sum(x));
+    }
+};
+template <> struct FitAcc<double> {
+    double r = 0.0, x = 0.0;
+    __device__ void add(double xv, double xh) {
+        double d = xv - xh;
+        r += d * d;
+        x += xv * xv;
+    }
+    __device__ void total(double &rr, double &xx) {
+        rr = warp_sum(r);
+        xx = warp_sum(x);
+    }
+};
+
+template <typename TS>
+__global__ void k_bcast_b(const double *B, TS *Bt, int J, int R) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < (long long)J * R) Bt[e] = (TS)B[e];
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_fit_rows(const TS *X, int K, int I, int J, int lds, const double *A,
+                                                  const TS *Bc, const double *C, const double *lam, int R,
+                                                  double *part) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double red_r[8], red_x[8];
+    const long long rows = (long long)K * I;
+    double tr = 0.0, tx = 0.0;
+    for (long long row = (long long)blockIdx.x * 8 + warp; row < rows; row += (long long)gridDim.x * 8) {
+        const int k = (int)(row / I), i = (int)(row % I);
+        TS w[32];
+        for (int r = 0; r < R; ++r) w[r] = (TS)(lam[r] * A[(long long)i * R + r] * C[(long long)k * R + r]);
+        const TS *xr = X + row * lds;
+        FitAcc<TS> acc;
+        for (int j = lane; j < J; j += 32) {
+            TS xh = 0;
+            const TS *b = Bc + (long long)j * R;
+            for (int r = 0; r < R; ++r) xh = fmadd(w[r], b[r], xh);
+            acc.add(xr[j], xh);
+        }
+        double rr, xx;
+        acc.total(rr, xx);
+        tr += rr;
+        tx += xx;
+    }
+    if (lane == 0) {
+        red_r[warp] = tr;
+        red_x[warp] = tx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            a += red_r[q];
+            b += red_x[q];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void k_fit_final(const double *part, int nb, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nb; ++q) {
+            a += part[2 * q];
+            b += part[2 * q + 1];
+        }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+static const int FIT_BLOCKS = 1216;
+
+long long fit_scratch_doubles(int K, int I, int J, int R) {
+    (void)K;
+    (void)I;
+    return 2LL * FIT_BLOCKS + (long long)J * R + 16;
+}
+
+cudaError_t launch_full_fit(const void *store, int sdtype, int K, int I, int J, int lds, const double *A,
+                            const double *B, const double *C, const double *lam, int R, double *out,
+                            double *scratch, cudaStream_t st) {
+    double *part = scratch;
+    void *bc = scratch + 2 * FIT_BLOCKS;
+    const long long nb = (long long)J * R;
+    if (sdtype == 0) {
+        k_bcast_b<double><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B, (double *)bc, J, R);
+        k_fit_rows<double><<<FIT_BLOCKS, 256, 0, st>>>((const double *)store, K, I, J, lds, A, (const double *)bc,
+                                                       C, lam, R, part);
+    } else {
+        k_bcast_b<float><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B, (float *)bc, J, R);
+        k_fit_rows<float><<<FIT_BLOCKS, 256, 0, st>>>((const float *)store, K, I, J, lds, A, (const float *)bc, C,
+                                                      lam, R, part);
+    }
+    k_fit_final<<<1, 32, 0, st>>>(part, FIT_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Init: sort components by lambda (descending, stable) and fix signs so that
+// sum A(:,r) >= 0 and sum B(:,r) >= 0, pushing signs into C.
+template <typename TF>
+__global__ void __launch_bounds__(256) k_canon(AlsDesc d, double *A, double *B, double *C, double *lam) {
+    const int R = d.R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int order[32];
+    __shared__ double sgn[2][32];
+    const TF *U0 = (const TF *)d.U[0], *U1 = (const TF *)d.U[1], *U2 = (const TF *)d.U[2];
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < R; ++r) order[r] = r;
+        for (int a = 1; a < R; ++a) {  // stable insertion sort, descending
+            int v = order[a], b = a - 1;
+            while (b >= 0 && d.lam[order[b]] < d.lam[v]) {
+                order[b + 1] = order[b];
+                --b;
+            }
+            order[b + 1] = v;
+        }
+    }
+    __syncthreads();
+    for (int pr = warp; pr < 2 * R; pr += 8) {
+        const int q = pr / R, r = pr % R;
+        const TF *U = q == 0 ? U0 : U1;
+        const int n = d.n[q];
+        double s = 0.0;
+        for (int x = lane; x < n; x += 32) s += (double)U[(long long)x * R + order[r]];
+        s = warp_sum(s);
+        if (lane == 0) sgn[q][r] = s < 0.0 ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)d.n[0] * R; e += blockDim.x) {
+        int x = (int)(e / R), r = (int)(e % R);
+        A[e] = sgn[0][r] * (double)U0[(long long)x * R + order[r]];
+    }
+    for (long long e = threadIdx.x; e < (long long)d.n[1] * R; e += blockDim.x) {
+        int x = (int)(e / R), r = (int)(e % R);
+        B[e] = sgn[1][r] * (double)U1[(long long)x * R + order[r]];
+    }
+    for (long long e = threadIdx.x; e < (long long)d.n[2] * R; e += blockDim.x) {
+        int x = (int)(e / R), r = (int)(e % R);
+        C[e] = sgn[0][r] * sgn[1][r] * (double)U2[(long long)x * R + order[r]];
+    }
+    if (threadIdx.x < R) lam[threadIdx.x] = d.lam[order[threadIdx.x]];
+}
+
+cudaError_t launch_canonicalize(const AlsDesc &d, double *A, double *B, double *C, double *lam,
+                                cudaStream_t st) {
+    if (d.elem == 0) k_canon<double><<<1, 256, 0, st>>>(d, A, B, C, lam);
+    else k_canon<float><<<1, 256, 0, st>>>(d, A, B, C, lam);
+    return cudaGetLastError();
+}
+
+}  // namespace sbt

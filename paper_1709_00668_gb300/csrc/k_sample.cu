@@ -1,0 +1,438 @@
+// Kernels before the ALS: Philox op, max |x|, append + Eq. 1 marginals,
+// weighted sampling without replacement, summary gather.
+#include "sbt_internal.cuh"
+
+namespace sbt {
+
+// ---------------------------------------------------------------------------
+// Philox op
+__global__ void k_philox(const uint4 *ctr, uint2 key, uint4 *out, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint32_t *out, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    k_philox<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)ctr, key, (uint4 *)out, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// max |x| (as ordered bits of a non-negative double) and non-finite detection
+template <typename T>
+__global__ void k_absmax(const T *X, long long n, DevStatus *status) {
+    double m = 0.0;
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = (double)X[i];
+        if (!isfinite(v)) bad = true;
+        else m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&status->amax_bits, (unsigned long long)__double_as_longlong(m));
+        if (anybad) atomicOr(&status->err, ERR_NONFINITE);
+    }
+}
+
+cudaError_t launch_absmax(const void *X, int dtype, long long n, DevStatus *status, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (dtype == 0)
+        k_absmax<double><<<(unsigned)blocks, 256, 0, st>>>((const double *)X, n, status);
+    else
+        k_absmax<float><<<(unsigned)blocks, 256, 0, st>>>((const float *)X, n, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Append + marginals (Eq. 1).  q(x) = floor((x*x) * 2^S): one correctly rounded
+// float64 product (never contracted), exact power-of-two scaling, truncation.
+__device__ __forceinline__ bool qsquare(double x, int S, unsigned long long *q) {
+    double sq = ldexp(__dmul_rn(x, x), S);
+    if (!(sq < 18446744073709551616.0)) return false;
+    *q = __double2ull_rz(sq);
+    return true;
+}
+
+__device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
+                                            DevStatus *status) {
+    if (v == 0) return;
+    unsigned long long old = atomicAdd(dst, v);
+    if (old + v < old) atomicOr(&status->err, ERR_RANGE);
+}
+
+constexpr int APPEND_ROWS = 64;      // rows of one slice per CTA
+constexpr int APPEND_SMEM_J = 4096;  // column sums kept in shared memory up to this J
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_append(const T *Xin, int I, int J, int ldin, T *store, int lds, int S,
+                                                unsigned long long *dxa, unsigned long long *dxb,
+                                                unsigned long long *xc_new, DevStatus *status) {
+    __shared__ unsigned long long colsum[APPEND_SMEM_J];
+    __shared__ unsigned long long slicesum;
+    const int k = blockIdx.y;
+    const int i0 = blockIdx.x * APPEND_ROWS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool smem_cols = J <= APPEND_SMEM_J;
+    if (smem_cols)
+        for (int j = threadIdx.x; j < J; j += blockDim.x) colsum[j] = 0;
+    if (threadIdx.x == 0) slicesum = 0;
+    __syncthreads();
+    bool bad = false, range = false;
+    unsigned long long wslice = 0;
+    for (int i = i0 + warp; i < min(I, i0 + APPEND_ROWS); i += 8) {
+        const T *src = Xin + ((long long)k * I + i) * ldin;
+        T *dst = store + ((long long)k * I + i) * lds;
+        unsigned long long rs = 0;
+        for (int j = lane; j < J; j += 32) {
+            T x = src[j];
+            dst[j] = x;
+            double xd = (double)x;
+            unsigned long long q = 0;
+            if (!isfinite(xd)) bad = true;
+            else if (!qsquare(xd, S, &q)) range = true;
+            if (rs + q < rs) range = true;
+            rs += q;
+            if (q) {
+                if (smem_cols) atomicAdd(&colsum[j], q);
+                else add_checked(&dxb[j], q, status);
+            }
+        }
+        // warp sum of the row (overflow checked pairwise)
+        for (int o = 16; o; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xffffffffu, rs, o);
+            if (rs + other < rs) range = true;
+            rs += other;
+        }
+        if (lane == 0) {
+            add_checked(&dxa[i], rs, status);
+            if (wslice + rs < wslice) range = true;
+            wslice += rs;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&status->err, ERR_NONFINITE);
+    if (__any_sync(0xffffffffu, range) && lane == 0) atomicOr(&status->err, ERR_RANGE);
+    if (lane == 0 && wslice) {
+        unsigned long long old = atomicAdd(&slicesum, wslice);
+        if (old + wslice < old) atomicOr(&status->err, ERR_RANGE);
+    }
+    __syncthreads();
+    if (smem_cols) {
+        for (int j = threadIdx.x; j < J; j += blockDim.x) add_checked(&dxb[j], colsum[j], status);
+    }
+    if (threadIdx.x == 0) add_checked(&xc_new[k], slicesum, status);
+}
+
+cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
+                          int lds, int S, unsigned long long *dxa, unsigned long long *dxb,
+                          unsigned long long *xc_new, DevStatus *status, cudaStream_t st) {
+    if (K_new <= 0) return cudaSuccess;
+    dim3 grid((I + APPEND_ROWS - 1) / APPEND_ROWS, (unsigned)K_new);
+    if (dtype == 0)
+        k_append<double><<<grid, 256, 0, st>>>((const double *)Xin, I, J, ldin, (double *)store, lds, S,
+                                               dxa, dxb, xc_new, status);
+    else
+        k_append<float><<<grid, 256, 0, st>>>((const float *)Xin, I, J, ldin, (float *)store, lds, S,
+                                              dxa, dxb, xc_new, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Weighted sampling without replacement (Section 4.1, Alg. 1 step 3).
+// Exponential keys: key = floor(L * 2^64 / w), L = -log2(u) in Q.32 with
+// u = (2v+1) / 2^33 and v Philox word 0 on counter (x, mode | rep<<4, batch, 1).
+// The n smallest (key, x) are found by an MSB-first radix select over the
+// composite (key_hi:40 | key_lo:64 | x:32) and compacted in index order.
+
+// Q.32 binary logarithm of 1 <= t < 2^33 by repeated squaring (Turner 2010):
+// y = t / 2^p held as Q1.62; each squaring is truncated back to Q2.62 and a
+// square at or above 2 emits a one bit and is halved.
+__device__ __forceinline__ unsigned long long log2_q32(unsigned long long t) {
+    int p = 63 - __clzll((long long)t);
+    unsigned long long y = t << (62 - p);
+    unsigned long long f = 0;
+#pragma unroll 4
+    for (int b = 0; b < 32; ++b) {
+        unsigned long long hi = __umul64hi(y, y), lo = y * y;
+        y = (hi << 2) | (lo >> 62);
+        f <<= 1;
+        if (y >> 63) {
+            f |= 1ull;
+            y >>= 1;
+        }
+    }
+    return ((unsigned long long)p << 32) | f;
+}
+
+// floor(L * 2^64 / w) for L < 2^38, w >= 1: high word L / w; the low word by
+// restoring division of (L mod w) * 2^64.
+__device__ __forceinline__ void key_div(unsigned long long L, unsigned long long w,
+                                        unsigned long long *qhi, unsigned long long *qlo) {
+    *qhi = L / w;
+    unsigned long long rem = L % w, q = 0;
+    for (int b = 0; b < 64; ++b) {
+        bool carry = rem >> 63;
+        rem <<= 1;
+        q <<= 1;
+        if (carry || rem >= w) {
+            rem -= w;
+            q |= 1ull;
+        }
+    }
+    *qlo = q;
+}
+
+constexpr unsigned long long KEY_HI_MAX = 0xFFFFFFFFFFull;  // 40 bits: never drawn
+
+__device__ __forceinline__ unsigned digit_of(int d, unsigned long long hi, unsigned long long lo,
+                                             unsigned x) {
+    if (d < 5) return (unsigned)(hi >> (32 - 8 * d)) & 0xFFu;
+    if (d < 13) return (unsigned)(lo >> (56 - 8 * (d - 5))) & 0xFFu;
+    return (x >> (24 - 8 * (d - 13))) & 0xFFu;
+}
+
+struct Prefix {
+    unsigned long long m2, m1, v2, v1;
+    unsigned m0, v0;
+};
+
+__device__ __forceinline__ bool prefix_eq(const Prefix &p, unsigned long long hi,
+                                          unsigned long long lo, unsigned x) {
+    return ((hi & p.m2) == p.v2) && ((lo & p.m1) == p.v1) && ((x & p.m0) == p.v0);
+}
+__device__ __forceinline__ bool prefix_le(const Prefix &p, unsigned long long hi,
+                                          unsigned long long lo, unsigned x) {
+    unsigned long long a2 = hi & p.m2, a1 = lo & p.m1;
+    unsigned a0 = x & p.m0;
+    if (a2 != p.v2) return a2 < p.v2;
+    if (a1 != p.v1) return a1 < p.v1;
+    return a0 <= p.v0;
+}
+
+__global__ void __launch_bounds__(1024) k_sample(SampleParams sp) {
+    const int nm = sp.nmodes;
+    const int b = blockIdx.x;
+    const int rep_local = b / nm, mi = b % nm;
+    const int rep = sp.rep0 + rep_local;
+    const int mode = sp.mode_id[mi];
+    const unsigned long long *w = sp.w[mi];
+    const int N = sp.N[mi], n = sp.n[mi];
+    int *out = sp.out + (long long)b * sp.out_stride;
+    unsigned long long *khi = sp.khi + (long long)b * sp.key_stride;
+    unsigned long long *klo = sp.klo + (long long)b * sp.key_stride;
+    const uint2 key = philox_key(sp.seed, sp.stream_id);
+
+    __shared__ unsigned hist[256];
+    __shared__ Prefix pre;
+    __shared__ int krem, done, npos_s;
+    __shared__ int warp_tot[32];
+    __shared__ int base_s, chunk_s;
+
+    if (threadIdx.x == 0) {
+        npos_s = 0;
+        pre.m2 = pre.m1 = pre.v2 = pre.v1 = 0;
+        pre.m0 = pre.v0 = 0;
+        krem = n;
+        done = 0;
+        base_s = 0;
+    }
+    __syncthreads();
+    int mypos = 0;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        unsigned long long wx = w[x];
+        if (wx == 0) {
+            khi[x] = KEY_HI_MAX;
+            klo[x] = ~0ull;
+        } else {
+            uint4 r = philox4x32_10(make_uint4((uint32_t)x, (uint32_t)mode | ((uint32_t)rep << 4),
+                                               sp.batch, 1u), key);
+            unsigned long long t = 2ull * r.x + 1ull;
+            unsigned long long L = (33ull << 32) - log2_q32(t);
+            unsigned long long qh, ql;
+            key_div(L, wx, &qh, &ql);
+            khi[x] = qh;
+            klo[x] = ql;
+            ++mypos;
+        }
+    }
+    atomicAdd(&npos_s, mypos);
+    __syncthreads();
+    if (n > npos_s) {
+        if (threadIdx.x == 0) atomicOr(&sp.status->err, ERR_SAMPLE);
+        return;
+    }
+    if (n == 0) return;
+    __threadfence_block();
+
+    for (int d = 0; d < 17; ++d) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+        __syncthreads();
+        Prefix p = pre;
+        for (int x = threadIdx.x; x < N; x += blockDim.x) {
+            unsigned long long hi = khi[x], lo = klo[x];
+            if (prefix_eq(p, hi, lo, (unsigned)x)) atomicAdd(&hist[digit_of(d, hi, lo, (unsigned)x)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cum = 0, bsel = 0;
+            for (bsel = 0; bsel < 255; ++bsel) {
+                if (cum + (int)hist[bsel] >= krem) break;
+                cum += hist[bsel];
+            }
+            krem -= cum;
+            unsigned long long dm = 0xFFull;
+            if (d < 5) {
+                int sh = 32 - 8 * d;
+                pre.m2 |= dm << sh;
+                pre.v2 |= (unsigned long long)bsel << sh;
+            } else if (d < 13) {
+                int sh = 56 - 8 * (d - 5);
+                pre.m1 |= dm << sh;
+                pre.v1 |= (unsigned long long)bsel << sh;
+            } else {
+                int sh = 24 - 8 * (d - 13);
+                pre.m0 |= 0xFFu << sh;
+                pre.v0 |= (unsigned)bsel << sh;
+            }
+            if ((int)hist[bsel] == krem) done = 1;
+        }
+        __syncthreads();
+        if (done) break;
+    }
+
+    // compaction in index order
+    const Prefix p = pre;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = 0; c < N; c += blockDim.x) {
+        int x = c + threadIdx.x;
+        bool f = (x < N) && prefix_le(p, khi[x], klo[x], (unsigned)x);
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_tot[wid] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int q = 0; q < nw; ++q) {
+                int v = warp_tot[q];
+                warp_tot[q] = s;
+                s += v;
+            }
+            chunk_s = s;
+        }
+        __syncthreads();
+        const int chunk_total = chunk_s;
+        const int pos = base_s + warp_tot[wid] + __popc(bal & ((1u << lane) - 1u));
+        if (f && pos < n) out[pos] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) base_s += chunk_total;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_sample(const SampleParams &sp, cudaStream_t st) {
+    int blocks = sp.nmodes * sp.nrep;
+    if (blocks <= 0) return cudaSuccess;
+    k_sample<<<blocks, 1024, 0, st>>>(sp);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Summary gather (Alg. 1 step 4): Xs[kk][ii][jj] = X(K'[kk], I_s[ii], J_s[jj]),
+// K' = K_s (old, ascending) followed by the new slices in arrival order.
+// Also the exact-product, double-float sum of squares of every summary row.
+template <typename TX> struct Quant;
+template <> struct Quant<double> {
+    template <typename TS> static __device__ __forceinline__ double q(TS v) { return (double)v; }
+};
+template <> struct Quant<float> {
+    template <typename TS> static __device__ __forceinline__ float q(TS v) { return (float)v; }
+};
+template <> struct Quant<__nv_bfloat16> {
+    // float64 stores round to float32 first, then to bfloat16 (both nearest-even)
+    template <typename TS> static __device__ __forceinline__ __nv_bfloat16 q(TS v) {
+        return __float2bfloat16_rn((float)v);
+    }
+};
+
+// sum of squares accumulators: float64 for float64 summaries, double-float otherwise
+struct SqD {
+    double a = 0.0;
+    __device__ void add(double v) { a = __fma_rn(v, v, a); }
+    __device__ double total() { return warp_sum(a); }
+};
+struct SqF {
+    DF a{0.f, 0.f};
+    __device__ void add(float v) { a = df_add_sq(a, v); }
+    __device__ double total() { return df_value(warp_df_sum(a)); }
+};
+template <typename TX> struct SqOf { using T = SqF; };
+template <> struct SqOf<double> { using T = SqD; };
+
+template <typename TS, typename TX>
+__global__ void __launch_bounds__(256) k_gather(GatherParams g) {
+    const int rep = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Kp = g.nK + g.K_new;
+    const long long row = (long long)blockIdx.x * 8 + warp;
+    if (row >= (long long)Kp * g.nI) return;
+    const int kk = (int)(row / g.nI), ii = (int)(row % g.nI);
+    const int *Is = g.samples + (long long)(rep * 3 + 0) * g.samp_stride;
+    const int *Js = g.samples + (long long)(rep * 3 + 1) * g.samp_stride;
+    const int *Ks = g.samples + (long long)(rep * 3 + 2) * g.samp_stride;
+    const int gk = kk < g.nK ? Ks[kk] : g.K_old + (kk - g.nK);
+    const TS *src = (const TS *)g.store + ((long long)gk * g.I + Is[ii]) * g.lds;
+    TX *dst = (TX *)g.Xs + rep * g.xrs + row * g.ldj;
+    typename SqOf<TX>::T acc;
+    for (int jj = lane; jj < g.ldj; jj += 32) {
+        TX v = Quant<TX>::q(jj < g.nJ ? src[Js[jj]] : (TS)0);
+        dst[jj] = v;
+        acc.add(widen_elem(v));
+    }
+    double t = acc.total();
+    if (lane == 0) g.rowsq[(long long)rep * Kp * g.nI + row] = t;
+}
+
+cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStream_t st) {
+    const long long rows = (long long)(g.nK + g.K_new) * g.nI;
+    if (rows <= 0 || g.nrep <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((rows + 7) / 8), g.nrep);
+    if (sdtype == 0) {
+        if (xelem == 0) k_gather<double, double><<<grid, 256, 0, st>>>(g);
+        else if (xelem == 1) k_gather<double, float><<<grid, 256, 0, st>>>(g);
+        else k_gather<double, __nv_bfloat16><<<grid, 256, 0, st>>>(g);
+    } else {
+        if (xelem == 0) k_gather<float, double><<<grid, 256, 0, st>>>(g);
+        else if (xelem == 1) k_gather<float, float><<<grid, 256, 0, st>>>(g);
+        else k_gather<float, __nv_bfloat16><<<grid, 256, 0, st>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+// Row sums of squares of a dense store (the identity summary of sbt_init).
+template <typename TS>
+__global__ void __launch_bounds__(256) k_rowsq(const TS *X, long long rows, int J, int lds,
+                                               double *rowsq) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * 8 + warp;
+    if (row >= rows) return;
+    const TS *src = X + row * lds;
+    typename SqOf<TS>::T acc;
+    for (int j = lane; j < J; j += 32) acc.add(src[j]);
+    double t = acc.total();
+    if (lane == 0) rowsq[row] = t;
+}
+
+cudaError_t launch_rowsq(const void *X, int sdtype, long long rows, int J, int lds, double *rowsq,
+                         cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((rows + 7) / 8);
+    if (sdtype == 0) k_rowsq<double><<<blocks, 256, 0, st>>>((const double *)X, rows, J, lds, rowsq);
+    else k_rowsq<float><<<blocks, 256, 0, st>>>((const float *)X, rows, J, lds, rowsq);
+    return cudaGetLastError();
+}
+
+}  // namespace sbt

@@ -1,0 +1,247 @@
+// Internal declarations shared by the translation units of libsambaten.
+// Device helpers (Philox, fixed-point log2, reductions) and the host-side
+// launchers of every kernel family.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sbt {
+
+// ---------------------------------------------------------------------------
+// update flags, same values as SBT_FLAG_* of the public header
+constexpr int SBT_FLAG_CHOL_REGULARIZED_DEV = 1;
+constexpr int SBT_FLAG_ZERO_COLUMN_DEV = 2;
+constexpr int SBT_FLAG_SAMPLE_LT_RANK_DEV = 4;
+
+// error bits of the device status word
+enum : unsigned {
+    ERR_NONFINITE = 1u,  // new slices hold NaN/Inf
+    ERR_RANGE = 2u,      // fixed-point marginal overflow
+    ERR_SAMPLE = 4u,     // sample size above the number of positive weights
+};
+
+// Device status block (mirrored to pinned host memory once per call).
+struct DevStatus {
+    unsigned err;
+    unsigned pad;
+    unsigned long long npos[3];  // positive-weight counts of x_a, x_b, x_c after commit
+    unsigned long long amax_bits;  // max |x| of a tensor, as ordered double bits
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with xor-folding, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t lo0 = m0 * c.x, hi0 = __umulhi(m0, c.x);
+        uint32_t lo1 = m1 * c.z, hi1 = __umulhi(m1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint2 philox_key(uint64_t seed, uint32_t stream_id) {
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ stream_id);
+}
+
+// Start value of the ALS factors: Philox word 0 >> 8, scaled by 2^-24, counter
+// (global index, r | mode << 8 | rep << 12, batch, 2).
+__device__ __forceinline__ double init_value(uint2 key, uint32_t gx, int r, int mode, int rep,
+                                             uint32_t batch) {
+    uint4 c = make_uint4(gx, (uint32_t)r | ((uint32_t)mode << 8) | ((uint32_t)rep << 12), batch, 2u);
+    uint4 o = philox4x32_10(c, key);
+    return (double)(o.x >> 8) * (1.0 / 16777216.0);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// fused multiply-add in the operand type (never promoted)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// widening loads of summary elements
+__device__ __forceinline__ double widen_elem(double v) { return v; }
+__device__ __forceinline__ float widen_elem(float v) { return v; }
+__device__ __forceinline__ float widen_elem(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---------------------------------------------------------------------------
+// Double-float accumulation on the float32 pipes (float64 is a slow unit on
+// this part): a value is the unevaluated sum hi + lo, sums use Knuth's
+// two-sum, products of squares are split exactly with an FMA.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    float h = __fadd_rn(s, e);
+    float l = __fsub_rn(e, __fsub_rn(h, s));
+    return DF{h, l};
+}
+__device__ __forceinline__ DF df_add_sq(DF a, float v) {
+    float p = __fmul_rn(v, v);
+    float pe = __fmaf_rn(v, v, -p);
+    return df_add(a, DF{p, pe});
+}
+__device__ __forceinline__ DF df_add_prod(DF a, float u, float v) {
+    float p = __fmul_rn(u, v);
+    float pe = __fmaf_rn(u, v, -p);
+    return df_add(a, DF{p, pe});
+}
+__device__ __forceinline__ DF warp_df_sum(DF a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        DF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, b);
+    }
+    return a;
+}
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
+// Parameters of the sampling and gather kernels
+struct SampleParams {
+    const unsigned long long *w[3];  // weights per listed mode
+    int N[3], n[3], mode_id[3];
+    int nmodes, nrep, rep0;
+    int *out;                 // [rep][nmodes][out_stride]
+    long long out_stride;
+    unsigned long long *khi, *klo;  // key scratch [rep][nmodes][key_stride]
+    long long key_stride;
+    uint64_t seed;
+    uint32_t stream_id, batch;
+    DevStatus *status;
+};
+
+struct GatherParams {
+    const void *store;
+    int I, lds;
+    const int *samples;       // [rep][3][samp_stride]
+    long long samp_stride;
+    int nI, nJ, nK, K_old, K_new, nrep;
+    void *Xs;                 // [rep][Kp][nI][ldj]
+    int ldj;
+    long long xrs;
+    double *rowsq;            // [rep][Kp * nI]
+};
+
+// ---------------------------------------------------------------------------
+// Problem description handed to the ALS kernels.  All repetitions share the
+// summary shape (n[0] = n_I, n[1] = n_J, n[2] = Kp).
+struct AlsDesc {
+    int nrep, R;
+    int n[3];
+    int ldj;          // row pitch of the summary (elements)
+    int nK;           // shared old rows of the time mode
+    int elem;         // 0 f64, 1 f32, 2 bf16
+    long long xrs;    // elements per repetition of X
+    const void *X;
+    void *U[3];       // [rep][n_m][R], double (elem 0) or float
+    double *M;        // [rep][nmax][R] reduced MTTKRP
+    void *part;       // [rep][P][nmax][R] partial sums (float or double)
+    long long prs;    // elements per repetition of part
+    long long mrs;    // elements per repetition of M
+    double *G;        // [rep][3][R][R]
+    double *lam;      // [rep][R]
+    double *fit, *fit_prev, *normX2;  // [rep]
+    int *iters, *conv, *flags;        // [rep]
+    double tol;
+    int max_iters, fixed_iters;
+    // tile choices
+    int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
+    long long rows_per;    // column kernel: rows per CTA
+    int nrs, cols;         // column kernel: row splits, columns per lane
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (all asynchronous on `st`)
+cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint32_t *out, long long n, cudaStream_t st);
+
+cudaError_t launch_absmax(const void *X, int dtype, long long n, DevStatus *status, cudaStream_t st);
+
+// Copy K_new slices (row pitch ldin; may alias the store) into the store and
+// add their fixed-point squares to the marginals: dxa (I), dxb (J), xc_new (K_new).
+cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
+                          int lds, int S, unsigned long long *dxa, unsigned long long *dxb,
+                          unsigned long long *xc_new, DevStatus *status, cudaStream_t st);
+
+cudaError_t launch_sample(const SampleParams &sp, cudaStream_t st);
+
+// Summaries: Xs[rep][kk][ii][jj], kk over K_s (n_K old) then K_old..K_old+K_new-1.
+cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStream_t st);
+// Row sums of squares of a dense store (identity summary of sbt_init).
+cudaError_t launch_rowsq(const void *X, int sdtype, long long rows, int J, int lds, double *rowsq,
+                         cudaStream_t st);
+
+// ALS: start values, Grams, ||X_s||^2; then the iterations.
+cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long samp_stride, int K_old,
+                               bool identity, uint64_t seed, uint32_t stream_id, uint32_t batch,
+                               const double *rowsq, cudaStream_t st);
+cudaError_t launch_als_iteration(const AlsDesc &d, cudaStream_t st);
+cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st);
+void choose_tiles(AlsDesc &d, int num_sms);
+long long partial_elems(const AlsDesc &d);  // per repetition
+
+// MTTKRP of one mode of a single tensor (d.nrep == 1, d.conv zero) into Mout
+// (factor type), through d.part and d.M.
+cudaError_t launch_mttkrp_op(AlsDesc &d, int mode, void *Mout, cudaStream_t st);
+
+// Match + project back (one CTA per repetition) and commit.
+struct MergeDesc {
+    int nrep, R, I, J, K_old, K_new, nI, nJ, nK;
+    const int *samples;  // [rep][3][samp_stride]
+    long long samp_stride;
+    const void *U[3];    // summary factors (float or double by elem)
+    int elem;
+    const double *lam_s; // [rep][R]
+    double *A, *B, *C, *lam;   // state (C has K_old + K_new rows after commit)
+    double *nu;          // [rep][3][R]   shared-row norms of the summary factors
+    double *cnew;        // [rep][K_new][R]
+    double *prop;        // [rep][3][pmax][R] zero-fill proposals (NaN = none)
+    int pmax;
+    double *lam_est;     // [rep][R]
+    int *perm;           // [rep][R]
+    double *min_score;   // [rep]
+    int *flags;          // [rep]
+    int lambda_mode;
+    unsigned long long *xa, *xb, *xc, *dxa, *dxb, *xc_new;
+    DevStatus *status;
+};
+cudaError_t launch_match(const MergeDesc &m, cudaStream_t st);
+// overflow check of the marginal fold; sets ERR_RANGE before anything changes
+cudaError_t launch_precommit(const MergeDesc &m, cudaStream_t st);
+cudaError_t launch_commit(const MergeDesc &m, cudaStream_t st);
+
+// Full fit: out[0] = sum (x - x_hat)^2, out[1] = sum x^2 over K slices of the
+// store.  scratch: at least fit_scratch_doubles(K, I, J, R) doubles.
+long long fit_scratch_doubles(int K, int I, int J, int R);
+cudaError_t launch_full_fit(const void *store, int sdtype, int K, int I, int J, int lds,
+                            const double *A, const double *B, const double *C, const double *lam,
+                            int R, double *out, double *scratch, cudaStream_t st);
+
+// Init: canonical order and signs of the ALS result, written to the state.
+cudaError_t launch_canonicalize(const AlsDesc &d, double *A, double *B, double *C, double *lam,
+                                cudaStream_t st);
+
+}  // namespace sbt

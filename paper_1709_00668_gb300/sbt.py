@@ -1,0 +1,351 @@
+"""Python binding of libsambaten (the C ABI in include/sambaten.h).
+
+Argument marshalling only: every step of the update runs in the library's CUDA
+kernels.  The library is loaded from the package's `_build/` directory; if it
+is missing the import fails loudly (there is no CPU fallback).  Build it with
+`paper_1709_00668_gb300.build.build()`.
+
+Device tensors are torch CUDA tensors passed by pointer; their work must be
+ordered on the stream handed to the library (by default torch's current
+stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsambaten.so")
+
+SBT_MAX_RANK = 32
+SBT_MAX_REPS = 64
+
+SBT_OK = 0
+SBT_E_INVALID = 1
+SBT_E_SHAPE = 2
+SBT_E_NOMEM = 3
+SBT_E_CUDA = 4
+SBT_E_NONFINITE = 5
+SBT_E_RANGE = 6
+SBT_E_TIMEOUT = 7
+SBT_E_STATE = 8
+
+SBT_F64 = 0
+SBT_F32 = 1
+SBT_PREC_F64 = 0
+SBT_PREC_F32 = 1
+SBT_PREC_BF16 = 2
+PREC = {"f64": SBT_PREC_F64, "f32": SBT_PREC_F32, "bf16": SBT_PREC_BF16}
+
+SBT_FLAG_CHOL_REGULARIZED = 1
+SBT_FLAG_ZERO_COLUMN = 2
+SBT_FLAG_SAMPLE_LT_RANK = 4
+
+EXPORTS = [
+    "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
+    "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
+    "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
+]
+
+
+class SbtTensor(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("on_device", ctypes.c_int32),
+                ("I", ctypes.c_int64), ("J", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("data", ctypes.c_void_p)]
+
+
+class SbtOptions(ctypes.Structure):
+    _fields_ = [("s_I", ctypes.c_int32), ("s_J", ctypes.c_int32), ("s_K", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("max_iters_init", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("stream_id", ctypes.c_uint32), ("prec", ctypes.c_int32),
+                ("lambda_mode", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
+                ("K_capacity", ctypes.c_int64), ("max_batch", ctypes.c_int64),
+                ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32)]
+
+
+class SbtStats(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("r", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("n_I", ctypes.c_int32), ("n_J", ctypes.c_int32), ("n_K", ctypes.c_int32),
+                ("flags", ctypes.c_int32),
+                ("iters", ctypes.c_int32 * SBT_MAX_REPS),
+                ("fit", ctypes.c_double * SBT_MAX_REPS),
+                ("min_score", ctypes.c_double * SBT_MAX_REPS),
+                ("perm", (ctypes.c_int32 * SBT_MAX_RANK) * SBT_MAX_REPS)]
+
+
+class SbtError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsambaten.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsambaten.so not found at {LIB_PATH}: run "
+                           "paper_1709_00668_gb300.build.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    S = ctypes.c_int
+    L.sbt_version.restype = ctypes.c_char_p
+    L.sbt_last_error.restype = ctypes.c_char_p
+    L.sbt_default_options.argtypes = [ctypes.POINTER(SbtOptions)]
+    L.sbt_init.argtypes = [ctypes.POINTER(SbtTensor), I32, ctypes.POINTER(SbtOptions), ctypes.POINTER(P)]
+    L.sbt_init_factors.argtypes = [ctypes.POINTER(SbtTensor), I32, P, P, P, P, ctypes.POINTER(SbtOptions),
+                                   ctypes.POINTER(P)]
+    L.sbt_update.argtypes = [P, ctypes.POINTER(SbtTensor)]
+    L.sbt_factors.argtypes = [P, P, P, P, P, ctypes.POINTER(I64)]
+    L.sbt_fit.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    L.sbt_stats.argtypes = [P, ctypes.POINTER(SbtStats)]
+    L.sbt_last_samples.argtypes = [P, I32, I32, P, I64, ctypes.POINTER(I64)]
+    L.sbt_last_summary.argtypes = [P, I32, P, I64, P]
+    L.sbt_last_summary_factors.argtypes = [P, I32, P, P, P, P]
+    L.sbt_destroy.argtypes = [P]
+    L.sbt_destroy.restype = None
+    L.sbt_philox4x32_10.argtypes = [P, U32, U32, P, I64, P]
+    L.sbt_sample.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
+    L.sbt_mttkrp.argtypes = [I32, P, I64, I64, I64, I64, P, P, P, I32, I32, P, P]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("sbt_version", "sbt_last_error", "sbt_destroy"):
+            f.restype = S
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != SBT_OK:
+        raise SbtError(status, where, lib().sbt_last_error().decode())
+
+
+def version() -> str:
+    return lib().sbt_version().decode()
+
+
+# ---------------------------------------------------------------------------
+def sbt_default_options(**kw) -> SbtOptions:
+    o = SbtOptions()
+    _check(lib().sbt_default_options(ctypes.byref(o)), "sbt_default_options")
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = int(v)
+        setattr(o, k, v)
+    return o
+
+
+def _tensor_desc(X, keep: list) -> SbtTensor:
+    """SbtTensor for a torch tensor (CUDA or CPU) or a numpy array, slice-major (K, I, J)."""
+    import torch
+    if isinstance(X, np.ndarray):
+        X = torch.from_numpy(np.ascontiguousarray(X))
+    if X.dim() != 3:
+        raise ValueError("X must be (K, I, J)")
+    if X.dtype == torch.float64:
+        dt = SBT_F64
+    elif X.dtype == torch.float32:
+        dt = SBT_F32
+    else:
+        raise ValueError("X must be float32 or float64")
+    X = X.contiguous()
+    keep.append(X)
+    K, I, J = X.shape
+    return SbtTensor(dt, 1 if X.is_cuda else 0, I, J, K, ctypes.c_void_p(X.data_ptr()))
+
+
+def _current_stream():
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+class SamBaTen:
+    """One tensor stream: resident store, factors and marginals on the GPU."""
+
+    def __init__(self, X0, R: int, *, factors=None, **opts):
+        if "cuda_stream" not in opts:
+            opts["cuda_stream"] = _current_stream()
+        self.opts = sbt_default_options(**opts)
+        self.R = int(R)
+        keep: list = []
+        desc = _tensor_desc(X0, keep)
+        self.I, self.J = int(desc.I), int(desc.J)
+        h = ctypes.c_void_p()
+        if factors is None:
+            _check(lib().sbt_init(ctypes.byref(desc), self.R, ctypes.byref(self.opts), ctypes.byref(h)),
+                   "sbt_init")
+        else:
+            lam, A, B, C = (np.ascontiguousarray(np.asarray(f, dtype=np.float64)) for f in factors)
+            _check(lib().sbt_init_factors(ctypes.byref(desc), self.R, lam.ctypes.data, A.ctypes.data,
+                                          B.ctypes.data, C.ctypes.data, ctypes.byref(self.opts),
+                                          ctypes.byref(h)), "sbt_init_factors")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sbt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, X_new):
+        keep: list = []
+        desc = _tensor_desc(X_new, keep)
+        _check(lib().sbt_update(self._h, ctypes.byref(desc)), "sbt_update")
+
+    def update_status(self, X_new) -> int:
+        """sbt_update returning the raw status instead of raising."""
+        keep: list = []
+        desc = _tensor_desc(X_new, keep)
+        return int(lib().sbt_update(self._h, ctypes.byref(desc)))
+
+    @property
+    def K(self) -> int:
+        k = ctypes.c_int64()
+        _check(lib().sbt_factors(self._h, None, None, None, None, ctypes.byref(k)), "sbt_factors")
+        return int(k.value)
+
+    def factors(self):
+        K = self.K
+        lam = np.empty(self.R)
+        A = np.empty((self.I, self.R))
+        B = np.empty((self.J, self.R))
+        C = np.empty((K, self.R))
+        k = ctypes.c_int64()
+        _check(lib().sbt_factors(self._h, lam.ctypes.data, A.ctypes.data, B.ctypes.data, C.ctypes.data,
+                                 ctypes.byref(k)), "sbt_factors")
+        return lam, A, B, C
+
+    def fit(self) -> float:
+        f = ctypes.c_double()
+        _check(lib().sbt_fit(self._h, ctypes.byref(f)), "sbt_fit")
+        return float(f.value)
+
+    def stats(self) -> dict:
+        st = SbtStats()
+        _check(lib().sbt_stats(self._h, ctypes.byref(st)), "sbt_stats")
+        r, R = st.r, st.R
+        return {"K": st.K, "r": r, "R": R, "n_I": st.n_I, "n_J": st.n_J, "n_K": st.n_K,
+                "flags": st.flags, "iters": list(st.iters[:r]), "fit": list(st.fit[:r]),
+                "min_score": list(st.min_score[:r]),
+                "perm": [list(st.perm[q][:R]) for q in range(r)]}
+
+    def last_samples(self, rep: int, mode: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().sbt_last_samples(self._h, rep, mode, None, 0, ctypes.byref(n)), "sbt_last_samples")
+        out = np.empty(max(1, n.value), np.int32)
+        _check(lib().sbt_last_samples(self._h, rep, mode, out.ctypes.data, n.value, ctypes.byref(n)),
+               "sbt_last_samples")
+        return out[:n.value].copy()
+
+    def last_summary(self, rep: int) -> np.ndarray:
+        dims = np.zeros(3, np.int64)
+        _check(lib().sbt_last_summary(self._h, rep, None, 0, dims.ctypes.data), "sbt_last_summary")
+        nI, nJ, Kp = (int(v) for v in dims)
+        out = np.empty((Kp, nI, nJ))
+        _check(lib().sbt_last_summary(self._h, rep, out.ctypes.data, out.size, dims.ctypes.data),
+               "sbt_last_summary")
+        return out
+
+    def last_summary_factors(self, rep: int):
+        """Summary factors of the last update after the shared-row normalisation."""
+        dims = np.zeros(3, np.int64)
+        _check(lib().sbt_last_summary(self._h, rep, None, 0, dims.ctypes.data), "sbt_last_summary")
+        nI, nJ, Kp = (int(v) for v in dims)
+        lam = np.empty(self.R)
+        A = np.empty((nI, self.R))
+        B = np.empty((nJ, self.R))
+        C = np.empty((Kp, self.R))
+        _check(lib().sbt_last_summary_factors(self._h, rep, lam.ctypes.data, A.ctypes.data, B.ctypes.data,
+                                              C.ctypes.data), "sbt_last_summary_factors")
+        return lam, A, B, C
+
+
+# module-level names of the C ABI --------------------------------------------
+def sbt_init(X0, R, **opts) -> SamBaTen:
+    return SamBaTen(X0, R, **opts)
+
+
+def sbt_init_factors(X0, R, lam, A, B, C, **opts) -> SamBaTen:
+    return SamBaTen(X0, R, factors=(lam, A, B, C), **opts)
+
+
+def sbt_update(ctx: SamBaTen, X_new):
+    ctx.update(X_new)
+
+
+def sbt_factors(ctx: SamBaTen):
+    return ctx.factors()
+
+
+def sbt_fit(ctx: SamBaTen) -> float:
+    return ctx.fit()
+
+
+def sbt_stats(ctx: SamBaTen) -> dict:
+    return ctx.stats()
+
+
+def sbt_destroy(ctx: SamBaTen):
+    ctx.close()
+
+
+def _stream_arg(stream):
+    if stream is None:
+        return _current_stream()
+    return stream if isinstance(stream, int) else int(stream)
+
+
+def sbt_philox4x32_10(ctr, key, stream=None):
+    """Philox4x32-10 of each row of a (n, 4) int32/uint32 CUDA tensor; returns (n, 4) int32."""
+    import torch
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib().sbt_philox4x32_10(ctr.data_ptr(), int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF,
+                                   out.data_ptr(), ctr.shape[0], _stream_arg(stream)), "sbt_philox4x32_10")
+    return out
+
+
+def sbt_sample(w, n, *, seed=0, stream_id=0, mode=0, rep=0, batch=0, stream=None):
+    """Weighted draw of n indices (ascending) from a CUDA int64 tensor of weights."""
+    import torch
+    w = w.contiguous()
+    out = torch.empty(max(1, int(n)), dtype=torch.int32, device=w.device)
+    _check(lib().sbt_sample(w.data_ptr(), w.numel(), int(n), int(seed) & ((1 << 64) - 1),
+                            int(stream_id) & 0xFFFFFFFF, int(mode), int(rep), int(batch) & 0xFFFFFFFF,
+                            out.data_ptr(), _stream_arg(stream)), "sbt_sample")
+    return out[:int(n)]
+
+
+def sbt_mttkrp(X, A, B, C, mode, *, stream=None):
+    """MTTKRP of a (K, I, J) CUDA tensor (last dim may be padded to a multiple of 8)."""
+    import torch
+    K, I, ld = X.shape
+    J = B.shape[0]
+    R = A.shape[1]
+    dt = SBT_F64 if X.dtype == torch.float64 else SBT_F32
+    n = (I, J, K)[mode]
+    out = torch.empty(n, R, dtype=X.dtype, device=X.device)
+    A, B, C = A.contiguous(), B.contiguous(), C.contiguous()
+    _check(lib().sbt_mttkrp(dt, X.data_ptr(), K, I, J, ld, A.data_ptr(), B.data_ptr(), C.data_ptr(), R,
+                            int(mode), out.data_ptr(), _stream_arg(stream)), "sbt_mttkrp")
+    return out

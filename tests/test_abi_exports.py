@@ -1,0 +1,70 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point that include/sambaten.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sambaten.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbt_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1709_00668_gb300 import build, sbt
+    build.build()
+    return sbt.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("sbt_init", "sbt_update", "sbt_factors", "sbt_fit", "sbt_destroy"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_1709_00668_gb300 import sbt
+    assert sorted(sbt.EXPORTS) == declared_symbols()
+
+
+def test_default_options_and_version(lib):
+    from paper_1709_00668_gb300 import sbt
+    o = sbt.sbt_default_options()
+    assert (o.s_I, o.s_J, o.s_K, o.r, o.max_iters) == (2, 2, 2, 4, 50)
+    assert o.tol == 1e-6 and o.prec == sbt.SBT_PREC_F32
+    assert "sm_103a" in sbt.version()
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    """Argument checks run before any device call."""
+    from paper_1709_00668_gb300 import sbt
+    h = ctypes.c_void_p()
+    o = sbt.sbt_default_options()
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 4, 4, 4, None)
+    assert lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(o), ctypes.byref(h)) == sbt.SBT_E_INVALID
+    o.r = 0
+    buf = (ctypes.c_float * 64)()
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 4, 4, 4, ctypes.cast(buf, ctypes.c_void_p))
+    assert lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(o), ctypes.byref(h)) == sbt.SBT_E_INVALID
+    o.r = 2
+    assert lib.sbt_init(ctypes.byref(t), 40, ctypes.byref(o), ctypes.byref(h)) == sbt.SBT_E_INVALID
+    assert lib.sbt_update(None, ctypes.byref(t)) == sbt.SBT_E_INVALID
+    assert b"null" in lib.sbt_last_error()
+
+
+def test_package_import_does_not_need_the_library():
+    import importlib
+    m = importlib.import_module("paper_1709_00668_gb300")
+    assert hasattr(m, "__all__")

@@ -1,0 +1,229 @@
+"""GPU parity of sbt_init / sbt_update / sbt_fit against the FP64 oracle.
+
+Sampled indices and gathered summaries are compared bit for bit; factors and
+fits within the tolerance of the arithmetic: float64 paths 1e-8 (relative,
+after identical sampling), float32 paths 1e-4 (relative), bfloat16 summaries
+1e-3 against the oracle run on the same bfloat16 values.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sambaten as O
+from tests._util import planted, rel_err, unit_factors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sbt():
+    from paper_1709_00668_gb300 import build, sbt as s
+    build.build()
+    s.lib()
+    return s
+
+
+def _pair(sbt, X, K0, R, fac, *, prec="f32", **kw):
+    opts = dict(s_I=2, s_J=2, s_K=2, r=2, tol=1e-6, max_iters=50, seed=0)
+    opts.update(kw)
+    ctx = sbt.SamBaTen(torch.from_numpy(X[:K0]).cuda(), R, factors=fac, prec=prec, **opts)
+    oo = O.Options(s_I=opts["s_I"], s_J=opts["s_J"], s_K=opts["s_K"], r=opts["r"], tol=opts["tol"],
+                   max_iters=opts["max_iters"], seed=opts["seed"], fixed_iters=bool(opts.get("fixed_iters", 0)),
+                   lambda_mode=opts.get("lambda_mode", 0), stream_id=opts.get("stream_id", 0), prec=prec)
+    ost = O.init_state_from_factors(X[:K0], *fac, oo)
+    return ctx, ost
+
+
+def _check_update(ctx, ost, traces, *, ftol, bits=True):
+    st = ctx.stats()
+    for rep, t in enumerate(traces):
+        assert np.array_equal(ctx.last_samples(rep, 0), t.Is)
+        assert np.array_equal(ctx.last_samples(rep, 1), t.Js)
+        assert np.array_equal(ctx.last_samples(rep, 2), t.Ks)
+        if bits and hasattr(t, "Xs"):
+            assert np.array_equal(ctx.last_summary(rep), t.Xs)
+        assert st["perm"][rep] == list(t.match.perm), rep
+    lam, A, B, C = ctx.factors()
+    assert C.shape == ost.C.shape
+    assert rel_err(C, ost.C) < ftol
+    assert rel_err(A, ost.A) < ftol and rel_err(B, ost.B) < ftol
+    assert rel_err(lam, ost.lam) < ftol
+
+
+def test_update_f64_matches_oracle_c1(sbt):
+    """Plain method, float64: 100 x 100 x (50 + 10), R = 5, s = 2, r = 4."""
+    X, A, B, C = planted(100, 100, 60, 5, dtype=torch.float64)
+    fac = unit_factors(A, B, C[:50])
+    ctx, ost = _pair(sbt, X, 50, 5, fac, prec="f64", r=4, fixed_iters=1, max_iters=30)
+    ost2, traces = O.update(ost, X[50:60], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[50:60]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-8)
+    st = ctx.stats()
+    for rep, t in enumerate(traces):
+        assert st["iters"][rep] == t.als.iters == 30
+        assert abs(st["fit"][rep] - t.als.fit) < 1e-10
+        lam_s, As, Bs, Cs = ctx.last_summary_factors(rep)
+        assert rel_err(As, t.Us[0]) < 1e-8 and rel_err(Cs, t.Us[2]) < 1e-8
+        assert rel_err(lam_s, t.lam_s) < 1e-8
+    f = ctx.fit()
+    assert abs(f - O.full_fit(ost2.X, ost2.lam, ost2.A, ost2.B, ost2.C)) < 1e-10
+
+
+def test_update_f64_tolerance_stop_stream(sbt):
+    """Three batches with the tolerance stop (iteration counts must agree)."""
+    X, A, B, C = planted(60, 50, 52, 4, dtype=torch.float64, seed=3)
+    fac = unit_factors(A, B, C[:30])
+    ctx, ost = _pair(sbt, X, 30, 4, fac, prec="f64", r=3, tol=1e-7, max_iters=60)
+    for k0, k1 in ((30, 40), (40, 41), (41, 52)):
+        ost, traces = O.update(ost, X[k0:k1], keep_summaries=True)
+        ctx.update(torch.from_numpy(X[k0:k1]).cuda())
+        _check_update(ctx, ost, traces, ftol=1e-7)
+        assert ctx.stats()["iters"] == [t.als.iters for t in traces]
+    assert ctx.K == 52
+
+
+def test_update_f32_matches_oracle_scaled_c2(sbt):
+    """Float32 store and MTTKRP: 200 x 200 x (100 + 20), R = 10, s = 5, r = 8."""
+    X, A, B, C = planted(200, 200, 120, 10, dtype=torch.float32, seed=1)
+    fac = unit_factors(A, B, C[:100])
+    ctx, ost = _pair(sbt, X, 100, 10, fac, prec="f32", s_I=5, s_J=5, s_K=5, r=8, fixed_iters=1, max_iters=20)
+    ost2, traces = O.update(ost, X[100:120], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[100:120]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-4)
+    f = ctx.fit()
+    assert abs(f - O.full_fit(ost2.X, ost2.lam, ost2.A, ost2.B, ost2.C)) < 1e-5
+
+
+def test_update_bf16_summary_bits_and_factors(sbt):
+    X, A, B, C = planted(120, 96, 70, 6, dtype=torch.float32, seed=2)
+    fac = unit_factors(A, B, C[:60])
+    ctx, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15)
+    ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[60:70]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-3)
+
+
+@pytest.mark.parametrize("case", ["singleton", "ragged", "rank1", "rank32", "r1", "lambda_avg", "stream_id"])
+def test_update_edge_cases(sbt, case):
+    I, J, K0, Kn, R, kw = 64, 48, 30, 8, 4, {}
+    if case == "singleton":
+        Kn = 1
+    elif case == "ragged":
+        I, J, K0, Kn, kw = 67, 45, 33, 7, {"s_I": 3, "s_J": 4, "s_K": 5}
+    elif case == "rank1":
+        R = 1
+    elif case == "rank32":
+        I, J, K0, R = 80, 72, 70, 32
+    elif case == "r1":
+        kw = {"r": 1}
+    elif case == "lambda_avg":
+        kw = {"lambda_mode": 1}
+    elif case == "stream_id":
+        kw = {"stream_id": 77, "seed": 2 ** 40 + 5}
+    X, A, B, C = planted(I, J, K0 + Kn, R, dtype=torch.float64, seed=7)
+    fac = unit_factors(A, B, C[:K0])
+    ctx, ost = _pair(sbt, X, K0, R, fac, prec="f64", fixed_iters=1, max_iters=8, **kw)
+    ost2, traces = O.update(ost, X[K0:K0 + Kn], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[K0:K0 + Kn]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-7)
+
+
+def test_zero_entries_filled(sbt):
+    X, A, B, C = planted(40, 36, 28, 3, noise=0.0, dtype=torch.float64, seed=5, dist="normal")
+    lam, A, B, C0 = unit_factors(A, B, C[:20])
+    A = A.copy()
+    B = B.copy()
+    A[3, 1] = 0.0
+    A[10, 2] = 0.0
+    B[4, 0] = 0.0
+    ctx, ost = _pair(sbt, X, 20, 3, (lam, A, B, C0), prec="f64", s_I=1, s_J=1, s_K=1, r=2, fixed_iters=1,
+                     max_iters=25)
+    ost2, traces = O.update(ost, X[20:28])
+    ctx.update(torch.from_numpy(X[20:28]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-7)
+    _, Ag, Bg, _ = ctx.factors()
+    assert Ag[3, 1] != 0.0 and Bg[4, 0] != 0.0
+
+
+def test_zero_slices_are_never_sampled(sbt):
+    X, A, B, C = planted(50, 40, 40, 3, dtype=torch.float64, seed=9)
+    X = X.copy()
+    X[3] = 0.0
+    X[7] = 0.0
+    X[:, 5, :] = 0.0
+    fac = unit_factors(A, B, C[:30])
+    ctx, ost = _pair(sbt, X, 30, 3, fac, prec="f64", r=3, fixed_iters=1, max_iters=6, s_K=1, s_I=1)
+    ost2, traces = O.update(ost, X[30:40], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[30:40]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-7)
+    st = ctx.stats()
+    assert st["n_K"] == 28 and st["n_I"] == 49
+    for rep in range(3):
+        assert 3 not in ctx.last_samples(rep, 2) and 5 not in ctx.last_samples(rep, 0)
+
+
+def test_nonfinite_batch_leaves_state_unchanged(sbt):
+    X, A, B, C = planted(30, 30, 24, 2, dtype=torch.float32, seed=4)
+    fac = unit_factors(A, B, C[:20])
+    ctx, _ = _pair(sbt, X, 20, 2, fac)
+    before = ctx.factors()
+    bad = X[20:24].copy()
+    bad[1, 2, 3] = np.inf
+    assert ctx.update_status(torch.from_numpy(bad).cuda()) == sbt.SBT_E_NONFINITE
+    after = ctx.factors()
+    assert ctx.K == 20
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    ctx.update(torch.from_numpy(X[20:24]).cuda())
+    assert ctx.K == 24
+
+
+def test_shape_and_dtype_errors(sbt):
+    X, A, B, C = planted(20, 18, 14, 2, dtype=torch.float32, seed=6)
+    fac = unit_factors(A, B, C[:10])
+    ctx, _ = _pair(sbt, X, 10, 2, fac)
+    assert ctx.update_status(torch.zeros(3, 20, 17).cuda()) == sbt.SBT_E_SHAPE
+    assert ctx.update_status(torch.zeros(3, 20, 18, dtype=torch.float64).cuda()) == sbt.SBT_E_INVALID
+    assert ctx.update_status(torch.zeros(0, 20, 18).cuda()) == sbt.SBT_E_SHAPE
+    with pytest.raises(ValueError):
+        ctx.update(torch.zeros(20, 18).cuda())
+    assert ctx.K == 10
+
+
+def test_host_input_equals_device_input(sbt):
+    X, A, B, C = planted(40, 32, 26, 3, dtype=torch.float32, seed=8)
+    fac = unit_factors(A, B, C[:20])
+    c1, _ = _pair(sbt, X, 20, 3, fac, fixed_iters=1, max_iters=5)
+    c2, _ = _pair(sbt, X, 20, 3, fac, fixed_iters=1, max_iters=5)
+    c1.update(torch.from_numpy(X[20:26]).cuda())
+    c2.update(X[20:26])
+    for a, b in zip(c1.factors(), c2.factors()):
+        assert np.array_equal(a, b)
+
+
+def test_store_grows_past_capacity(sbt):
+    X, A, B, C = planted(24, 20, 60, 2, dtype=torch.float64, seed=10)
+    fac = unit_factors(A, B, C[:10])
+    ctx, ost = _pair(sbt, X, 10, 2, fac, prec="f64", K_capacity=12, fixed_iters=1, max_iters=5)
+    for k0 in range(10, 60, 10):
+        ost, traces = O.update(ost, X[k0:k0 + 10])
+        ctx.update(torch.from_numpy(X[k0:k0 + 10]).cuda())
+    assert ctx.K == 60
+    _check_update(ctx, ost, traces, ftol=1e-7)
+    assert abs(ctx.fit() - O.full_fit(ost.X, ost.lam, ost.A, ost.B, ost.C)) < 1e-10
+
+
+def test_init_als_matches_oracle(sbt):
+    X, *_ = planted(50, 40, 30, 4, dtype=torch.float64, seed=11)
+    ctx = sbt.SamBaTen(torch.from_numpy(X).cuda(), 4, prec="f64", max_iters_init=25, fixed_iters=1, seed=3)
+    st, res = O.init_decomposition(X, 4, O.Options(max_iters_init=25, fixed_iters=True, seed=3))
+    lam, A, B, C = ctx.factors()
+    assert rel_err(lam, st.lam) < 1e-8
+    assert rel_err(A, st.A) < 1e-8 and rel_err(B, st.B) < 1e-8 and rel_err(C, st.C) < 1e-8
+
+
+def test_init_als_f32_fit(sbt):
+    X, *_ = planted(80, 70, 60, 5, dtype=torch.float32, seed=12)
+    ctx = sbt.SamBaTen(torch.from_numpy(X).cuda(), 5, max_iters_init=40, fixed_iters=1, seed=1)
+    st, res = O.init_decomposition(X, 5, O.Options(max_iters_init=40, fixed_iters=True, seed=1))
+    assert abs(ctx.fit() - O.full_fit(X, st.lam, st.A, st.B, st.C)) < 1e-4
