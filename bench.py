@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark: slices absorbed per second by the batch-incremental CP update.
+
+Workload (dense FP32 single stream): planted rank-10 tensor 1000 x 1000 x
+(500 initial + batches of 50 slices), factors U[0,1], noise 0.01 * RMS;
+sampling factor 5 in every mode, 8 repetitions, ALS tol 1e-6 / 50 iterations,
+summary MTTKRP in bfloat16 with float32 accumulation (the chosen form), the
+plain float32 path measured beside it.  A step is one sbt_update: append,
+sampling, gather, CP-ALS of the 8 summaries, match, project back and commit.
+
+One JSON line on rank 0.  `python bench.py --impl reference` times the FP64
+CPU oracle (a deliberately slow reference) on the same workload instead.
+Multi-GPU (torchrun): independent replicas, one per GPU, no data-path
+collective; value = slices of all ranks / max over ranks of the timed span.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(I=1000, J=1000, K0=500, batch=50, R=10, s=5, r=8, tol=1e-6, max_iters=50, noise=0.01, seed=0)
+WORKLOAD_NAME = "dense-fp32 1000x1000x(500+50/batch) R=10 s=5 r=8"
+METRIC = "slices absorbed/sec at fit within 1e-3 of FP64; p50/p99 batch-update latency"
+UNIT = "slices/s"
+
+# ncu DRAM bytes per MTTKRP launch, keyed by the hash of the kernel source the
+# capture was taken on (null once the kernel changes)
+TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_1709_00668_gb300", "csrc", "k_als.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier and max-over-ranks only)
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is None:
+        return
+    if device is not None:
+        dist.barrier(device_ids=[device.index])
+    else:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Largest value over the ranks (the timed span of the slowest replica)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def make_data(steps: int, warmup: int, device):
+    import torch
+    from paper_1709_00668_gb300 import synth
+    w = WORKLOAD
+    nb = max(steps, warmup, 10)
+    K_total = w["K0"] + nb * w["batch"]
+    p = synth.planted_dense(w["I"], w["J"], K_total, w["R"], noise=w["noise"], seed=w["seed"],
+                            dtype=torch.float32, device=device)
+    return p, nb
+
+
+def opts_for(prec: str, stream):
+    w = WORKLOAD
+    return dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
+                max_iters_init=50, seed=w["seed"], prec=prec, cuda_stream=stream,
+                K_capacity=w["K0"] + 64 * w["batch"])
+
+
+def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
+    """Run the updates back to back; returns (total seconds, per-step ms, d2h bytes)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(batches) + 1)]
+    d2h = 0
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    for i, b in enumerate(batches):
+        ctx.update(b)
+        if read_back:
+            lam, A, B, C = ctx.factors()
+            d2h += C.nbytes + lam.nbytes
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(batches))]
+    dev = ev[0].elapsed_time(ev[-1]) / 1e3
+    return (wall if (host or read_back) else dev), per, d2h
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    f, c = math.floor(k), math.ceil(k)
+    return xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def cpu_baseline(p, nb_used: int, reps_sample: int = 2) -> dict:
+    """The FP64 oracle on the host cores: one batch, `reps_sample` of the 8
+    repetitions timed; the batch time is the shared part plus 8 x the mean
+    repetition time."""
+    import numpy as np
+    from oracle import sambaten as O
+    w = WORKLOAD
+    K0, b = w["K0"], w["batch"]
+    X = p.X[:K0 + b].cpu().numpy()
+    A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
+    na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
+    opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=reps_sample, tol=w["tol"], max_iters=w["max_iters"],
+                     seed=w["seed"], prec="bf16")
+    st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
+    t0 = time.perf_counter()
+    _, traces = O.update(st, X[K0:K0 + b])
+    total = time.perf_counter() - t0
+    rep = [t.seconds for t in traces]
+    common = total - sum(rep)
+    t_batch = common + w["r"] * (sum(rep) / len(rep))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": b / t_batch, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one batch of {b} slices, {reps_sample} of {w['r']} repetitions timed "
+                      f"({total:.1f} s); batch time = shared part + {w['r']} x mean repetition time "
+                      f"= {t_batch:.1f} s; numpy/BLAS threads on all listed cores",
+            "seconds_per_batch": t_batch}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    from oracle import sambaten as O
+    import oracle
+    oracle.build()
+    w = WORKLOAD
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    p, nb = make_data(args.steps, args.warmup, dev)
+    K0, b = w["K0"], w["batch"]
+    X = p.X.cpu().numpy()
+    A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
+    na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
+    opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=1, tol=w["tol"], max_iters=w["max_iters"],
+                     seed=w["seed"], prec=args.prec)
+    st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
+    # each step: one batch update of the oracle with one of the 8 repetitions
+    # (a bounded sample); the batch time is the shared part + 8 x repetition
+    batch_times = []
+    for i in range(args.warmup + args.steps):
+        k0 = K0 + (i % nb) * b
+        t0 = time.perf_counter()
+        _, traces = O.update(st, X[k0:k0 + b])
+        total = time.perf_counter() - t0
+        rep = traces[0].seconds
+        if i >= args.warmup:
+            batch_times.append((total - rep) + w["r"] * rep)
+    t = sum(batch_times)
+    value = args.steps * b / t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, **w, "prec_values": args.prec},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step one batch of {b} slices with 1 of {w['r']} repetitions "
+                                       f"run; batch time = shared part + {w['r']} x repetition time"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "latency_ms": {"p50": percentile([1e3 * x for x in batch_times], 0.5),
+                           "p99": percentile([1e3 * x for x in batch_times], 0.99)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_00668_gb300 import sbt
+    w = WORKLOAD
+    stream = torch.cuda.current_stream(device)
+    sptr = stream.cuda_stream
+    p, nb = make_data(args.steps, args.warmup, device)
+    K0, b = w["K0"], w["batch"]
+    X0 = p.X[:K0]
+    batches = [p.X[K0 + i * b:K0 + (i + 1) * b] for i in range(nb)]
+    torch.cuda.synchronize()
+
+    # warm-up on a separate context (same shapes, first batches)
+    ctx_w = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+    for i in range(args.warmup):
+        ctx_w.update(batches[i % nb])
+    ctx_w.close()
+
+    # timed: device-resident inputs, the chosen precision
+    ctx = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+    ctx.profile_reset(timing=True)
+    clocks = ClockSampler(local)
+    timed = [batches[i % nb] for i in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier(dist, device)
+    clocks.start()
+    secs, per, _ = time_updates(ctx, timed, torch, stream)
+    clk = clocks.stop()
+    barrier(dist, device)
+    prof = ctx.profile()
+    secs_max = max_over_ranks(dist, secs, device)
+    slices_all = sum_over_ranks(dist, float(args.steps * b), device)
+    value = slices_all / secs_max
+    stats = ctx.stats()
+    fit_gpu = ctx.fit()
+    ctx.close()
+
+    # plain float32 GPU method on the same batches
+    plain = None
+    if not args.no_plain and args.prec != "f32":
+        cp = sbt.SamBaTen(X0, w["R"], **opts_for("f32", sptr))
+        torch.cuda.synchronize()
+        barrier(dist, device)
+        s_p, per_p, _ = time_updates(cp, timed, torch, stream)
+        barrier(dist, device)
+        s_p = max_over_ranks(dist, s_p, device)
+        plain = {"value": slices_all / s_p, "unit": UNIT, "ms_per_step": 1e3 * s_p / args.steps,
+                 "fit": cp.fit(), "p50_ms": percentile(per_p, 0.5), "p99_ms": percentile(per_p, 0.99)}
+        cp.close()
+
+    # end to end through the C ABI with host (pinned) buffers and a result read-back
+    e2e = None
+    if not args.no_e2e:
+        hb = [t.cpu().pin_memory() for t in timed]
+        ce = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+        torch.cuda.synchronize()
+        barrier(dist, device)
+        s_e, _, d2h = time_updates(ce, hb, torch, stream, host=True, read_back=True)
+        barrier(dist, device)
+        s_e = max_over_ranks(dist, s_e, device)
+        e2e = {"value": slices_all / s_e, "unit": UNIT,
+               "h2d_bytes_per_step": int(b * w["I"] * w["J"] * 4),
+               "d2h_bytes_per_step": int(d2h / args.steps)}
+        ce.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (MTTKRP passes), measured in the timed region
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_note = "of measured" if peak else "of fallback"
+    peak = peak or 6800.0
+    achieved = prof["mttkrp_bytes"] / (prof["mttkrp_ms"] / 1e3) / 1e9 if prof["mttkrp_ms"] > 0 else None
+    kh = kernel_hash()
+    per_launch_bytes = prof["mttkrp_bytes"] / max(1, prof["mttkrp_launches"])
+    traffic = TRAFFIC.get((kh, args.prec))
+    roofline = {"bound": "hbm", "kernel": "MTTKRP pass (k_mtt_row / k_mtt_col)", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "peak_source": peak_note, "traffic": traffic,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_us": 1e3 * prof["mttkrp_ms"] / max(1, prof["mttkrp_launches"]),
+                "launches": prof["mttkrp_launches"], "mttkrp_share_of_step":
+                    prof["mttkrp_ms"] / (1e3 * secs) if secs > 0 else None, "kernel_hash": kh}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_baseline(p, nb)
+        except Exception as e:  # report, do not fail the benchmark line
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec,
+                       "l2": "inputs larger than L2 (200 MB batch per step, 4 GB resident store)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},
+            "fit": {"full_tensor_fit_after_steps": fit_gpu,
+                    "planted_noise_floor": 1.0 - w["noise"],
+                    "summary_fit_last_batch": stats["fit"], "als_iters_last_batch": stats["iters"]},
+            "plain_f32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": prof["launches"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -158,6 +158,23 @@ sbt_status sbt_last_summary(const sbt_ctx *ctx, int32_t rep, double *out, int64_
 sbt_status sbt_last_summary_factors(const sbt_ctx *ctx, int32_t rep, double *lambda,
                                     double *A, double *B, double *C);
 
+/* Counters for measurement (the benchmark's roofline figure). */
+typedef struct {
+    int64_t launches;        /* kernels launched by the library (process-wide) since the reset */
+    int64_t updates;         /* sbt_update calls committed since the reset */
+    int64_t mttkrp_launches; /* MTTKRP pass launches (one per mode per ALS iteration) */
+    double mttkrp_ms;        /* their summed device time from CUDA events (timing enabled), else 0 */
+    double mttkrp_bytes;     /* algorithmic bytes they read: each summary element of every
+                                repetition still iterating, once per pass */
+} sbt_profile;
+
+/* Zero the counters; timing = 1 also brackets every MTTKRP launch of this
+ * context with CUDA events on its stream (a few microseconds per update). */
+sbt_status sbt_profile_reset(sbt_ctx *ctx, int32_t timing);
+
+/* Read the counters (synchronises the context's stream). */
+sbt_status sbt_profile_read(sbt_ctx *ctx, sbt_profile *out);
+
 /* Free every device and host resource of the context.  NULL is a no-op. */
 void sbt_destroy(sbt_ctx *ctx);
 

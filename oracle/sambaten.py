@@ -48,6 +48,7 @@ repository's design notes):
 from __future__ import annotations
 
 import math
+import time
 from dataclasses import dataclass, field, replace
 
 import numpy as np
@@ -129,11 +130,18 @@ def quantized_squares(X: np.ndarray, S: int) -> np.ndarray:
 def marginals(X: np.ndarray, S: int):
     """Eq. 1 for all three modes: x_a(i) = sum_{j,k} X(i,j,k)^2 (and x_b, x_c).
 
-    X is slice-major (K, I, J).  Returns uint64 (x_a, x_b, x_c)."""
-    q = quantized_squares(X, S)
-    xa = q.sum(axis=(0, 2), dtype=np.uint64)
-    xb = q.sum(axis=(0, 1), dtype=np.uint64)
-    xc = q.sum(axis=(1, 2), dtype=np.uint64)
+    X is slice-major (K, I, J).  Returns uint64 (x_a, x_b, x_c).  Integer sums
+    are exact, so slices are processed in blocks to bound memory."""
+    K, I, J = X.shape
+    xa = np.zeros(I, np.uint64)
+    xb = np.zeros(J, np.uint64)
+    xc = np.zeros(K, np.uint64)
+    step = max(1, (1 << 24) // max(1, I * J))
+    for k0 in range(0, K, step):
+        q = quantized_squares(X[k0:k0 + step], S)
+        xa += q.sum(axis=(0, 2), dtype=np.uint64)
+        xb += q.sum(axis=(0, 1), dtype=np.uint64)
+        xc[k0:k0 + step] = q.sum(axis=(1, 2), dtype=np.uint64)
     return xa, xb, xc
 
 
@@ -451,6 +459,7 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
     X_all = np.concatenate([state.X, X_new.astype(state.X.dtype)], axis=0)
     traces = []
     for rho in range(opts.r):
+        t_rep = time.perf_counter()
         flags = FLAG_SAMPLE_LT_RANK if min(nI, nJ, nK) < R else 0
         # step 3: sample each mode without replacement
         Is = sample_mode(state.xa, nI, opts, 0, rho, state.batch)
@@ -480,6 +489,7 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         traces[-1].lam_est = lam_est
         if keep_summaries:
             traces[-1].Xs = Xs
+        traces[-1].seconds = time.perf_counter() - t_rep
     # step 10 and 12: average C_new over the repetitions, append to C
     Cnew = np.zeros((K_new, R))
     for t in traces:

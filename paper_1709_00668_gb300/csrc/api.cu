@@ -123,6 +123,18 @@ struct sbt_ctx {
     // workspace
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging;
+    // profiling
+    Buf prof_bytes;  // unsigned long long, device
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    long long launch_base = 0, updates = 0, mtt_launches = 0;
+    ~sbt_ctx() {
+        for (auto &e : events) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    }
     // last update
     bool have_last = false;
     int last_nI = 0, last_nJ = 0, last_nK = 0, last_Knew = 0, last_ldj = 0;
@@ -168,9 +180,10 @@ static sbt_status check_options(const sbt_options *o, int R) {
 }
 
 static sbt_status check_tensor(const sbt_tensor *X) {
-    if (!X || !X->data) return fail(SBT_E_INVALID, "null tensor");
-    if (X->dtype != SBT_F64 && X->dtype != SBT_F32) return fail(SBT_E_INVALID, "unknown dtype");
+    if (!X) return fail(SBT_E_INVALID, "null tensor");
     if (X->I < 1 || X->J < 1 || X->K < 1) return fail(SBT_E_SHAPE, "tensor dimensions must be >= 1");
+    if (!X->data) return fail(SBT_E_INVALID, "null tensor data");
+    if (X->dtype != SBT_F64 && X->dtype != SBT_F32) return fail(SBT_E_INVALID, "unknown dtype");
     if (X->I > (1 << 30) || X->J > (1 << 30) || X->K > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
     return SBT_OK;
 }
@@ -254,15 +267,38 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.iters = c->iters.as<int>();
     d.conv = c->conv.as<int>();
     d.flags = c->flags.as<int>();
+    d.bytes_ctr = c->prof_bytes.as<unsigned long long>();
     return SBT_OK;
 }
 
 // Run ALS iterations until every repetition converged (polled every
 // check_every iterations) or max_iters.
+static sbt_status timed_mttkrp(sbt_ctx *c, const AlsDesc &d, int mode) {
+    c->mtt_launches += 1;
+    if (!c->timing) {
+        CK(launch_mttkrp(d, mode, c->stream));
+        return SBT_OK;
+    }
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        c->events.emplace_back(a, b);
+    }
+    auto &ev = c->events[c->events_used++];
+    CK(cudaEventRecord(ev.first, c->stream));
+    CK(launch_mttkrp(d, mode, c->stream));
+    CK(cudaEventRecord(ev.second, c->stream));
+    return SBT_OK;
+}
+
 static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     for (int it = 1; it <= max_iters; ++it) {
-        CK(launch_als_iteration(d, c->stream));
+        for (int mode = 0; mode < 3; ++mode) {
+            TRY(timed_mttkrp(c, d, mode));
+            CK(launch_reduce_tail(d, mode, c->stream));
+        }
         if (it == max_iters || (!c->opt.fixed_iters && it % every == 0)) {
             CK(cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
@@ -306,6 +342,8 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     TRY(c->dxb.ensure((size_t)c->J * 8));
     TRY(c->status.ensure(sizeof(DevStatus)));
     TRY(c->h_status.ensure(sizeof(DevStatus)));
+    TRY(c->prof_bytes.ensure(8));
+    CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
     CK(cudaMemsetAsync(c->xa.p, 0, (size_t)c->I * 8, c->stream));
     CK(cudaMemsetAsync(c->xb.p, 0, (size_t)c->J * 8, c->stream));
@@ -595,6 +633,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     std::memcpy(&hs, hb, sizeof(DevStatus));
     if (hs.err) return status_error(hs.err);
     // the update is committed
+    c->updates += 1;
     c->K = K_old + K_new;
     c->batch += 1;
     for (int q = 0; q < 3; ++q) c->npos[q] = (int64_t)hs.npos[q];
@@ -752,6 +791,40 @@ extern "C" sbt_status sbt_last_summary_factors(const sbt_ctx *c, int32_t rep, do
     }
     if (lambda)
         for (int a = 0; a < R; ++a) lambda[a] = ls[a] * nu[a] * nu[R + a] * nu[2 * R + a];
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    DeviceGuard dg(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->timing = timing != 0;
+    c->events_used = 0;
+    c->launch_base = launch_count();
+    c->updates = 0;
+    c->mtt_launches = 0;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
+    if (!c || !out) return fail(SBT_E_INVALID, "null argument");
+    DeviceGuard dg(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned long long bytes = 0;
+    CK(cudaMemcpy(&bytes, c->prof_bytes.p, 8, cudaMemcpyDeviceToHost));
+    double ms = 0.0;
+    for (size_t q = 0; q < c->events_used; ++q) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->events[q].first, c->events[q].second));
+        ms += t;
+    }
+    out->launches = launch_count() - c->launch_base;
+    out->updates = c->updates;
+    out->mttkrp_launches = c->mtt_launches;
+    out->mttkrp_ms = ms;
+    out->mttkrp_bytes = (double)bytes;
     return SBT_OK;
 }
 

@@ -9,8 +9,13 @@
 #include "sbt_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace sbt {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launches(int n) { g_launches += n; }
 
 // ---------------------------------------------------------------------------
 // vector loads of summary elements (16 bytes) widened to the factor type
@@ -91,6 +96,10 @@ __global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
     const TF *C = (const TF *)d.U[2] + (long long)rep * Kp * R;
     const TX *X = (const TX *)d.X + rep * d.xrs;
     const int nkk = max(0, k1 - k0);
+    if (d.bytes_ctr && threadIdx.x == 0) {
+        const int rows = min(8, NI - ib * 8);
+        atomicAdd(d.bytes_ctr, (unsigned long long)rows * nkk * NJ * sizeof(TX));
+    }
     const int lane_r = lane / (32 / RP);
     const bool lane_writes = (lane % (32 / RP)) == 0 && lane_r < R;
 
@@ -170,6 +179,10 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
     const long long r0 = (long long)rs * d.rows_per, r1 = min(rows, r0 + d.rows_per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j0 = jb * 32 * COLS + lane * COLS;
+    if (d.bytes_ctr && threadIdx.x == 0) {
+        const int cols = min(NJ, (jb + 1) * 32 * COLS) - jb * 32 * COLS;
+        atomicAdd(d.bytes_ctr, (unsigned long long)max(0LL, r1 - r0) * cols * sizeof(TX));
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TF *red = reinterpret_cast<TF *>(smem_raw);  // [8][32*COLS][RP]
     const TF *A = (const TF *)d.U[0] + (long long)rep * NI * R;
@@ -601,14 +614,24 @@ static cudaError_t reduce_dispatch(const AlsDesc &d, int mode, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st) {
-    cudaError_t e = mtt_dispatch(d, mode, st);
-    if (e != cudaSuccess) return e;
-    e = reduce_dispatch(d, mode, st);
+cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st) {
+    count_launches(1);
+    return mtt_dispatch(d, mode, st);
+}
+
+cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
+    cudaError_t e = reduce_dispatch(d, mode, st);
     if (e != cudaSuccess) return e;
     if (d.elem == 0) k_tail<double><<<d.nrep, 256, 0, st>>>(d, mode);
     else k_tail<float><<<d.nrep, 256, 0, st>>>(d, mode);
+    count_launches(2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st) {
+    cudaError_t e = launch_mttkrp(d, mode, st);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_tail(d, mode, st);
 }
 
 cudaError_t launch_als_iteration(const AlsDesc &d, cudaStream_t st) {
@@ -628,6 +651,7 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
     else
         k_prepare<float><<<d.nrep, 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
                                                  stream_id, batch, rowsq);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -640,6 +664,7 @@ __global__ void k_store_m(const double *M, TF *out, long long cnt) {
 }
 
 cudaError_t launch_mttkrp_op(AlsDesc &d, int mode, void *Mout, cudaStream_t st) {
+    count_launches(3);
     cudaError_t e = mtt_dispatch(d, mode, st);
     if (e != cudaSuccess) return e;
     e = reduce_dispatch(d, mode, st);

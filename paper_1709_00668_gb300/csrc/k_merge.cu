@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
 }
 
 cudaError_t launch_match(const MergeDesc &m, cudaStream_t st) {
+    count_launches(1);
     if (m.elem == 0) k_match<double><<<m.nrep, 256, 0, st>>>(m);
     else k_match<float><<<m.nrep, 256, 0, st>>>(m);
     return cudaGetLastError();
@@ -206,6 +207,7 @@ __global__ void k_precommit(MergeDesc m) {
 
 cudaError_t launch_precommit(const MergeDesc &m, cudaStream_t st) {
     long long n = (long long)m.I + m.J;
+    count_launches(1);
     k_precommit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
     return cudaGetLastError();
 }
@@ -302,6 +304,7 @@ cudaError_t launch_commit(const MergeDesc &m, cudaStream_t st) {
     long long n = (long long)m.K_new * R + (long long)m.I * R + (long long)m.J * R + (long long)m.K_old * R + R +
                   m.I + m.J + m.K_old + m.K_new;
     k_commit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -418,6 +421,7 @@ cudaError_t launch_full_fit(const void *store, int sdtype, int K, int I, int J, 
                                                       lam, R, part);
     }
     k_fit_final<<<1, 32, 0, st>>>(part, FIT_BLOCKS, out);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(256) k_canon(AlsDesc d, double *A, double *B, 
 
 cudaError_t launch_canonicalize(const AlsDesc &d, double *A, double *B, double *C, double *lam,
                                 cudaStream_t st) {
+    count_launches(1);
     if (d.elem == 0) k_canon<double><<<1, 256, 0, st>>>(d, A, B, C, lam);
     else k_canon<float><<<1, 256, 0, st>>>(d, A, B, C, lam);
     return cudaGetLastError();

@@ -15,6 +15,7 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint32_t *out, long lo
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     k_philox<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)ctr, key, (uint4 *)out, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -42,6 +43,7 @@ cudaError_t launch_absmax(const void *X, int dtype, long long n, DevStatus *stat
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
+    count_launches(1);
     if (dtype == 0)
         k_absmax<double><<<(unsigned)blocks, 256, 0, st>>>((const double *)X, n, status);
     else
@@ -133,6 +135,7 @@ cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, in
                           unsigned long long *xc_new, DevStatus *status, cudaStream_t st) {
     if (K_new <= 0) return cudaSuccess;
     dim3 grid((I + APPEND_ROWS - 1) / APPEND_ROWS, (unsigned)K_new);
+    count_launches(1);
     if (dtype == 0)
         k_append<double><<<grid, 256, 0, st>>>((const double *)Xin, I, J, ldin, (double *)store, lds, S,
                                                dxa, dxb, xc_new, status);
@@ -337,6 +340,7 @@ cudaError_t launch_sample(const SampleParams &sp, cudaStream_t st) {
     int blocks = sp.nmodes * sp.nrep;
     if (blocks <= 0) return cudaSuccess;
     k_sample<<<blocks, 1024, 0, st>>>(sp);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -400,6 +404,7 @@ cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStre
     const long long rows = (long long)(g.nK + g.K_new) * g.nI;
     if (rows <= 0 || g.nrep <= 0) return cudaSuccess;
     dim3 grid((unsigned)((rows + 7) / 8), g.nrep);
+    count_launches(1);
     if (sdtype == 0) {
         if (xelem == 0) k_gather<double, double><<<grid, 256, 0, st>>>(g);
         else if (xelem == 1) k_gather<double, float><<<grid, 256, 0, st>>>(g);
@@ -430,6 +435,7 @@ cudaError_t launch_rowsq(const void *X, int sdtype, long long rows, int J, int l
                          cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((rows + 7) / 8);
+    count_launches(1);
     if (sdtype == 0) k_rowsq<double><<<blocks, 256, 0, st>>>((const double *)X, rows, J, lds, rowsq);
     else k_rowsq<float><<<blocks, 256, 0, st>>>((const float *)X, rows, J, lds, rowsq);
     return cudaGetLastError();

@@ -9,6 +9,10 @@
 
 namespace sbt {
 
+// kernels launched by the library (process-wide), for the launch counter
+long long launch_count();
+void count_launches(int n);
+
 // ---------------------------------------------------------------------------
 // update flags, same values as SBT_FLAG_* of the public header
 constexpr int SBT_FLAG_CHOL_REGULARIZED_DEV = 1;
@@ -168,6 +172,7 @@ struct AlsDesc {
     int *iters, *conv, *flags;        // [rep]
     double tol;
     int max_iters, fixed_iters;
+    unsigned long long *bytes_ctr;  // algorithmic bytes read by MTTKRP passes (nullable)
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -200,6 +205,9 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
                                const double *rowsq, cudaStream_t st);
 cudaError_t launch_als_iteration(const AlsDesc &d, cudaStream_t st);
 cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st);
+// the two halves of launch_als_mode: the MTTKRP pass, then reduction + tail
+cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st);
+cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
 long long partial_elems(const AlsDesc &d);  // per repetition
 

@@ -47,6 +47,7 @@ EXPORTS = [
     "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
     "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
+    "sbt_profile_reset", "sbt_profile_read",
 ]
 
 
@@ -74,6 +75,12 @@ class SbtStats(ctypes.Structure):
                 ("fit", ctypes.c_double * SBT_MAX_REPS),
                 ("min_score", ctypes.c_double * SBT_MAX_REPS),
                 ("perm", (ctypes.c_int32 * SBT_MAX_RANK) * SBT_MAX_REPS)]
+
+
+class SbtProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
+                ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
+                ("mttkrp_bytes", ctypes.c_double)]
 
 
 class SbtError(RuntimeError):
@@ -114,6 +121,8 @@ def lib() -> ctypes.CDLL:
     L.sbt_philox4x32_10.argtypes = [P, U32, U32, P, I64, P]
     L.sbt_sample.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_mttkrp.argtypes = [I32, P, I64, I64, I64, I64, P, P, P, I32, I32, P, P]
+    L.sbt_profile_reset.argtypes = [P, I32]
+    L.sbt_profile_read.argtypes = [P, ctypes.POINTER(SbtProfile)]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("sbt_version", "sbt_last_error", "sbt_destroy"):
@@ -248,6 +257,15 @@ class SamBaTen:
                 "flags": st.flags, "iters": list(st.iters[:r]), "fit": list(st.fit[:r]),
                 "min_score": list(st.min_score[:r]),
                 "perm": [list(st.perm[q][:R]) for q in range(r)]}
+
+    def profile_reset(self, timing: bool = True):
+        _check(lib().sbt_profile_reset(self._h, 1 if timing else 0), "sbt_profile_reset")
+
+    def profile(self) -> dict:
+        p = SbtProfile()
+        _check(lib().sbt_profile_read(self._h, ctypes.byref(p)), "sbt_profile_read")
+        return {"launches": p.launches, "updates": p.updates, "mttkrp_launches": p.mttkrp_launches,
+                "mttkrp_ms": p.mttkrp_ms, "mttkrp_bytes": p.mttkrp_bytes}
 
     def last_samples(self, rep: int, mode: int) -> np.ndarray:
         n = ctypes.c_int64()

@@ -227,3 +227,19 @@ def test_init_als_f32_fit(sbt):
     ctx = sbt.SamBaTen(torch.from_numpy(X).cuda(), 5, max_iters_init=40, fixed_iters=1, seed=1)
     st, res = O.init_decomposition(X, 5, O.Options(max_iters_init=40, fixed_iters=True, seed=1))
     assert abs(ctx.fit() - O.full_fit(X, st.lam, st.A, st.B, st.C)) < 1e-4
+
+
+def test_profile_counters(sbt):
+    """MTTKRP bytes counted = passes x repetitions x summary bytes (fixed iterations)."""
+    X, A, B, C = planted(64, 48, 40, 4, dtype=torch.float32, seed=13)
+    fac = unit_factors(A, B, C[:30])
+    ctx, _ = _pair(sbt, X, 30, 4, fac, prec="bf16", r=3, fixed_iters=1, max_iters=7)
+    ctx.profile_reset(timing=True)
+    ctx.update(torch.from_numpy(X[30:40]).cuda())
+    p = ctx.profile()
+    st = ctx.stats()
+    Kp = st["n_K"] + 10
+    assert p["updates"] == 1
+    assert p["mttkrp_launches"] == 3 * 7
+    assert p["mttkrp_bytes"] == 3 * 7 * 3 * Kp * st["n_I"] * st["n_J"] * 2
+    assert p["mttkrp_ms"] > 0 and p["launches"] > p["mttkrp_launches"]
