@@ -208,6 +208,25 @@ sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_
                       const void *A, const void *B, const void *C, int32_t R, int32_t mode,
                       void *M, void *stream);
 
+/* The weighted draw of sbt_sample for callers that must not allocate device
+ * memory during the call -- for example a serving process that gives the whole
+ * device to its own pool at start-up, or a latency-critical loop where a
+ * cudaMalloc (which may synchronise the device) is not allowed.  The paper has
+ * no counterpart to this entry point; it is a deployment variant.
+ *
+ * Same arguments, results and errors as sbt_sample; N must not exceed
+ * SBT_SAMPLE_NOALLOC_MAX_N (SBT_E_INVALID otherwise).  Scratch: one fixed
+ * array of SBT_SAMPLE_NOALLOC_MAX_N * 16 + 256 bytes (about 4 MiB) in the
+ * library's device memory, held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (unordered streams or threads) race on it. */
+#define SBT_SAMPLE_NOALLOC_MAX_N 262144
+sbt_status sbt_sample_noalloc(const uint64_t *w, int64_t N, int64_t n, uint64_t seed,
+                              uint32_t stream_id, int32_t mode, int32_t rep, uint32_t batch,
+                              int32_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

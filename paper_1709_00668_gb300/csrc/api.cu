@@ -104,6 +104,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void sbt::set_last_error(const std::string &msg) { g_err = msg; }
+
 struct sbt_ctx {
     int device = 0;
     int num_sms = 0;

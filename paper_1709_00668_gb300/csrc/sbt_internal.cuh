@@ -7,7 +7,12 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace sbt {
+
+// message returned by sbt_last_error() on this thread
+void set_last_error(const std::string &msg);
 
 // kernels launched by the library (process-wide), for the launch counter
 long long launch_count();

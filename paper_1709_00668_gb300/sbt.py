@@ -47,8 +47,9 @@ EXPORTS = [
     "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
     "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
-    "sbt_profile_reset", "sbt_profile_read",
+    "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
 ]
+SBT_SAMPLE_NOALLOC_MAX_N = 262144
 
 
 class SbtTensor(ctypes.Structure):
@@ -121,6 +122,7 @@ def lib() -> ctypes.CDLL:
     L.sbt_philox4x32_10.argtypes = [P, U32, U32, P, I64, P]
     L.sbt_sample.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_mttkrp.argtypes = [I32, P, I64, I64, I64, I64, P, P, P, I32, I32, P, P]
+    L.sbt_sample_noalloc.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_profile_reset.argtypes = [P, I32]
     L.sbt_profile_read.argtypes = [P, ctypes.POINTER(SbtProfile)]
     for name in EXPORTS:
@@ -351,6 +353,20 @@ def sbt_sample(w, n, *, seed=0, stream_id=0, mode=0, rep=0, batch=0, stream=None
     _check(lib().sbt_sample(w.data_ptr(), w.numel(), int(n), int(seed) & ((1 << 64) - 1),
                             int(stream_id) & 0xFFFFFFFF, int(mode), int(rep), int(batch) & 0xFFFFFFFF,
                             out.data_ptr(), _stream_arg(stream)), "sbt_sample")
+    return out[:int(n)]
+
+
+def sbt_sample_noalloc(w, n, *, seed=0, stream_id=0, mode=0, rep=0, batch=0, stream=None, out=None):
+    """sbt_sample without any device allocation inside the call (scratch is a
+    fixed array in the library, N <= SBT_SAMPLE_NOALLOC_MAX_N).  `out` may be a
+    preallocated CUDA int32 tensor of at least n elements."""
+    import torch
+    w = w.contiguous()
+    if out is None:
+        out = torch.empty(max(1, int(n)), dtype=torch.int32, device=w.device)
+    _check(lib().sbt_sample_noalloc(w.data_ptr(), w.numel(), int(n), int(seed) & ((1 << 64) - 1),
+                                    int(stream_id) & 0xFFFFFFFF, int(mode), int(rep), int(batch) & 0xFFFFFFFF,
+                                    out.data_ptr(), _stream_arg(stream)), "sbt_sample_noalloc")
     return out[:int(n)]
 
 
