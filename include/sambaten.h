@@ -52,7 +52,8 @@ typedef enum {
     SBT_E_STATE = 8      /* call not valid in the context's current state */
 } sbt_status;
 
-typedef enum { SBT_F64 = 0, SBT_F32 = 1 } sbt_dtype; /* storage type of X */
+/* Storage type of X.  SBT_BF16 is accepted by sbt_mttkrp only. */
+typedef enum { SBT_F64 = 0, SBT_F32 = 1, SBT_BF16 = 2 } sbt_dtype;
 
 /* Arithmetic of the summary MTTKRP (the hot loop).  F64: float64 throughout
  * (needs an F64 store).  F32: float32 values, float32 accumulation.  BF16:
@@ -200,10 +201,14 @@ sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64_t seed,
                       uint32_t stream_id, int32_t mode, int32_t rep, uint32_t batch,
                       int32_t *out, void *stream);
 
-/* MTTKRP of a dense slice-major tensor (K x I x J, row pitch ld >= J elements)
- * for one mode (0: M = X_(1)(C kr B) -> I x R; 1: J x R; 2: K x R), the
- * contraction inside every ALS step of Alg. 1 step 5.  dtype SBT_F64 or
- * SBT_F32 applies to X, the factors A (I x R), B (J x R), C (K x R) and M. */
+/* MTTKRP of a dense slice-major tensor (K x I x J, row pitch ld >= J elements,
+ * ld a multiple of 8, X 16-byte aligned) for one mode (0: M = X_(1)(C kr B)
+ * -> I x R; 1: J x R; 2: K x R), the contraction inside every ALS step of
+ * Alg. 1 step 5.  dtype SBT_F64 or SBT_F32 applies to X, the factors A (I x R),
+ * B (J x R), C (K x R) and M (CUDA cores).  dtype SBT_BF16: X is bfloat16, the
+ * factors and M are float32, and the product runs on the tensor cores
+ * (tcgen05, factors split into two bfloat16 halves); SBT_E_INVALID if R or
+ * the contraction length is beyond that kernel's shared-memory plan. */
 sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
                       const void *A, const void *B, const void *C, int32_t R, int32_t mode,
                       void *M, void *stream);

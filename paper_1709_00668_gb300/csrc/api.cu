@@ -102,6 +102,14 @@ struct DeviceGuard {
     }
 };
 
+// tensor-core plan for bfloat16 summaries: tensor maps over the summary and
+// its transposed copy
+struct TcPlan {
+    bool on = false;
+    alignas(64) CUtensorMap m1;  // [slice][ii][jj]: contraction over jj
+    alignas(64) CUtensorMap m2;  // [slice][jj][ii]: contraction over ii
+};
+
 }  // namespace
 
 void sbt::set_last_error(const std::string &msg) { g_err = msg; }
@@ -124,7 +132,8 @@ struct sbt_ctx {
     HBuf h_status, h_poll, h_stats;
     // workspace
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
-    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging;
+    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt;
+    TcPlan tc;
     // profiling
     Buf prof_bytes;  // unsigned long long, device
     bool timing = false;
@@ -220,6 +229,7 @@ static sbt_status status_error(unsigned err) {
     if (err & ERR_NONFINITE) return fail(SBT_E_NONFINITE, "non-finite value in the input slices");
     if (err & ERR_RANGE) return fail(SBT_E_RANGE, "fixed-point marginal would overflow 64 bits");
     if (err & ERR_SAMPLE) return fail(SBT_E_STATE, "sample size above the number of positive weights");
+    if (err & ERR_TIMEOUT) return fail(SBT_E_TIMEOUT, "a bounded device wait gave up");
     return SBT_OK;
 }
 
@@ -275,10 +285,40 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
 
 // Run ALS iterations until every repetition converged (polled every
 // check_every iterations) or max_iters.
-static sbt_status timed_mttkrp(sbt_ctx *c, const AlsDesc &d, int mode) {
+static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode) {
+    if (!tc || !tc->on) return launch_mttkrp(d, mode, c->stream);
+    const int R = d.R, NI = d.n[0], NJ = d.n[1], Kp = d.n[2];
+    const float *U0 = (const float *)d.U[0], *U1 = (const float *)d.U[1], *U2 = (const float *)d.U[2];
+    unsigned *err = &c->status.as<DevStatus>()->err;
+    int P = 0;
+    if (mode == 0)
+        return launch_mttkrp_tc(tc->m1, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
+                                (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+    if (mode == 1)
+        return launch_mttkrp_tc(tc->m2, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
+                                (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+    return launch_mttkrp_tc(tc->m1, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
+                            (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+}
+
+// partial counts of the tensor-core kernels, fixed by the shapes
+static void tc_partials(AlsDesc &d, int num_sms) {
+    int npb, nks, spc;
+    tc_tiles(d.nrep, d.n[0], d.n[2], num_sms, &npb, &nks, &spc);
+    d.P[0] = nks;
+    const long long e0 = (long long)nks * d.n[0];
+    const long long e2 = (long long)npb * d.n[2];
+    d.P[2] = npb;
+    tc_tiles(d.nrep, d.n[1], d.n[2], num_sms, &npb, &nks, &spc);
+    d.P[1] = nks;
+    const long long e1 = (long long)nks * d.n[1];
+    d.prs = std::max(e0, std::max(e1, e2)) * d.R;
+}
+
+static sbt_status timed_mttkrp(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode) {
     c->mtt_launches += 1;
     if (!c->timing) {
-        CK(launch_mttkrp(d, mode, c->stream));
+        CK(mttkrp_mode(c, d, tc, mode));
         return SBT_OK;
     }
     if (c->events_used == c->events.size()) {
@@ -289,16 +329,16 @@ static sbt_status timed_mttkrp(sbt_ctx *c, const AlsDesc &d, int mode) {
     }
     auto &ev = c->events[c->events_used++];
     CK(cudaEventRecord(ev.first, c->stream));
-    CK(launch_mttkrp(d, mode, c->stream));
+    CK(mttkrp_mode(c, d, tc, mode));
     CK(cudaEventRecord(ev.second, c->stream));
     return SBT_OK;
 }
 
-static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters) {
+static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcPlan *tc = nullptr) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     for (int it = 1; it <= max_iters; ++it) {
         for (int mode = 0; mode < 3; ++mode) {
-            TRY(timed_mttkrp(c, d, mode));
+            TRY(timed_mttkrp(c, d, tc, mode));
             CK(launch_reduce_tail(d, mode, c->stream));
         }
         if (it == max_iters || (!c->opt.fixed_iters && it % every == 0)) {
@@ -565,9 +605,22 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     AlsDesc d;
     const int n[3] = {nI, nJ, Kp};
     TRY(setup_als(c, d, r, n, ldj, nK, c->elem, c->Xs.p, xrs, c->opt.max_iters));
+    // bfloat16 summaries: tensor-core MTTKRP over the summary and its transposed copy
+    TcPlan &tc = c->tc;
+    tc.on = c->elem == 2 && tc_supported(R, nI) && tc_supported(R, nJ);
+    if (tc.on) {
+        const int ldi = round8(nI);
+        TRY(c->Xt.ensure((size_t)r * Kp * nJ * ldi * 2));
+        CK(launch_transpose_bf16(c->Xs.p, c->Xt.p, nI, nJ, ldj, ldi, (long long)r * Kp, c->stream));
+        CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp));
+        CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp));
+        tc_partials(d, c->num_sms);
+        TRY(c->part.ensure((size_t)r * d.prs * 4));
+        d.part = c->part.p;
+    }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
                           c->batch, c->rowsq.as<double>(), c->stream));
-    TRY(run_als(c, d, c->opt.max_iters));
+    TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
     // 5. normalise, match, project back; 6. commit
     const int pmax = (int)samp_stride;
     TRY(c->nu.ensure((size_t)r * 3 * R * 8));
@@ -886,16 +939,82 @@ extern "C" sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64
     return SBT_OK;
 }
 
+static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J, int64_t ld, const void *A,
+                                 const void *B, const void *C, int32_t R, int32_t mode, void *M, cudaStream_t st) {
+    const int NP = (int)(mode == 1 ? J : I), NC = (int)(mode == 1 ? I : J);
+    if (!tc_supported(R, NC)) return fail(SBT_E_INVALID, "R or the contraction length exceeds the tensor-core plan");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AlsDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nrep = 1;
+    d.R = R;
+    d.n[0] = (int)I;
+    d.n[1] = (int)J;
+    d.n[2] = (int)K;
+    d.elem = 2;
+    int npb, nks, spc;
+    tc_tiles(1, NP, (int)K, sms, &npb, &nks, &spc);
+    const int P = mode == 2 ? npb : nks;
+    d.P[mode] = P;
+    d.prs = (long long)P * (mode == 2 ? K : NP) * R;
+    d.mrs = (long long)std::max(I, std::max(J, K)) * R;
+    const int ldi = round8(I);
+    const size_t xt_bytes = mode == 1 ? (size_t)K * J * ldi * 2 : 0;
+    const size_t off_m = 256, off_part = off_m + (size_t)d.mrs * 8, off_xt = (off_part + (size_t)d.prs * 4 + 255) / 256 * 256;
+    char *scr = nullptr;
+    CK(cudaMallocAsync((void **)&scr, off_xt + xt_bytes + 256, st));
+    d.conv = (int *)scr;
+    unsigned *err = (unsigned *)(scr + 64);
+    d.M = (double *)(scr + off_m);
+    d.part = scr + off_part;
+    cudaError_t e = cudaMemsetAsync(scr, 0, 256, st);
+    alignas(64) CUtensorMap map;
+    int Pk = 0;
+    if (e == cudaSuccess) {
+        if (mode == 1) {
+            e = launch_transpose_bf16(X, scr + off_xt, (int)I, (int)J, (int)ld, ldi, K, st);
+            if (e == cudaSuccess) e = make_summary_tmap(&map, scr + off_xt, (int)I, (int)J, ldi, K);
+        } else {
+            e = make_summary_tmap(&map, X, (int)J, (int)I, (int)ld, K);
+        }
+    }
+    if (e == cudaSuccess) {
+        if (mode == 0)
+            e = launch_mttkrp_tc(map, 0, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)C, 0,
+                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+        else if (mode == 1)
+            e = launch_mttkrp_tc(map, 0, 1, R, (int)J, (int)I, (int)K, (const float *)A, 0, (const float *)C, 0,
+                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+        else
+            e = launch_mttkrp_tc(map, 1, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)A, 0,
+                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+    }
+    if (e == cudaSuccess) e = launch_reduce_only(d, mode, st);
+    if (e == cudaSuccess) e = launch_store_m(d, mode, M, st);
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(scr, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("sbt_mttkrp (bf16): ") + cudaGetErrorString(e));
+    if (herr) return fail(SBT_E_TIMEOUT, "sbt_mttkrp (bf16): a bounded device wait gave up");
+    return SBT_OK;
+}
+
 extern "C" sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
                                  const void *A, const void *B, const void *C, int32_t R, int32_t mode, void *M,
                                  void *stream) {
     if (!X || !A || !B || !C || !M) return fail(SBT_E_INVALID, "null pointer");
-    if (dtype != SBT_F64 && dtype != SBT_F32) return fail(SBT_E_INVALID, "dtype must be SBT_F64 or SBT_F32");
+    if (dtype != SBT_F64 && dtype != SBT_F32 && dtype != SBT_BF16)
+        return fail(SBT_E_INVALID, "dtype must be SBT_F64, SBT_F32 or SBT_BF16");
     if (K < 1 || I < 1 || J < 1 || ld < J || ld % 8 != 0) return fail(SBT_E_SHAPE, "need K, I, J >= 1 and ld >= J, ld % 8 == 0");
     if (((uintptr_t)X) % 16 != 0) return fail(SBT_E_INVALID, "X must be 16-byte aligned");
     if (R < 1 || R > SBT_MAX_RANK || mode < 0 || mode > 2) return fail(SBT_E_INVALID, "R or mode out of range");
     if (K > (1 << 30) || I > (1 << 30) || J > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
     cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == SBT_BF16) return mttkrp_bf16_op(X, K, I, J, ld, A, B, C, R, mode, M, st);
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -67,6 +67,12 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[RP], int lane) {
     return v[0];
 }
 
+template <typename TF>
+__global__ void k_store_m(const double *M, TF *out, long long cnt) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < cnt) out[e] = (TF)M[e];
+}
+
 template <typename TX> struct FactorOf { using T = float; };
 template <> struct FactorOf<double> { using T = double; };
 
@@ -527,6 +533,9 @@ void choose_tiles(AlsDesc &d, int num_sms) {
     nrs = std::max(1LL, std::min(nrs, rows));
     d.rows_per = (rows + nrs - 1) / nrs;
     d.nrs = (int)((rows + d.rows_per - 1) / d.rows_per);
+    d.P[0] = d.nks;
+    d.P[1] = d.nrs;
+    d.P[2] = d.nib;
 }
 
 long long partial_elems(const AlsDesc &d) {
@@ -604,7 +613,7 @@ static cudaError_t mtt_dispatch(const AlsDesc &d, int mode, cudaStream_t st) {
 }
 
 static cudaError_t reduce_dispatch(const AlsDesc &d, int mode, cudaStream_t st) {
-    const int P = mode == 0 ? d.nks : (mode == 1 ? d.nrs : d.nib);
+    const int P = d.P[mode];
     const long long cnt = (long long)d.n[mode] * d.R;
     dim3 grid((unsigned)((cnt + 255) / 256), d.nrep);
     if (d.elem == 0)
@@ -617,6 +626,20 @@ static cudaError_t reduce_dispatch(const AlsDesc &d, int mode, cudaStream_t st) 
 cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st) {
     count_launches(1);
     return mtt_dispatch(d, mode, st);
+}
+
+cudaError_t launch_reduce_only(const AlsDesc &d, int mode, cudaStream_t st) {
+    count_launches(1);
+    return reduce_dispatch(d, mode, st);
+}
+
+cudaError_t launch_store_m(const AlsDesc &d, int mode, void *Mout, cudaStream_t st) {
+    const long long cnt = (long long)d.n[mode] * d.R;
+    unsigned blocks = (unsigned)((cnt + 255) / 256);
+    count_launches(1);
+    if (d.elem == 0) k_store_m<double><<<blocks, 256, 0, st>>>(d.M, (double *)Mout, cnt);
+    else k_store_m<float><<<blocks, 256, 0, st>>>(d.M, (float *)Mout, cnt);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
@@ -657,11 +680,6 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
 
 // ---------------------------------------------------------------------------
 // MTTKRP op: one mode, one tensor, result in the factor type.
-template <typename TF>
-__global__ void k_store_m(const double *M, TF *out, long long cnt) {
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e < cnt) out[e] = (TF)M[e];
-}
 
 cudaError_t launch_mttkrp_op(AlsDesc &d, int mode, void *Mout, cudaStream_t st) {
     count_launches(3);

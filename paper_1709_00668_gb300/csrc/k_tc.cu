@@ -1,0 +1,499 @@
+// MTTKRP of bfloat16 summaries on the 5th-generation tensor cores (tcgen05).
+//
+// Per slice kk of a summary, Z = X_kk . F is a dense product: 128 rows of
+// X_kk (an M = 128 tile, rows beyond the summary zero-filled by TMA) times the
+// contraction factor F (K = the other summary dimension, N = 2 * RH columns:
+// F rounded to bfloat16 and the bfloat16 rounding error of F, so that
+// bf16 x (hi + lo) keeps ~16 bits of the float32 factor).  The accumulators
+// live in tensor memory; four epilogue warps read them back and fold the
+// ALS weights in:
+//   ROWSUM (modes 1 and 2): M(p, r) += Z(p, r) C(kk, r), summed over the
+//       CTA's slices in registers -> part[rep][ks][p][r];
+//   COLSUM (mode 3): M3(kk, r) = sum_p Z(p, r) A(p, r) over the tile's rows
+//       -> part[rep][pb][kk][r].
+// Mode 2 reads a transposed copy of the summary ([kk][jj][ii]) so that every
+// operand is K-major.  Warp roles: warp 0 issues TMA loads into a ring of
+// 16 KB stages, warp 1 owns tensor memory and issues the MMAs (one thread),
+// warps 2-5 are the epilogue.  Every mbarrier wait is bounded; a timeout sets
+// an error word, stops the CTA's loops, waits for its outstanding copies and
+// frees its tensor memory.
+#include "sbt_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+namespace sbt {
+
+constexpr int TC_M = 128;
+constexpr int TC_BOX_BYTES = TC_M * 128;  // 128 rows x 64 bfloat16
+constexpr unsigned TC_SPIN_LIMIT = 1u << 24;  // ~0.5 s of polling per wait
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand in the 128-byte swizzled layout: 8-row atoms of 128 B,
+// atoms 1024 B apart (stride byte offset); the leading offset is unused.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading byte offset (16 B, ignored for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: 1024 B between 8-row atoms
+    d |= (uint64_t)1 << 46;              // descriptor version of the 5th-generation tensor core
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A and B bfloat16, D float32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4)                     // D format: float32
+           | (1u << 7)                   // A format: bfloat16
+           | (1u << 10)                  // B format: bfloat16
+           | ((uint32_t)(N >> 3) << 17)  // N / 8
+           | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+struct TcParams {
+    int nrep, R, NP, NC, Kp;
+    int nkb, npb, spc, nks;
+    int epi;                 // 0 ROWSUM (weights C(kk)), 1 COLSUM (weights A(p))
+    const float *F;          // contraction factor [rep][NC][R]
+    long long frs;
+    const float *W;          // epilogue factor [rep][Kp][R] (ROWSUM) or [rep][NP][R] (COLSUM)
+    long long wrs;
+    float *part;
+    long long prs;
+    const int *conv;
+    unsigned long long *bytes_ctr;
+    unsigned *err;           // device status word (ERR_TIMEOUT on a wait that gave up)
+    int stages;
+};
+
+struct TcShared {
+    uint64_t full[8], empty[8], accf[2], acce[2];
+    uint32_t tmem_base;
+    int abort_flag;
+    float red[4][32];
+};
+
+// bounded wait; on timeout raise the abort flag and the error word
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *err) {
+    for (unsigned it = 0; it < TC_SPIN_LIMIT; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (it > 64) __nanosleep(32);
+    }
+    *abort_flag = 1;
+    atomicOr(err, ERR_TIMEOUT);
+    return false;
+}
+
+template <int N>
+__global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap, TcParams p) {
+    constexpr int RH = N / 2;
+    const int rep = blockIdx.y;
+    if (p.conv[rep]) return;
+    const int pb = blockIdx.x % p.npb, ks = blockIdx.x / p.npb;
+    const int k0 = ks * p.spc, k1 = min(p.Kp, k0 + p.spc);
+    const int nsl = k1 - k0;
+    if (nsl <= 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = p.stages;
+
+    extern __shared__ unsigned char smem_dyn[];
+    // 1024-byte alignment for the swizzled tiles
+    const uint32_t base_u32 = smem_u32(smem_dyn);
+    unsigned char *smem = smem_dyn + ((1024u - (base_u32 & 1023u)) & 1023u);
+    unsigned char *ring = smem;                                   // S x 16 KB
+    unsigned char *btile = ring + (size_t)S * TC_BOX_BYTES;        // nkb x N x 128 B
+    TcShared *sh = reinterpret_cast<TcShared *>(btile + (size_t)p.nkb * N * 128);
+    volatile int *abort_flag = &sh->abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sh->accf[a], 1);
+            mbar_init(&sh->acce[a], 128);
+        }
+        sh->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(2 * N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // B operand: rows n < RH hold bf16(F), rows RH.. hold bf16(F - bf16(F)); K-major, swizzled
+    const float *F = p.F + rep * p.frs;
+    const int R = p.R;
+    for (int e = threadIdx.x; e < p.nkb * N * 64; e += blockDim.x) {
+        const int kb = e / (N * 64), rem = e % (N * 64), n = rem / 64, k = rem % 64;
+        const int j = kb * 64 + k, r = n % RH;
+        float f = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
+        __nv_bfloat16 hi = __float2bfloat16_rn(f);
+        __nv_bfloat16 v = n < RH ? hi : __float2bfloat16_rn(f - __bfloat162float(hi));
+        const int chunk = (k >> 3) ^ (n & 7);
+        *reinterpret_cast<__nv_bfloat16 *>(btile + (size_t)kb * N * 128 + n * 128 + chunk * 16 + (k & 7) * 2) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            for (int t = 0; t < nsl && !*abort_flag; ++t) {
+                for (int kb = 0; kb < p.nkb; ++kb) {
+                    if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+                    mbar_expect_tx(&sh->full[stage], TC_BOX_BYTES);
+                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, &tmap, kb * 64, pb * TC_M,
+                                rep * p.Kp + k0 + t, &sh->full[stage]);
+                    ++issued;
+                    if (++stage == S) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let the copies in flight land before the CTA leaves (bounded)
+                int s = stage;
+                uint32_t ph = phase;
+                for (int q = 0; q < min(issued, S); ++q) {
+                    if (--s < 0) {
+                        s = S - 1;
+                        ph ^= 1u;
+                    }
+                    for (unsigned it = 0; it < TC_SPIN_LIMIT && !mbar_try_wait(&sh->full[s], ph); ++it) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc_idesc(TC_M, N);
+            int stage = 0;
+            uint32_t phase = 0;
+            const uint32_t bbase = smem_u32(btile);
+            for (int t = 0; t < nsl && !*abort_flag; ++t) {
+                const int a = t & 1;
+                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+                if (!tc_wait(&sh->acce[a], aph ^ 1u, abort_flag, p.err)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * N);
+                bool ok = true;
+                for (int kb = 0; kb < p.nkb; ++kb) {
+                    if (!tc_wait(&sh->full[stage], phase, abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t abase = smem_u32(ring + (size_t)stage * TC_BOX_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        tc_mma(d, sw128_desc(abase + k * 32), sw128_desc(bbase + kb * N * 128 + k * 32), idesc,
+                               (kb | k) != 0);
+                    }
+                    tc_commit(&sh->empty[stage]);
+                    if (++stage == S) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc_commit(&sh->accf[a]);
+            }
+        }
+    } else {
+        // epilogue: thread <-> tile row
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int pidx = pb * TC_M + row;
+        const bool valid = pidx < p.NP;
+        const float *W = p.W + rep * p.wrs;
+        float acc[RH];
+        float arow[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            acc[r] = 0.f;
+            arow[r] = (p.epi == 1 && valid && r < R) ? W[(long long)pidx * R + r] : 0.f;
+        }
+        float *part = p.part + rep * p.prs;
+        const int etid = threadIdx.x - 64;
+        for (int t = 0; t < nsl; ++t) {
+            const int a = t & 1;
+            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+            const bool got = tc_wait(&sh->accf[a], aph, abort_flag, p.err);
+            float z[RH];
+            if (got) {
+                tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * N);
+                float v[32];
+#pragma unroll
+                for (int c = 0; c < N; c += 32) {
+                    tmem_ld32(taddr + c, v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = c + i;
+                        if (col < RH) z[col] = v[i];
+                        else z[col - RH] += v[i];
+                    }
+                }
+                tc_fence_before();
+            } else {
+#pragma unroll
+                for (int r = 0; r < RH; ++r) z[r] = 0.f;
+            }
+            mbar_arrive(&sh->acce[a]);
+            const int kk = k0 + t;
+            // after an abort every remaining wait returns at once; the loop
+            // runs to its end so that all 128 threads meet the same barriers
+            if (p.epi == 0) {
+                if (valid) {
+                    const float *c = W + (long long)kk * R;
+#pragma unroll
+                    for (int r = 0; r < RH; ++r)
+                        if (r < R) acc[r] = fmaf(z[r], c[r], acc[r]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RH; ++r) {
+                    float v = warp_sum(z[r] * arow[r]);
+                    if (lane == 0) sh->red[quarter][r] = v;
+                }
+                epi_bar();
+                if (etid < R) {
+                    float s = ((sh->red[0][etid] + sh->red[1][etid]) + sh->red[2][etid]) + sh->red[3][etid];
+                    part[((long long)pb * p.Kp + kk) * R + etid] = s;
+                }
+                epi_bar();
+            }
+        }
+        if (p.epi == 0 && valid) {
+#pragma unroll
+            for (int r = 0; r < RH; ++r)
+                if (r < R) part[((long long)ks * p.NP + pidx) * R + r] = acc[r];
+        }
+        if (p.bytes_ctr && etid == 0) {
+            const int rows = min(TC_M, p.NP - pb * TC_M);
+            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed copy of bfloat16 summaries: Y[s][j][i] = X[s][i][j] (64 x 64 tiles)
+__global__ void __launch_bounds__(256) k_transpose_bf16(const __nv_bfloat16 *X, __nv_bfloat16 *Y, int NI, int NJ,
+                                                       int ldx, int ldy) {
+    __shared__ __nv_bfloat16 tile[64][66];
+    const long long s = blockIdx.z;
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    const __nv_bfloat16 *xs = X + s * NI * (long long)ldx;
+    __nv_bfloat16 *ys = Y + s * NJ * (long long)ldy;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+    for (int i = ty; i < 64; i += 4) {
+        const int gi = i0 + i, gj = j0 + tx;
+        tile[i][tx] = (gi < NI && gj < NJ) ? xs[(long long)gi * ldx + gj] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int j = ty; j < 64; j += 4) {
+        const int gj = j0 + j, gi = i0 + tx;
+        if (gj < NJ && gi < NI) ys[(long long)gj * ldy + gi] = tile[tx][j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// 3-D map over [slices][NP][ld] bfloat16, box 64 x 128 x 1, 128-byte swizzle,
+// zero fill outside (columns >= NC, rows >= NP).
+cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (((uintptr_t)base & 15) || (ld * 2) % 16) return cudaErrorInvalidValue;
+    cuuint64_t dims[3] = {(cuuint64_t)NC, (cuuint64_t)NP, (cuuint64_t)nslices};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)NP * ld * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)TC_M, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static int tc_n_of(int R) { return R <= 16 ? 32 : 64; }
+
+static size_t tc_smem_bytes(int nkb, int N, int stages) {
+    return 1024 + (size_t)stages * TC_BOX_BYTES + (size_t)nkb * N * 128 + sizeof(TcShared);
+}
+
+bool tc_supported(int R, int NC) {
+    const int N = tc_n_of(R);
+    const int nkb = (NC + 63) / 64;
+    return R <= 32 && (size_t)nkb * N * 128 <= 96 * 1024;
+}
+
+// Work split for one mode: CTAs = nrep x npb x nks, about two per SM.
+void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc) {
+    *npb = (NP + TC_M - 1) / TC_M;
+    long long target = 2LL * num_sms;
+    long long n = target / std::max(1LL, (long long)nrep * *npb);
+    n = std::max(1LL, std::min<long long>(n, Kp));
+    *spc = (int)((Kp + n - 1) / n);
+    *nks = (Kp + *spc - 1) / *spc;
+}
+
+cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
+                             const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
+                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
+                             int *P_out, cudaStream_t st) {
+    TcParams p{};
+    p.nrep = nrep;
+    p.R = R;
+    p.NP = NP;
+    p.NC = NC;
+    p.Kp = Kp;
+    p.nkb = (NC + 63) / 64;
+    tc_tiles(nrep, NP, Kp, num_sms, &p.npb, &p.nks, &p.spc);
+    p.epi = epi;
+    p.F = F;
+    p.frs = frs;
+    p.W = W;
+    p.wrs = wrs;
+    p.part = part;
+    p.prs = prs;
+    p.conv = conv;
+    p.bytes_ctr = bytes_ctr;
+    p.err = err;
+    const int N = tc_n_of(R);
+    const size_t budget = 110 * 1024;
+    const size_t fixed = 1024 + (size_t)p.nkb * N * 128 + sizeof(TcShared);
+    int stages = (int)std::min<size_t>(8, (budget > fixed ? (budget - fixed) : 0) / TC_BOX_BYTES);
+    p.stages = std::max(2, stages);
+    const size_t smem = tc_smem_bytes(p.nkb, N, p.stages);
+    *P_out = epi == 0 ? p.nks : p.npb;
+    dim3 grid(p.npb * p.nks, nrep);
+    count_launches(1);
+    if (N == 32) {
+        cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mtt_tc<32><<<grid, 192, smem, st>>>(tmap, p);
+    } else {
+        cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mtt_tc<64><<<grid, 192, smem, st>>>(tmap, p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
+                                  cudaStream_t st) {
+    for (long long s0 = 0; s0 < nslices; s0 += 65535) {
+        const long long ns = std::min<long long>(65535, nslices - s0);
+        dim3 grid((NJ + 63) / 64, (NI + 63) / 64, (unsigned)ns);
+        count_launches(1);
+        k_transpose_bf16<<<grid, 256, 0, st>>>((const __nv_bfloat16 *)X + s0 * NI * (long long)ldx,
+                                               (__nv_bfloat16 *)Y + s0 * NJ * (long long)ldy, NI, NJ, ldx, ldy);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sbt

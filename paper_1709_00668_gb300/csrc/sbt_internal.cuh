@@ -3,6 +3,7 @@
 // launchers of every kernel family.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -29,6 +30,7 @@ enum : unsigned {
     ERR_NONFINITE = 1u,  // new slices hold NaN/Inf
     ERR_RANGE = 2u,      // fixed-point marginal overflow
     ERR_SAMPLE = 4u,     // sample size above the number of positive weights
+    ERR_TIMEOUT = 8u,    // a bounded device wait gave up
 };
 
 // Device status block (mirrored to pinned host memory once per call).
@@ -178,6 +180,7 @@ struct AlsDesc {
     double tol;
     int max_iters, fixed_iters;
     unsigned long long *bytes_ctr;  // algorithmic bytes read by MTTKRP passes (nullable)
+    int P[3];              // partial sums per mode (set by the chosen MTTKRP kernels)
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -215,6 +218,20 @@ cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st);
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
 long long partial_elems(const AlsDesc &d);  // per repetition
+
+// tcgen05 MTTKRP of bfloat16 summaries (k_tc.cu)
+bool tc_supported(int R, int NC);
+void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc);
+cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices);
+cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
+                             const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
+                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
+                             int *P_out, cudaStream_t st);
+cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
+                                  cudaStream_t st);
+// reduction of d.P[mode] partials into d.M, then the tail
+cudaError_t launch_reduce_only(const AlsDesc &d, int mode, cudaStream_t st);
+cudaError_t launch_store_m(const AlsDesc &d, int mode, void *Mout, cudaStream_t st);
 
 // MTTKRP of one mode of a single tensor (d.nrep == 1, d.conv zero) into Mout
 // (factor type), through d.part and d.M.

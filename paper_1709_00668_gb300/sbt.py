@@ -34,6 +34,7 @@ SBT_E_STATE = 8
 
 SBT_F64 = 0
 SBT_F32 = 1
+SBT_BF16 = 2
 SBT_PREC_F64 = 0
 SBT_PREC_F32 = 1
 SBT_PREC_BF16 = 2
@@ -371,14 +372,15 @@ def sbt_sample_noalloc(w, n, *, seed=0, stream_id=0, mode=0, rep=0, batch=0, str
 
 
 def sbt_mttkrp(X, A, B, C, mode, *, stream=None):
-    """MTTKRP of a (K, I, J) CUDA tensor (last dim may be padded to a multiple of 8)."""
+    """MTTKRP of a (K, I, ld) CUDA tensor (ld >= J, a multiple of 8; J = B.shape[0]).
+    bfloat16 X takes float32 factors and returns float32 (tensor cores)."""
     import torch
     K, I, ld = X.shape
     J = B.shape[0]
     R = A.shape[1]
-    dt = SBT_F64 if X.dtype == torch.float64 else SBT_F32
+    dt = {torch.float64: SBT_F64, torch.float32: SBT_F32, torch.bfloat16: SBT_BF16}[X.dtype]
     n = (I, J, K)[mode]
-    out = torch.empty(n, R, dtype=X.dtype, device=X.device)
+    out = torch.empty(n, R, dtype=torch.float32 if dt == SBT_BF16 else X.dtype, device=X.device)
     A, B, C = A.contiguous(), B.contiguous(), C.contiguous()
     _check(lib().sbt_mttkrp(dt, X.data_ptr(), K, I, J, ld, A.data_ptr(), B.data_ptr(), C.data_ptr(), R,
                             int(mode), out.data_ptr(), _stream_arg(stream)), "sbt_mttkrp")

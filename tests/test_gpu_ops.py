@@ -96,3 +96,23 @@ def test_mttkrp_ignores_padding(sbt):
         assert np.all(np.isfinite(got))
         want = O.mttkrp(Xd[:, :, :J].double().cpu().numpy(), [u.double().cpu().numpy() for u in Ud], mode)
         assert np.allclose(got, want, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("K,I,J,R", [(3, 5, 7, 1), (9, 130, 70, 10), (24, 200, 200, 10), (7, 256, 64, 16),
+                                     (13, 100, 300, 20), (5, 129, 129, 32), (40, 64, 520, 8)])
+def test_mttkrp_bf16_tensor_cores_match_oracle(sbt, K, I, J, R):
+    """tcgen05 path: bfloat16 X (exact in float64), float32 factors, all three modes."""
+    rng = np.random.default_rng(K + I + J + R)
+    ld = (J + 7) // 8 * 8
+    Xp = torch.zeros(K, I, ld, dtype=torch.bfloat16)
+    Xp[:, :, :J] = torch.from_numpy(rng.standard_normal((K, I, J))).to(torch.bfloat16)
+    Xd = Xp.cuda()
+    U = [torch.from_numpy(rng.standard_normal((n, R))).float().cuda() for n in (I, J, K)]
+    Xv = Xp[:, :, :J].double().numpy()
+    Uv = [u.double().cpu().numpy() for u in U]
+    for mode in range(3):
+        want = O.mttkrp(Xv, Uv, mode)
+        got = sbt.sbt_mttkrp(Xd, *U, mode).double().cpu().numpy()
+        scale = np.max(np.abs(want)) + 1e-300
+        # bf16 x (hi + lo) keeps ~2^-16 of each factor; float32 accumulation
+        assert np.max(np.abs(got - want)) / scale < 2e-4, mode
