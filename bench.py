@@ -55,7 +55,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: same summary shapes, 200 initial slices (a few GB on the device)")
+    args = ap.parse_args()
+    if args.small:
+        WORKLOAD["K0"] = 200
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -158,7 +163,7 @@ def make_data(steps: int, warmup: int, device):
     import torch
     from paper_1709_00668_gb300 import synth
     w = WORKLOAD
-    nb = max(steps, warmup, 10)
+    nb = max(steps, warmup, 10) if w["K0"] == 500 else max(steps, warmup, 1)
     K_total = w["K0"] + nb * w["batch"]
     p = synth.planted_dense(w["I"], w["J"], K_total, w["R"], noise=w["noise"], seed=w["seed"],
                             dtype=torch.float32, device=device)

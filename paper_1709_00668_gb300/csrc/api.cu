@@ -132,7 +132,9 @@ struct sbt_ctx {
     HBuf h_status, h_poll, h_stats;
     // workspace
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
-    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt;
+    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
+    cudaStream_t side = nullptr;  // runs V^-1 of a mode beside its MTTKRP pass
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TcPlan tc;
     // profiling
     Buf prof_bytes;  // unsigned long long, device
@@ -145,6 +147,9 @@ struct sbt_ctx {
             cudaEventDestroy(e.first);
             cudaEventDestroy(e.second);
         }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
     }
     // last update
     bool have_last = false;
@@ -268,6 +273,26 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     TRY(c->conv.ensure((size_t)nrep * 4));
     TRY(c->flags.ensure((size_t)nrep * 4));
     TRY(c->h_poll.ensure((size_t)nrep * 4));
+    d.tchunks = (nmax + 63) / 64;
+    TRY(c->tpart.ensure((size_t)nrep * d.tchunks * (R * (R + 1) / 2 + 1) * sizeof(DF)));
+    d.tpart = c->tpart.as<DF>();
+    if (elem != 0) {
+        TRY(c->xinv.ensure((size_t)nrep * 2048 * 4));
+        d.xinv = c->xinv.as<float>();
+        TRY(c->Gf.ensure((size_t)nrep * 3 * R * R * sizeof(DF)));
+        d.Gf = c->Gf.as<DF>();
+        TRY(c->dfs.ensure((size_t)nrep * 2 * sizeof(DF)));
+        d.nx2f = c->dfs.as<DF>();
+        d.fitpf = d.nx2f + nrep;
+        if (!c->side) {
+            CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        }
+    }
+    TRY(c->tail_cnt.ensure((size_t)nrep * 4));
+    CK(cudaMemsetAsync(c->tail_cnt.p, 0, (size_t)nrep * 4, c->stream));
+    d.tail_cnt = c->tail_cnt.as<int>();
     for (int m = 0; m < 3; ++m) d.U[m] = c->U[m].p;
     d.M = c->M.as<double>();
     d.part = c->part.p;
@@ -338,7 +363,15 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     for (int it = 1; it <= max_iters; ++it) {
         for (int mode = 0; mode < 3; ++mode) {
+            if (d.xinv) {
+                // V^-1 of this mode on the side stream, beside the MTTKRP pass
+                CK(cudaEventRecord(c->ev_fork, c->stream));
+                CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+                CK(launch_xinv(d, mode, c->side));
+                CK(cudaEventRecord(c->ev_join, c->side));
+            }
             TRY(timed_mttkrp(c, d, tc, mode));
+            if (d.xinv) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
             CK(launch_reduce_tail(d, mode, c->stream));
         }
         if (it == max_iters || (!c->opt.fixed_iters && it % every == 0)) {

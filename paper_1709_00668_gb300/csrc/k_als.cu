@@ -430,6 +430,388 @@ __global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
 }
 
 // ---------------------------------------------------------------------------
+// Tail of one mode for float32 factors, in two kernels.  float64 is a slow
+// unit here, so only the R x R work (Hadamard of Grams, Cholesky, inverse,
+// fit) is float64; the n x R work runs in double-float on the float32 pipes.
+//
+// V^-1 for mode `mode` from the Grams of the other two modes, by Gauss-Jordan
+// elimination on [V | I] in double-float, all R x 2R entries updated in
+// parallel (R pivot steps).  For symmetric V the pivots are the squared
+// Cholesky diagonals, so a non-positive pivot means V is not positive
+// definite: then V + 1e-12 tr(V)/R I is used and `reg` is set; if that fails
+// too, X = 0 and `reg` is set.  Called by a whole CTA; W holds 32 x 64 values.
+// X is written as two float planes (hi, lo) of 32 x 32.
+__device__ void block_inverse_df(const DF *Gf, int R, int mode, DF *W, float *X, int *reg) {
+    const int ld = 64;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int e = threadIdx.x; e < R * 2 * R; e += blockDim.x) {
+            const int i = e / (2 * R), j = e % (2 * R);
+            DF v;
+            if (j < R) {
+                v = DF{1.f, 0.f};
+                for (int m = 0; m < 3; ++m)
+                    if (m != mode) v = df_mul(v, Gf[m * R * R + i * R + j]);
+            } else {
+                v = DF{(j - R == i) ? 1.f : 0.f, 0.f};
+            }
+            W[i * ld + j] = v;
+        }
+        __syncthreads();
+        if (attempt == 1) {
+            if (threadIdx.x == 0) {
+                DF tr{0.f, 0.f};
+                for (int i = 0; i < R; ++i) tr = df_add(tr, W[i * ld + i]);
+                const DF shift = df_mul(tr, DF{1e-12f / (float)R, 0.f});
+                for (int i = 0; i < R; ++i) W[i * ld + i] = df_add(W[i * ld + i], shift);
+            }
+            __syncthreads();
+        }
+        bool ok = true;
+        for (int k = 0; k < R; ++k) {
+            const DF piv = W[k * ld + k];
+            if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
+                ok = false;
+                break;
+            }
+            const DF inv = df_div(DF{1.f, 0.f}, piv);
+            DF rowk[8], colk[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int e = threadIdx.x + c * blockDim.x;
+                if (e < R * 2 * R) {
+                    const int i = e / (2 * R), j = e % (2 * R);
+                    rowk[c] = W[k * ld + j];
+                    colk[c] = W[i * ld + k];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int e = threadIdx.x + c * blockDim.x;
+                if (e < R * 2 * R) {
+                    const int i = e / (2 * R), j = e % (2 * R);
+                    const DF t = df_mul(rowk[c], inv);
+                    if (i == k) W[i * ld + j] = t;
+                    else W[i * ld + j] = df_sub(W[i * ld + j], df_mul(colk[c], t));
+                }
+            }
+            __syncthreads();
+        }
+        if (ok) {
+            for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+                const int i = e / 32, j = e % 32;
+                const DF v = (i < R && j < R) ? W[i * ld + R + j] : DF{0.f, 0.f};
+                X[e] = v.hi;
+                X[1024 + e] = v.lo;
+            }
+            if (attempt == 1 && threadIdx.x == 0) *reg = 1;
+            __syncthreads();
+            return;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 2 * 32 * 32; e += blockDim.x) X[e] = 0.f;
+    if (threadIdx.x == 0) *reg = 1;
+    __syncthreads();
+}
+
+// k_tail_rows: grid (row chunks of TAIL_ROWS, repetitions).  Every CTA
+// solves the R x R system itself (it keeps the chunks independent): a float32
+// Cholesky factorisation and inverse X0 of V (one warp), then Newton steps
+// X <- X (2I - V X) in double-float, which carry X0 to float64-level accuracy
+// (iterative refinement of the normal equations); float64 factorisation only
+// if the float32 one breaks down.  It sums the MTTKRP partials of its rows in
+// fixed order, forms U_raw = M V^-1 (written unnormalised) and the chunk's
+// share of U_raw^T U_raw and of <M, U_raw>.
+constexpr int TAIL_ROWS = 64;
+
+// float32 Cholesky (one warp, lane per row): V = L L^T; false if not positive definite
+__device__ bool warp_cholesky_f(const float (*V)[33], float (*L)[33], int R, int lane) {
+    for (int j = 0; j < R; ++j) {
+        if (lane == j) {
+            float s = V[j][j];
+            for (int k = 0; k < j; ++k) s = fmaf(-L[j][k], L[j][k], s);
+            L[j][j] = s > 0.f ? sqrtf(s) : -1.f;
+        }
+        __syncwarp();
+        const float djj = L[j][j];
+        if (!(djj > 0.f)) return false;
+        const float inv = 1.f / djj;
+        if (lane > j && lane < R) {
+            float s = V[lane][j];
+            for (int k = 0; k < j; ++k) s = fmaf(-L[lane][k], L[j][k], s);
+            L[lane][j] = s * inv;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// X = (L L^T)^-1 in float32: lane c solves for column c, working column in Y
+__device__ void warp_inverse_f(const float (*L)[33], float (*Y)[33], float (*X)[33], int R, int lane) {
+    if (lane < R) {
+        for (int i = 0; i < R; ++i) {
+            float s = (i == lane) ? 1.f : 0.f;
+            for (int k = 0; k < i; ++k) s = fmaf(-L[i][k], Y[k][lane], s);
+            Y[i][lane] = s / L[i][i];
+        }
+        for (int i = R - 1; i >= 0; --i) {
+            float s = Y[i][lane];
+            for (int k = i + 1; k < R; ++k) s = fmaf(-L[k][i], Y[k][lane], s);
+            Y[i][lane] = s / L[i][i];
+        }
+        for (int i = 0; i < R; ++i) X[i][lane] = Y[i][lane];
+    }
+    __syncwarp();
+}
+
+__device__ void tail_finish(const AlsDesc &d, int mode, int rep);
+
+// dynamic shared memory of k_tail_rows
+struct TailSmem {
+    float xh[32][33], xl[32][33];   // V^-1 in double-float
+    float nh[32][33], nl[32][33];   // chunk shares before the fixed-order combine
+    float in_h[128], in_l[128];
+};
+
+template <int RP>
+__host__ __device__ constexpr size_t tail_smem_bytes() {
+    return sizeof(TailSmem) + (size_t)3 * TAIL_ROWS * (RP + 1) * sizeof(float);
+}
+
+template <int RP>
+__global__ void __launch_bounds__(128) k_tail_rows(AlsDesc d, int mode) {
+    const int rep = blockIdx.y, chunk = blockIdx.x;
+    if (d.conv[rep]) return;
+    const int R = d.R, n = d.n[mode], P = d.P[mode];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
+    TailSmem &S = *reinterpret_cast<TailSmem *>(tsm_raw);
+    auto xh = S.xh, xl = S.xl, nh = S.nh, nl = S.nl;
+    float *in_h = S.in_h, *in_l = S.in_l;
+    float (*mh)[RP + 1] = reinterpret_cast<float (*)[RP + 1]>(tsm_raw + sizeof(TailSmem));
+    float (*ml)[RP + 1] = mh + TAIL_ROWS;
+    float (*ur)[RP + 1] = ml + TAIL_ROWS;
+    const float *part = (const float *)d.part + rep * d.prs;
+    const long long pstride = (long long)n * R;
+    float *U = (float *)d.U[mode] + (long long)rep * n * R;
+    const int x0 = chunk * TAIL_ROWS;
+    const int rows = min(TAIL_ROWS, n - x0);
+
+    // V^-1 of this mode (double-float planes, computed beside the MTTKRP pass)
+    const float *Xg = d.xinv + (long long)rep * 2048;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        xh[e / 32][e % 32] = Xg[e];
+        xl[e / 32][e % 32] = Xg[1024 + e];
+    }
+    // partial sums in fixed order per (row, r) item; four items per pass with
+    // four partials each, so that sixteen loads are in flight per thread
+    const int nitems = rows * R;
+    for (int base = threadIdx.x; base < nitems; base += 4 * blockDim.x) {
+        DF acc[4];
+        const float *pp[4];
+        bool live[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int it = base + u * blockDim.x;
+            live[u] = it < nitems;
+            const int t = live[u] ? it / R : 0, r = live[u] ? it % R : 0;
+            pp[u] = part + (long long)(x0 + t) * R + r;
+            acc[u] = DF{0.f, 0.f};
+        }
+        int q = 0;
+        for (; q + 4 <= P; q += 4) {
+            float v[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) v[u][w] = live[u] ? pp[u][(q + w) * pstride] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u] = df_add(acc[u], DF{v[u][w], 0.f});
+        }
+        for (; q < P; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (live[u]) acc[u] = df_add(acc[u], DF{pp[u][q * pstride], 0.f});
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int it = base + u * blockDim.x;
+            if (it < nitems) {
+                mh[it / R][it % R] = acc[u].hi;
+                ml[it / R][it % R] = acc[u].lo;
+            }
+        }
+    }
+    __syncthreads();
+    // U_raw = M X for the chunk's rows; <M, U_raw> per thread
+    DF inner{0.f, 0.f};
+    for (int it = threadIdx.x; it < rows * R; it += blockDim.x) {
+        const int t = it / R, r = it % R;
+        DF a{0.f, 0.f};
+        for (int k = 0; k < R; ++k) a = df_fma(a, DF{mh[t][k], ml[t][k]}, DF{xh[k][r], xl[k][r]});
+        const float uf = __fadd_rn(a.hi, a.lo);
+        ur[t][r] = uf;
+        U[(long long)(x0 + t) * R + r] = uf;
+        inner = df_fma(inner, DF{mh[t][r], ml[t][r]}, DF{uf, 0.f});
+    }
+    in_h[threadIdx.x] = inner.hi;
+    in_l[threadIdx.x] = inner.lo;
+    __syncthreads();
+    // chunk shares: (U_raw^T U_raw)(r, s) for r <= s, and <M, U_raw> (slot npairs);
+    // tps threads per slot each take every tps-th row, combined in fixed order
+    const int npairs = R * (R + 1) / 2;
+    const int slots = npairs + 1;
+    const int tps = slots >= (int)blockDim.x ? 1 : (slots * 4 <= (int)blockDim.x ? 4 : (slots * 2 <= (int)blockDim.x ? 2 : 1));
+    DF *tp = d.tpart + ((long long)rep * d.tchunks + chunk) * (npairs + 1);
+    __syncthreads();
+    for (int w0 = threadIdx.x; w0 < slots * tps; w0 += blockDim.x) {
+        const int pq = w0 / tps, sub = w0 % tps;
+        DF a{0.f, 0.f};
+        if (pq < npairs) {
+            int r = 0, rem = pq;
+            while (rem >= R - r) {
+                rem -= R - r;
+                ++r;
+            }
+            const int s2 = r + rem;
+            for (int t = sub; t < rows; t += tps) a = df_add_prod(a, ur[t][r], ur[t][s2]);
+        } else {
+            for (int t = sub; t < (int)blockDim.x; t += tps) a = df_add(a, DF{in_h[t], in_l[t]});
+        }
+        // park the share in the (now unused) matrices: slot-major, sub-minor
+        (&nh[0][0])[w0] = a.hi;
+        (&nl[0][0])[w0] = a.lo;
+    }
+    __syncthreads();
+    for (int pq = threadIdx.x; pq < slots; pq += blockDim.x) {
+        DF a{0.f, 0.f};
+        for (int sub = 0; sub < tps; ++sub) a = df_add(a, DF{(&nh[0][0])[pq * tps + sub], (&nl[0][0])[pq * tps + sub]});
+        tp[pq] = a;
+    }
+    // the last chunk CTA of this repetition to finish completes the mode
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int nch = (n + TAIL_ROWS - 1) / TAIL_ROWS;
+        const int old = atomicAdd(&d.tail_cnt[rep], 1);
+        is_last = (old == nch - 1);
+        if (is_last) d.tail_cnt[rep] = 0;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    tail_finish(d, mode, rep);
+}
+
+// Finish of one mode for one repetition (the last chunk CTA), in double-float:
+// sums the chunk shares in fixed order: lambda_r = sqrt((U_raw^T U_raw)(r,r)),
+// the Gram of the normalised factor, U /= lambda; after mode 3 the fit
+// 1 - sqrt(||X||^2 + lambda^T (G1*G2*G3) lambda - 2 <M, U_raw>) / ||X|| and the
+// convergence flag.  Shares and rows of the other CTAs are read through L2.
+__device__ __forceinline__ DF ldcg_df(const DF *p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return DF{v.x, v.y};
+}
+
+__device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
+    const int R = d.R, n = d.n[mode];
+    const int npairs = R * (R + 1) / 2;
+    const int nch = (n + TAIL_ROWS - 1) / TAIL_ROWS;
+    __shared__ DF graw[32 * 33 / 2 + 1];
+    __shared__ DF lam_s[32], inv_l[32];
+    __shared__ float inv_lam[32];
+    __shared__ DF gm[32 * 32];
+    __shared__ DF xh_part[32];
+    __shared__ int zero_flag;
+    DF *Gf = d.Gf + (long long)rep * 3 * R * R;
+    const DF *tp = d.tpart + (long long)rep * d.tchunks * (npairs + 1);
+    for (int pq = threadIdx.x; pq <= npairs; pq += blockDim.x) {
+        DF a{0.f, 0.f};
+        for (int c = 0; c < nch; ++c) a = df_add(a, ldcg_df(&tp[(long long)c * (npairs + 1) + pq]));
+        graw[pq] = a;
+    }
+    if (threadIdx.x == 0) zero_flag = 0;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        DF l = df_sqrt(graw[r * R - r * (r - 1) / 2]);  // diagonal pair (r, r)
+        if (l.hi == 0.f) {
+            l = DF{1.f, 0.f};
+            zero_flag = 1;
+        }
+        lam_s[r] = l;
+        inv_l[r] = df_div(DF{1.f, 0.f}, l);
+        inv_lam[r] = __fadd_rn(inv_l[r].hi, inv_l[r].lo);
+    }
+    __syncthreads();
+    for (int pq = threadIdx.x; pq < npairs; pq += blockDim.x) {
+        int r = 0, rem = pq;
+        while (rem >= R - r) {
+            rem -= R - r;
+            ++r;
+        }
+        const int s2 = r + rem;
+        const DF g = df_mul(df_mul(graw[pq], inv_l[r]), inv_l[s2]);
+        Gf[mode * R * R + r * R + s2] = g;
+        Gf[mode * R * R + s2 * R + r] = g;
+        gm[r * R + s2] = g;
+        gm[s2 * R + r] = g;
+    }
+    float *U = (float *)d.U[mode] + (long long)rep * n * R;
+    for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x)
+        U[e] = __ldcg(&U[e]) * inv_lam[(int)(e % R)];
+    __syncthreads();
+    if (mode == 2) {
+        DF a{0.f, 0.f};
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+            const int r = e / R, s2 = e % R;
+            DF t = df_mul(df_mul(lam_s[r], lam_s[s2]), df_mul(df_mul(Gf[e], Gf[R * R + e]), gm[e]));
+            a = df_add(a, t);
+        }
+        a = warp_df_sum(a);
+        if ((threadIdx.x & 31) == 0) xh_part[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DF xh{0.f, 0.f};
+            for (int t = 0; t < (int)(blockDim.x >> 5); ++t) xh = df_add(xh, xh_part[t]);
+            DF in{0.f, 0.f};  // <X, X_hat> = sum_r lambda_r <M(:,r), U(:,r)> = <M, U_raw>
+            for (int c = 0; c < nch; ++c) in = df_add(in, ldcg_df(&tp[(long long)c * (npairs + 1) + npairs]));
+            const DF nx2 = d.nx2f[rep];
+            DF res2 = df_sub(df_add(nx2, xh), df_add(in, in));
+            if (!(res2.hi > 0.f)) res2 = DF{0.f, 0.f};
+            const DF ratio = nx2.hi > 0.f ? df_div(df_sqrt(res2), df_sqrt(nx2)) : DF{1.f, 0.f};
+            const DF fit = df_sub(DF{1.f, 0.f}, ratio);
+            const DF diff = df_sub(fit, d.fitpf[rep]);
+            const int it = d.iters[rep] + 1;
+            d.iters[rep] = it;
+            d.fit[rep] = df_value(fit);
+            bool stop = it >= d.max_iters;
+            if (!d.fixed_iters && fabsf(__fadd_rn(diff.hi, diff.lo)) < (float)d.tol) stop = true;
+            d.fitpf[rep] = fit;
+            if (stop) d.conv[rep] = 1;
+        }
+        if (threadIdx.x < R) d.lam[rep * R + threadIdx.x] = df_value(lam_s[threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && zero_flag) d.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
+}
+
+// V^-1 of mode `mode` (its Grams are final): one CTA per repetition, run on a
+// side stream while the mode's MTTKRP pass runs.
+__global__ void __launch_bounds__(256) k_xinv(AlsDesc d, int mode) {
+    const int rep = blockIdx.x;
+    if (d.conv[rep]) return;
+    __shared__ DF W[32 * 64];
+    __shared__ int reg;
+    if (threadIdx.x == 0) reg = 0;
+    __syncthreads();
+    block_inverse_df(d.Gf + (long long)rep * 3 * d.R * d.R, d.R, mode, W, d.xinv + (long long)rep * 2048, &reg);
+    if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
+}
+
+// ---------------------------------------------------------------------------
 // Start values, Grams and ||X_s||^2 (one CTA per repetition)
 template <typename TF>
 __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, long long samp_stride,
@@ -466,12 +848,24 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
                 ++r;
             }
             int s = r + rem;
-            double a = 0.0;
-            for (int x = lane; x < n; x += 32) a += (double)U[(long long)x * R + r] * (double)U[(long long)x * R + s];
-            a = warp_sum(a);
-            if (lane == 0) {
-                G[m * R * R + r * R + s] = a;
-                G[m * R * R + s * R + r] = a;
+            if (d.Gf) {
+                // float32 factors: exact products, double-float sums
+                DF a{0.f, 0.f};
+                for (int x = lane; x < n; x += 32)
+                    a = df_add_prod(a, (float)U[(long long)x * R + r], (float)U[(long long)x * R + s]);
+                a = warp_df_sum(a);
+                if (lane == 0) {
+                    d.Gf[((long long)rep * 3 + m) * R * R + r * R + s] = a;
+                    d.Gf[((long long)rep * 3 + m) * R * R + s * R + r] = a;
+                }
+            } else {
+                double a = 0.0;
+                for (int x = lane; x < n; x += 32) a += (double)U[(long long)x * R + r] * (double)U[(long long)x * R + s];
+                a = warp_sum(a);
+                if (lane == 0) {
+                    G[m * R * R + r * R + s] = a;
+                    G[m * R * R + s * R + r] = a;
+                }
             }
         }
     }
@@ -489,6 +883,10 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
     }
     if (threadIdx.x == 0) {
         d.normX2[rep] = red[0];
+        if (d.nx2f) {
+            d.nx2f[rep] = df_from_double(red[0]);
+            d.fitpf[rep] = DF{0.f, 0.f};
+        }
         d.fit_prev[rep] = 0.0;
         d.fit[rep] = 0.0;
         d.iters[rep] = 0;
@@ -643,6 +1041,23 @@ cudaError_t launch_store_m(const AlsDesc &d, int mode, void *Mout, cudaStream_t 
 }
 
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
+    if (d.elem != 0) {
+        // float32 factors: row kernel (partial reduction fused) + finish kernel
+        const int RP = rp_of(d.R);
+        dim3 grid((d.n[mode] + TAIL_ROWS - 1) / TAIL_ROWS, d.nrep);
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_tail_rows<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<8>());
+            cudaFuncSetAttribute(k_tail_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<16>());
+            cudaFuncSetAttribute(k_tail_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<32>());
+            attr_set = true;
+        }
+        if (RP == 8) k_tail_rows<8><<<grid, 128, tail_smem_bytes<8>(), st>>>(d, mode);
+        else if (RP == 16) k_tail_rows<16><<<grid, 128, tail_smem_bytes<16>(), st>>>(d, mode);
+        else k_tail_rows<32><<<grid, 128, tail_smem_bytes<32>(), st>>>(d, mode);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     cudaError_t e = reduce_dispatch(d, mode, st);
     if (e != cudaSuccess) return e;
     if (d.elem == 0) k_tail<double><<<d.nrep, 256, 0, st>>>(d, mode);
@@ -651,8 +1066,16 @@ cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st) {
+    k_xinv<<<d.nrep, 256, 0, st>>>(d, mode);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st) {
-    cudaError_t e = launch_mttkrp(d, mode, st);
+    cudaError_t e = cudaSuccess;
+    if (d.elem != 0) e = launch_xinv(d, mode, st);
+    if (e == cudaSuccess) e = launch_mttkrp(d, mode, st);
     if (e != cudaSuccess) return e;
     return launch_reduce_tail(d, mode, st);
 }

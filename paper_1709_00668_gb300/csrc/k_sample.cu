@@ -23,18 +23,18 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint32_t *out, long lo
 // max |x| (as ordered bits of a non-negative double) and non-finite detection
 template <typename T>
 __global__ void k_absmax(const T *X, long long n, DevStatus *status) {
-    double m = 0.0;
+    T m = 0;
     bool bad = false;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double v = (double)X[i];
+        const T v = X[i];
         if (!isfinite(v)) bad = true;
         else m = fmax(m, fabs(v));
     }
     for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     unsigned anybad = __ballot_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0) {
-        atomicMax(&status->amax_bits, (unsigned long long)__double_as_longlong(m));
+        atomicMax(&status->amax_bits, (unsigned long long)__double_as_longlong((double)m));
         if (anybad) atomicOr(&status->err, ERR_NONFINITE);
     }
 }
@@ -61,6 +61,35 @@ __device__ __forceinline__ bool qsquare(double x, int S, unsigned long long *q) 
     return true;
 }
 
+// The same q for a float32 x without float64 arithmetic: x = m * 2^e with a
+// 24-bit integer m, so x*x = m^2 * 2^(2e) exactly and q = floor(m^2 * 2^(2e+S))
+// is an integer shift of the 48-bit m^2.  Returns false on overflow (q >= 2^64).
+__device__ __forceinline__ bool qsquare(float x, int S, unsigned long long *q) {
+    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+    const int be = (int)(b >> 23);
+    uint32_t m = b & 0x7FFFFFu;
+    int e;
+    if (be == 0) {
+        e = -149;  // subnormal: no implicit bit
+    } else {
+        m |= 0x800000u;
+        e = be - 150;
+    }
+    const unsigned long long m2 = (unsigned long long)m * (unsigned long long)m;  // < 2^48
+    const int sh = 2 * e + S;
+    if (m2 == 0) {
+        *q = 0;
+        return true;
+    }
+    if (sh >= 0) {
+        if (sh >= 64 || (m2 >> (63 - sh)) >> 1) return false;  // m2 * 2^sh >= 2^64
+        *q = m2 << sh;
+    } else {
+        *q = sh <= -64 ? 0ull : (m2 >> (-sh));
+    }
+    return true;
+}
+
 __device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
                                             DevStatus *status) {
     if (v == 0) return;
@@ -68,21 +97,19 @@ __device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned lo
     if (old + v < old) atomicOr(&status->err, ERR_RANGE);
 }
 
-constexpr int APPEND_ROWS = 64;      // rows of one slice per CTA
-constexpr int APPEND_SMEM_J = 4096;  // column sums kept in shared memory up to this J
+constexpr int APPEND_ROWS = 64;        // rows of one slice per CTA (row pass)
+constexpr int APPEND_COL_ROWS = 512;   // rows per CTA of the column pass
 
+// Row pass: copy the new slices into the store; x_a (rows) and x_c (slices)
+// from a warp per row.  Integer sums are exact, so the order is free.
 template <typename T>
 __global__ void __launch_bounds__(256) k_append(const T *Xin, int I, int J, int ldin, T *store, int lds, int S,
-                                                unsigned long long *dxa, unsigned long long *dxb,
-                                                unsigned long long *xc_new, DevStatus *status) {
-    __shared__ unsigned long long colsum[APPEND_SMEM_J];
-    __shared__ unsigned long long slicesum;
+                                                unsigned long long *dxa, unsigned long long *xc_new,
+                                                DevStatus *status) {
     const int k = blockIdx.y;
     const int i0 = blockIdx.x * APPEND_ROWS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool smem_cols = J <= APPEND_SMEM_J;
-    if (smem_cols)
-        for (int j = threadIdx.x; j < J; j += blockDim.x) colsum[j] = 0;
+    __shared__ unsigned long long slicesum;
     if (threadIdx.x == 0) slicesum = 0;
     __syncthreads();
     bool bad = false, range = false;
@@ -94,18 +121,12 @@ __global__ void __launch_bounds__(256) k_append(const T *Xin, int I, int J, int 
         for (int j = lane; j < J; j += 32) {
             T x = src[j];
             dst[j] = x;
-            double xd = (double)x;
             unsigned long long q = 0;
-            if (!isfinite(xd)) bad = true;
-            else if (!qsquare(xd, S, &q)) range = true;
+            if (!isfinite(x)) bad = true;
+            else if (!qsquare(x, S, &q)) range = true;
             if (rs + q < rs) range = true;
             rs += q;
-            if (q) {
-                if (smem_cols) atomicAdd(&colsum[j], q);
-                else add_checked(&dxb[j], q, status);
-            }
         }
-        // warp sum of the row (overflow checked pairwise)
         for (int o = 16; o; o >>= 1) {
             unsigned long long other = __shfl_xor_sync(0xffffffffu, rs, o);
             if (rs + other < rs) range = true;
@@ -124,10 +145,29 @@ __global__ void __launch_bounds__(256) k_append(const T *Xin, int I, int J, int 
         if (old + wslice < old) atomicOr(&status->err, ERR_RANGE);
     }
     __syncthreads();
-    if (smem_cols) {
-        for (int j = threadIdx.x; j < J; j += blockDim.x) add_checked(&dxb[j], colsum[j], status);
-    }
     if (threadIdx.x == 0) add_checked(&xc_new[k], slicesum, status);
+}
+
+// Column pass: x_b from the rows just written, a thread per column over a
+// block of APPEND_COL_ROWS rows (reads are coalesced across the threads).
+template <typename T>
+__global__ void __launch_bounds__(256) k_append_cols(const T *store, long long rows, int J, int lds, int S,
+                                                     unsigned long long *dxb, DevStatus *status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const long long r0 = (long long)blockIdx.y * APPEND_COL_ROWS;
+    const long long r1 = min(rows, r0 + APPEND_COL_ROWS);
+    unsigned long long cs = 0;
+    bool range = false;
+    for (long long r = r0; r < r1; ++r) {
+        unsigned long long q = 0;
+        const T x = store[r * lds + j];
+        if (isfinite(x) && !qsquare(x, S, &q)) range = true;
+        if (cs + q < cs) range = true;
+        cs += q;
+    }
+    if (range) atomicOr(&status->err, ERR_RANGE);
+    add_checked(&dxb[j], cs, status);
 }
 
 cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
@@ -135,13 +175,18 @@ cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, in
                           unsigned long long *xc_new, DevStatus *status, cudaStream_t st) {
     if (K_new <= 0) return cudaSuccess;
     dim3 grid((I + APPEND_ROWS - 1) / APPEND_ROWS, (unsigned)K_new);
-    count_launches(1);
-    if (dtype == 0)
-        k_append<double><<<grid, 256, 0, st>>>((const double *)Xin, I, J, ldin, (double *)store, lds, S,
-                                               dxa, dxb, xc_new, status);
-    else
-        k_append<float><<<grid, 256, 0, st>>>((const float *)Xin, I, J, ldin, (float *)store, lds, S,
-                                              dxa, dxb, xc_new, status);
+    const long long rows = K_new * I;
+    dim3 cgrid((J + 255) / 256, (unsigned)((rows + APPEND_COL_ROWS - 1) / APPEND_COL_ROWS));
+    count_launches(2);
+    if (dtype == 0) {
+        k_append<double><<<grid, 256, 0, st>>>((const double *)Xin, I, J, ldin, (double *)store, lds, S, dxa,
+                                               xc_new, status);
+        k_append_cols<double><<<cgrid, 256, 0, st>>>((const double *)store, rows, J, lds, S, dxb, status);
+    } else {
+        k_append<float><<<grid, 256, 0, st>>>((const float *)Xin, I, J, ldin, (float *)store, lds, S, dxa,
+                                              xc_new, status);
+        k_append_cols<float><<<cgrid, 256, 0, st>>>((const float *)store, rows, J, lds, S, dxb, status);
+    }
     return cudaGetLastError();
 }
 

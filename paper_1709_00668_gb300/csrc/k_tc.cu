@@ -474,13 +474,15 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     *P_out = epi == 0 ? p.nks : p.npb;
     dim3 grid(p.npb * p.nks, nrep);
     count_launches(1);
-    if (N == 32) {
-        cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_mtt_tc<32><<<grid, 192, smem, st>>>(tmap, p);
-    } else {
-        cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_mtt_tc<64><<<grid, 192, smem, st>>>(tmap, p);
+    // the attribute is raised once per process to the largest plan
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
     }
+    if (N == 32) k_mtt_tc<32><<<grid, 192, smem, st>>>(tmap, p);
+    else k_mtt_tc<64><<<grid, 192, smem, st>>>(tmap, p);
     return cudaGetLastError();
 }
 

@@ -129,6 +129,47 @@ __device__ __forceinline__ DF warp_df_sum(DF a) {
     return a;
 }
 __device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+// acc + a * b with a, b double-float: exact leading product by FMA, cross terms in float
+__device__ __forceinline__ DF df_fma(DF acc, DF a, DF b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_add(acc, DF{p, e});
+}
+__device__ __forceinline__ DF df_from_double(double v) {
+    float h = (float)v;
+    return DF{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_quick(p, e);
+}
+// a / b: quotient of the leading parts, corrected once by the remainder
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF r = df_sub(a, df_mul(DF{q1, 0.f}, b));
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return df_quick(q1, q2);
+}
+// sqrt(a) for a >= 0: float square root, corrected once by the remainder
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    if (!(a.hi > 0.f)) return DF{0.f, 0.f};
+    const float s = __fsqrt_rn(a.hi);
+    const float p = __fmul_rn(s, s);
+    const DF r = df_sub(a, DF{p, __fmaf_rn(s, s, -p)});
+    return df_quick(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
+}
+__device__ __forceinline__ DF warp_df_sum2(DF a) { return warp_df_sum(a); }
 
 // ---------------------------------------------------------------------------
 // Parameters of the sampling and gather kernels
@@ -181,6 +222,12 @@ struct AlsDesc {
     int max_iters, fixed_iters;
     unsigned long long *bytes_ctr;  // algorithmic bytes read by MTTKRP passes (nullable)
     int P[3];              // partial sums per mode (set by the chosen MTTKRP kernels)
+    DF *tpart;             // tail chunk shares [rep][tchunks][R(R+1)/2 + 1]
+    float *xinv;           // V^-1 of the mode being solved, double-float planes [rep][2][32][32]
+    DF *Gf;                // Grams in double-float [rep][3][R][R] (float32 factor path)
+    DF *nx2f, *fitpf;      // ||X_s||^2 and the previous fit in double-float [rep]
+    int *tail_cnt;         // [rep] chunk CTAs finished (the last one completes the mode; zero between uses)
+    int tchunks;           // row chunks of 128 for the largest mode
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -216,6 +263,8 @@ cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st);
 // the two halves of launch_als_mode: the MTTKRP pass, then reduction + tail
 cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st);
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st);
+// V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
+cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
 long long partial_elems(const AlsDesc &d);  // per repetition
 

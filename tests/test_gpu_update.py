@@ -243,3 +243,28 @@ def test_profile_counters(sbt):
     assert p["mttkrp_launches"] == 3 * 7
     assert p["mttkrp_bytes"] == 3 * 7 * 3 * Kp * st["n_I"] * st["n_J"] * 2
     assert p["mttkrp_ms"] > 0 and p["launches"] > p["mttkrp_launches"]
+
+
+def test_marginals_of_extreme_magnitudes_sample_like_oracle(sbt):
+    """Fixed-point marginals of float32 data spanning many binades (and subnormals)
+    drive identical draws (integer path vs the oracle's float64 definition)."""
+    rng = np.random.default_rng(14)
+    X, A, B, C = planted(48, 40, 30, 3, dtype=torch.float32, seed=15)
+    X = X.copy()
+    X *= np.float32(2.0) ** rng.integers(-60, 20, size=X.shape).astype(np.float32)
+    X[0, 0, :5] = np.float32(1e-45)  # subnormals
+    fac = unit_factors(A, B, C[:24])
+    ctx, ost = _pair(sbt, X, 24, 3, fac, prec="f32", r=3, fixed_iters=1, max_iters=2, s_I=3, s_J=3, s_K=3)
+    ost2, traces = O.update(ost, X[24:30])
+    ctx.update(torch.from_numpy(X[24:30]).cuda())
+    for rep, t in enumerate(traces):
+        assert np.array_equal(ctx.last_samples(rep, 0), t.Is)
+        assert np.array_equal(ctx.last_samples(rep, 1), t.Js)
+        assert np.array_equal(ctx.last_samples(rep, 2), t.Ks)
+    # the next batch samples from the folded marginals
+    X2 = X[24:30] * np.float32(3.0)
+    ost3, traces3 = O.update(ost2, X2)
+    ctx.update(torch.from_numpy(np.ascontiguousarray(X2)).cuda())
+    for rep, t in enumerate(traces3):
+        assert np.array_equal(ctx.last_samples(rep, 0), t.Is)
+        assert np.array_equal(ctx.last_samples(rep, 2), t.Ks)
