@@ -41,7 +41,7 @@ TRAFFIC = {}
 
 
 def kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_1709_00668_gb300", "csrc", "k_als.cu")
+    p = os.path.join(ROOT, "paper_1709_00668_gb300", "csrc", "k_tc.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 

@@ -1,13 +1,14 @@
 // C ABI of libsambaten: context management and the per-batch pipeline of
 // Algorithm 1 (sample -> gather -> CP-ALS -> normalise/match -> project back ->
 // commit), all on one CUDA stream, one host synchronisation per update.
-#include "../../include/sambaten.h"
+#include "sambaten.h"
 #include "sbt_internal.cuh"
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -106,18 +107,32 @@ struct DeviceGuard {
 // its transposed copy
 struct TcPlan {
     bool on = false;
-    alignas(64) CUtensorMap m1;  // [slice][ii][jj]: contraction over jj
-    alignas(64) CUtensorMap m2;  // [slice][jj][ii]: contraction over ii
+    CUtensorMap m1;  // [slice][ii][jj]: contraction over jj
+    CUtensorMap m2;  // [slice][jj][ii]: contraction over ii
 };
 
 }  // namespace
 
 void sbt::set_last_error(const std::string &msg) { g_err = msg; }
 
+// Raise the kernels' shared-memory limits once per device (outside any capture).
+static cudaError_t ensure_kernel_attributes(int device) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= 64 || done[device]) return cudaSuccess;
+    cudaError_t e = set_als_kernel_attributes();
+    if (e == cudaSuccess) e = set_tc_kernel_attributes();
+    if (e == cudaSuccess) done[device] = true;
+    return e;
+}
+
 struct sbt_ctx {
     int device = 0;
     int num_sms = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t user = nullptr;    // the caller's stream (inputs are ordered on it)
+    cudaStream_t stream = nullptr;  // the library's own stream (capturable)
+    cudaEvent_t ev_user = nullptr;
     sbt_options opt{};
     int I = 0, J = 0, R = 0;
     int64_t K = 0, Kcap = 0;
@@ -139,17 +154,19 @@ struct sbt_ctx {
     // profiling
     Buf prof_bytes;  // unsigned long long, device
     bool timing = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-    size_t events_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
+    double mtt_ms = 0.0;
     long long launch_base = 0, updates = 0, mtt_launches = 0;
     ~sbt_ctx() {
-        for (auto &e : events) {
+        for (auto &e : gev) {
             cudaEventDestroy(e.first);
             cudaEventDestroy(e.second);
         }
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
+        if (ev_user) cudaEventDestroy(ev_user);
+        if (stream) cudaStreamDestroy(stream);
     }
     // last update
     bool have_last = false;
@@ -204,6 +221,13 @@ static sbt_status check_tensor(const sbt_tensor *X) {
     return SBT_OK;
 }
 
+// Order the library's stream after the caller's stream (device inputs).
+static sbt_status order_after_user(sbt_ctx *c) {
+    CK(cudaEventRecord(c->ev_user, c->user));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_user, 0));
+    return SBT_OK;
+}
+
 // Move K_new slices (host or device) into the store at slice K0 and add their
 // marginals into (ma, mb, mc).
 static sbt_status append_slices(sbt_ctx *c, const sbt_tensor *X, int64_t K0, unsigned long long *ma,
@@ -255,6 +279,7 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.tol = c->opt.tol;
     d.max_iters = max_iters;
     d.fixed_iters = c->opt.fixed_iters;
+    d.pr = elem == 0 ? c->R : (c->R + 3) / 4 * 4;
     choose_tiles(d, c->num_sms);
     const int R = c->R;
     const size_t tfs = esize_tf(elem);
@@ -318,12 +343,12 @@ static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, i
     int P = 0;
     if (mode == 0)
         return launch_mttkrp_tc(tc->m1, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
     if (mode == 1)
         return launch_mttkrp_tc(tc->m2, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
     return launch_mttkrp_tc(tc->m1, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
-                            (float *)d.part, d.prs, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
 }
 
 // partial counts of the tensor-core kernels, fixed by the shapes
@@ -337,53 +362,98 @@ static void tc_partials(AlsDesc &d, int num_sms) {
     tc_tiles(d.nrep, d.n[1], d.n[2], num_sms, &npb, &nks, &spc);
     d.P[1] = nks;
     const long long e1 = (long long)nks * d.n[1];
-    d.prs = std::max(e0, std::max(e1, e2)) * d.R;
+    d.prs = std::max(e0, std::max(e1, e2)) * d.pr;
 }
 
-static sbt_status timed_mttkrp(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode) {
-    c->mtt_launches += 1;
-    if (!c->timing) {
-        CK(mttkrp_mode(c, d, tc, mode));
-        return SBT_OK;
+// One captured CUDA graph runs G ALS iterations (three modes each: V^-1 on
+// the side stream beside the MTTKRP pass, then the tail); the host polls the
+// convergence flags between graph launches.  Kernel launches are counted when
+// the graph is launched, not when it is captured.
+static sbt_status capture_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G,
+                                     cudaGraphExec_t *exec, long long *launches_per) {
+    cudaGraph_t graph = nullptr;
+    const long long base = launch_count();
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int slot = 0;
+    for (int it = 0; it < G && e == cudaSuccess; ++it) {
+        for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode, ++slot) {
+            if (d.xinv) {
+                e = cudaEventRecord(c->ev_fork, c->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+                if (e == cudaSuccess) e = launch_xinv(d, mode, c->side);
+                if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+            }
+            if (e == cudaSuccess && c->timing)
+                e = cudaEventRecordWithFlags(c->gev[slot].first, c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = mttkrp_mode(c, d, tc, mode);
+            if (e == cudaSuccess && c->timing)
+                e = cudaEventRecordWithFlags(c->gev[slot].second, c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess && d.xinv) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            if (e == cudaSuccess) e = launch_reduce_tail(d, mode, c->stream);
+        }
     }
-    if (c->events_used == c->events.size()) {
-        cudaEvent_t a, b;
-        CK(cudaEventCreate(&a));
-        CK(cudaEventCreate(&b));
-        c->events.emplace_back(a, b);
-    }
-    auto &ev = c->events[c->events_used++];
-    CK(cudaEventRecord(ev.first, c->stream));
-    CK(mttkrp_mode(c, d, tc, mode));
-    CK(cudaEventRecord(ev.second, c->stream));
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    *launches_per = launch_count() - base;
+    count_launches(-(int)*launches_per);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS graph: ") + cudaGetErrorString(e));
     return SBT_OK;
 }
 
+// Run ALS iterations until every repetition converged (polled every
+// check_every iterations) or max_iters.  Kernels of converged repetitions
+// exit at once, so running past convergence inside a graph is harmless.
 static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcPlan *tc = nullptr) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
-    for (int it = 1; it <= max_iters; ++it) {
-        for (int mode = 0; mode < 3; ++mode) {
-            if (d.xinv) {
-                // V^-1 of this mode on the side stream, beside the MTTKRP pass
-                CK(cudaEventRecord(c->ev_fork, c->stream));
-                CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-                CK(launch_xinv(d, mode, c->side));
-                CK(cudaEventRecord(c->ev_join, c->side));
-            }
-            TRY(timed_mttkrp(c, d, tc, mode));
-            if (d.xinv) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-            CK(launch_reduce_tail(d, mode, c->stream));
+    const int G = std::max(1, std::min(every, max_iters));
+    if (c->timing) {
+        while ((int)c->gev.size() < 3 * G) {
+            cudaEvent_t a, b;
+            CK(cudaEventCreate(&a));
+            CK(cudaEventCreate(&b));
+            c->gev.emplace_back(a, b);
         }
-        if (it == max_iters || (!c->opt.fixed_iters && it % every == 0)) {
-            CK(cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
+    }
+    cudaGraphExec_t exec = nullptr;
+    long long lpg = 0;
+    TRY(capture_iterations(c, d, tc, G, &exec, &lpg));
+    const int nl = (max_iters + G - 1) / G;
+    sbt_status st = SBT_OK;
+    for (int k = 0; k < nl && st == SBT_OK; ++k) {
+        cudaError_t e = cudaGraphLaunch(exec, c->stream);
+        if (e != cudaSuccess) {
+            st = fail(SBT_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+            break;
+        }
+        count_launches((int)lpg);
+        c->mtt_launches += 3LL * G;
+        const bool poll = (k == nl - 1) || !c->opt.fixed_iters;
+        if (c->timing || poll) {
+            if (poll) e = cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                st = fail(SBT_E_CUDA, std::string("ALS poll: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (c->timing) {
+            for (int q = 0; q < 3 * G; ++q) {
+                float t = 0.f;
+                if (cudaEventElapsedTime(&t, c->gev[q].first, c->gev[q].second) == cudaSuccess) c->mtt_ms += t;
+            }
+        }
+        if (poll) {
             const int *h = c->h_poll.as<int>();
             bool all = true;
             for (int q = 0; q < d.nrep; ++q) all = all && h[q];
             if (all) break;
         }
     }
-    return SBT_OK;
+    cudaGraphExecDestroy(exec);
+    return st;
 }
 
 static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const sbt_options *opt) {
@@ -394,7 +464,11 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     c->opt = *opt;
     CK(cudaGetDevice(&c->device));
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-    c->stream = (cudaStream_t)opt->cuda_stream;
+    CK(ensure_kernel_attributes(c->device));
+    c->user = (cudaStream_t)opt->cuda_stream;
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming));
+    TRY(order_after_user(c));
     c->I = (int)X0->I;
     c->J = (int)X0->J;
     c->R = R;
@@ -560,6 +634,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
     if (X->dtype != c->sdtype) return fail(SBT_E_INVALID, "dtype must match the initial tensor");
     DeviceGuard dg(c->device);
+    TRY(order_after_user(c));
     const int R = c->R, r = c->opt.r;
     const int K_new = (int)X->K;
     const int64_t K_old = c->K;
@@ -889,7 +964,7 @@ extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->timing = timing != 0;
-    c->events_used = 0;
+    c->mtt_ms = 0.0;
     c->launch_base = launch_count();
     c->updates = 0;
     c->mtt_launches = 0;
@@ -902,12 +977,7 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
     CK(cudaStreamSynchronize(c->stream));
     unsigned long long bytes = 0;
     CK(cudaMemcpy(&bytes, c->prof_bytes.p, 8, cudaMemcpyDeviceToHost));
-    double ms = 0.0;
-    for (size_t q = 0; q < c->events_used; ++q) {
-        float t = 0.f;
-        CK(cudaEventElapsedTime(&t, c->events[q].first, c->events[q].second));
-        ms += t;
-    }
+    const double ms = c->mtt_ms;
     out->launches = launch_count() - c->launch_base;
     out->updates = c->updates;
     out->mttkrp_launches = c->mtt_launches;
@@ -987,6 +1057,7 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     d.n[1] = (int)J;
     d.n[2] = (int)K;
     d.elem = 2;
+    d.pr = R;
     int npb, nks, spc;
     tc_tiles(1, NP, (int)K, sms, &npb, &nks, &spc);
     const int P = mode == 2 ? npb : nks;
@@ -1003,7 +1074,7 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     d.M = (double *)(scr + off_m);
     d.part = scr + off_part;
     cudaError_t e = cudaMemsetAsync(scr, 0, 256, st);
-    alignas(64) CUtensorMap map;
+    CUtensorMap map;
     int Pk = 0;
     if (e == cudaSuccess) {
         if (mode == 1) {
@@ -1016,13 +1087,13 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     if (e == cudaSuccess) {
         if (mode == 0)
             e = launch_mttkrp_tc(map, 0, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)C, 0,
-                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
         else if (mode == 1)
             e = launch_mttkrp_tc(map, 0, 1, R, (int)J, (int)I, (int)K, (const float *)A, 0, (const float *)C, 0,
-                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
         else
             e = launch_mttkrp_tc(map, 1, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)A, 0,
-                                 (float *)d.part, d.prs, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
     }
     if (e == cudaSuccess) e = launch_reduce_only(d, mode, st);
     if (e == cudaSuccess) e = launch_store_m(d, mode, M, st);
@@ -1047,9 +1118,10 @@ extern "C" sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_
     if (R < 1 || R > SBT_MAX_RANK || mode < 0 || mode > 2) return fail(SBT_E_INVALID, "R or mode out of range");
     if (K > (1 << 30) || I > (1 << 30) || J > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
     cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == SBT_BF16) return mttkrp_bf16_op(X, K, I, J, ld, A, B, C, R, mode, M, st);
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
+    CK(ensure_kernel_attributes(dev));
+    if (dtype == SBT_BF16) return mttkrp_bf16_op(X, K, I, J, ld, A, B, C, R, mode, M, st);
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     AlsDesc d;
     std::memset(&d, 0, sizeof(d));
@@ -1061,6 +1133,7 @@ extern "C" sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_
     d.ldj = (int)ld;
     d.nK = (int)K;
     d.elem = dtype == SBT_F64 ? 0 : 1;
+    d.pr = R;
     d.X = X;
     d.xrs = 0;
     d.U[0] = (void *)A;

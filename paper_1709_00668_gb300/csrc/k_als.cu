@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
         if (ii < NI && lane < R) {
             TF s = TF(0);
             for (int t = 0; t < nkk; ++t) s = fmadd(z[((size_t)t * 8 + warp) * RP + lane], C[(long long)(k0 + t) * R + lane], s);
-            part[((long long)ks * NI + ii) * R + lane] = s;
+            part[((long long)ks * NI + ii) * d.pr + lane] = s;
         }
     } else {
         // part[ib][kk][r]
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
                 int i = ib * 8 + w;
                 if (i < NI) s = fmadd(z[((size_t)t * 8 + w) * RP + r], A[(long long)i * R + r], s);
             }
-            part[((long long)ib * Kp + (k0 + t)) * R + r] = s;
+            part[((long long)ib * Kp + (k0 + t)) * d.pr + r] = s;
         }
     }
 }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
         if (jj >= NJ) continue;
         TF s = TF(0);
         for (int w = 0; w < 8; ++w) s += red[((size_t)w * 32 * COLS + cl) * RP + r];
-        part[((long long)rs * NJ + jj) * R + r] = s;
+        part[((long long)rs * NJ + jj) * d.pr + r] = s;
     }
 }
 
@@ -524,6 +524,8 @@ __device__ void block_inverse_df(const DF *Gf, int R, int mode, DF *W, float *X,
 // fixed order, forms U_raw = M V^-1 (written unnormalised) and the chunk's
 // share of U_raw^T U_raw and of <M, U_raw>.
 constexpr int TAIL_ROWS = 64;
+constexpr int TAIL_PB = 16;        // partials staged per block
+constexpr int TAIL_THREADS = 256;
 
 // float32 Cholesky (one warp, lane per row): V = L L^T; false if not positive definite
 __device__ bool warp_cholesky_f(const float (*V)[33], float (*L)[33], int R, int lane) {
@@ -571,16 +573,17 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep);
 struct TailSmem {
     float xh[32][33], xl[32][33];   // V^-1 in double-float
     float nh[32][33], nl[32][33];   // chunk shares before the fixed-order combine
-    float in_h[128], in_l[128];
+    float in_h[256], in_l[256];
 };
 
 template <int RP>
 __host__ __device__ constexpr size_t tail_smem_bytes() {
-    return sizeof(TailSmem) + (size_t)3 * TAIL_ROWS * (RP + 1) * sizeof(float);
+    return sizeof(TailSmem) + (size_t)3 * TAIL_ROWS * (RP + 1) * sizeof(float) + 16 +
+           (size_t)TAIL_PB * TAIL_ROWS * RP * sizeof(float);
 }
 
 template <int RP>
-__global__ void __launch_bounds__(128) k_tail_rows(AlsDesc d, int mode) {
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode) {
     const int rep = blockIdx.y, chunk = blockIdx.x;
     if (d.conv[rep]) return;
     const int R = d.R, n = d.n[mode], P = d.P[mode];
@@ -604,44 +607,61 @@ __global__ void __launch_bounds__(128) k_tail_rows(AlsDesc d, int mode) {
         xh[e / 32][e % 32] = Xg[e];
         xl[e / 32][e % 32] = Xg[1024 + e];
     }
-    // partial sums in fixed order per (row, r) item; four items per pass with
-    // four partials each, so that sixteen loads are in flight per thread
+    // partial sums in fixed order per (row, r) item.  The chunk's share of
+    // each partial is one contiguous, 16-byte aligned run of rows*pr floats
+    // (rows padded to pr), so blocks of TAIL_PB partials are staged in shared
+    // memory with coalesced float4 loads (four in flight per thread), then
+    // summed item by item.
+    const int pr = d.pr;
     const int nitems = rows * R;
-    for (int base = threadIdx.x; base < nitems; base += 4 * blockDim.x) {
-        DF acc[4];
-        const float *pp[4];
-        bool live[4];
+    const int nrun = rows * pr;          // floats per partial in this chunk (multiple of 4)
+    const long long pstride4 = (long long)n * pr;
+    float *stage = reinterpret_cast<float *>(
+        (reinterpret_cast<uintptr_t>(ur + TAIL_ROWS) + 15) & ~(uintptr_t)15);  // [TAIL_PB][rows*pr]
+    constexpr int IPT = (TAIL_ROWS * RP + TAIL_THREADS - 1) / TAIL_THREADS;  // items per thread
+    DF acc[IPT];
+    int soff[IPT];  // offset of each item in a staged partial (row * pr + r)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int it = base + u * blockDim.x;
-            live[u] = it < nitems;
-            const int t = live[u] ? it / R : 0, r = live[u] ? it % R : 0;
-            pp[u] = part + (long long)(x0 + t) * R + r;
-            acc[u] = DF{0.f, 0.f};
-        }
-        int q = 0;
-        for (; q + 4 <= P; q += 4) {
-            float v[4][4];
+    for (int u = 0; u < IPT; ++u) {
+        acc[u] = DF{0.f, 0.f};
+        const int it = threadIdx.x + u * TAIL_THREADS;
+        soff[u] = it < nitems ? (it / R) * pr + it % R : -1;
+    }
+    for (int q0 = 0; q0 < P; q0 += TAIL_PB) {
+        const int pb = min(TAIL_PB, P - q0);
+        const int n4 = nrun / 4, total4 = pb * n4;
+        for (int e0 = threadIdx.x; e0 < total4; e0 += 4 * blockDim.x) {
+            float4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int w = 0; w < 4; ++w) v[u][w] = live[u] ? pp[u][(q + w) * pstride] : 0.f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int w = 0; w < 4; ++w) acc[u] = df_add(acc[u], DF{v[u][w], 0.f});
-        }
-        for (; q < P; ++q)
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (live[u]) acc[u] = df_add(acc[u], DF{pp[u][q * pstride], 0.f});
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int it = base + u * blockDim.x;
-            if (it < nitems) {
-                mh[it / R][it % R] = acc[u].hi;
-                ml[it / R][it % R] = acc[u].lo;
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < total4) {
+                    const int q = e / n4, w = e % n4;
+                    v[u] = *reinterpret_cast<const float4 *>(part + (long long)(q0 + q) * pstride4 +
+                                                             (long long)x0 * pr + 4 * w);
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < total4) reinterpret_cast<float4 *>(stage)[e] = v[u];
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < pb; ++q) {
+            const float *sq = stage + q * nrun;
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+                if (soff[u] >= 0) acc[u] = df_add(acc[u], DF{sq[soff[u]], 0.f});
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int it = threadIdx.x + u * TAIL_THREADS;
+        if (it < nitems) {
+            mh[it / R][it % R] = acc[u].hi;
+            ml[it / R][it % R] = acc[u].lo;
         }
     }
     __syncthreads();
@@ -656,8 +676,11 @@ __global__ void __launch_bounds__(128) k_tail_rows(AlsDesc d, int mode) {
         U[(long long)(x0 + t) * R + r] = uf;
         inner = df_fma(inner, DF{mh[t][r], ml[t][r]}, DF{uf, 0.f});
     }
-    in_h[threadIdx.x] = inner.hi;
-    in_l[threadIdx.x] = inner.lo;
+    inner = warp_df_sum(inner);
+    if ((threadIdx.x & 31) == 0) {
+        in_h[threadIdx.x >> 5] = inner.hi;
+        in_l[threadIdx.x >> 5] = inner.lo;
+    }
     __syncthreads();
     // chunk shares: (U_raw^T U_raw)(r, s) for r <= s, and <M, U_raw> (slot npairs);
     // tps threads per slot each take every tps-th row, combined in fixed order
@@ -678,7 +701,7 @@ __global__ void __launch_bounds__(128) k_tail_rows(AlsDesc d, int mode) {
             const int s2 = r + rem;
             for (int t = sub; t < rows; t += tps) a = df_add_prod(a, ur[t][r], ur[t][s2]);
         } else {
-            for (int t = sub; t < (int)blockDim.x; t += tps) a = df_add(a, DF{in_h[t], in_l[t]});
+            for (int t = sub; t < (int)(blockDim.x >> 5); t += tps) a = df_add(a, DF{in_h[t], in_l[t]});
         }
         // park the share in the (now unused) matrices: slot-major, sub-minor
         (&nh[0][0])[w0] = a.hi;
@@ -761,8 +784,16 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
         gm[s2 * R + r] = g;
     }
     float *U = (float *)d.U[mode] + (long long)rep * n * R;
-    for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x)
-        U[e] = __ldcg(&U[e]) * inv_lam[(int)(e % R)];
+    {
+        // column index tracked incrementally (no division per element)
+        const int step = (int)(blockDim.x % R);
+        int r = (int)(threadIdx.x % R);
+        for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x) {
+            U[e] = __ldcg(&U[e]) * inv_lam[r];
+            r += step;
+            if (r >= R) r -= R;
+        }
+    }
     __syncthreads();
     if (mode == 2) {
         DF a{0.f, 0.f};
@@ -940,7 +971,7 @@ long long partial_elems(const AlsDesc &d) {
     long long a = (long long)d.nks * d.n[0];
     long long b = (long long)d.nrs * d.n[1];
     long long c = (long long)d.nib * d.n[2];
-    return std::max(a, std::max(b, c)) * d.R;
+    return std::max(a, std::max(b, c)) * (d.pr > 0 ? d.pr : d.R);
 }
 
 static size_t row_smem(const AlsDesc &d) {
@@ -955,11 +986,6 @@ static size_t col_smem(const AlsDesc &d) {
 template <typename TX, int RP>
 static cudaError_t run_row(const AlsDesc &d, int mode, cudaStream_t st) {
     size_t sm = row_smem(d);
-    static bool attr = false;  // per instantiation
-    if (!attr) {
-        cudaFuncSetAttribute(k_mtt_row<TX, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
     dim3 grid(d.nib * d.nks, d.nrep);
     k_mtt_row<TX, RP><<<grid, 256, sm, st>>>(d, mode);
     return cudaGetLastError();
@@ -968,11 +994,6 @@ static cudaError_t run_row(const AlsDesc &d, int mode, cudaStream_t st) {
 template <typename TX, int RP, int COLS>
 static cudaError_t run_col(const AlsDesc &d, cudaStream_t st) {
     size_t sm = col_smem(d);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mtt_col<TX, RP, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
     const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
     dim3 grid(njb * d.nrs, d.nrep);
     k_mtt_col<TX, RP, COLS><<<grid, 256, sm, st>>>(d);
@@ -1045,16 +1066,9 @@ cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
         // float32 factors: row kernel (partial reduction fused) + finish kernel
         const int RP = rp_of(d.R);
         dim3 grid((d.n[mode] + TAIL_ROWS - 1) / TAIL_ROWS, d.nrep);
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_tail_rows<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<8>());
-            cudaFuncSetAttribute(k_tail_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<16>());
-            cudaFuncSetAttribute(k_tail_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<32>());
-            attr_set = true;
-        }
-        if (RP == 8) k_tail_rows<8><<<grid, 128, tail_smem_bytes<8>(), st>>>(d, mode);
-        else if (RP == 16) k_tail_rows<16><<<grid, 128, tail_smem_bytes<16>(), st>>>(d, mode);
-        else k_tail_rows<32><<<grid, 128, tail_smem_bytes<32>(), st>>>(d, mode);
+        if (RP == 8) k_tail_rows<8><<<grid, TAIL_THREADS, tail_smem_bytes<8>(), st>>>(d, mode);
+        else if (RP == 16) k_tail_rows<16><<<grid, TAIL_THREADS, tail_smem_bytes<16>(), st>>>(d, mode);
+        else k_tail_rows<32><<<grid, TAIL_THREADS, tail_smem_bytes<32>(), st>>>(d, mode);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -1064,6 +1078,39 @@ cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
     else k_tail<float><<<d.nrep, 256, 0, st>>>(d, mode);
     count_launches(2);
     return cudaGetLastError();
+}
+
+template <typename TX, int RP>
+static cudaError_t raise_smem_limits() {
+    cudaError_t e = cudaFuncSetAttribute(k_mtt_row<TX, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mtt_col<TX, RP, cols_for<TX, RP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+    return e;
+}
+
+// Raise the dynamic shared-memory limits of every ALS kernel once, outside any
+// stream capture.
+cudaError_t set_als_kernel_attributes() {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = raise_smem_limits<double, 8>();
+    if (e == cudaSuccess) e = raise_smem_limits<double, 16>();
+    if (e == cudaSuccess) e = raise_smem_limits<double, 32>();
+    if (e == cudaSuccess) e = raise_smem_limits<float, 8>();
+    if (e == cudaSuccess) e = raise_smem_limits<float, 16>();
+    if (e == cudaSuccess) e = raise_smem_limits<float, 32>();
+    if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 8>();
+    if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 16>();
+    if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 32>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tail_rows<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<8>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tail_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tail_smem_bytes<16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tail_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tail_smem_bytes<32>());
+    return e;
 }
 
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st) {

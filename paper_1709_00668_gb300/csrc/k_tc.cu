@@ -137,11 +137,14 @@ struct TcParams {
     long long wrs;
     float *part;
     long long prs;
+    int pr;                  // row stride of the partials
     const int *conv;
     unsigned long long *bytes_ctr;
     unsigned *err;           // device status word (ERR_TIMEOUT on a wait that gave up)
     int stages;
 };
+
+constexpr int TC_MAX_SPC = 64;  // slices per CTA (epilogue weights staged in shared memory)
 
 struct TcShared {
     uint64_t full[8], empty[8], accf[2], acce[2];
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     unsigned char *ring = smem;                                   // S x 16 KB
     unsigned char *btile = ring + (size_t)S * TC_BOX_BYTES;        // nkb x N x 128 B
     TcShared *sh = reinterpret_cast<TcShared *>(btile + (size_t)p.nkb * N * 128);
+    float *wst = reinterpret_cast<float *>(sh + 1);                // [TC_MAX_SPC][RH] epilogue weights
     volatile int *abort_flag = &sh->abort_flag;
 
     if (threadIdx.x == 0) {
@@ -200,23 +204,40 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                      "r"(2 * N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // B operand: rows n < RH hold bf16(F), rows RH.. hold bf16(F - bf16(F)); K-major, swizzled
-    const float *F = p.F + rep * p.frs;
-    const int R = p.R;
-    for (int e = threadIdx.x; e < p.nkb * N * 64; e += blockDim.x) {
-        const int kb = e / (N * 64), rem = e % (N * 64), n = rem / 64, k = rem % 64;
-        const int j = kb * 64 + k, r = n % RH;
-        float f = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
-        __nv_bfloat16 hi = __float2bfloat16_rn(f);
-        __nv_bfloat16 v = n < RH ? hi : __float2bfloat16_rn(f - __bfloat162float(hi));
-        const int chunk = (k >> 3) ^ (n & 7);
-        *reinterpret_cast<__nv_bfloat16 *>(btile + (size_t)kb * N * 128 + n * 128 + chunk * 16 + (k & 7) * 2) = v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
+    const int R = p.R;
+    if (warp != 0) {
+        // warps 1-5 (160 threads), while warp 0 already streams X: the B operand
+        // (rows n < RH: bf16(F), rows RH..: bf16(F - bf16(F)); K-major, swizzled),
+        // one thread per contraction index j, and the epilogue weights C(kk, :)
+        const float *F = p.F + rep * p.frs;
+        const int t = threadIdx.x - 32;
+        for (int j = t; j < p.nkb * 64; j += 160) {
+            const int kb = j >> 6, k = j & 63;
+            unsigned char *col = btile + (size_t)kb * N * 128 + (k & 7) * 2;
+#pragma unroll 4
+            for (int r = 0; r < RH; ++r) {
+                const float f = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+                const int nh = r, nl = RH + r;
+                *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
+                *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
+            }
+        }
+        if (p.epi == 0) {
+            const float *W = p.W + rep * p.wrs;
+            for (int e = t; e < nsl * RH; e += 160) {
+                const int tt = e / RH, r = e % RH;
+                wst[e] = r < R ? W[(long long)(k0 + tt) * R + r] : 0.f;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("bar.sync 2, 160;" ::: "memory");
+    }
 
     if (warp == 0) {
         if (lane == 0) {
@@ -332,7 +353,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             // runs to its end so that all 128 threads meet the same barriers
             if (p.epi == 0) {
                 if (valid) {
-                    const float *c = W + (long long)kk * R;
+                    const float *c = wst + t * RH;
 #pragma unroll
                     for (int r = 0; r < RH; ++r)
                         if (r < R) acc[r] = fmaf(z[r], c[r], acc[r]);
@@ -346,7 +367,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 epi_bar();
                 if (etid < R) {
                     float s = ((sh->red[0][etid] + sh->red[1][etid]) + sh->red[2][etid]) + sh->red[3][etid];
-                    part[((long long)pb * p.Kp + kk) * R + etid] = s;
+                    part[((long long)pb * p.Kp + kk) * p.pr + etid] = s;
                 }
                 epi_bar();
             }
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         if (p.epi == 0 && valid) {
 #pragma unroll
             for (int r = 0; r < RH; ++r)
-                if (r < R) part[((long long)ks * p.NP + pidx) * R + r] = acc[r];
+                if (r < R) part[((long long)ks * p.NP + pidx) * p.pr + r] = acc[r];
         }
         if (p.bytes_ctr && etid == 0) {
             const int rows = min(TC_M, p.NP - pb * TC_M);
@@ -424,7 +445,8 @@ cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, 
 static int tc_n_of(int R) { return R <= 16 ? 32 : 64; }
 
 static size_t tc_smem_bytes(int nkb, int N, int stages) {
-    return 1024 + (size_t)stages * TC_BOX_BYTES + (size_t)nkb * N * 128 + sizeof(TcShared);
+    return 1024 + (size_t)stages * TC_BOX_BYTES + (size_t)nkb * N * 128 + sizeof(TcShared) +
+           (size_t)TC_MAX_SPC * (N / 2) * sizeof(float);
 }
 
 bool tc_supported(int R, int NC) {
@@ -439,12 +461,13 @@ void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *sp
     long long target = 2LL * num_sms;
     long long n = target / std::max(1LL, (long long)nrep * *npb);
     n = std::max(1LL, std::min<long long>(n, Kp));
-    *spc = (int)((Kp + n - 1) / n);
+    *spc = std::min(TC_MAX_SPC, (int)((Kp + n - 1) / n));
     *nks = (Kp + *spc - 1) / *spc;
 }
 
 cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
+                             int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
                              int *P_out, cudaStream_t st) {
     TcParams p{};
@@ -462,28 +485,30 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     p.wrs = wrs;
     p.part = part;
     p.prs = prs;
+    p.pr = pr;
     p.conv = conv;
     p.bytes_ctr = bytes_ctr;
     p.err = err;
     const int N = tc_n_of(R);
     const size_t budget = 110 * 1024;
-    const size_t fixed = 1024 + (size_t)p.nkb * N * 128 + sizeof(TcShared);
+    const size_t fixed = 1024 + (size_t)p.nkb * N * 128 + sizeof(TcShared) + (size_t)TC_MAX_SPC * (N / 2) * 4;
     int stages = (int)std::min<size_t>(8, (budget > fixed ? (budget - fixed) : 0) / TC_BOX_BYTES);
     p.stages = std::max(2, stages);
     const size_t smem = tc_smem_bytes(p.nkb, N, p.stages);
     *P_out = epi == 0 ? p.nks : p.npb;
     dim3 grid(p.npb * p.nks, nrep);
     count_launches(1);
-    // the attribute is raised once per process to the largest plan
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
     if (N == 32) k_mtt_tc<32><<<grid, 192, smem, st>>>(tmap, p);
     else k_mtt_tc<64><<<grid, 192, smem, st>>>(tmap, p);
     return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of the tensor-core kernels once,
+// outside any stream capture.
+cudaError_t set_tc_kernel_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return e;
 }
 
 cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,

@@ -16,7 +16,7 @@
 // stream capture.  All calls share the array and it keeps the last call's
 // contents, so the status word is cleared before every launch; calls that
 // overlap on the GPU (unordered streams or threads) race on the array.
-#include "../../include/sambaten.h"
+#include "sambaten.h"
 #include "sbt_internal.cuh"
 
 #include <cstring>

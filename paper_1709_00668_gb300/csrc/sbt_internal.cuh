@@ -213,6 +213,7 @@ struct AlsDesc {
     double *M;        // [rep][nmax][R] reduced MTTKRP
     void *part;       // [rep][P][nmax][R] partial sums (float or double)
     long long prs;    // elements per repetition of part
+    int pr;           // row stride of the partials: R (float64 path) or R rounded up to 4
     long long mrs;    // elements per repetition of M
     double *G;        // [rep][3][R][R]
     double *lam;      // [rep][R]
@@ -263,6 +264,10 @@ cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st);
 // the two halves of launch_als_mode: the MTTKRP pass, then reduction + tail
 cudaError_t launch_mttkrp(const AlsDesc &d, int mode, cudaStream_t st);
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st);
+// dynamic shared-memory limits of the ALS and tensor-core kernels (call once
+// per process and device, outside any stream capture)
+cudaError_t set_als_kernel_attributes();
+cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
@@ -274,6 +279,7 @@ void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *sp
 cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices);
 cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
+                             int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
                              int *P_out, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
