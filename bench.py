@@ -35,9 +35,17 @@ WORKLOAD_NAME = "dense-fp32 1000x1000x(500+50/batch) R=10 s=5 r=8"
 METRIC = "slices absorbed/sec at fit within 1e-3 of FP64; p50/p99 batch-update latency"
 UNIT = "slices/s"
 
-# ncu DRAM bytes per MTTKRP launch, keyed by the hash of the kernel source the
-# capture was taken on (null once the kernel changes)
-TRAFFIC = {}
+# ncu DRAM traffic of the MTTKRP kernel (dram__bytes_read.sum + write.sum) per
+# algorithmic byte, keyed by (hash of the kernel source the capture was taken
+# on, precision); null once the kernel changes.  Captured on the --small case
+# (same summary shapes, 90 slices per summary, 57.6 MB per launch), where
+# traffic scales with the slices processed; scaled here to the full launch.
+TRAFFIC = {
+    ("3d206003445c6898", "bf16"): {"ratio": (57.735168e6 + 13.056e3) / 57.6e6,
+                                   "capture": "k_mtt_tc<32> grid 36x8, 18.78 us, --small --steps 1 --warmup 1"},
+}
+KERNEL_NAME = {"bf16": "k_mtt_tc (tcgen05 MTTKRP, bf16 summaries)",
+               "f32": "k_mtt_row / k_mtt_col (CUDA-core MTTKRP, f32 summaries)"}
 
 
 def kernel_hash() -> str:
@@ -170,11 +178,12 @@ def make_data(steps: int, warmup: int, device):
     return p, nb
 
 
-def opts_for(prec: str, stream):
+def opts_for(prec: str, stream, nb: int):
+    """Options of one context that will absorb nb batches (store sized for exactly that)."""
     w = WORKLOAD
     return dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
                 max_iters_init=50, seed=w["seed"], prec=prec, cuda_stream=stream,
-                K_capacity=w["K0"] + 64 * w["batch"])
+                K_capacity=w["K0"] + nb * w["batch"])
 
 
 def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
@@ -300,13 +309,13 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # warm-up on a separate context (same shapes, first batches)
-    ctx_w = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+    ctx_w = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr, args.warmup))
     for i in range(args.warmup):
         ctx_w.update(batches[i % nb])
     ctx_w.close()
 
     # timed: device-resident inputs, the chosen precision
-    ctx = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+    ctx = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr, args.steps))
     ctx.profile_reset(timing=True)
     clocks = ClockSampler(local)
     timed = [batches[i % nb] for i in range(args.steps)]
@@ -327,7 +336,7 @@ def run_ours(args):
     # plain float32 GPU method on the same batches
     plain = None
     if not args.no_plain and args.prec != "f32":
-        cp = sbt.SamBaTen(X0, w["R"], **opts_for("f32", sptr))
+        cp = sbt.SamBaTen(X0, w["R"], **opts_for("f32", sptr, args.steps))
         torch.cuda.synchronize()
         barrier(dist, device)
         s_p, per_p, _ = time_updates(cp, timed, torch, stream)
@@ -341,7 +350,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         hb = [t.cpu().pin_memory() for t in timed]
-        ce = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr))
+        ce = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr, args.steps))
         torch.cuda.synchronize()
         barrier(dist, device)
         s_e, _, d2h = time_updates(ce, hb, torch, stream, host=True, read_back=True)
@@ -370,8 +379,9 @@ def run_ours(args):
     achieved = prof["mttkrp_bytes"] / (prof["mttkrp_ms"] / 1e3) / 1e9 if prof["mttkrp_ms"] > 0 else None
     kh = kernel_hash()
     per_launch_bytes = prof["mttkrp_bytes"] / max(1, prof["mttkrp_launches"])
-    traffic = TRAFFIC.get((kh, args.prec))
-    roofline = {"bound": "hbm", "kernel": "MTTKRP pass (k_mtt_row / k_mtt_col)", "achieved": achieved,
+    tr = TRAFFIC.get((kh, args.prec))
+    traffic = tr["ratio"] * per_launch_bytes if tr else None
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAME[args.prec], "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                 "peak_source": peak_note, "traffic": traffic,
                 "algorithmic_bytes_per_launch": per_launch_bytes,

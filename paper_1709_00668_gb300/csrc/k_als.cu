@@ -1,10 +1,20 @@
 // CP-ALS on the r summaries (Alg. 1 step 5), batched over repetitions.
 //
-// Per iteration and mode n: MTTKRP partial sums (one CTA per tile, no atomics),
-// a fixed-order reduction of the partials, and a per-repetition tail that
-// forms V = Hadamard of the other Grams, factors it (float64 Cholesky),
-// inverts it, solves U_n = M_n V^-1, normalises columns (lambda) and refreshes
-// the Gram; after mode 3 the tail computes the fit and the convergence flag.
+// Per iteration and mode n: MTTKRP partial sums (one CTA per tile, no atomics)
+// and a tail that solves U_n = M_n V^-1 with V the Hadamard product of the
+// other modes' Grams, normalises the columns (lambda) and refreshes the Gram;
+// after mode 3 the tail also computes the fit and the convergence flag.
+//
+// float64 summaries: a fixed-order reduction of the partials, then one CTA per
+// repetition factors V (float64 Cholesky in one warp) and does the rest.
+// float32 / bfloat16 summaries (float32 factors): float64 is a slow unit on
+// this GPU, so the R x R work is done in double-float (pairs of floats with
+// error-free sums and products, ~44 significant bits).  V^-1 (Gauss-Jordan)
+// is computed by k_xinv on a side stream while the MTTKRP runs; k_tail_rows
+// then reduces the partials of 64 rows per CTA, forms U = M V^-1 and the
+// chunk's share of the new Gram, and the last CTA of a repetition to finish
+// (an atomic ticket, no waiting) combines the shares in chunk order, takes
+// lambda, rescales U and computes the fit.
 // Every reduction runs in a fixed order, so results do not depend on timing.
 #include "sbt_internal.cuh"
 
