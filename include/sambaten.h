@@ -86,7 +86,8 @@ typedef struct {
     int32_t lambda_mode;   /* 0: keep lambda; 1: average with the summaries' estimate (Alg. 1 step 13) */
     int32_t fixed_iters;   /* 1: ignore tol, run exactly max_iters iterations (parity mode) */
     int64_t K_capacity;    /* slices the store is sized for up front (0: 2 * K0); grows on demand */
-    int64_t max_batch;     /* largest K_new sized up front (0: K0); grows on demand */
+    int64_t max_batch;     /* > 0: at init, size the workspace for every K_new <= max_batch
+                              up to K_capacity slices (sbt_reserve); 0: size on demand */
     void *cuda_stream;     /* cudaStream_t for all device work; NULL: the legacy default stream */
     int32_t check_every;   /* ALS convergence poll interval in iterations (0: 4) */
 } sbt_options;
@@ -142,6 +143,25 @@ sbt_status sbt_fit(sbt_ctx *ctx, double *fit);
 /* Statistics of the last sbt_update. */
 sbt_status sbt_stats(const sbt_ctx *ctx, sbt_update_stats *st);
 
+/* ---- device memory of a context ------------------------------------------
+ * No counterpart in the paper: these let a caller (the server below) admit
+ * work by a device-memory budget and keep allocation out of the update path. */
+
+/* Device bytes the context holds now (store, factors, marginals, workspace). */
+sbt_status sbt_device_bytes(sbt_ctx *ctx, uint64_t *bytes);
+
+/* Device bytes the context would hold after an sbt_update of K_new slices,
+ * computed on the host without allocating (buffers only grow).
+ * SBT_E_INVALID for K_new < 1; SBT_E_STATE if a mode has no positive weight. */
+sbt_status sbt_update_bytes(sbt_ctx *ctx, int64_t K_new, uint64_t *bytes);
+
+/* Size the store for K_max slices and the workspace for every update that
+ * keeps K <= K_max with K_new <= K_new_max, so that those updates allocate
+ * and free nothing (cudaFree waits for the whole device).  The init calls do
+ * this when opts.max_batch > 0, with K_max = the store capacity.
+ * SBT_E_INVALID unless K_new_max >= 1 and K_max > K; SBT_E_NOMEM. */
+sbt_status sbt_reserve(sbt_ctx *ctx, int64_t K_max, int64_t K_new_max);
+
 /* Inspection of the last sbt_update (for parity checks): the sampled indices
  * of repetition rep in mode (0: I_s, 1: J_s, 2: K_s over the old slices),
  * ascending.  *n receives the count; at most cap are written. */
@@ -170,7 +190,8 @@ typedef struct {
 } sbt_profile;
 
 /* Zero the counters; timing = 1 also brackets every MTTKRP launch of this
- * context with CUDA events on its stream (a few microseconds per update). */
+ * context with CUDA events on its stream (event nodes in the ALS graphs: a
+ * few microseconds per MTTKRP launch, so leave it off for throughput). */
 sbt_status sbt_profile_reset(sbt_ctx *ctx, int32_t timing);
 
 /* Read the counters (synchronises the context's stream). */
@@ -178,6 +199,96 @@ sbt_status sbt_profile_read(sbt_ctx *ctx, sbt_profile *out);
 
 /* Free every device and host resource of the context.  NULL is a no-op. */
 void sbt_destroy(sbt_ctx *ctx);
+
+/* ---- serving loop ---------------------------------------------------------
+ * No counterpart in the paper, which absorbs one stream.  A server owns many
+ * tensor streams, each a context whose store, factors and marginals stay
+ * resident on the device, and runs their update batches concurrently:
+ * `slots` worker threads each drive one sbt_update at a time on the CUDA
+ * streams of that tensor stream's own context, so updates of different
+ * streams overlap on the GPU.  A queued batch is admitted when a slot is free
+ * and the device bytes its stream will hold after the update
+ * (sbt_update_bytes) fit the budget together with every other stream's
+ * bytes; a batch that cannot fit even alone fails with SBT_E_NOMEM.  Batches
+ * of one stream run in submission order; batches of different streams are
+ * admitted in arrival order, skipping those that do not fit yet (they wait
+ * until a stream is closed).  Results do not depend on which batches share
+ * the GPU: every kernel reduces in a fixed order.
+ *
+ * A batch is borrowed, not copied: the tensor given to sbt_server_submit must
+ * stay valid until its ticket is done, and device data must be complete on
+ * the stream named by the stream's options (cuda_stream; NULL: the legacy
+ * default stream) when its update starts.  All calls are thread-safe except
+ * sbt_server_destroy, which must not race with other calls on the server. */
+typedef struct sbt_server sbt_server;
+
+typedef struct {
+    int32_t slots;        /* concurrent updates (worker threads), 1..64; 0: 4 */
+    uint64_t mem_budget;  /* device bytes all streams may hold; 0: 90 % of the free memory at create */
+    int32_t device;       /* CUDA device; -1: the calling thread's current device */
+} sbt_server_options;
+
+typedef struct {
+    int32_t status;       /* sbt_status of the update (the stream is unchanged unless SBT_OK) */
+    int32_t stream;       /* the stream id */
+    int64_t K;            /* slices the stream held after the update */
+    double queue_ms;      /* submit -> update started */
+    double service_ms;    /* update started -> committed */
+    double total_ms;      /* submit -> committed */
+} sbt_request_result;
+
+typedef struct {
+    int64_t submitted, completed, failed;  /* batches since the last reset */
+    int64_t queued, in_flight, streams;    /* now */
+    int64_t slices;                        /* slices absorbed since the reset */
+    uint64_t resident_bytes;               /* device bytes held by all streams now */
+    uint64_t peak_resident_bytes;          /* the most held (or reserved) since the reset */
+    uint64_t mem_budget;
+    double latency_p50_ms, latency_p99_ms; /* submit -> committed, completed batches */
+    double service_p50_ms, service_p99_ms; /* update started -> committed */
+    double busy_fraction;                  /* wall time with an update in flight / elapsed */
+    double elapsed_s;                      /* since the reset */
+} sbt_serving_stats;
+
+/* Defaults: 4 slots, 90 % of free memory, the current device. */
+sbt_status sbt_server_default_options(sbt_server_options *opts);
+
+/* Start a server and its worker threads.  opts may be NULL (defaults). */
+sbt_status sbt_server_create(const sbt_server_options *opts, sbt_server **out);
+
+/* Open a tensor stream: sbt_init(X0, R, opts) on the server's device in the
+ * calling thread, admitted only if the context fits the memory budget
+ * (SBT_E_NOMEM otherwise, nothing kept).  Use opts.K_capacity and
+ * opts.max_batch so that later updates allocate nothing.  *sid receives the
+ * stream id. */
+sbt_status sbt_server_open_stream(sbt_server *srv, const sbt_tensor *X0, int32_t R, const sbt_options *opts,
+                                  int32_t *sid);
+
+/* Queue one batch (sbt_update semantics) for stream sid; returns at once.
+ * *ticket identifies it for sbt_server_wait.  SBT_E_INVALID: unknown or
+ * closing stream; SBT_E_SHAPE: empty batch. */
+sbt_status sbt_server_submit(sbt_server *srv, int32_t sid, const sbt_tensor *X_new, uint64_t *ticket);
+
+/* Wait for a batch (timeout_ms < 0: no limit).  On SBT_OK *res (may be NULL)
+ * receives its result and the ticket is released; SBT_E_TIMEOUT leaves it
+ * pending; SBT_E_INVALID: unknown ticket.  One thread waits for a ticket. */
+sbt_status sbt_server_wait(sbt_server *srv, uint64_t ticket, int32_t timeout_ms, sbt_request_result *res);
+
+/* The stream's context, for sbt_factors / sbt_fit / sbt_stats while the
+ * stream has no batch queued or in flight (SBT_E_STATE otherwise).  Owned by
+ * the server; do not destroy it. */
+sbt_status sbt_server_stream_ctx(sbt_server *srv, int32_t sid, sbt_ctx **ctx);
+
+/* Wait for the stream's queued batches, then free its context and memory. */
+sbt_status sbt_server_close_stream(sbt_server *srv, int32_t sid);
+
+/* Counters and latency percentiles since the last reset. */
+sbt_status sbt_server_stats(sbt_server *srv, sbt_serving_stats *st);
+sbt_status sbt_server_stats_reset(sbt_server *srv);
+
+/* Fail the batches not yet started (SBT_E_STATE), let the ones in flight
+ * finish, stop the workers and free every stream.  NULL is a no-op. */
+void sbt_server_destroy(sbt_server *srv);
 
 /* ---- device-level operations (device pointers, ordered on `stream`) -------
  * These run one kernel family on caller buffers and return without a host

@@ -153,6 +153,11 @@ struct sbt_ctx {
     TcPlan tc;
     // profiling
     Buf prof_bytes;  // unsigned long long, device
+    Buf passes;      // pass counter of the device-side ALS loop
+    HBuf h_passes;
+    bool passes_pending = false;
+    long long launches_per_pass = 0;
+    int pass_iters = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
     double mtt_ms = 0.0;
@@ -262,9 +267,22 @@ static sbt_status status_error(unsigned err) {
     return SBT_OK;
 }
 
-// ALS descriptor over the ctx workspace for nrep summaries of shape n[3]
-static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
-                            const void *X, long long xrs, int max_iters) {
+// Workspace sizing: every per-call buffer goes through one Sizer, which either
+// allocates (Buf::ensure) or, in a dry run, records what would be needed so
+// that a context's footprint after a call can be predicted exactly.
+struct Sizer {
+    bool dry = false;
+    std::vector<std::pair<const Buf *, size_t>> want;
+    sbt_status need(Buf &b, size_t bytes) {
+        if (!dry) return b.ensure(bytes);
+        want.emplace_back(&b, std::max<size_t>(bytes, 256));
+        return SBT_OK;
+    }
+};
+
+// ALS descriptor scalars and tiles for nrep summaries of shape n[3] (no memory)
+static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
+                      int max_iters) {
     std::memset(&d, 0, sizeof(d));
     d.nrep = nrep;
     d.R = c->R;
@@ -274,39 +292,53 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.ldj = ldj;
     d.nK = nK;
     d.elem = elem;
-    d.xrs = xrs;
-    d.X = X;
     d.tol = c->opt.tol;
     d.max_iters = max_iters;
     d.fixed_iters = c->opt.fixed_iters;
     d.pr = elem == 0 ? c->R : (c->R + 3) / 4 * 4;
     choose_tiles(d, c->num_sms);
-    const int R = c->R;
-    const size_t tfs = esize_tf(elem);
     const int nmax = std::max(n[0], std::max(n[1], n[2]));
-    for (int m = 0; m < 3; ++m) TRY(c->U[m].ensure((size_t)nrep * n[m] * R * tfs));
-    d.mrs = (long long)nmax * R;
-    TRY(c->M.ensure((size_t)nrep * d.mrs * 8));
+    d.mrs = (long long)nmax * c->R;
     d.prs = partial_elems(d);
-    TRY(c->part.ensure((size_t)nrep * d.prs * tfs));
-    TRY(c->G.ensure((size_t)nrep * 3 * R * R * 8));
-    TRY(c->lam_s.ensure((size_t)nrep * R * 8));
-    TRY(c->fit.ensure((size_t)nrep * 8));
-    TRY(c->fit_prev.ensure((size_t)nrep * 8));
-    TRY(c->normX2.ensure((size_t)nrep * 8));
-    TRY(c->iters.ensure((size_t)nrep * 4));
-    TRY(c->conv.ensure((size_t)nrep * 4));
-    TRY(c->flags.ensure((size_t)nrep * 4));
-    TRY(c->h_poll.ensure((size_t)nrep * 4));
     d.tchunks = (nmax + 63) / 64;
-    TRY(c->tpart.ensure((size_t)nrep * d.tchunks * (R * (R + 1) / 2 + 1) * sizeof(DF)));
+}
+
+// ALS workspace of a descriptor from als_shape; part_bytes covers the partial
+// sums of every MTTKRP kernel that will run on it
+static sbt_status als_sizes(sbt_ctx *c, const AlsDesc &d, size_t part_bytes, Sizer &z) {
+    const int R = c->R, nrep = d.nrep;
+    const size_t tfs = esize_tf(d.elem);
+    for (int m = 0; m < 3; ++m) TRY(z.need(c->U[m], (size_t)nrep * d.n[m] * R * tfs));
+    TRY(z.need(c->M, (size_t)nrep * d.mrs * 8));
+    TRY(z.need(c->part, part_bytes));
+    TRY(z.need(c->G, (size_t)nrep * 3 * R * R * 8));
+    TRY(z.need(c->lam_s, (size_t)nrep * R * 8));
+    TRY(z.need(c->fit, (size_t)nrep * 8));
+    TRY(z.need(c->fit_prev, (size_t)nrep * 8));
+    TRY(z.need(c->normX2, (size_t)nrep * 8));
+    TRY(z.need(c->iters, (size_t)nrep * 4));
+    TRY(z.need(c->conv, (size_t)nrep * 4));
+    TRY(z.need(c->flags, (size_t)nrep * 4));
+    TRY(z.need(c->tpart, (size_t)nrep * d.tchunks * (R * (R + 1) / 2 + 1) * sizeof(DF)));
+    if (d.elem != 0) {
+        TRY(z.need(c->xinv, (size_t)nrep * 2048 * 4));
+        TRY(z.need(c->Gf, (size_t)nrep * 3 * R * R * sizeof(DF)));
+        TRY(z.need(c->dfs, (size_t)nrep * 2 * sizeof(DF)));
+    }
+    TRY(z.need(c->tail_cnt, (size_t)nrep * 4));
+    if (!z.dry) TRY(c->h_poll.ensure((size_t)nrep * 4));
+    return SBT_OK;
+}
+
+// Point the descriptor at the (already sized) workspace
+static sbt_status als_bind(sbt_ctx *c, AlsDesc &d, const void *X, long long xrs) {
+    const int nrep = d.nrep;
+    d.X = X;
+    d.xrs = xrs;
     d.tpart = c->tpart.as<DF>();
-    if (elem != 0) {
-        TRY(c->xinv.ensure((size_t)nrep * 2048 * 4));
+    if (d.elem != 0) {
         d.xinv = c->xinv.as<float>();
-        TRY(c->Gf.ensure((size_t)nrep * 3 * R * R * sizeof(DF)));
         d.Gf = c->Gf.as<DF>();
-        TRY(c->dfs.ensure((size_t)nrep * 2 * sizeof(DF)));
         d.nx2f = c->dfs.as<DF>();
         d.fitpf = d.nx2f + nrep;
         if (!c->side) {
@@ -315,7 +347,6 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
             CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         }
     }
-    TRY(c->tail_cnt.ensure((size_t)nrep * 4));
     CK(cudaMemsetAsync(c->tail_cnt.p, 0, (size_t)nrep * 4, c->stream));
     d.tail_cnt = c->tail_cnt.as<int>();
     for (int m = 0; m < 3; ++m) d.U[m] = c->U[m].p;
@@ -331,6 +362,15 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.flags = c->flags.as<int>();
     d.bytes_ctr = c->prof_bytes.as<unsigned long long>();
     return SBT_OK;
+}
+
+// ALS descriptor over the ctx workspace for nrep summaries of shape n[3]
+static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
+                            const void *X, long long xrs, int max_iters) {
+    als_shape(c, d, nrep, n, ldj, nK, elem, max_iters);
+    Sizer z;
+    TRY(als_sizes(c, d, (size_t)nrep * d.prs * esize_tf(elem), z));
+    return als_bind(c, d, X, xrs);
 }
 
 // Run ALS iterations until every repetition converged (polled every
@@ -365,15 +405,10 @@ static void tc_partials(AlsDesc &d, int num_sms) {
     d.prs = std::max(e0, std::max(e1, e2)) * d.pr;
 }
 
-// One captured CUDA graph runs G ALS iterations (three modes each: V^-1 on
-// the side stream beside the MTTKRP pass, then the tail); the host polls the
-// convergence flags between graph launches.  Kernel launches are counted when
-// the graph is launched, not when it is captured.
-static sbt_status capture_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G,
-                                     cudaGraphExec_t *exec, long long *launches_per) {
-    cudaGraph_t graph = nullptr;
-    const long long base = launch_count();
-    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+// The kernels of G ALS iterations on the library's stream: per mode, V^-1 on
+// the side stream beside the MTTKRP pass, then the tail.  With timing, CUDA
+// events bracket every MTTKRP launch (slots from `slot`).
+static cudaError_t launch_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G, bool timed) {
     cudaError_t e = cudaSuccess;
     int slot = 0;
     for (int it = 0; it < G && e == cudaSuccess; ++it) {
@@ -384,66 +419,113 @@ static sbt_status capture_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan 
                 if (e == cudaSuccess) e = launch_xinv(d, mode, c->side);
                 if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
             }
-            if (e == cudaSuccess && c->timing)
-                e = cudaEventRecordWithFlags(c->gev[slot].first, c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess && timed) e = cudaEventRecord(c->gev[slot].first, c->stream);
             if (e == cudaSuccess) e = mttkrp_mode(c, d, tc, mode);
-            if (e == cudaSuccess && c->timing)
-                e = cudaEventRecordWithFlags(c->gev[slot].second, c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess && timed) e = cudaEventRecord(c->gev[slot].second, c->stream);
             if (e == cudaSuccess && d.xinv) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
             if (e == cudaSuccess) e = launch_reduce_tail(d, mode, c->stream);
         }
     }
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
-    *launches_per = launch_count() - base;
-    count_launches(-(int)*launches_per);
-    if (e == cudaSuccess) e = e2;
+    return e;
+}
+
+// The whole ALS as one CUDA graph: a WHILE node whose body runs G iterations
+// and then k_als_continue, which keeps the loop going while a repetition has
+// not converged, for at most ceil(max_iters / G) passes.  The convergence
+// test runs on the device: no host round trip inside the ALS.
+static sbt_status build_als_loop(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G, int max_passes,
+                                 cudaGraphExec_t *exec, long long *launches_per_pass) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    const long long base = launch_count();
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = launch_iterations(c, d, tc, G, false);
+            if (el == cudaSuccess)
+                el = launch_als_continue(h, d.conv, d.nrep, c->passes.as<int>(), max_passes, c->stream);
+            cudaGraph_t got = nullptr;
+            e = cudaStreamEndCapture(c->stream, &got);
+            if (el != cudaSuccess) e = el;
+        }
+    }
+    *launches_per_pass = launch_count() - base;
+    count_launches(-(int)*launches_per_pass);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS graph: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS loop graph: ") + cudaGetErrorString(e));
     return SBT_OK;
 }
 
-// Run ALS iterations until every repetition converged (polled every
-// check_every iterations) or max_iters.  Kernels of converged repetitions
-// exit at once, so running past convergence inside a graph is harmless.
+// Launches and MTTKRP passes of the last device-side ALS loop, known once
+// its pass counter has been read back (after the caller's synchronisation).
+static void settle_als_counts(sbt_ctx *c) {
+    if (!c->passes_pending) return;
+    const int passes = *c->h_passes.as<int>();
+    count_launches((int)(passes * c->launches_per_pass));
+    c->mtt_launches += 3LL * c->pass_iters * passes;
+    c->passes_pending = false;
+}
+
+// Run ALS iterations until every repetition has converged or max_iters.
+// Throughput path: one graph launch of the device-side loop; the pass count
+// is read back with the caller's next synchronisation.  Timing path (CUDA
+// events around every MTTKRP launch): the same kernels issued directly on the
+// stream, convergence polled every check_every iterations.  Kernels of
+// converged repetitions exit at once, so iterations past convergence cost
+// only their launches.
 static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcPlan *tc = nullptr) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     const int G = std::max(1, std::min(every, max_iters));
-    if (c->timing) {
-        while ((int)c->gev.size() < 3 * G) {
-            cudaEvent_t a, b;
-            CK(cudaEventCreate(&a));
-            CK(cudaEventCreate(&b));
-            c->gev.emplace_back(a, b);
-        }
-    }
-    cudaGraphExec_t exec = nullptr;
-    long long lpg = 0;
-    TRY(capture_iterations(c, d, tc, G, &exec, &lpg));
     const int nl = (max_iters + G - 1) / G;
-    sbt_status st = SBT_OK;
-    for (int k = 0; k < nl && st == SBT_OK; ++k) {
-        cudaError_t e = cudaGraphLaunch(exec, c->stream);
-        if (e != cudaSuccess) {
-            st = fail(SBT_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
-            break;
-        }
-        count_launches((int)lpg);
+    if (c->passes_pending) {  // an earlier loop's count not read yet (its call failed before syncing)
+        CK(cudaStreamSynchronize(c->stream));
+        settle_als_counts(c);
+    }
+    if (!c->timing) {
+        TRY(c->passes.ensure(sizeof(int)));
+        TRY(c->h_passes.ensure(sizeof(int)));
+        cudaGraphExec_t exec = nullptr;
+        long long lpp = 0;
+        TRY(build_als_loop(c, d, tc, G, nl, &exec, &lpp));
+        cudaError_t e = cudaMemsetAsync(c->passes.p, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->h_passes.p, c->passes.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS loop launch: ") + cudaGetErrorString(e));
+        c->passes_pending = true;
+        c->launches_per_pass = lpp;
+        c->pass_iters = G;
+        return SBT_OK;
+    }
+    while ((int)c->gev.size() < 3 * G) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        c->gev.emplace_back(a, b);
+    }
+    for (int k = 0; k < nl; ++k) {
+        cudaError_t e = launch_iterations(c, d, tc, G, true);
         c->mtt_launches += 3LL * G;
         const bool poll = (k == nl - 1) || !c->opt.fixed_iters;
-        if (c->timing || poll) {
-            if (poll) e = cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) {
-                st = fail(SBT_E_CUDA, std::string("ALS poll: ") + cudaGetErrorString(e));
-                break;
-            }
-        }
-        if (c->timing) {
-            for (int q = 0; q < 3 * G; ++q) {
-                float t = 0.f;
-                if (cudaEventElapsedTime(&t, c->gev[q].first, c->gev[q].second) == cudaSuccess) c->mtt_ms += t;
-            }
+        if (e == cudaSuccess && poll)
+            e = cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS (timed): ") + cudaGetErrorString(e));
+        for (int q = 0; q < 3 * G; ++q) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->gev[q].first, c->gev[q].second) == cudaSuccess) c->mtt_ms += t;
         }
         if (poll) {
             const int *h = c->h_poll.as<int>();
@@ -452,8 +534,7 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
             if (all) break;
         }
     }
-    cudaGraphExecDestroy(exec);
-    return st;
+    return SBT_OK;
 }
 
 static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const sbt_options *opt) {
@@ -538,6 +619,8 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     return SBT_OK;
 }
 
+static sbt_status reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max);
+
 extern "C" sbt_status sbt_init(const sbt_tensor *X0, int32_t R, const sbt_options *opt, sbt_ctx **out) {
     if (!out) return fail(SBT_E_INVALID, "null output pointer");
     *out = nullptr;
@@ -571,7 +654,9 @@ extern "C" sbt_status sbt_init(const sbt_tensor *X0, int32_t R, const sbt_option
                                 c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) s = fail(SBT_E_CUDA, std::string("init canonicalize: ") + cudaGetErrorString(e));
+        else settle_als_counts(c);
     }
+    if (s == SBT_OK && opt->max_batch > 0) s = reserve(c, c->Kcap, opt->max_batch);
     if (s != SBT_OK) {
         delete c;
         return s;
@@ -594,6 +679,7 @@ extern "C" sbt_status sbt_init_factors(const sbt_tensor *X0, int32_t R, const do
         if (e == cudaSuccess) e = cudaMemcpy(c->lam.p, lambda, (size_t)R * 8, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) s = fail(SBT_E_CUDA, std::string("factor upload: ") + cudaGetErrorString(e));
     }
+    if (s == SBT_OK && opt->max_batch > 0) s = reserve(c, c->Kcap, opt->max_batch);
     if (s != SBT_OK) {
         delete c;
         return s;
@@ -628,6 +714,146 @@ static sbt_status grow_store(sbt_ctx *c, int64_t need) {
     return SBT_OK;
 }
 
+// Shapes of one update of K_new slices on K_old old ones: the sample sizes of
+// Section 4.1 (ceil(N / s), clamped to the positive weights) and everything
+// the workspace depends on.  With `bound` the clamps are replaced by their
+// largest possible values (used to size for future updates).
+struct UpdShape {
+    int64_t K_old = 0;
+    int K_new = 0, nI = 0, nJ = 0, nK = 0, Kp = 0, ldj = 0, ldi = 0;
+    long long samp_stride = 0, key_stride = 0, xrs = 0;
+    bool tc = false;
+};
+
+static sbt_status update_shape(const sbt_ctx *c, int64_t K_old, int K_new, bool bound, UpdShape &u) {
+    u.K_old = K_old;
+    u.K_new = K_new;
+    const int64_t pos[3] = {bound ? c->I : c->npos[0], bound ? c->J : c->npos[1], bound ? K_old : c->npos[2]};
+    u.nI = (int)std::min<int64_t>(ceil_div(c->I, c->opt.s_I), pos[0]);
+    u.nJ = (int)std::min<int64_t>(ceil_div(c->J, c->opt.s_J), pos[1]);
+    u.nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), pos[2]);
+    if (u.nI < 1 || u.nJ < 1 || u.nK < 1) return fail(SBT_E_STATE, "a mode has no positive weight to sample");
+    u.Kp = u.nK + K_new;
+    u.ldj = round8(u.nJ);
+    u.ldi = round8(u.nI);
+    u.samp_stride = std::max(u.nI, std::max(u.nJ, u.nK));
+    u.key_stride = std::max<int64_t>(std::max(c->I, c->J), K_old);
+    u.xrs = (long long)u.Kp * u.nI * u.ldj;
+    u.tc = c->elem == 2 && tc_supported(c->R, u.nI) && tc_supported(c->R, u.nJ);
+    return SBT_OK;
+}
+
+// bytes of MTTKRP partial sums for an update of this shape; with `bound`, the
+// largest over all summary lengths up to u.Kp (tile counts are not monotone)
+static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound) {
+    const int r = c->opt.r;
+    size_t best = 0;
+    for (int Kp = bound ? 1 : u.Kp; Kp <= u.Kp; ++Kp) {
+        AlsDesc d;
+        const int n[3] = {u.nI, u.nJ, Kp};
+        als_shape(c, d, r, n, u.ldj, u.nK, c->elem, c->opt.max_iters);
+        best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(c->elem));
+        if (u.tc) {
+            tc_partials(d, c->num_sms);
+            best = std::max<size_t>(best, (size_t)r * d.prs * 4);
+        }
+    }
+    return best;
+}
+
+// every device buffer an update of shape u uses (the store and its growth
+// included only in a dry run: grow_store moves the contents itself)
+static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &z) {
+    const int r = c->opt.r, R = c->R;
+    TRY(z.need(c->samples, (size_t)r * 3 * u.samp_stride * 4));
+    TRY(z.need(c->khi, (size_t)r * 3 * u.key_stride * 8));
+    TRY(z.need(c->klo, (size_t)r * 3 * u.key_stride * 8));
+    TRY(z.need(c->Xs, (size_t)r * u.xrs * esize_elem(c->elem)));
+    TRY(z.need(c->rowsq, (size_t)r * u.Kp * u.nI * 8));
+    TRY(z.need(c->xc_new, (size_t)u.K_new * 8));
+    AlsDesc d;
+    const int n[3] = {u.nI, u.nJ, u.Kp};
+    als_shape(c, d, r, n, u.ldj, u.nK, c->elem, c->opt.max_iters);
+    TRY(als_sizes(c, d, update_part_bytes(c, u, bound), z));
+    if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * 2));
+    const size_t pmax = (size_t)u.samp_stride;
+    TRY(z.need(c->nu, (size_t)r * 3 * R * 8));
+    TRY(z.need(c->cnew, (size_t)r * u.K_new * R * 8));
+    TRY(z.need(c->prop, (size_t)r * 3 * pmax * R * 8));
+    TRY(z.need(c->lam_est, (size_t)r * R * 8));
+    TRY(z.need(c->perm, (size_t)r * R * 4));
+    TRY(z.need(c->min_score, (size_t)r * 8));
+    if (z.dry && u.K_old + u.K_new > c->Kcap) {
+        const int64_t ncap = std::max<int64_t>(u.K_old + u.K_new, c->Kcap * 2);
+        TRY(z.need(c->store, (size_t)ncap * c->I * c->lds * esize_store(c->sdtype)));
+        TRY(z.need(c->C, (size_t)ncap * R * 8));
+        TRY(z.need(c->xc, (size_t)ncap * 8));
+    }
+    return SBT_OK;
+}
+
+// all device buffers of a context
+static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
+    return {&c->store, &c->A, &c->B, &c->C, &c->lam, &c->xa, &c->xb, &c->xc, &c->dxa, &c->dxb, &c->xc_new,
+            &c->status, &c->samples, &c->khi, &c->klo, &c->Xs, &c->rowsq, &c->U[0], &c->U[1], &c->U[2], &c->M,
+            &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
+            &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
+            &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes};
+}
+
+// device bytes after the needs of z (every buffer at max(capacity, need))
+static uint64_t footprint(sbt_ctx *c, const Sizer &z) {
+    uint64_t total = 0;
+    for (Buf *b : ctx_bufs(c)) {
+        size_t cap = b->cap;
+        for (const auto &w : z.want)
+            if (w.first == b) cap = std::max(cap, w.second);
+        total += cap;
+    }
+    return total;
+}
+
+// Size the store and the workspace so that every update that keeps K <= K_max
+// with K_new <= K_new_max allocates nothing.
+static sbt_status reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max) {
+    if (K_new_max < 1 || K_max <= c->K) return fail(SBT_E_INVALID, "sbt_reserve: need K_new_max >= 1, K_max > K");
+    K_new_max = std::min<int64_t>(K_new_max, K_max - c->K);
+    TRY(grow_store(c, K_max));
+    Sizer z;
+    // sizes grow with K_old and K_new except the tile counts, which
+    // update_part_bytes bounds over every summary length
+    UpdShape u;
+    TRY(update_shape(c, K_max - 1, 1, true, u));
+    TRY(size_update(c, u, true, z));
+    TRY(update_shape(c, K_max - K_new_max, (int)K_new_max, true, u));
+    TRY(size_update(c, u, true, z));
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_device_bytes(sbt_ctx *c, uint64_t *bytes) {
+    if (!c || !bytes) return fail(SBT_E_INVALID, "null argument");
+    Sizer z;
+    *bytes = footprint(c, z);
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_update_bytes(sbt_ctx *c, int64_t K_new, uint64_t *bytes) {
+    if (!c || !bytes || K_new < 1 || K_new > INT32_MAX) return fail(SBT_E_INVALID, "sbt_update_bytes: bad arguments");
+    UpdShape u;
+    TRY(update_shape(c, c->K, (int)K_new, false, u));
+    Sizer z;
+    z.dry = true;
+    TRY(size_update(c, u, false, z));
+    *bytes = footprint(c, z);
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    DeviceGuard dg(c->device);
+    return reserve(c, K_max, K_new_max);
+}
+
 extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     if (!c) return fail(SBT_E_INVALID, "null context");
     TRY(check_tensor(X));
@@ -638,23 +864,15 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     const int R = c->R, r = c->opt.r;
     const int K_new = (int)X->K;
     const int64_t K_old = c->K;
+    UpdShape u;
+    TRY(update_shape(c, K_old, K_new, false, u));
     TRY(grow_store(c, K_old + K_new));
-    // sample sizes (Section 4.1): ceil(N / s), clamped to the positive weights
-    const int nI = (int)std::min<int64_t>(ceil_div(c->I, c->opt.s_I), c->npos[0]);
-    const int nJ = (int)std::min<int64_t>(ceil_div(c->J, c->opt.s_J), c->npos[1]);
-    const int nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), c->npos[2]);
-    if (nI < 1 || nJ < 1 || nK < 1) return fail(SBT_E_STATE, "a mode has no positive weight to sample");
-    const int Kp = nK + K_new;
-    const int ldj = round8(nJ);
-    const long long samp_stride = std::max(nI, std::max(nJ, nK));
-    const long long key_stride = std::max<int64_t>(std::max(c->I, c->J), K_old);
-    TRY(c->samples.ensure((size_t)r * 3 * samp_stride * 4));
-    TRY(c->khi.ensure((size_t)r * 3 * key_stride * 8));
-    TRY(c->klo.ensure((size_t)r * 3 * key_stride * 8));
-    const long long xrs = (long long)Kp * nI * ldj;
-    TRY(c->Xs.ensure((size_t)r * xrs * esize_elem(c->elem)));
-    TRY(c->rowsq.ensure((size_t)r * Kp * nI * 8));
-    TRY(c->xc_new.ensure((size_t)K_new * 8));
+    {
+        Sizer z;
+        TRY(size_update(c, u, false, z));
+    }
+    const int nI = u.nI, nJ = u.nJ, nK = u.nK, Kp = u.Kp, ldj = u.ldj;
+    const long long samp_stride = u.samp_stride, key_stride = u.key_stride, xrs = u.xrs;
     // 1. append + marginal deltas
     CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
     CK(cudaMemsetAsync(c->dxa.p, 0, (size_t)c->I * 8, c->stream));
@@ -712,31 +930,23 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     // 4. CP-ALS on the r summaries
     AlsDesc d;
     const int n[3] = {nI, nJ, Kp};
-    TRY(setup_als(c, d, r, n, ldj, nK, c->elem, c->Xs.p, xrs, c->opt.max_iters));
+    als_shape(c, d, r, n, ldj, nK, c->elem, c->opt.max_iters);
+    TRY(als_bind(c, d, c->Xs.p, xrs));
     // bfloat16 summaries: tensor-core MTTKRP over the summary and its transposed copy
     TcPlan &tc = c->tc;
-    tc.on = c->elem == 2 && tc_supported(R, nI) && tc_supported(R, nJ);
+    tc.on = u.tc;
     if (tc.on) {
-        const int ldi = round8(nI);
-        TRY(c->Xt.ensure((size_t)r * Kp * nJ * ldi * 2));
+        const int ldi = u.ldi;
         CK(launch_transpose_bf16(c->Xs.p, c->Xt.p, nI, nJ, ldj, ldi, (long long)r * Kp, c->stream));
         CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp));
         CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp));
         tc_partials(d, c->num_sms);
-        TRY(c->part.ensure((size_t)r * d.prs * 4));
-        d.part = c->part.p;
     }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
                           c->batch, c->rowsq.as<double>(), c->stream));
     TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
     // 5. normalise, match, project back; 6. commit
     const int pmax = (int)samp_stride;
-    TRY(c->nu.ensure((size_t)r * 3 * R * 8));
-    TRY(c->cnew.ensure((size_t)r * K_new * R * 8));
-    TRY(c->prop.ensure((size_t)r * 3 * pmax * R * 8));
-    TRY(c->lam_est.ensure((size_t)r * R * 8));
-    TRY(c->perm.ensure((size_t)r * R * 4));
-    TRY(c->min_score.ensure((size_t)r * 8));
     MergeDesc m;
     std::memset(&m, 0, sizeof(m));
     m.nrep = r;
@@ -792,6 +1002,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     off += (size_t)r * 4;
     CK(cudaMemcpyAsync(hb + off, m.perm, (size_t)r * R * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
     DevStatus hs;
     std::memcpy(&hs, hb, sizeof(DevStatus));
     if (hs.err) return status_error(hs.err);
@@ -961,6 +1172,7 @@ extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     if (!c) return fail(SBT_E_INVALID, "null context");
     DeviceGuard dg(c->device);
     CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
     CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->timing = timing != 0;
@@ -975,6 +1187,7 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
     if (!c || !out) return fail(SBT_E_INVALID, "null argument");
     DeviceGuard dg(c->device);
     CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
     unsigned long long bytes = 0;
     CK(cudaMemcpy(&bytes, c->prof_bytes.p, 8, cudaMemcpyDeviceToHost));
     const double ms = c->mtt_ms;

@@ -1123,6 +1123,27 @@ cudaError_t set_als_kernel_attributes() {
     return e;
 }
 
+// Condition of the device-side ALS loop (the WHILE node of the ALS graph):
+// run another pass while some repetition has not converged, at most
+// max_passes passes (the counter is advanced here, every pass, so the loop
+// always ends).
+__global__ void k_als_continue(cudaGraphConditionalHandle h, const int *conv, int nrep, int *passes,
+                               int max_passes) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int p = *passes + 1;
+    *passes = p;
+    bool more = false;
+    for (int q = 0; q < nrep; ++q) more = more || conv[q] == 0;
+    cudaGraphSetConditional(h, (more && p < max_passes) ? 1u : 0u);
+}
+
+cudaError_t launch_als_continue(cudaGraphConditionalHandle h, const int *conv, int nrep, int *passes,
+                                int max_passes, cudaStream_t st) {
+    k_als_continue<<<1, 32, 0, st>>>(h, conv, nrep, passes, max_passes);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st) {
     k_xinv<<<d.nrep, 256, 0, st>>>(d, mode);
     count_launches(1);

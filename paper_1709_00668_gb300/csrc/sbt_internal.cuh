@@ -270,6 +270,8 @@ cudaError_t set_als_kernel_attributes();
 cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
+cudaError_t launch_als_continue(cudaGraphConditionalHandle h, const int *conv, int nrep, int *passes,
+                                int max_passes, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
 long long partial_elems(const AlsDesc &d);  // per repetition
 

@@ -1,0 +1,421 @@
+// Serving loop: many tensor streams, each absorbed by its own SamBaTen
+// context (Alg. 1 per batch), updated concurrently on one GPU.
+//
+// The paper absorbs a single stream.  Here a server keeps every stream's
+// store, factors and marginals resident on the device and runs update
+// batches from many streams at once: `slots` worker threads each drive one
+// sbt_update at a time, on the CUDA streams of that tensor stream's own
+// context, so the kernels of different streams' updates overlap on the GPU.
+// A queued batch is admitted as soon as a slot is free and the device bytes
+// its stream will hold after the update (sbt_update_bytes, computed on the
+// host) fit the memory budget together with every other stream's bytes.
+// Batches of one stream run one at a time in submission order; batches of
+// different streams are admitted in arrival order, skipping those that do
+// not fit yet.  Every kernel reduces in a fixed order, so a stream's results
+// do not depend on which other batches shared the GPU.
+#include "sambaten.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace sbt {
+void set_last_error(const std::string &msg);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+sbt_status fail(sbt_status s, const std::string &msg) {
+    sbt::set_last_error(msg);
+    return s;
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t sid = 0;
+    sbt_tensor X{};
+    Clock::time_point t_submit, t_start, t_end;
+    bool done = false;
+    sbt_request_result res{};
+};
+
+struct Stream {
+    sbt_ctx *ctx = nullptr;
+    std::deque<Request *> queue;  // not yet started, in submission order
+    bool busy = false;            // a batch of this stream is in flight
+    bool closing = false;
+    uint64_t bytes = 0;           // device bytes held (or reserved for the batch in flight)
+};
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, v.size() - 1);
+    const double f = pos - (double)lo;
+    return v[lo] * (1.0 - f) + v[hi] * f;
+}
+
+}  // namespace
+
+struct sbt_server {
+    sbt_server_options opt{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work;  // workers: a batch may be admissible
+    std::condition_variable cv_done;  // waiters: a batch finished / a stream went idle
+    std::map<int32_t, Stream> streams;
+    std::deque<int32_t> ready;  // streams with a queued batch and none in flight, by arrival
+    std::unordered_map<uint64_t, Request *> requests;
+    int32_t next_sid = 1;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    // accounting
+    uint64_t resident = 0, peak_resident = 0;
+    int64_t in_flight = 0, queued = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, slices = 0;
+    std::vector<double> lat_total, lat_service;
+    Clock::time_point t_reset, busy_since;
+    double busy_ms = 0.0;
+
+    void worker();
+    // the first admissible stream of `ready` (-1: none); fails batches that can never fit
+    int32_t pick_locked();
+    void finish_locked(Request *q, sbt_status st);
+};
+
+void sbt_server::finish_locked(Request *q, sbt_status st) {
+    q->t_end = Clock::now();
+    q->done = true;
+    q->res.status = st;
+    q->res.stream = q->sid;
+    q->res.queue_ms = ms_between(q->t_submit, q->t_start);
+    q->res.service_ms = ms_between(q->t_start, q->t_end);
+    q->res.total_ms = ms_between(q->t_submit, q->t_end);
+    if (st == SBT_OK) {
+        completed += 1;
+        slices += q->X.K;
+        lat_total.push_back(q->res.total_ms);
+        lat_service.push_back(q->res.service_ms);
+    } else {
+        failed += 1;
+    }
+}
+
+int32_t sbt_server::pick_locked() {
+    for (auto it = ready.begin(); it != ready.end();) {
+        const int32_t sid = *it;
+        Stream &s = streams[sid];
+        Request *q = s.queue.front();
+        uint64_t after = 0;
+        sbt_status st = sbt_update_bytes(s.ctx, q->X.K, &after);
+        if (st == SBT_OK && after > opt.mem_budget) {
+            st = SBT_E_NOMEM;
+            sbt::set_last_error("batch needs more device memory than the whole budget");
+        }
+        if (st != SBT_OK) {  // can never run: fail it, keep the stream's order
+            s.queue.pop_front();
+            queued -= 1;
+            q->t_start = Clock::now();
+            finish_locked(q, st);
+            if (s.queue.empty()) {
+                it = ready.erase(it);
+            } else {
+                ++it;
+            }
+            cv_done.notify_all();
+            continue;
+        }
+        const uint64_t grow = after > s.bytes ? after - s.bytes : 0;
+        if (resident + grow <= opt.mem_budget) {
+            ready.erase(it);
+            resident += grow;
+            s.bytes += grow;
+            peak_resident = std::max(peak_resident, resident);
+            return sid;
+        }
+        ++it;
+    }
+    return -1;
+}
+
+void sbt_server::worker() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lock(mu);
+    for (;;) {
+        int32_t sid = -1;
+        cv_work.wait(lock, [&] {
+            if (stop) return true;
+            sid = pick_locked();
+            return sid >= 0;
+        });
+        if (sid < 0) return;  // stop
+        Stream &s = streams[sid];
+        Request *q = s.queue.front();
+        s.queue.pop_front();
+        queued -= 1;
+        s.busy = true;
+        if (in_flight == 0) busy_since = Clock::now();
+        in_flight += 1;
+        q->t_start = Clock::now();
+        sbt_ctx *ctx = s.ctx;
+        lock.unlock();
+        sbt_status st = sbt_update(ctx, &q->X);
+        int64_t K = 0;
+        if (st == SBT_OK) st = sbt_factors(ctx, nullptr, nullptr, nullptr, nullptr, &K);
+        uint64_t now_bytes = 0;
+        sbt_device_bytes(ctx, &now_bytes);
+        lock.lock();
+        Stream &s2 = streams[sid];
+        resident = resident - s2.bytes + now_bytes;
+        s2.bytes = now_bytes;
+        q->res.K = K;
+        finish_locked(q, st);
+        in_flight -= 1;
+        if (in_flight == 0) busy_ms += ms_between(busy_since, Clock::now());
+        s2.busy = false;
+        if (!s2.queue.empty()) ready.push_back(sid);
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+}
+
+extern "C" sbt_status sbt_server_default_options(sbt_server_options *o) {
+    if (!o) return fail(SBT_E_INVALID, "null options");
+    o->slots = 4;
+    o->mem_budget = 0;
+    o->device = -1;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_create(const sbt_server_options *o, sbt_server **out) {
+    if (!out) return fail(SBT_E_INVALID, "null output pointer");
+    *out = nullptr;
+    sbt_server_options opt;
+    sbt_server_default_options(&opt);
+    if (o) opt = *o;
+    if (opt.slots <= 0) opt.slots = 4;
+    if (opt.slots > 64) return fail(SBT_E_INVALID, "slots must be <= 64");
+    int dev = opt.device;
+    if (dev < 0) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    if (opt.mem_budget == 0) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaError_t e = cudaSetDevice(dev);
+        size_t fr = 0, tot = 0;
+        if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("cudaMemGetInfo: ") + cudaGetErrorString(e));
+        opt.mem_budget = (uint64_t)(0.9 * (double)fr);
+    }
+    sbt_server *srv = new sbt_server();
+    srv->opt = opt;
+    srv->device = dev;
+    srv->t_reset = Clock::now();
+    for (int w = 0; w < opt.slots; ++w) srv->workers.emplace_back([srv] { srv->worker(); });
+    *out = srv;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_open_stream(sbt_server *srv, const sbt_tensor *X0, int32_t R,
+                                             const sbt_options *opts, int32_t *sid) {
+    if (!srv || !X0 || !opts || !sid) return fail(SBT_E_INVALID, "null argument");
+    if (X0->I < 1 || X0->J < 1 || X0->K < 1) return fail(SBT_E_SHAPE, "X0 must be non-empty");
+    // the store alone must fit before anything is allocated
+    const int64_t kcap = opts->K_capacity > 0 ? opts->K_capacity : 2 * X0->K;
+    const uint64_t store_bytes =
+        (uint64_t)std::max<int64_t>(kcap, X0->K + 1) * (uint64_t)X0->I * (uint64_t)((X0->J + 7) / 8 * 8) *
+        (X0->dtype == SBT_F64 ? 8u : 4u);
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        if (srv->stop) return fail(SBT_E_STATE, "server is shutting down");
+        if (srv->resident + store_bytes > srv->opt.mem_budget)
+            return fail(SBT_E_NOMEM, "stream store does not fit the server's memory budget");
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(srv->device);
+    sbt_options o = *opts;
+    sbt_ctx *ctx = nullptr;
+    sbt_status st = sbt_init(X0, R, &o, &ctx);
+    uint64_t bytes = 0;
+    if (st == SBT_OK) st = sbt_device_bytes(ctx, &bytes);
+    cudaSetDevice(prev);
+    if (st != SBT_OK) {
+        if (ctx) sbt_destroy(ctx);
+        return st;
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (srv->resident + bytes > srv->opt.mem_budget) {
+        sbt_destroy(ctx);
+        return fail(SBT_E_NOMEM, "stream does not fit the server's memory budget");
+    }
+    const int32_t id = srv->next_sid++;
+    Stream &s = srv->streams[id];
+    s.ctx = ctx;
+    s.bytes = bytes;
+    srv->resident += bytes;
+    srv->peak_resident = std::max(srv->peak_resident, srv->resident);
+    *sid = id;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_submit(sbt_server *srv, int32_t sid, const sbt_tensor *X_new, uint64_t *ticket) {
+    if (!srv || !X_new || !ticket) return fail(SBT_E_INVALID, "null argument");
+    if (X_new->K < 1) return fail(SBT_E_SHAPE, "empty batch");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    auto it = srv->streams.find(sid);
+    if (it == srv->streams.end() || it->second.closing) return fail(SBT_E_INVALID, "unknown stream");
+    if (srv->stop) return fail(SBT_E_STATE, "server is shutting down");
+    Request *q = new Request();
+    q->ticket = srv->next_ticket++;
+    q->sid = sid;
+    q->X = *X_new;
+    q->t_submit = Clock::now();
+    Stream &s = it->second;
+    const bool was_idle = s.queue.empty() && !s.busy;
+    s.queue.push_back(q);
+    if (was_idle) srv->ready.push_back(sid);
+    srv->requests[q->ticket] = q;
+    srv->queued += 1;
+    srv->submitted += 1;
+    *ticket = q->ticket;
+    srv->cv_work.notify_one();
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_wait(sbt_server *srv, uint64_t ticket, int32_t timeout_ms,
+                                      sbt_request_result *res) {
+    if (!srv) return fail(SBT_E_INVALID, "null server");
+    std::unique_lock<std::mutex> lock(srv->mu);
+    auto it = srv->requests.find(ticket);
+    if (it == srv->requests.end()) return fail(SBT_E_INVALID, "unknown ticket");
+    Request *q = it->second;
+    auto pred = [&] { return q->done; };
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(lock, pred);
+    } else if (!srv->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred)) {
+        return fail(SBT_E_TIMEOUT, "batch not finished within the timeout");
+    }
+    if (res) *res = q->res;
+    srv->requests.erase(it);
+    delete q;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_stream_ctx(sbt_server *srv, int32_t sid, sbt_ctx **ctx) {
+    if (!srv || !ctx) return fail(SBT_E_INVALID, "null argument");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    auto it = srv->streams.find(sid);
+    if (it == srv->streams.end()) return fail(SBT_E_INVALID, "unknown stream");
+    if (it->second.busy || !it->second.queue.empty()) return fail(SBT_E_STATE, "stream has batches queued or in flight");
+    *ctx = it->second.ctx;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_close_stream(sbt_server *srv, int32_t sid) {
+    if (!srv) return fail(SBT_E_INVALID, "null server");
+    std::unique_lock<std::mutex> lock(srv->mu);
+    auto it = srv->streams.find(sid);
+    if (it == srv->streams.end() || it->second.closing) return fail(SBT_E_INVALID, "unknown stream");
+    it->second.closing = true;
+    srv->cv_done.wait(lock, [&] { return !srv->streams[sid].busy && srv->streams[sid].queue.empty(); });
+    Stream &s = srv->streams[sid];
+    sbt_ctx *ctx = s.ctx;
+    srv->resident -= s.bytes;
+    srv->streams.erase(sid);
+    lock.unlock();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(srv->device);
+    sbt_destroy(ctx);
+    cudaSetDevice(prev);
+    srv->cv_work.notify_all();  // memory freed: batches waiting for it may fit now
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_stats(sbt_server *srv, sbt_serving_stats *st) {
+    if (!srv || !st) return fail(SBT_E_INVALID, "null argument");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    const auto now = Clock::now();
+    st->submitted = srv->submitted;
+    st->completed = srv->completed;
+    st->failed = srv->failed;
+    st->queued = srv->queued;
+    st->in_flight = srv->in_flight;
+    st->streams = (int64_t)srv->streams.size();
+    st->resident_bytes = srv->resident;
+    st->peak_resident_bytes = srv->peak_resident;
+    st->mem_budget = srv->opt.mem_budget;
+    st->latency_p50_ms = percentile(srv->lat_total, 0.5);
+    st->latency_p99_ms = percentile(srv->lat_total, 0.99);
+    st->service_p50_ms = percentile(srv->lat_service, 0.5);
+    st->service_p99_ms = percentile(srv->lat_service, 0.99);
+    const double el = ms_between(srv->t_reset, now);
+    const double busy = srv->busy_ms + (srv->in_flight > 0 ? ms_between(srv->busy_since, now) : 0.0);
+    st->busy_fraction = el > 0 ? busy / el : 0.0;
+    st->slices = srv->slices;
+    st->elapsed_s = el / 1e3;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_server_stats_reset(sbt_server *srv) {
+    if (!srv) return fail(SBT_E_INVALID, "null server");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->submitted = srv->completed = srv->failed = srv->slices = 0;
+    srv->lat_total.clear();
+    srv->lat_service.clear();
+    srv->t_reset = Clock::now();
+    srv->busy_ms = 0.0;
+    if (srv->in_flight > 0) srv->busy_since = srv->t_reset;
+    srv->peak_resident = srv->resident;
+    return SBT_OK;
+}
+
+extern "C" void sbt_server_destroy(sbt_server *srv) {
+    if (!srv) return;
+    {
+        std::unique_lock<std::mutex> lock(srv->mu);
+        srv->stop = true;
+        // batches not yet started end with SBT_E_STATE
+        for (auto &kv : srv->streams) {
+            for (Request *q : kv.second.queue) {
+                q->t_start = Clock::now();
+                srv->finish_locked(q, SBT_E_STATE);
+            }
+            srv->queued -= (int64_t)kv.second.queue.size();
+            kv.second.queue.clear();
+        }
+        srv->ready.clear();
+        srv->cv_work.notify_all();
+        srv->cv_done.notify_all();
+    }
+    for (auto &t : srv->workers) t.join();  // in-flight batches finish first
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(srv->device);
+    for (auto &kv : srv->streams) sbt_destroy(kv.second.ctx);
+    cudaSetDevice(prev);
+    for (auto &kv : srv->requests) delete kv.second;
+    delete srv;
+}

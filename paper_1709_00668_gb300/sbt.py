@@ -49,6 +49,10 @@ EXPORTS = [
     "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
     "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
+    "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve",
+    "sbt_server_default_options", "sbt_server_create", "sbt_server_open_stream", "sbt_server_submit",
+    "sbt_server_wait", "sbt_server_stream_ctx", "sbt_server_close_stream", "sbt_server_stats",
+    "sbt_server_stats_reset", "sbt_server_destroy",
 ]
 SBT_SAMPLE_NOALLOC_MAX_N = 262144
 
@@ -83,6 +87,25 @@ class SbtProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
                 ("mttkrp_bytes", ctypes.c_double)]
+
+
+class SbtServerOptions(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("mem_budget", ctypes.c_uint64), ("device", ctypes.c_int32)]
+
+
+class SbtRequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("stream", ctypes.c_int32), ("K", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+class SbtServingStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("streams", ctypes.c_int64),
+                ("slices", ctypes.c_int64), ("resident_bytes", ctypes.c_uint64),
+                ("peak_resident_bytes", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("service_p50_ms", ctypes.c_double), ("service_p99_ms", ctypes.c_double),
+                ("busy_fraction", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
 
 
 class SbtError(RuntimeError):
@@ -126,6 +149,21 @@ def lib() -> ctypes.CDLL:
     L.sbt_sample_noalloc.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_profile_reset.argtypes = [P, I32]
     L.sbt_profile_read.argtypes = [P, ctypes.POINTER(SbtProfile)]
+    L.sbt_device_bytes.argtypes = [P, ctypes.POINTER(U64)]
+    L.sbt_update_bytes.argtypes = [P, I64, ctypes.POINTER(U64)]
+    L.sbt_reserve.argtypes = [P, I64, I64]
+    L.sbt_server_default_options.argtypes = [ctypes.POINTER(SbtServerOptions)]
+    L.sbt_server_create.argtypes = [ctypes.POINTER(SbtServerOptions), ctypes.POINTER(P)]
+    L.sbt_server_open_stream.argtypes = [P, ctypes.POINTER(SbtTensor), I32, ctypes.POINTER(SbtOptions),
+                                         ctypes.POINTER(I32)]
+    L.sbt_server_submit.argtypes = [P, I32, ctypes.POINTER(SbtTensor), ctypes.POINTER(U64)]
+    L.sbt_server_wait.argtypes = [P, U64, I32, ctypes.POINTER(SbtRequestResult)]
+    L.sbt_server_stream_ctx.argtypes = [P, I32, ctypes.POINTER(P)]
+    L.sbt_server_close_stream.argtypes = [P, I32]
+    L.sbt_server_stats.argtypes = [P, ctypes.POINTER(SbtServingStats)]
+    L.sbt_server_stats_reset.argtypes = [P]
+    L.sbt_server_destroy.argtypes = [P]
+    L.sbt_server_destroy.restype = None
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("sbt_version", "sbt_last_error", "sbt_destroy"):
@@ -204,14 +242,35 @@ class SamBaTen:
                                           ctypes.byref(h)), "sbt_init_factors")
         self._h = h
 
+    @classmethod
+    def _borrow(cls, h, R: int, I: int, J: int) -> "SamBaTen":
+        """View of a context owned elsewhere (a server stream); close() does not free it."""
+        obj = cls.__new__(cls)
+        obj._h, obj.R, obj.I, obj.J, obj._owned = h, int(R), int(I), int(J), False
+        return obj
+
     @property
     def handle(self):
         return self._h
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().sbt_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib().sbt_destroy(self._h)
             self._h = None
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_uint64()
+        _check(lib().sbt_device_bytes(self._h, ctypes.byref(b)), "sbt_device_bytes")
+        return int(b.value)
+
+    def update_bytes(self, K_new: int) -> int:
+        b = ctypes.c_uint64()
+        _check(lib().sbt_update_bytes(self._h, int(K_new), ctypes.byref(b)), "sbt_update_bytes")
+        return int(b.value)
+
+    def reserve(self, K_max: int, K_new_max: int):
+        _check(lib().sbt_reserve(self._h, int(K_max), int(K_new_max)), "sbt_reserve")
 
     def __del__(self):
         try:
@@ -385,3 +444,90 @@ def sbt_mttkrp(X, A, B, C, mode, *, stream=None):
     _check(lib().sbt_mttkrp(dt, X.data_ptr(), K, I, J, ld, A.data_ptr(), B.data_ptr(), C.data_ptr(), R,
                             int(mode), out.data_ptr(), _stream_arg(stream)), "sbt_mttkrp")
     return out
+
+
+# ---------------------------------------------------------------------------
+class Server:
+    """Serving loop over many tensor streams (sbt_server_*).
+
+    Batches are borrowed until their ticket is waited for: the binding keeps a
+    reference to each submitted tensor until then."""
+
+    def __init__(self, slots: int = 4, mem_budget: int = 0, device: int = -1):
+        o = SbtServerOptions()
+        _check(lib().sbt_server_default_options(ctypes.byref(o)), "sbt_server_default_options")
+        o.slots, o.mem_budget, o.device = int(slots), int(mem_budget), int(device)
+        h = ctypes.c_void_p()
+        _check(lib().sbt_server_create(ctypes.byref(o), ctypes.byref(h)), "sbt_server_create")
+        self._h = h
+        self._keep = {}
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sbt_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_stream(self, X0, R: int, **opts) -> int:
+        o = sbt_default_options(**opts)
+        keep: list = []
+        desc = _tensor_desc(X0, keep)
+        sid = ctypes.c_int32()
+        _check(lib().sbt_server_open_stream(self._h, ctypes.byref(desc), int(R), ctypes.byref(o),
+                                            ctypes.byref(sid)), "sbt_server_open_stream")
+        self._shape[sid.value] = (int(R), int(desc.I), int(desc.J))
+        return int(sid.value)
+
+    def open_stream_status(self, X0, R: int, **opts):
+        """(status, sid) without raising."""
+        o = sbt_default_options(**opts)
+        keep: list = []
+        desc = _tensor_desc(X0, keep)
+        sid = ctypes.c_int32()
+        st = int(lib().sbt_server_open_stream(self._h, ctypes.byref(desc), int(R), ctypes.byref(o),
+                                              ctypes.byref(sid)))
+        if st == SBT_OK:
+            self._shape[sid.value] = (int(R), int(desc.I), int(desc.J))
+        return st, int(sid.value)
+
+    def submit(self, sid: int, X_new) -> int:
+        keep: list = []
+        desc = _tensor_desc(X_new, keep)
+        t = ctypes.c_uint64()
+        _check(lib().sbt_server_submit(self._h, int(sid), ctypes.byref(desc), ctypes.byref(t)),
+               "sbt_server_submit")
+        self._keep[t.value] = keep
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = SbtRequestResult()
+        _check(lib().sbt_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(r)), "sbt_server_wait")
+        self._keep.pop(int(ticket), None)
+        return {"status": r.status, "stream": r.stream, "K": r.K, "queue_ms": r.queue_ms,
+                "service_ms": r.service_ms, "total_ms": r.total_ms}
+
+    def stream(self, sid: int) -> SamBaTen:
+        """The stream's context (factors, fit, stats) while it has no batch queued or in flight."""
+        h = ctypes.c_void_p()
+        _check(lib().sbt_server_stream_ctx(self._h, int(sid), ctypes.byref(h)), "sbt_server_stream_ctx")
+        R, I, J = self._shape[int(sid)]
+        return SamBaTen._borrow(h, R, I, J)
+
+    def close_stream(self, sid: int):
+        _check(lib().sbt_server_close_stream(self._h, int(sid)), "sbt_server_close_stream")
+        self._shape.pop(int(sid), None)
+
+    def stats(self) -> dict:
+        st = SbtServingStats()
+        _check(lib().sbt_server_stats(self._h, ctypes.byref(st)), "sbt_server_stats")
+        return {f: getattr(st, f) for f, _ in SbtServingStats._fields_}
+
+    def stats_reset(self):
+        _check(lib().sbt_server_stats_reset(self._h), "sbt_server_stats_reset")

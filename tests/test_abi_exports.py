@@ -68,3 +68,40 @@ def test_package_import_does_not_need_the_library():
     import importlib
     m = importlib.import_module("paper_1709_00668_gb300")
     assert hasattr(m, "__all__")
+
+
+def test_server_host_logic_without_gpu(lib):
+    """The serving loop's bookkeeping: unknown streams and tickets are
+    rejected, counters start at zero, destroy joins the workers."""
+    from paper_1709_00668_gb300 import sbt
+    o = sbt.SbtServerOptions()
+    assert lib.sbt_server_default_options(ctypes.byref(o)) == sbt.SBT_OK
+    assert (o.slots, o.mem_budget, o.device) == (4, 0, -1)
+    o.slots, o.mem_budget, o.device = 3, 1 << 30, 0
+    srv = ctypes.c_void_p()
+    assert lib.sbt_server_create(ctypes.byref(o), ctypes.byref(srv)) == sbt.SBT_OK
+    buf = (ctypes.c_float * 16)()
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 2, 2, 4, ctypes.cast(buf, ctypes.c_void_p))
+    ticket = ctypes.c_uint64()
+    assert lib.sbt_server_submit(srv, 7, ctypes.byref(t), ctypes.byref(ticket)) == sbt.SBT_E_INVALID
+    t0 = sbt.SbtTensor(sbt.SBT_F32, 0, 2, 2, 0, ctypes.cast(buf, ctypes.c_void_p))
+    assert lib.sbt_server_submit(srv, 7, ctypes.byref(t0), ctypes.byref(ticket)) == sbt.SBT_E_SHAPE
+    res = sbt.SbtRequestResult()
+    assert lib.sbt_server_wait(srv, 12345, 0, ctypes.byref(res)) == sbt.SBT_E_INVALID
+    ctx = ctypes.c_void_p()
+    assert lib.sbt_server_stream_ctx(srv, 1, ctypes.byref(ctx)) == sbt.SBT_E_INVALID
+    assert lib.sbt_server_close_stream(srv, 1) == sbt.SBT_E_INVALID
+    # a store larger than the budget is refused before anything is allocated
+    big = sbt.SbtTensor(sbt.SBT_F32, 0, 4096, 4096, 64, ctypes.cast(buf, ctypes.c_void_p))
+    so = sbt.sbt_default_options(K_capacity=128)
+    sid = ctypes.c_int32()
+    assert lib.sbt_server_open_stream(srv, ctypes.byref(big), 3, ctypes.byref(so),
+                                      ctypes.byref(sid)) == sbt.SBT_E_NOMEM
+    st = sbt.SbtServingStats()
+    assert lib.sbt_server_stats(srv, ctypes.byref(st)) == sbt.SBT_OK
+    assert (st.submitted, st.completed, st.queued, st.in_flight, st.streams, st.resident_bytes) == (0,) * 6
+    assert st.mem_budget == 1 << 30
+    assert lib.sbt_server_stats_reset(srv) == sbt.SBT_OK
+    lib.sbt_server_destroy(srv)
+    slots_bad = sbt.SbtServerOptions(65, 1, 0)
+    assert lib.sbt_server_create(ctypes.byref(slots_bad), ctypes.byref(srv)) == sbt.SBT_E_INVALID

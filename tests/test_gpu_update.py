@@ -270,3 +270,33 @@ def test_marginals_of_extreme_magnitudes_sample_like_oracle(sbt):
     for rep, t in enumerate(traces3):
         assert np.array_equal(ctx.last_samples(rep, 0), t.Is)
         assert np.array_equal(ctx.last_samples(rep, 2), t.Ks)
+
+
+def test_device_loop_equals_directly_launched_iterations(sbt):
+    """The ALS as one graph with a device-side WHILE loop (throughput path)
+    gives bit-identical results to the same kernels launched one by one with
+    host polling (timing path), with fixed iterations and with the tolerance
+    stop, and reports the passes it ran."""
+    X, A, B, C = planted(64, 48, 46, 4, dtype=torch.float32, seed=16)
+    fac = unit_factors(A, B, C[:30])
+    for kw in (dict(fixed_iters=1, max_iters=7), dict(fixed_iters=0, max_iters=40, tol=1e-3)):
+        for prec in ("bf16", "f32"):
+            c_loop, _ = _pair(sbt, X, 30, 4, fac, prec=prec, r=3, **kw)
+            c_timed, _ = _pair(sbt, X, 30, 4, fac, prec=prec, r=3, **kw)
+            c_loop.profile_reset(timing=False)
+            c_timed.profile_reset(timing=True)
+            for k0 in (30, 38):
+                c_loop.update(torch.from_numpy(X[k0:k0 + 8]).cuda())
+                c_timed.update(torch.from_numpy(X[k0:k0 + 8]).cuda())
+            for a, b in zip(c_loop.factors(), c_timed.factors()):
+                assert np.array_equal(a, b)
+            s1, s2 = c_loop.stats(), c_timed.stats()
+            assert s1["iters"] == s2["iters"] and s1["fit"] == s2["fit"]
+            p1, p2 = c_loop.profile(), c_timed.profile()
+            if kw["fixed_iters"]:
+                assert p1["mttkrp_launches"] == p2["mttkrp_launches"] == 2 * 3 * 8
+            else:
+                assert max(s1["iters"]) < kw["max_iters"]
+                assert p1["mttkrp_launches"] % 12 == 0 and p1["mttkrp_launches"] > 0
+            assert p1["mttkrp_bytes"] == p2["mttkrp_bytes"]
+            assert p1["mttkrp_ms"] == 0 and p2["mttkrp_ms"] > 0
