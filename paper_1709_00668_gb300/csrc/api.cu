@@ -300,7 +300,7 @@ static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     const int nmax = std::max(n[0], std::max(n[1], n[2]));
     d.mrs = (long long)nmax * c->R;
     d.prs = partial_elems(d);
-    d.tchunks = (nmax + 63) / 64;
+    d.tchunks = (nmax + TAIL_ROWS - 1) / TAIL_ROWS;
 }
 
 // ALS workspace of a descriptor from als_shape; part_bytes covers the partial
@@ -926,6 +926,11 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     g.ldj = ldj;
     g.xrs = xrs;
     g.rowsq = c->rowsq.as<double>();
+    if (u.tc) {  // the transposed copy for the mode-2 tensor-core pass, written by the gather
+        g.Xt = c->Xt.p;
+        g.ldi = u.ldi;
+        g.xtrs = (long long)Kp * nJ * u.ldi;
+    }
     CK(launch_gather(g, c->sdtype, c->elem, c->stream));
     // 4. CP-ALS on the r summaries
     AlsDesc d;
@@ -937,7 +942,6 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     tc.on = u.tc;
     if (tc.on) {
         const int ldi = u.ldi;
-        CK(launch_transpose_bf16(c->Xs.p, c->Xt.p, nI, nJ, ldj, ldi, (long long)r * Kp, c->stream));
         CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp));
         CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp));
         tc_partials(d, c->num_sms);

@@ -533,8 +533,7 @@ __device__ void block_inverse_df(const DF *Gf, int R, int mode, DF *W, float *X,
 // if the float32 one breaks down.  It sums the MTTKRP partials of its rows in
 // fixed order, forms U_raw = M V^-1 (written unnormalised) and the chunk's
 // share of U_raw^T U_raw and of <M, U_raw>.
-constexpr int TAIL_ROWS = 64;
-constexpr int TAIL_PB = 16;        // partials staged per block
+constexpr int TAIL_PB = 32;        // partials staged per block
 constexpr int TAIL_THREADS = 256;
 
 // float32 Cholesky (one warp, lane per row): V = L L^T; false if not positive definite

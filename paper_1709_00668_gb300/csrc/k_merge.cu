@@ -82,16 +82,47 @@ __device__ void hungarian_max(const double *score, int ld, int R, int *perm) {
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per repetition.
+// Dot products of k_match.  Summary factors of the float32 / bfloat16 path are
+// float32 and the anchors (the old factors) float64: the products are summed
+// in double-float on the float32 pipes (float64 is a slow unit here); the
+// float64 path sums in float64.
+template <typename TF> struct MatchAcc;
+template <> struct MatchAcc<double> {
+    using Anchor = double;
+    double v = 0.0;
+    __device__ __forceinline__ static Anchor anchor(double a) { return a; }
+    __device__ __forceinline__ void add_prod(double u, Anchor a) { v = fma(u, a, v); }
+    __device__ __forceinline__ void add_sq(double u) { v = fma(u, u, v); }
+    __device__ __forceinline__ void add_sq_anchor(Anchor a) { v = fma(a, a, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct MatchAcc<float> {
+    using Anchor = DF;
+    DF v{0.f, 0.f};
+    __device__ __forceinline__ static Anchor anchor(double a) { return df_from_double(a); }
+    __device__ __forceinline__ void add_prod(float u, Anchor a) { v = df_fma(v, DF{u, 0.f}, a); }
+    __device__ __forceinline__ void add_sq(float u) { v = df_add_sq(v, u); }
+    __device__ __forceinline__ void add_sq_anchor(Anchor a) { v = df_fma(v, a, a); }
+    __device__ __forceinline__ double value() const { return df_value(v); }
+};
+
+constexpr int MATCH_TS = 16;                                      // rows staged per tile
+constexpr int MATCH_ITEMS = (32 * 32 + 2 * 32 + 255) / 256;      // accumulators per thread
+
+// One CTA per repetition: shared-row norms (Alg. 1 step 6), cosines and the
+// matching (Lemma 1, Alg. 1 step 7), project back (steps 8-9).
 template <typename TF>
 __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
+    using Acc = MatchAcc<TF>;
+    using Anchor = typename Acc::Anchor;
     const int rep = blockIdx.x;
     const int R = m.R;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Kp = m.nK + m.K_new;
     const int n[3] = {m.nI, m.nJ, Kp};
     const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
-    __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32];
+    __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32], scale[3][32];
+    __shared__ TF su[MATCH_TS * 32];
+    __shared__ Anchor sa[MATCH_TS * 32];
     __shared__ int perm[32];
     __shared__ int zflag;
     const TF *U[3];
@@ -102,35 +133,60 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         S[q] = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
     }
     if (threadIdx.x == 0) zflag = 0;
-    __syncthreads();
-    // shared-row norms of the summary columns (Alg. 1 step 6) and of the anchors
-    for (int pr = warp; pr < 6 * R; pr += 8) {
-        const int which = pr / (3 * R), q = (pr / R) % 3, r = pr % R;
-        double a = 0.0;
-        for (int t = lane; t < nsh[q]; t += 32) {
-            double x = which == 0 ? (double)U[q][(long long)t * R + r] : old[q][(long long)S[q][t] * R + r];
-            a += x * x;
-        }
-        a = warp_sum(a);
-        if (lane == 0) {
-            double s = sqrt(a);
-            if (s == 0.0) {
-                s = 1.0;
-                if (which == 0) zflag = 1;
+    const int nitems = R * R + 2 * R;
+    // per mode over the shared rows: U'(:,r')^T anchor(:,r), |U'(:,r')|^2, |anchor(:,r)|^2
+    for (int q = 0; q < 3; ++q) {
+        Acc acc[MATCH_ITEMS];
+        for (int t0 = 0; t0 < nsh[q]; t0 += MATCH_TS) {
+            const int rows = min(MATCH_TS, nsh[q] - t0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+                const int t = t0 + e / R, c = e % R;
+                su[e] = U[q][(long long)t * R + c];
+                sa[e] = Acc::anchor(old[q][(long long)S[q][t] * R + c]);
             }
-            if (which == 0) nu[q][r] = s;
-            else Nn[q][r] = s;
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < MATCH_ITEMS; ++u) {
+                const int item = threadIdx.x + u * 256;
+                if (item >= nitems) break;
+                if (item < R * R) {
+                    const int rp = item / R, r = item % R;
+                    for (int t = 0; t < rows; ++t) acc[u].add_prod(su[t * R + rp], sa[t * R + r]);
+                } else if (item < R * R + R) {
+                    const int rp = item - R * R;
+                    for (int t = 0; t < rows; ++t) acc[u].add_sq(su[t * R + rp]);
+                } else {
+                    const int r = item - R * R - R;
+                    for (int t = 0; t < rows; ++t) acc[u].add_sq_anchor(sa[t * R + r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < MATCH_ITEMS; ++u) {
+            const int item = threadIdx.x + u * 256;
+            if (item >= nitems) break;
+            const double v = acc[u].value();
+            if (item < R * R) {
+                gam[q][item / R][item % R] = v;  // the dot product; divided by the norms below
+            } else if (item < R * R + R) {
+                double s = sqrt(v);
+                if (s == 0.0) {
+                    s = 1.0;
+                    zflag = 1;
+                }
+                nu[q][item - R * R] = s;
+            } else {
+                const double s = sqrt(v);
+                Nn[q][item - R * R - R] = s == 0.0 ? 1.0 : s;
+            }
         }
     }
     __syncthreads();
     // cosines Gamma_q(r', r) between unit summary and unit anchor columns
-    for (int tr = warp; tr < 3 * R * R; tr += 8) {
-        const int q = tr / (R * R), rp = (tr / R) % R, r = tr % R;
-        double a = 0.0;
-        for (int t = lane; t < nsh[q]; t += 32)
-            a += (double)U[q][(long long)t * R + rp] * old[q][(long long)S[q][t] * R + r];
-        a = warp_sum(a);
-        if (lane == 0) gam[q][rp][r] = a / (nu[q][rp] * Nn[q][r]);
+    for (int e = threadIdx.x; e < 3 * R * R; e += blockDim.x) {
+        const int q = e / (R * R), rp = (e / R) % R, r = e % R;
+        gam[q][rp][r] /= nu[q][rp] * Nn[q][r];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -157,23 +213,24 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         if (zflag) m.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
     }
     __syncthreads();
-    // least-squares scale of a summary column of mode q in the matched old scale
-    auto coef = [&](int q, int rp) -> double {
-        const int r = perm[rp];
+    // least-squares scale of a summary column of mode q in the matched old
+    // scale, per unit of the raw summary value
+    if (threadIdx.x < 3 * R) {
+        const int q = threadIdx.x / R, rp = threadIdx.x % R, r = perm[rp];
         double num = lsp[rp], den = m.lam[r];
         for (int o = 0; o < 3; ++o)
             if (o != q) {
                 num *= gam[o][rp][r];
                 den *= Nn[o][r];
             }
-        return den != 0.0 ? num / den : 0.0;
-    };
+        scale[q][rp] = den != 0.0 ? num / den / nu[q][rp] : 0.0;
+    }
+    __syncthreads();
     // new rows of C (Alg. 1 step 9)
     double *cn = m.cnew + (long long)rep * m.K_new * R;
     for (int e = threadIdx.x; e < m.K_new * R; e += blockDim.x) {
         const int k = e / R, rp = e % R;
-        const double u = (double)U[2][(long long)(m.nK + k) * R + rp] / nu[2][rp];
-        cn[(long long)k * R + perm[rp]] = coef(2, rp) * u;
+        cn[(long long)k * R + perm[rp]] = scale[2][rp] * (double)U[2][(long long)(m.nK + k) * R + rp];
     }
     // zero-entry proposals (Alg. 1 step 8)
     for (int q = 0; q < 3; ++q) {
@@ -181,8 +238,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         for (int e = threadIdx.x; e < nsh[q] * R; e += blockDim.x) {
             const int t = e / R, rp = e % R, r = perm[rp];
             double val = NAN;
-            if (old[q][(long long)S[q][t] * R + r] == 0.0)
-                val = coef(q, rp) * (double)U[q][(long long)t * R + rp] / nu[q][rp];
+            if (old[q][(long long)S[q][t] * R + r] == 0.0) val = scale[q][rp] * (double)U[q][(long long)t * R + rp];
             pp[(long long)t * R + r] = val;
         }
     }

@@ -97,96 +97,122 @@ __device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned lo
     if (old + v < old) atomicOr(&status->err, ERR_RANGE);
 }
 
-constexpr int APPEND_ROWS = 64;        // rows of one slice per CTA (row pass)
-constexpr int APPEND_COL_ROWS = 512;   // rows per CTA of the column pass
+constexpr int APPEND_ROWS = 128;  // rows (k, i) of the new slices per CTA
+constexpr int APPEND_THREADS = 256;
 
-// Row pass: copy the new slices into the store; x_a (rows) and x_c (slices)
-// from a warp per row.  Integer sums are exact, so the order is free.
+// One pass over the new slices: copy them into the store and add the
+// fixed-point squares q(x) to x_a (per row i), x_b (per column j) and x_c
+// (per slice k).  A CTA covers APPEND_ROWS consecutive rows (k, i) and one
+// chunk of 256 * V columns; each thread owns V adjacent columns (one 16-byte
+// vector when the rows are aligned), so its column sums stay in registers.
+// Row sums are reduced per warp, then over the CTA's warps.  All sums are
+// exact 64-bit integers, so the atomics may land in any order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_append(const T *Xin, int I, int J, int ldin, T *store, int lds, int S,
-                                                unsigned long long *dxa, unsigned long long *xc_new,
-                                                DevStatus *status) {
-    const int k = blockIdx.y;
-    const int i0 = blockIdx.x * APPEND_ROWS;
+__global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long long nrows, int I, int J, int ldin,
+                                                           T *store, int lds, int S, int vec_ok,
+                                                           unsigned long long *dxa, unsigned long long *dxb,
+                                                           unsigned long long *xc_new, DevStatus *status) {
+    constexpr int V = 16 / sizeof(T);
+    constexpr int NW = APPEND_THREADS / 32;
+    const long long r0 = (long long)blockIdx.x * APPEND_ROWS;
+    const int rows = (int)min((long long)APPEND_ROWS, nrows - r0);
+    const int jc = blockIdx.y * (APPEND_THREADS * V) + threadIdx.x * V;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ unsigned long long slicesum;
-    if (threadIdx.x == 0) slicesum = 0;
+    __shared__ unsigned long long rowp[APPEND_ROWS][NW];
+    __shared__ unsigned long long slice_acc[APPEND_ROWS + 1];
+    __shared__ int range_flag;
+    if (threadIdx.x == 0) range_flag = 0;
+    for (int t = threadIdx.x; t <= APPEND_ROWS; t += APPEND_THREADS) slice_acc[t] = 0;
     __syncthreads();
+    unsigned long long cs[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) cs[v] = 0;
     bool bad = false, range = false;
-    unsigned long long wslice = 0;
-    for (int i = i0 + warp; i < min(I, i0 + APPEND_ROWS); i += 8) {
-        const T *src = Xin + ((long long)k * I + i) * ldin;
-        T *dst = store + ((long long)k * I + i) * lds;
-        unsigned long long rs = 0;
-        for (int j = lane; j < J; j += 32) {
-            T x = src[j];
-            dst[j] = x;
-            unsigned long long q = 0;
-            if (!isfinite(x)) bad = true;
-            else if (!qsquare(x, S, &q)) range = true;
-            if (rs + q < rs) range = true;
-            rs += q;
+    const bool vec = vec_ok && jc + V <= J;
+    for (int t = 0; t < rows; ++t) {
+        const long long r = r0 + t;
+        unsigned long long rp = 0;
+        if (jc < J) {
+            const T *src = Xin + r * ldin + jc;
+            T *dst = store + r * lds + jc;
+            T x[V];
+            if (vec) {
+                *reinterpret_cast<uint4 *>(x) = *reinterpret_cast<const uint4 *>(src);
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(x);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    x[v] = jc + v < J ? src[v] : T(0);
+                    if (jc + v < J) dst[v] = x[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                unsigned long long q = 0;
+                if (!isfinite(x[v])) bad = true;
+                else if (!qsquare(x[v], S, &q)) range = true;
+                if (cs[v] + q < cs[v]) range = true;
+                cs[v] += q;
+                if (rp + q < rp) range = true;
+                rp += q;
+            }
         }
+#pragma unroll
         for (int o = 16; o; o >>= 1) {
-            unsigned long long other = __shfl_xor_sync(0xffffffffu, rs, o);
-            if (rs + other < rs) range = true;
-            rs += other;
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, rp, o);
+            if (rp + other < rp) range = true;
+            rp += other;
         }
-        if (lane == 0) {
-            add_checked(&dxa[i], rs, status);
-            if (wslice + rs < wslice) range = true;
-            wslice += rs;
-        }
+        if (lane == 0) rowp[t][warp] = rp;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&status->err, ERR_NONFINITE);
-    if (__any_sync(0xffffffffu, range) && lane == 0) atomicOr(&status->err, ERR_RANGE);
-    if (lane == 0 && wslice) {
-        unsigned long long old = atomicAdd(&slicesum, wslice);
-        if (old + wslice < old) atomicOr(&status->err, ERR_RANGE);
+    if (range) range_flag = 1;
+    __syncthreads();
+    // rows: x_a[i] += row sum; slice sums gathered per slice in shared memory
+    const long long k_first = r0 / I;
+    for (int t = threadIdx.x; t < rows; t += APPEND_THREADS) {
+        unsigned long long s = 0;
+        bool ov = false;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (s + rowp[t][w] < s) ov = true;
+            s += rowp[t][w];
+        }
+        const long long r = r0 + t;
+        const long long k = r / I;
+        const int i = (int)(r - k * I);
+        add_checked(&dxa[i], s, status);
+        if (s) {
+            const unsigned long long old = atomicAdd(&slice_acc[k - k_first], s);
+            if (old + s < old) ov = true;
+        }
+        if (ov) range_flag = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) add_checked(&xc_new[k], slicesum, status);
-}
-
-// Column pass: x_b from the rows just written, a thread per column over a
-// block of APPEND_COL_ROWS rows (reads are coalesced across the threads).
-template <typename T>
-__global__ void __launch_bounds__(256) k_append_cols(const T *store, long long rows, int J, int lds, int S,
-                                                     unsigned long long *dxb, DevStatus *status) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= J) return;
-    const long long r0 = (long long)blockIdx.y * APPEND_COL_ROWS;
-    const long long r1 = min(rows, r0 + APPEND_COL_ROWS);
-    unsigned long long cs = 0;
-    bool range = false;
-    for (long long r = r0; r < r1; ++r) {
-        unsigned long long q = 0;
-        const T x = store[r * lds + j];
-        if (isfinite(x) && !qsquare(x, S, &q)) range = true;
-        if (cs + q < cs) range = true;
-        cs += q;
-    }
-    if (range) atomicOr(&status->err, ERR_RANGE);
-    add_checked(&dxb[j], cs, status);
+    const int nslices = (int)((r0 + rows - 1) / I - k_first) + 1;
+    for (int t = threadIdx.x; t < nslices; t += APPEND_THREADS) add_checked(&xc_new[k_first + t], slice_acc[t], status);
+    // columns: x_b[j] += column sums of this CTA's rows
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (jc + v < J) add_checked(&dxb[jc + v], cs[v], status);
+    if (threadIdx.x == 0 && range_flag) atomicOr(&status->err, ERR_RANGE);
 }
 
 cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
                           int lds, int S, unsigned long long *dxa, unsigned long long *dxb,
                           unsigned long long *xc_new, DevStatus *status, cudaStream_t st) {
     if (K_new <= 0) return cudaSuccess;
-    dim3 grid((I + APPEND_ROWS - 1) / APPEND_ROWS, (unsigned)K_new);
-    const long long rows = K_new * I;
-    dim3 cgrid((J + 255) / 256, (unsigned)((rows + APPEND_COL_ROWS - 1) / APPEND_COL_ROWS));
-    count_launches(2);
-    if (dtype == 0) {
-        k_append<double><<<grid, 256, 0, st>>>((const double *)Xin, I, J, ldin, (double *)store, lds, S, dxa,
-                                               xc_new, status);
-        k_append_cols<double><<<cgrid, 256, 0, st>>>((const double *)store, rows, J, lds, S, dxb, status);
-    } else {
-        k_append<float><<<grid, 256, 0, st>>>((const float *)Xin, I, J, ldin, (float *)store, lds, S, dxa,
-                                              xc_new, status);
-        k_append_cols<float><<<cgrid, 256, 0, st>>>((const float *)store, rows, J, lds, S, dxb, status);
-    }
+    const long long nrows = K_new * I;
+    const int V = dtype == 0 ? 2 : 4;
+    dim3 grid((unsigned)((nrows + APPEND_ROWS - 1) / APPEND_ROWS), (J + APPEND_THREADS * V - 1) / (APPEND_THREADS * V));
+    const int vec_ok = ldin % V == 0 && lds % V == 0 && ((uintptr_t)Xin & 15) == 0 && ((uintptr_t)store & 15) == 0;
+    count_launches(1);
+    if (dtype == 0)
+        k_append<double><<<grid, APPEND_THREADS, 0, st>>>((const double *)Xin, nrows, I, J, ldin, (double *)store, lds,
+                                                          S, vec_ok, dxa, dxb, xc_new, status);
+    else
+        k_append<float><<<grid, APPEND_THREADS, 0, st>>>((const float *)Xin, nrows, I, J, ldin, (float *)store, lds,
+                                                         S, vec_ok, dxa, dxb, xc_new, status);
     return cudaGetLastError();
 }
 
@@ -445,9 +471,85 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams g) {
     if (lane == 0) g.rowsq[(long long)rep * Kp * g.nI + row] = t;
 }
 
+// bfloat16 summaries with their transposed copy in one pass: a CTA gathers
+// 32 rows x 256 columns of one summary slice into shared memory, writes them
+// row-major (Xs) and column-major (Xt, the operand of the mode-2 MTTKRP).
+// Repetitions are the fastest grid index, so the CTAs of one slice in every
+// summary run together (the new slices are in all of them).  Each lane sums
+// its columns in the same order as k_gather, so the row sums of squares are
+// the same numbers.
+constexpr int GT_ROWS = 32, GT_COLS = 256;
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
+    const int tiles_i = (g.nI + GT_ROWS - 1) / GT_ROWS;
+    const int rep = (int)(blockIdx.x % g.nrep);
+    const long long tix = blockIdx.x / g.nrep;
+    const int kk = (int)(tix / tiles_i), ii0 = (int)(tix % tiles_i) * GT_ROWS;
+    const int Kp = g.nK + g.K_new;
+    if (kk >= Kp) return;
+    const int rows = min(GT_ROWS, g.nI - ii0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int *Is = g.samples + (long long)(rep * 3 + 0) * g.samp_stride;
+    const int *Js = g.samples + (long long)(rep * 3 + 1) * g.samp_stride;
+    const int *Ks = g.samples + (long long)(rep * 3 + 2) * g.samp_stride;
+    const int gk = kk < g.nK ? Ks[kk] : g.K_old + (kk - g.nK);
+    __shared__ __nv_bfloat16 tile[GT_ROWS][GT_COLS + 2];
+    SqF acc[GT_ROWS / 8];
+    __nv_bfloat16 *xs = (__nv_bfloat16 *)g.Xs + rep * g.xrs + (long long)kk * g.nI * g.ldj;
+    __nv_bfloat16 *xt = (__nv_bfloat16 *)g.Xt + rep * g.xtrs + (long long)kk * g.nJ * g.ldi;
+    for (int j0 = 0; j0 < g.ldj; j0 += GT_COLS) {
+#pragma unroll
+        for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
+            const int r = warp + 8 * rr;
+            if (r < rows) {
+                const TS *src = (const TS *)g.store + ((long long)gk * g.I + Is[ii0 + r]) * g.lds;
+                __nv_bfloat16 *dst = xs + (long long)(ii0 + r) * g.ldj;
+                for (int c = lane; c < GT_COLS && j0 + c < g.ldj; c += 32) {
+                    const int jj = j0 + c;
+                    const __nv_bfloat16 v = Quant<__nv_bfloat16>::q(jj < g.nJ ? src[Js[jj]] : (TS)0);
+                    dst[jj] = v;
+                    tile[r][c] = v;
+                    acc[rr].add(widen_elem(v));
+                }
+            }
+        }
+        __syncthreads();
+        // Xt[kk][jj][ii0 + r]: 16 threads per column jj, two rows each
+        const int jn = min(GT_COLS, g.nJ - j0);
+        for (int e = threadIdx.x; e < jn * 16; e += blockDim.x) {
+            const int c = e >> 4, r = (e & 15) * 2;
+            if (r < rows) {
+                __nv_bfloat16 *o = xt + (long long)(j0 + c) * g.ldi + ii0 + r;
+                if (r + 1 < rows) {
+                    *reinterpret_cast<__nv_bfloat162 *>(o) = __halves2bfloat162(tile[r][c], tile[r + 1][c]);
+                } else {
+                    o[0] = tile[r][c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
+        const int r = warp + 8 * rr;
+        if (r < rows) {
+            const double t = acc[rr].total();
+            if (lane == 0) g.rowsq[(long long)rep * Kp * g.nI + (long long)kk * g.nI + ii0 + r] = t;
+        }
+    }
+}
+
 cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStream_t st) {
     const long long rows = (long long)(g.nK + g.K_new) * g.nI;
     if (rows <= 0 || g.nrep <= 0) return cudaSuccess;
+    if (xelem == 2 && g.Xt) {
+        const long long tiles = (long long)(g.nK + g.K_new) * ((g.nI + GT_ROWS - 1) / GT_ROWS) * g.nrep;
+        count_launches(1);
+        if (sdtype == 0) k_gather_bf16_t<double><<<(unsigned)tiles, 256, 0, st>>>(g);
+        else k_gather_bf16_t<float><<<(unsigned)tiles, 256, 0, st>>>(g);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)((rows + 7) / 8), g.nrep);
     count_launches(1);
     if (sdtype == 0) {

@@ -458,7 +458,10 @@ bool tc_supported(int R, int NC) {
 // Work split for one mode: CTAs = nrep x npb x nks, about two per SM.
 void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc) {
     *npb = (NP + TC_M - 1) / TC_M;
-    long long target = 2LL * num_sms;
+    // one wave at two CTAs per SM, less one slot per repetition for the V^-1
+    // kernel that runs beside the pass (a full grid would push CTAs into a
+    // second wave behind it)
+    long long target = 2LL * num_sms - nrep;
     long long n = target / std::max(1LL, (long long)nrep * *npb);
     n = std::max(1LL, std::min<long long>(n, Kp));
     *spc = std::min(TC_MAX_SPC, (int)((Kp + n - 1) / n));

@@ -196,7 +196,15 @@ struct GatherParams {
     int ldj;
     long long xrs;
     double *rowsq;            // [rep][Kp * nI]
+    void *Xt;                 // bfloat16 only, may be null: transposed copy [rep][Kp][nJ][ldi]
+    int ldi;
+    long long xtrs;
 };
+
+// rows of one tail CTA (float32 / bfloat16 summaries): the partial-sum
+// reduction after each MTTKRP pass is spread over ceil(n / TAIL_ROWS) CTAs
+// per repetition
+constexpr int TAIL_ROWS = 16;
 
 // ---------------------------------------------------------------------------
 // Problem description handed to the ALS kernels.  All repetitions share the
@@ -228,7 +236,7 @@ struct AlsDesc {
     DF *Gf;                // Grams in double-float [rep][3][R][R] (float32 factor path)
     DF *nx2f, *fitpf;      // ||X_s||^2 and the previous fit in double-float [rep]
     int *tail_cnt;         // [rep] chunk CTAs finished (the last one completes the mode; zero between uses)
-    int tchunks;           // row chunks of 128 for the largest mode
+    int tchunks;           // row chunks of TAIL_ROWS for the largest mode
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
