@@ -594,6 +594,10 @@ __host__ __device__ constexpr size_t tail_smem_bytes() {
 template <int RP>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode) {
     const int rep = blockIdx.y, chunk = blockIdx.x;
+    // programmatic dependent launch: let the next MTTKRP pass be scheduled,
+    // then wait for the pass this tail reduces (and its memory)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (d.conv[rep]) return;
     const int R = d.R, n = d.n[mode], P = d.P[mode];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1074,12 +1078,26 @@ cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
     if (d.elem != 0) {
         // float32 factors: row kernel (partial reduction fused) + finish kernel
         const int RP = rp_of(d.R);
-        dim3 grid((d.n[mode] + TAIL_ROWS - 1) / TAIL_ROWS, d.nrep);
-        if (RP == 8) k_tail_rows<8><<<grid, TAIL_THREADS, tail_smem_bytes<8>(), st>>>(d, mode);
-        else if (RP == 16) k_tail_rows<16><<<grid, TAIL_THREADS, tail_smem_bytes<16>(), st>>>(d, mode);
-        else k_tail_rows<32><<<grid, TAIL_THREADS, tail_smem_bytes<32>(), st>>>(d, mode);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((d.n[mode] + TAIL_ROWS - 1) / TAIL_ROWS, d.nrep);
+        cfg.blockDim = dim3(TAIL_THREADS);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         count_launches(1);
-        return cudaGetLastError();
+        if (RP == 8) {
+            cfg.dynamicSmemBytes = tail_smem_bytes<8>();
+            return cudaLaunchKernelEx(&cfg, k_tail_rows<8>, d, mode);
+        }
+        if (RP == 16) {
+            cfg.dynamicSmemBytes = tail_smem_bytes<16>();
+            return cudaLaunchKernelEx(&cfg, k_tail_rows<16>, d, mode);
+        }
+        cfg.dynamicSmemBytes = tail_smem_bytes<32>();
+        return cudaLaunchKernelEx(&cfg, k_tail_rows<32>, d, mode);
     }
     cudaError_t e = reduce_dispatch(d, mode, st);
     if (e != cudaSuccess) return e;

@@ -169,6 +169,13 @@ template <int N>
 __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     constexpr int RH = N / 2;
     const int rep = blockIdx.y;
+    // programmatic dependent launch: the next kernel of the stream may be
+    // scheduled now.  This grid reads the previous kernel's results (the
+    // factors, the convergence flags) only after griddepcontrol.wait below;
+    // the summary tiles do not depend on it, so warp 0 starts streaming them
+    // at once.  The flag read here may predate a convergence decided by the
+    // kernel just before; it is read again after the wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (p.conv[rep]) return;
     const int pb = blockIdx.x % p.npb, ks = blockIdx.x / p.npb;
     const int k0 = ks * p.spc, k1 = min(p.Kp, k0 + p.spc);
@@ -210,6 +217,8 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     const uint32_t tmem = sh->tmem_base;
     const int R = p.R;
     if (warp != 0) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        if (threadIdx.x == 32 && p.conv[rep]) *abort_flag = 2;  // converged just before: skip, no error
         // warps 1-5 (160 threads), while warp 0 already streams X: the B operand
         // (rows n < RH: bf16(F), rows RH..: bf16(F - bf16(F)); K-major, swizzled),
         // one thread per contraction index j, and the epilogue weights C(kk, :)
@@ -365,19 +374,20 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                     if (lane == 0) sh->red[quarter][r] = v;
                 }
                 epi_bar();
-                if (etid < R) {
+                if (etid < R && *abort_flag != 2) {
                     float s = ((sh->red[0][etid] + sh->red[1][etid]) + sh->red[2][etid]) + sh->red[3][etid];
                     part[((long long)pb * p.Kp + kk) * p.pr + etid] = s;
                 }
                 epi_bar();
             }
         }
-        if (p.epi == 0 && valid) {
+        const bool skipped = *abort_flag == 2;
+        if (p.epi == 0 && valid && !skipped) {
 #pragma unroll
             for (int r = 0; r < RH; ++r)
                 if (r < R) part[((long long)ks * p.NP + pidx) * p.pr + r] = acc[r];
         }
-        if (p.bytes_ctr && etid == 0) {
+        if (p.bytes_ctr && etid == 0 && !skipped) {
             const int rows = min(TC_M, p.NP - pb * TC_M);
             atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl);
         }
@@ -499,11 +509,19 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     p.stages = std::max(2, stages);
     const size_t smem = tc_smem_bytes(p.nkb, N, p.stages);
     *P_out = epi == 0 ? p.nks : p.npb;
-    dim3 grid(p.npb * p.nks, nrep);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.npb * p.nks, nrep);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     count_launches(1);
-    if (N == 32) k_mtt_tc<32><<<grid, 192, smem, st>>>(tmap, p);
-    else k_mtt_tc<64><<<grid, 192, smem, st>>>(tmap, p);
-    return cudaGetLastError();
+    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32>, tmap, p);
+    return cudaLaunchKernelEx(&cfg, k_mtt_tc<64>, tmap, p);
 }
 
 // Raise the dynamic shared-memory limit of the tensor-core kernels once,
