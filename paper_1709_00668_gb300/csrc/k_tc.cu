@@ -130,6 +130,7 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 struct TcParams {
     int nrep, R, NP, NC, Kp;
     int nkb, npb, spc, nks;
+    int br;                  // summary rows per tile (tiles of equal height, a multiple of 8, <= 128)
     int epi;                 // 0 ROWSUM (weights C(kk)), 1 COLSUM (weights A(p))
     const float *F;          // contraction factor [rep][NC][R]
     long long frs;
@@ -206,6 +207,16 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         sh->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (p.br < TC_M) {
+        // TMA fills rows [0, br) of a stage; rows [br, 128) stay zero (whole
+        // 8-row swizzle atoms), so the M = 128 products add nothing there
+        const int zb = (TC_M - p.br) * 128 / 16;  // 16-byte words per stage
+        for (int e = threadIdx.x; e < S * zb; e += blockDim.x) {
+            const int st = e / zb, w = e % zb;
+            reinterpret_cast<uint4 *>(ring + (size_t)st * TC_BOX_BYTES + (size_t)p.br * 128)[w] = make_uint4(0, 0, 0, 0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
                      "r"(2 * N));
@@ -257,8 +268,8 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             for (int t = 0; t < nsl && !*abort_flag; ++t) {
                 for (int kb = 0; kb < p.nkb; ++kb) {
                     if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
-                    mbar_expect_tx(&sh->full[stage], TC_BOX_BYTES);
-                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, &tmap, kb * 64, pb * TC_M,
+                    mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
+                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, &tmap, kb * 64, pb * p.br,
                                 rep * p.Kp + k0 + t, &sh->full[stage]);
                     ++issued;
                     if (++stage == S) {
@@ -320,8 +331,8 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         // epilogue: thread <-> tile row
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const int pidx = pb * TC_M + row;
-        const bool valid = pidx < p.NP;
+        const int pidx = pb * p.br + row;
+        const bool valid = row < p.br && pidx < p.NP;
         const float *W = p.W + rep * p.wrs;
         float acc[RH];
         float arow[RH];
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 if (r < R) part[((long long)ks * p.NP + pidx) * p.pr + r] = acc[r];
         }
         if (p.bytes_ctr && etid == 0 && !skipped) {
-            const int rows = min(TC_M, p.NP - pb * TC_M);
+            const int rows = min(p.br, p.NP - pb * p.br);
             atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl);
         }
     }
@@ -436,15 +447,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over [slices][NP][ld] bfloat16, box 64 x 128 x 1, 128-byte swizzle,
-// zero fill outside (columns >= NC, rows >= NP).
+// Rows per tile: ceil(NP / 128) tiles of equal height (rounded up to a
+// multiple of 8, the swizzle atom), so every CTA streams the same bytes.
+int tc_box_rows(int NP) {
+    const int npb = (NP + TC_M - 1) / TC_M;
+    const int br = (NP + npb - 1) / npb;
+    return std::min(TC_M, (br + 7) / 8 * 8);
+}
+
+// 3-D map over [slices][NP][ld] bfloat16, box 64 x tc_box_rows(NP) x 1,
+// 128-byte swizzle, zero fill outside (columns >= NC, rows >= NP).
 cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     if (((uintptr_t)base & 15) || (ld * 2) % 16) return cudaErrorInvalidValue;
     cuuint64_t dims[3] = {(cuuint64_t)NC, (cuuint64_t)NP, (cuuint64_t)nslices};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)NP * ld * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)TC_M, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)tc_box_rows(NP), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -491,6 +510,7 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     p.Kp = Kp;
     p.nkb = (NC + 63) / 64;
     tc_tiles(nrep, NP, Kp, num_sms, &p.npb, &p.nks, &p.spc);
+    p.br = tc_box_rows(NP);
     p.epi = epi;
     p.F = F;
     p.frs = frs;
