@@ -80,6 +80,7 @@ class Options:
     lambda_mode: int = 0
     fixed_iters: bool = False
     prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16
+    refine_sweeps: int = 0     # bf16 only: ALS iterations on the split summary after the bf16 ALS
 
 
 @dataclass
@@ -170,6 +171,16 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
     b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
     return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def split_bf16(Xs: np.ndarray) -> np.ndarray:
+    """hi + lo with hi = bf16(x) and lo = bf16(x - hi), x as float32 (the
+    difference is exact in float32); returns float64.  |x - (hi + lo)| is at
+    most one half unit in the last place of lo: about 2^-17 |x|."""
+    x = np.ascontiguousarray(Xs, dtype=np.float32)
+    hi = bf16_round(x)
+    lo = bf16_round((x - hi.astype(np.float32)).astype(np.float32))
+    return hi + lo
 
 
 def summary_values(Xs: np.ndarray, prec: str) -> np.ndarray:
@@ -473,6 +484,12 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
               init_factor(Js, R, 1, rho, state.batch, opts),
               init_factor(Kp, R, 2, rho, state.batch, opts)]
         res = cp_als(Xs, U0, opts.tol, opts.max_iters, opts.fixed_iters)
+        if opts.prec == "bf16" and opts.refine_sweeps > 0:
+            # refinement: continue the same ALS from its factors for a fixed
+            # number of iterations on the split (hi + lo) summary
+            Xr = split_bf16(summary(X_all, Is, Js, Kp))
+            ref = cp_als(Xr, res.U, opts.tol, opts.refine_sweeps, fixed_iters=True)
+            res = ALSResult(U=ref.U, lam=ref.lam, iters=res.iters, fit=ref.fit, flags=res.flags | ref.flags)
         flags |= res.flags
         # step 6: normalise over shared rows
         Us, lam_s, f = normalize_shared(res.U, res.lam, nK)

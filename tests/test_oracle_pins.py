@@ -201,6 +201,43 @@ def test_bf16_round_matches_torch():
     assert np.array_equal(O.bf16_round(x), ref)
 
 
+def test_split_bf16_bound_hi_and_exact_cases():
+    """hi + lo split: hi is the bfloat16 rounding itself, the pair carries
+    about 16 significant bits (|x - (hi + lo)| <= 2^-16 |x|), and values with
+    at most 16 significant bits are represented exactly."""
+    rng = np.random.default_rng(41)
+    x = (rng.standard_normal(20000) * np.exp2(rng.integers(-40, 40, 20000))).astype(np.float32)
+    y = O.split_bf16(x)
+    assert np.all(np.abs(x.astype(np.float64) - y) <= np.exp2(-16) * np.abs(x.astype(np.float64)))
+    hi = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    lo = y - hi
+    # lo is itself a bfloat16 value and no larger than half an ulp of hi
+    assert np.array_equal(O.bf16_round(lo.astype(np.float32)), lo)
+    assert np.all(np.abs(lo) <= np.exp2(-8) * np.abs(hi) + 1e-300)
+    m = rng.integers(1, 2 ** 16, 3000)
+    e = rng.integers(-30, 30, 3000)
+    x16 = np.ldexp(m.astype(np.float64), e).astype(np.float32)  # <= 16 significant bits
+    assert np.array_equal(O.split_bf16(x16), x16.astype(np.float64))
+
+
+def test_refinement_brings_bf16_als_to_float32_accuracy():
+    """ALS continued on the split summary lands at the float32 solution:
+    much closer to the float32 ALS than the bfloat16 ALS it started from."""
+    X = synth.planted_dense(30, 26, 24, 3, noise=0.01, seed=42, dtype=torch.float32).X.numpy()
+    rng = np.random.default_rng(43)
+    U0 = [rng.random((30, 3)), rng.random((26, 3)), rng.random((24, 3))]
+    ref = O.cp_als(X.astype(np.float64), U0, 0.0, 200, fixed_iters=True)
+    b16 = O.cp_als(O.summary_values(X, "bf16"), U0, 0.0, 200, fixed_iters=True)
+    fine = O.cp_als(O.split_bf16(X), b16.U, 0.0, 60, fixed_iters=True)
+
+    def dist(a, b):  # unit-column factors from the same start: no permutation to undo
+        return max(float(np.max(np.abs(ua - ub))) for ua, ub in zip(a.U, b.U))
+    d16, dfine = dist(b16, ref), dist(fine, ref)
+    assert d16 > 1e-4
+    assert dfine < d16 / 20
+    assert abs(fine.fit - ref.fit) < abs(b16.fit - ref.fit) / 20 + 1e-9
+
+
 # --------------------------------------------------------------- MTTKRP ----
 def test_mttkrp_bruteforce():
     rng = np.random.default_rng(5)
