@@ -66,6 +66,7 @@ typedef enum { SBT_PREC_F64 = 0, SBT_PREC_F32 = 1, SBT_PREC_BF16 = 2 } sbt_prec;
 #define SBT_FLAG_CHOL_REGULARIZED 1 /* a Gram Hadamard product was not positive definite */
 #define SBT_FLAG_ZERO_COLUMN 2      /* a factor column had zero norm */
 #define SBT_FLAG_SAMPLE_LT_RANK 4   /* a sample had fewer indices than R */
+#define SBT_FLAG_NO_REFINE 8        /* refine_sweeps requested but not run (no tensor-core plan) */
 
 typedef struct {
     int32_t dtype;     /* sbt_dtype of data */
@@ -90,6 +91,10 @@ typedef struct {
                               up to K_capacity slices (sbt_reserve); 0: size on demand */
     void *cuda_stream;     /* cudaStream_t for all device work; NULL: the legacy default stream */
     int32_t check_every;   /* ALS convergence poll interval in iterations (0: 4) */
+    int32_t refine_sweeps; /* SBT_PREC_BF16 only: after the bf16 ALS, this many ALS iterations whose
+                              MTTKRP reads the split summary x ~ hi + lo (hi = bf16(x), lo =
+                              bf16(x - hi), ~16 significant bits); 0: none.  Needs the
+                              tensor-core MTTKRP (R <= 32); otherwise flagged and skipped */
 } sbt_options;
 
 typedef struct {

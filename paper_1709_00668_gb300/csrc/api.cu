@@ -107,8 +107,10 @@ struct DeviceGuard {
 // its transposed copy
 struct TcPlan {
     bool on = false;
-    CUtensorMap m1;  // [slice][ii][jj]: contraction over jj
-    CUtensorMap m2;  // [slice][jj][ii]: contraction over ii
+    bool split = false;  // refinement: add the lo parts (m1lo, m2lo) into every product
+    CUtensorMap m1;      // [slice][ii][jj]: contraction over jj
+    CUtensorMap m2;      // [slice][jj][ii]: contraction over ii
+    CUtensorMap m1lo, m2lo;
 };
 
 }  // namespace
@@ -148,6 +150,7 @@ struct sbt_ctx {
     // workspace
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
+    Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     cudaStream_t side = nullptr;  // runs V^-1 of a mode beside its MTTKRP pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TcPlan tc;
@@ -214,6 +217,7 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (!(o->tol >= 0.0)) return fail(SBT_E_INVALID, "tol must be >= 0");
     if (o->prec < SBT_PREC_F64 || o->prec > SBT_PREC_BF16) return fail(SBT_E_INVALID, "unknown precision");
     if (o->lambda_mode != 0 && o->lambda_mode != 1) return fail(SBT_E_INVALID, "lambda_mode must be 0 or 1");
+    if (o->refine_sweeps < 0 || o->refine_sweeps > 1000) return fail(SBT_E_INVALID, "refine_sweeps out of [0, 1000]");
     return SBT_OK;
 }
 
@@ -382,12 +386,12 @@ static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, i
     unsigned *err = &c->status.as<DevStatus>()->err;
     int P = 0;
     if (mode == 0)
-        return launch_mttkrp_tc(tc->m1, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
+        return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
                                 (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
     if (mode == 1)
-        return launch_mttkrp_tc(tc->m2, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
+        return launch_mttkrp_tc(tc->m2, tc->split ? &tc->m2lo : nullptr, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
                                 (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
-    return launch_mttkrp_tc(tc->m1, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
+    return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
                             (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
 }
 
@@ -776,6 +780,12 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
     als_shape(c, d, r, n, u.ldj, u.nK, c->elem, c->opt.max_iters);
     TRY(als_sizes(c, d, update_part_bytes(c, u, bound), z));
     if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * 2));
+    if (u.tc && c->opt.refine_sweeps > 0) {
+        TRY(z.need(c->Xlo, (size_t)r * u.xrs * 2));
+        TRY(z.need(c->Xtlo, (size_t)r * u.Kp * u.nJ * u.ldi * 2));
+        TRY(z.need(c->rowsq2, (size_t)r * u.Kp * u.nI * 8));
+        TRY(z.need(c->iters_main, (size_t)r * 4));
+    }
     const size_t pmax = (size_t)u.samp_stride;
     TRY(z.need(c->nu, (size_t)r * 3 * R * 8));
     TRY(z.need(c->cnew, (size_t)r * u.K_new * R * 8));
@@ -798,7 +808,8 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->status, &c->samples, &c->khi, &c->klo, &c->Xs, &c->rowsq, &c->U[0], &c->U[1], &c->U[2], &c->M,
             &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
-            &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes};
+            &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
+            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main};
 }
 
 // device bytes after the needs of z (every buffer at max(capacity, need))
@@ -930,6 +941,11 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         g.Xt = c->Xt.p;
         g.ldi = u.ldi;
         g.xtrs = (long long)Kp * nJ * u.ldi;
+        if (c->opt.refine_sweeps > 0) {  // and the lo parts of the split summary
+            g.Xlo = c->Xlo.p;
+            g.Xtlo = c->Xtlo.p;
+            g.rowsq2 = c->rowsq2.as<double>();
+        }
     }
     CK(launch_gather(g, c->sdtype, c->elem, c->stream));
     // 4. CP-ALS on the r summaries
@@ -949,6 +965,27 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
                           c->batch, c->rowsq.as<double>(), c->stream));
     TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
+    // refinement sweeps: the same ALS continued for refine_sweeps iterations
+    // with every MTTKRP on the split summary (hi + lo)
+    bool refined = false, no_refine = false;
+    if (c->opt.refine_sweeps > 0 && c->elem == 2) {
+        if (!tc.on) {
+            no_refine = true;
+        } else {
+            CK(make_summary_tmap(&tc.m1lo, c->Xlo.p, nJ, nI, ldj, (long long)r * Kp));
+            CK(make_summary_tmap(&tc.m2lo, c->Xtlo.p, nI, nJ, u.ldi, (long long)r * Kp));
+            CK(cudaMemcpyAsync(c->iters_main.p, d.iters, (size_t)r * 4, cudaMemcpyDeviceToDevice, c->stream));
+            CK(launch_refine_start(d, c->rowsq2.as<double>(), c->stream));
+            AlsDesc dr = d;
+            dr.fixed_iters = 1;
+            dr.max_iters = c->opt.refine_sweeps;
+            tc.split = true;
+            const sbt_status rs = run_als(c, dr, c->opt.refine_sweeps, &tc);
+            tc.split = false;
+            TRY(rs);
+            refined = true;
+        }
+    }
     // 5. normalise, match, project back; 6. commit
     const int pmax = (int)samp_stride;
     MergeDesc m;
@@ -996,7 +1033,8 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     char *hb = c->h_stats.as<char>();
     CK(cudaMemcpyAsync(hb, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
     size_t off = sizeof(DevStatus);
-    CK(cudaMemcpyAsync(hb + off, d.iters, (size_t)r * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hb + off, refined ? c->iters_main.p : (void *)d.iters, (size_t)r * 4,
+                       cudaMemcpyDeviceToHost, c->stream));
     off += (size_t)r * 4;
     CK(cudaMemcpyAsync(hb + off, d.fit, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
     off += (size_t)r * 8;
@@ -1033,6 +1071,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     const int *fl = (const int *)(hb + off);
     off += (size_t)r * 4;
     const int *pm = (const int *)(hb + off);
+    if (no_refine) st.flags |= SBT_FLAG_NO_REFINE;
     for (int q = 0; q < r; ++q) {
         st.iters[q] = it[q];
         st.fit[q] = ft[q];
@@ -1303,13 +1342,13 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     }
     if (e == cudaSuccess) {
         if (mode == 0)
-            e = launch_mttkrp_tc(map, 0, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)C, 0,
+            e = launch_mttkrp_tc(map, nullptr, 0, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)C, 0,
                                  (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
         else if (mode == 1)
-            e = launch_mttkrp_tc(map, 0, 1, R, (int)J, (int)I, (int)K, (const float *)A, 0, (const float *)C, 0,
+            e = launch_mttkrp_tc(map, nullptr, 0, 1, R, (int)J, (int)I, (int)K, (const float *)A, 0, (const float *)C, 0,
                                  (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
         else
-            e = launch_mttkrp_tc(map, 1, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)A, 0,
+            e = launch_mttkrp_tc(map, nullptr, 1, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)A, 0,
                                  (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
     }
     if (e == cudaSuccess) e = launch_reduce_only(d, mode, st);

@@ -939,6 +939,41 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
     }
 }
 
+// Start of the refinement sweeps (one CTA per repetition): ||X_s||^2 of the
+// split summary (hi + lo) from its row sums, fixed order as in k_prepare;
+// the fit history, iteration counts and convergence flags start again.  The
+// factors and Grams carry over from the bfloat16 ALS.
+__global__ void __launch_bounds__(256) k_refine_start(AlsDesc d, const double *rowsq2) {
+    const int rep = blockIdx.x;
+    __shared__ double red[256];
+    const long long rows = (long long)d.n[2] * d.n[0];
+    const double *rq = rowsq2 + rep * rows;
+    double a = 0.0;
+    for (long long e = threadIdx.x; e < rows; e += blockDim.x) a += rq[e];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = 128; s; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        d.normX2[rep] = red[0];
+        if (d.nx2f) {
+            d.nx2f[rep] = df_from_double(red[0]);
+            d.fitpf[rep] = DF{0.f, 0.f};
+        }
+        d.fit_prev[rep] = 0.0;
+        d.iters[rep] = 0;
+        d.conv[rep] = 0;
+    }
+}
+
+cudaError_t launch_refine_start(const AlsDesc &d, const double *rowsq2, cudaStream_t st) {
+    k_refine_start<<<d.nrep, 256, 0, st>>>(d, rowsq2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // host side
 static int rp_of(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams g) {
 // the same numbers.
 constexpr int GT_ROWS = 32, GT_COLS = 256;
 
-template <typename TS>
+template <typename TS, bool SPLIT>
 __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
     const int tiles_i = (g.nI + GT_ROWS - 1) / GT_ROWS;
     const int rep = (int)(blockIdx.x % g.nrep);
@@ -495,9 +495,12 @@ __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
     const int *Ks = g.samples + (long long)(rep * 3 + 2) * g.samp_stride;
     const int gk = kk < g.nK ? Ks[kk] : g.K_old + (kk - g.nK);
     __shared__ __nv_bfloat16 tile[GT_ROWS][GT_COLS + 2];
-    SqF acc[GT_ROWS / 8];
-    __nv_bfloat16 *xs = (__nv_bfloat16 *)g.Xs + rep * g.xrs + (long long)kk * g.nI * g.ldj;
-    __nv_bfloat16 *xt = (__nv_bfloat16 *)g.Xt + rep * g.xtrs + (long long)kk * g.nJ * g.ldi;
+    __shared__ __nv_bfloat16 tlo[SPLIT ? GT_ROWS : 1][GT_COLS + 2];
+    SqF acc[GT_ROWS / 8], acc2[SPLIT ? GT_ROWS / 8 : 1];
+    const long long soff = rep * g.xrs + (long long)kk * g.nI * g.ldj;
+    const long long toff = rep * g.xtrs + (long long)kk * g.nJ * g.ldi;
+    __nv_bfloat16 *xs = (__nv_bfloat16 *)g.Xs + soff;
+    __nv_bfloat16 *xt = (__nv_bfloat16 *)g.Xt + toff;
     for (int j0 = 0; j0 < g.ldj; j0 += GT_COLS) {
 #pragma unroll
         for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
@@ -507,10 +510,19 @@ __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
                 __nv_bfloat16 *dst = xs + (long long)(ii0 + r) * g.ldj;
                 for (int c = lane; c < GT_COLS && j0 + c < g.ldj; c += 32) {
                     const int jj = j0 + c;
-                    const __nv_bfloat16 v = Quant<__nv_bfloat16>::q(jj < g.nJ ? src[Js[jj]] : (TS)0);
+                    const TS x = jj < g.nJ ? src[Js[jj]] : (TS)0;
+                    const __nv_bfloat16 v = Quant<__nv_bfloat16>::q(x);
                     dst[jj] = v;
                     tile[r][c] = v;
                     acc[rr].add(widen_elem(v));
+                    if constexpr (SPLIT) {
+                        // lo = bf16(x - hi), x as float32 (the difference is exact)
+                        const float hf = __bfloat162float(v);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn((float)x - hf);
+                        ((__nv_bfloat16 *)g.Xlo + soff)[(long long)(ii0 + r) * g.ldj + jj] = lo;
+                        tlo[r][c] = lo;
+                        acc2[rr].add(hf + __bfloat162float(lo));
+                    }
                 }
             }
         }
@@ -520,11 +532,20 @@ __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
         for (int e = threadIdx.x; e < jn * 16; e += blockDim.x) {
             const int c = e >> 4, r = (e & 15) * 2;
             if (r < rows) {
-                __nv_bfloat16 *o = xt + (long long)(j0 + c) * g.ldi + ii0 + r;
+                const long long oi = (long long)(j0 + c) * g.ldi + ii0 + r;
+                __nv_bfloat16 *o = xt + oi;
                 if (r + 1 < rows) {
                     *reinterpret_cast<__nv_bfloat162 *>(o) = __halves2bfloat162(tile[r][c], tile[r + 1][c]);
                 } else {
                     o[0] = tile[r][c];
+                }
+                if constexpr (SPLIT) {
+                    __nv_bfloat16 *ol = (__nv_bfloat16 *)g.Xtlo + toff + oi;
+                    if (r + 1 < rows) {
+                        *reinterpret_cast<__nv_bfloat162 *>(ol) = __halves2bfloat162(tlo[r][c], tlo[r + 1][c]);
+                    } else {
+                        ol[0] = tlo[r][c];
+                    }
                 }
             }
         }
@@ -534,8 +555,13 @@ __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
     for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
         const int r = warp + 8 * rr;
         if (r < rows) {
+            const long long ri = (long long)rep * Kp * g.nI + (long long)kk * g.nI + ii0 + r;
             const double t = acc[rr].total();
-            if (lane == 0) g.rowsq[(long long)rep * Kp * g.nI + (long long)kk * g.nI + ii0 + r] = t;
+            if (lane == 0) g.rowsq[ri] = t;
+            if constexpr (SPLIT) {
+                const double t2 = acc2[rr].total();
+                if (lane == 0) g.rowsq2[ri] = t2;
+            }
         }
     }
 }
@@ -546,8 +572,14 @@ cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStre
     if (xelem == 2 && g.Xt) {
         const long long tiles = (long long)(g.nK + g.K_new) * ((g.nI + GT_ROWS - 1) / GT_ROWS) * g.nrep;
         count_launches(1);
-        if (sdtype == 0) k_gather_bf16_t<double><<<(unsigned)tiles, 256, 0, st>>>(g);
-        else k_gather_bf16_t<float><<<(unsigned)tiles, 256, 0, st>>>(g);
+        const bool split = g.Xlo && g.Xtlo && g.rowsq2;
+        if (sdtype == 0) {
+            if (split) k_gather_bf16_t<double, true><<<(unsigned)tiles, 256, 0, st>>>(g);
+            else k_gather_bf16_t<double, false><<<(unsigned)tiles, 256, 0, st>>>(g);
+        } else {
+            if (split) k_gather_bf16_t<float, true><<<(unsigned)tiles, 256, 0, st>>>(g);
+            else k_gather_bf16_t<float, false><<<(unsigned)tiles, 256, 0, st>>>(g);
+        }
         return cudaGetLastError();
     }
     dim3 grid((unsigned)((rows + 7) / 8), g.nrep);

@@ -131,6 +131,7 @@ struct TcParams {
     int nrep, R, NP, NC, Kp;
     int nkb, npb, spc, nks;
     int br;                  // summary rows per tile (tiles of equal height, a multiple of 8, <= 128)
+    int split;               // 1: add the lo part of a split summary (second tensor map) into each product
     int epi;                 // 0 ROWSUM (weights C(kk)), 1 COLSUM (weights A(p))
     const float *F;          // contraction factor [rep][NC][R]
     long long frs;
@@ -167,7 +168,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
 }
 
 template <int N>
-__global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap, TcParams p) {
+__global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap,
+                                                   const __grid_constant__ CUtensorMap tmap_lo, TcParams p) {
     constexpr int RH = N / 2;
     const int rep = blockIdx.y;
     // programmatic dependent launch: the next kernel of the stream may be
@@ -265,12 +267,14 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             int stage = 0;
             uint32_t phase = 0;
             int issued = 0;
+            const int nkb2 = p.nkb * (1 + p.split);
             for (int t = 0; t < nsl && !*abort_flag; ++t) {
-                for (int kb = 0; kb < p.nkb; ++kb) {
+                for (int kb2 = 0; kb2 < nkb2; ++kb2) {
+                    const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
                     if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
                     mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
-                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, &tmap, kb * 64, pb * p.br,
-                                rep * p.Kp + k0 + t, &sh->full[stage]);
+                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * 64,
+                                pb * p.br, rep * p.Kp + k0 + t, &sh->full[stage]);
                     ++issued;
                     if (++stage == S) {
                         stage = 0;
@@ -305,7 +309,9 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * N);
                 bool ok = true;
-                for (int kb = 0; kb < p.nkb; ++kb) {
+                const int nkb2 = p.nkb * (1 + p.split);
+                for (int kb2 = 0; kb2 < nkb2; ++kb2) {
+                    const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
                     if (!tc_wait(&sh->full[stage], phase, abort_flag, p.err)) {
                         ok = false;
                         break;
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         tc_mma(d, sw128_desc(abase + k * 32), sw128_desc(bbase + kb * N * 128 + k * 32), idesc,
-                               (kb | k) != 0);
+                               (kb2 | k) != 0);
                     }
                     tc_commit(&sh->empty[stage]);
                     if (++stage == S) {
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
         if (p.bytes_ctr && etid == 0 && !skipped) {
             const int rows = min(p.br, p.NP - pb * p.br);
-            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl);
+            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl * (1 + p.split));
         }
     }
     tc_fence_before();
@@ -497,7 +503,8 @@ void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *sp
     *nks = (Kp + *spc - 1) / *spc;
 }
 
-cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
+cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo, int epi, int nrep, int R, int NP,
+                             int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
@@ -511,6 +518,8 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     p.nkb = (NC + 63) / 64;
     tc_tiles(nrep, NP, Kp, num_sms, &p.npb, &p.nks, &p.spc);
     p.br = tc_box_rows(NP);
+    p.split = tmap_lo ? 1 : 0;
+    const CUtensorMap &lo = tmap_lo ? *tmap_lo : tmap;
     p.epi = epi;
     p.F = F;
     p.frs = frs;
@@ -540,8 +549,8 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launches(1);
-    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32>, tmap, p);
-    return cudaLaunchKernelEx(&cfg, k_mtt_tc<64>, tmap, p);
+    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32>, tmap, lo, p);
+    return cudaLaunchKernelEx(&cfg, k_mtt_tc<64>, tmap, lo, p);
 }
 
 // Raise the dynamic shared-memory limit of the tensor-core kernels once,

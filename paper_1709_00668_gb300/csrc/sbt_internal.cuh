@@ -199,6 +199,8 @@ struct GatherParams {
     void *Xt;                 // bfloat16 only, may be null: transposed copy [rep][Kp][nJ][ldi]
     int ldi;
     long long xtrs;
+    void *Xlo, *Xtlo;         // bfloat16 with Xt only, may be null: lo parts bf16(x - hi), same layouts
+    double *rowsq2;           // with Xlo: row sums of (hi + lo)^2
 };
 
 // rows of one tail CTA (float32 / bfloat16 summaries): the partial-sum
@@ -278,6 +280,7 @@ cudaError_t set_als_kernel_attributes();
 cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
+cudaError_t launch_refine_start(const AlsDesc &d, const double *rowsq2, cudaStream_t st);
 cudaError_t launch_als_continue(cudaGraphConditionalHandle h, const int *conv, int nrep, int *passes,
                                 int max_passes, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);
@@ -287,7 +290,9 @@ long long partial_elems(const AlsDesc &d);  // per repetition
 bool tc_supported(int R, int NC);
 void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc);
 cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices);
-cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, int epi, int nrep, int R, int NP, int NC, int Kp,
+// tmap_lo: null, or the map of the lo part of a split summary (added into every product)
+cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo, int epi, int nrep, int R, int NP,
+                             int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,

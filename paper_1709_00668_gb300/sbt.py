@@ -43,6 +43,7 @@ PREC = {"f64": SBT_PREC_F64, "f32": SBT_PREC_F32, "bf16": SBT_PREC_BF16}
 SBT_FLAG_CHOL_REGULARIZED = 1
 SBT_FLAG_ZERO_COLUMN = 2
 SBT_FLAG_SAMPLE_LT_RANK = 4
+SBT_FLAG_NO_REFINE = 8
 
 EXPORTS = [
     "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
@@ -70,7 +71,8 @@ class SbtOptions(ctypes.Structure):
                 ("stream_id", ctypes.c_uint32), ("prec", ctypes.c_int32),
                 ("lambda_mode", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
                 ("K_capacity", ctypes.c_int64), ("max_batch", ctypes.c_int64),
-                ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32),
+                ("refine_sweeps", ctypes.c_int32)]
 
 
 class SbtStats(ctypes.Structure):

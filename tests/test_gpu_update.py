@@ -29,7 +29,8 @@ def _pair(sbt, X, K0, R, fac, *, prec="f32", **kw):
     ctx = sbt.SamBaTen(torch.from_numpy(X[:K0]).cuda(), R, factors=fac, prec=prec, **opts)
     oo = O.Options(s_I=opts["s_I"], s_J=opts["s_J"], s_K=opts["s_K"], r=opts["r"], tol=opts["tol"],
                    max_iters=opts["max_iters"], seed=opts["seed"], fixed_iters=bool(opts.get("fixed_iters", 0)),
-                   lambda_mode=opts.get("lambda_mode", 0), stream_id=opts.get("stream_id", 0), prec=prec)
+                   lambda_mode=opts.get("lambda_mode", 0), stream_id=opts.get("stream_id", 0), prec=prec,
+                   refine_sweeps=opts.get("refine_sweeps", 0))
     ost = O.init_state_from_factors(X[:K0], *fac, oo)
     return ctx, ost
 
@@ -101,6 +102,42 @@ def test_update_bf16_summary_bits_and_factors(sbt):
     ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
     ctx.update(torch.from_numpy(X[60:70]).cuda())
     _check_update(ctx, ost2, traces, ftol=1e-3)
+
+
+def test_update_bf16_refinement_matches_oracle(sbt):
+    """bf16 ALS, then refinement sweeps on the split summary, against the
+    oracle doing the same: samples and summaries bit-exact, main iteration
+    counts kept, factors within the tolerance of the split arithmetic."""
+    X, A, B, C = planted(120, 96, 70, 6, dtype=torch.float32, seed=2)
+    fac = unit_factors(A, B, C[:60])
+    ctx, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15,
+                     refine_sweeps=6)
+    ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[60:70]).cuda())
+    _check_update(ctx, ost2, traces, ftol=2e-4)
+    st = ctx.stats()
+    assert st["iters"] == [15] * 4 and not (st["flags"] & sbt.SBT_FLAG_NO_REFINE)
+    for rep, t in enumerate(traces):
+        assert abs(st["fit"][rep] - t.als.fit) < 1e-4
+
+
+def test_refinement_moves_bf16_towards_float32(sbt):
+    """The refined bf16 update is closer to the float32 oracle than the plain
+    bf16 update (same samples, same start)."""
+    X, A, B, C = planted(120, 96, 70, 6, dtype=torch.float32, seed=12)
+    fac = unit_factors(A, B, C[:60])
+    kw = dict(s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=30)
+    c16, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", **kw)
+    cref, _ = _pair(sbt, X, 60, 6, fac, prec="bf16", refine_sweeps=20, **kw)
+    o32 = O.Options(s_I=3, s_J=3, s_K=3, r=4, fixed_iters=True, max_iters=50, prec="f32")
+    ost32 = O.init_state_from_factors(X[:60], *fac, o32)
+    ost32, _ = O.update(ost32, X[60:70])
+    c16.update(torch.from_numpy(X[60:70]).cuda())
+    cref.update(torch.from_numpy(X[60:70]).cuda())
+    e16 = rel_err(c16.factors()[3][60:], ost32.C[60:])
+    eref = rel_err(cref.factors()[3][60:], ost32.C[60:])
+    print("new C rows vs float32 oracle: bf16", e16, "refined", eref)
+    assert eref < e16 / 5
 
 
 @pytest.mark.parametrize("case", ["singleton", "ragged", "rank1", "rank32", "r1", "lambda_avg", "stream_id"])
