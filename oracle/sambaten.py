@@ -79,7 +79,7 @@ class Options:
     stream_id: int = 0
     lambda_mode: int = 0
     fixed_iters: bool = False
-    prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16
+    prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16 | fp8
     refine_sweeps: int = 0     # bf16 only: ALS iterations on the split summary after the bf16 ALS
 
 
@@ -181,6 +181,41 @@ def split_bf16(Xs: np.ndarray) -> np.ndarray:
     hi = bf16_round(x)
     lo = bf16_round((x - hi.astype(np.float32)).astype(np.float32))
     return hi + lo
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to float8 e4m3 (the finite variant: 4 exponent
+    bits with bias 7, 3 mantissa bits, largest value 448, subnormals spaced
+    2^-9 below 2^-6), to nearest with ties to even, saturating at +-448;
+    returns float64."""
+    v = np.asarray(x, dtype=np.float32).astype(np.float64)
+    a = np.abs(v)
+    _, ex = np.frexp(a)                                  # a = m 2^ex, m in [0.5, 1)
+    binade = np.maximum(np.where(a > 0, ex - 1, -6), -6)  # below 2^-6 the spacing stays 2^-9
+    ulp = np.ldexp(1.0, binade - 3)
+    q = np.minimum(np.rint(a / ulp) * ulp, E4M3_MAX)
+    return np.copysign(q, v)
+
+
+def slice_amax(X: np.ndarray) -> np.ndarray:
+    """max |x| of every stored slice (float32 values)."""
+    return np.max(np.abs(X.astype(np.float32)).reshape(X.shape[0], -1), axis=1).astype(np.float32)
+
+
+def fp8_summary_values(Xs: np.ndarray, amax: np.ndarray) -> np.ndarray:
+    """e4m3 codes with one scale per summary slice: in float32, inv = 448 /
+    amax and q = e4m3(x * inv); the value is q * (amax / 448).  amax[kk] is
+    the max |x| of the stored slice behind summary slice kk (0: all zero)."""
+    x = np.ascontiguousarray(Xs, dtype=np.float32)
+    amax = np.asarray(amax, dtype=np.float32)
+    pos = amax > 0
+    inv = np.where(pos, np.float32(E4M3_MAX) / np.where(pos, amax, np.float32(1)), np.float32(0)).astype(np.float32)
+    scale = (amax / np.float32(E4M3_MAX)).astype(np.float32)
+    q = e4m3_round((x * inv[:, None, None]).astype(np.float32))
+    return q * scale.astype(np.float64)[:, None, None]
 
 
 def summary_values(Xs: np.ndarray, prec: str) -> np.ndarray:
@@ -478,7 +513,10 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         Ks = sample_mode(state.xc, nK, opts, 2, rho, state.batch)
         Kp = np.concatenate([Ks.astype(np.int64), np.arange(K_old, K_old + K_new)])
         # step 4: the summary
-        Xs = summary_values(summary(X_all, Is, Js, Kp), opts.prec)
+        if opts.prec == "fp8":
+            Xs = fp8_summary_values(summary(X_all, Is, Js, Kp), slice_amax(X_all)[Kp])
+        else:
+            Xs = summary_values(summary(X_all, Is, Js, Kp), opts.prec)
         # step 5: CP of the summary
         U0 = [init_factor(Is, R, 0, rho, state.batch, opts),
               init_factor(Js, R, 1, rho, state.batch, opts),

@@ -238,6 +238,42 @@ def test_refinement_brings_bf16_als_to_float32_accuracy():
     assert abs(fine.fit - ref.fit) < abs(b16.fit - ref.fit) / 20 + 1e-9
 
 
+def test_e4m3_round_matches_torch_and_the_format():
+    """float8 e4m3 rounding: torch's conversion where it does not saturate
+    (|x| < 464), every code of the format a fixed point, ties to even, and
+    saturation at 448 (torch returns NaN there instead)."""
+    rng = np.random.default_rng(44)
+    x = (rng.standard_normal(20000) * np.exp2(rng.integers(-12, 9, 20000))).astype(np.float32)
+    x = x[np.abs(x) < 464]
+    ties = np.array([1.0625, 1.1875, -1.0625, 2 ** -10, 3 * 2 ** -11, 0.0], np.float32)
+    x = np.concatenate([x, ties])
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(O.e4m3_round(x), ref)
+    codes = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    codes = codes[np.isfinite(codes)]
+    assert np.array_equal(O.e4m3_round(codes.astype(np.float32)), codes)
+    assert codes.max() == 448.0 and np.min(codes[codes > 0]) == 2.0 ** -9
+    assert O.e4m3_round(np.float32(1.0625)) == 1.0 and O.e4m3_round(np.float32(1.1875)) == 1.25
+    assert np.array_equal(O.e4m3_round(np.array([470.0, 1e30, -1e6], np.float32)), [448.0, 448.0, -448.0])
+
+
+def test_fp8_summary_scale_and_error_bound():
+    """Per-slice scaled e4m3 summary: the slice's largest value maps to code
+    448 exactly and every value is within half a code step (2^-4 relative in
+    the normal range, 2^-10 * scale below it)."""
+    rng = np.random.default_rng(45)
+    Xs = (rng.standard_normal((5, 7, 9)) * np.array([1e-3, 1.0, 50.0, 0.0, 3.0])[:, None, None]).astype(np.float32)
+    amax = np.max(np.abs(Xs).reshape(5, -1), axis=1)
+    V = O.fp8_summary_values(Xs, amax)
+    assert np.all(V[3] == 0.0)
+    for k in (0, 1, 2, 4):
+        s = np.float64(np.float32(amax[k] / np.float32(448.0)))
+        i = np.unravel_index(np.argmax(np.abs(Xs[k])), Xs[k].shape)
+        assert abs(V[k][i]) == 448.0 * s
+        err = np.abs(V[k] - Xs[k].astype(np.float64))
+        assert np.all(err <= 2.0 ** -4 * np.abs(Xs[k]) * 1.0001 + 2.0 ** -10 * s)
+
+
 # --------------------------------------------------------------- MTTKRP ----
 def test_mttkrp_bruteforce():
     rng = np.random.default_rng(5)
@@ -486,3 +522,19 @@ def test_fms_identities():
     # scaling every mode by 3 multiplies lambda by 27: penalty 1 - 26/27 per component
     assert abs(O.fms(lam, U, lam[p], [u[:, p] * 3.0 for u in U]) - 1 / 27) < 1e-12
     assert abs(O.fms(lam, U, lam[p], [u[:, p] for u in U]) - 1.0) < 1e-12
+
+
+def test_fp8_update_close_to_float64_update():
+    """A whole update on e4m3 summaries stays close to the float64 update:
+    quantisation noise of ~2^-5 per element costs little full-tensor fit."""
+    p = synth.planted_dense(40, 36, 34, 3, noise=0.01, seed=46, dtype=torch.float32)
+    X, A, B, C = p.X.numpy(), p.A.numpy(), p.B.numpy(), p.C.numpy()
+    na, nb, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C[:28]))
+    fits = {}
+    for prec in ("f64", "fp8"):
+        o = O.Options(s_I=2, s_J=2, s_K=2, r=2, max_iters=30, fixed_iters=True, prec=prec)
+        st = O.init_state_from_factors(X[:28], na * nb * nc, A / na, B / nb, C[:28] / nc, o)
+        st, _ = O.update(st, X[28:34])
+        fits[prec] = O.full_fit(st.X, st.lam, st.A, st.B, st.C)
+    assert fits["f64"] > 0.95
+    assert abs(fits["fp8"] - fits["f64"]) < 0.05
