@@ -60,7 +60,10 @@ typedef enum { SBT_F64 = 0, SBT_F32 = 1, SBT_BF16 = 2 } sbt_dtype;
  * summary rounded to bfloat16 (nearest-even), float32 accumulation.  The R x R
  * Cholesky factorisation, inversion, column norms and the fit stay float64 in
  * every mode. */
-typedef enum { SBT_PREC_F64 = 0, SBT_PREC_F32 = 1, SBT_PREC_BF16 = 2 } sbt_prec;
+/* Values the summary MTTKRP reads: float64, float32, bfloat16, or float8 e4m3
+ * codes with one scale per stored slice (scale = max|x| of the slice / 448,
+ * code = e4m3(x * 448 / max|x|), ties to even, saturating; needs R <= 32). */
+typedef enum { SBT_PREC_F64 = 0, SBT_PREC_F32 = 1, SBT_PREC_BF16 = 2, SBT_PREC_FP8 = 3 } sbt_prec;
 
 /* Update flags (sbt_update_stats.flags), OR-ed over repetitions. */
 #define SBT_FLAG_CHOL_REGULARIZED 1 /* a Gram Hadamard product was not positive definite */

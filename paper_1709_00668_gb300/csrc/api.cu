@@ -86,8 +86,20 @@ struct HBuf {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int round8(int64_t x) { return (int)((x + 7) / 8 * 8); }
+inline int round16(int64_t x) { return (int)((x + 15) / 16 * 16); }
 inline int esize_store(int dt) { return dt == SBT_F64 ? 8 : 4; }
-inline int esize_elem(int elem) { return elem == 0 ? 8 : (elem == 1 ? 4 : 2); }
+inline int esize_elem(int elem) { return elem == 0 ? 8 : (elem == 1 ? 4 : (elem == 2 ? 2 : 1)); }
+// summary row pitch: 16 bytes at least (TMA strides), 8 elements (vector loads)
+inline int summary_ld(int n, int elem) { return elem == 3 ? round16(n) : round8(n); }
+
+// value of a float8 e4m3 code (4 exponent bits, bias 7, 3 mantissa bits;
+// exponent 0 is subnormal, 0x7F / 0xFF are NaN)
+double e4m3_value(unsigned char c) {
+    const int sgn = c >> 7, e = (c >> 3) & 15, m = c & 7;
+    if (e == 15 && m == 7) return std::nan("");
+    const double v = e == 0 ? std::ldexp((double)m, -9) : std::ldexp(1.0 + m / 8.0, e - 7);
+    return sgn ? -v : v;
+}
 inline int esize_tf(int elem) { return elem == 0 ? 8 : 4; }
 
 struct DeviceGuard {
@@ -111,6 +123,7 @@ struct TcPlan {
     CUtensorMap m1;      // [slice][ii][jj]: contraction over jj
     CUtensorMap m2;      // [slice][jj][ii]: contraction over ii
     CUtensorMap m1lo, m2lo;
+    const float *sscale = nullptr;  // float8 summaries: scale of every summary slice
 };
 
 }  // namespace
@@ -141,7 +154,7 @@ struct sbt_ctx {
     int sdtype = SBT_F32;
     int lds = 0;
     int S = 0;
-    int elem = 1;  // summary element: 0 f64, 1 f32, 2 bf16
+    int elem = 1;  // summary element: 0 f64, 1 f32, 2 bf16, 3 float8 e4m3 (scaled per slice)
     uint32_t batch = 0;
     int64_t npos[3] = {0, 0, 0};
     // resident state
@@ -151,6 +164,7 @@ struct sbt_ctx {
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
+    Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
     cudaStream_t side = nullptr;  // runs V^-1 of a mode beside its MTTKRP pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TcPlan tc;
@@ -215,7 +229,7 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (R < 1 || R > SBT_MAX_RANK) return fail(SBT_E_INVALID, "R out of range [1, SBT_MAX_RANK]");
     if (o->max_iters < 1 || o->max_iters_init < 1) return fail(SBT_E_INVALID, "iteration caps must be >= 1");
     if (!(o->tol >= 0.0)) return fail(SBT_E_INVALID, "tol must be >= 0");
-    if (o->prec < SBT_PREC_F64 || o->prec > SBT_PREC_BF16) return fail(SBT_E_INVALID, "unknown precision");
+    if (o->prec < SBT_PREC_F64 || o->prec > SBT_PREC_FP8) return fail(SBT_E_INVALID, "unknown precision");
     if (o->lambda_mode != 0 && o->lambda_mode != 1) return fail(SBT_E_INVALID, "lambda_mode must be 0 or 1");
     if (o->refine_sweeps < 0 || o->refine_sweeps > 1000) return fail(SBT_E_INVALID, "refine_sweeps out of [0, 1000]");
     return SBT_OK;
@@ -252,7 +266,7 @@ static sbt_status append_slices(sbt_ctx *c, const sbt_tensor *X, int64_t K0, uns
         ldin = c->lds;
     }
     CK(launch_append(src, c->sdtype, X->K, c->I, c->J, ldin, dst, c->lds, c->S, ma, mb, mc,
-                     c->status.as<DevStatus>(), c->stream));
+                     c->samax.p ? c->samax.as<unsigned>() + K0 : nullptr, c->status.as<DevStatus>(), c->stream));
     return SBT_OK;
 }
 
@@ -285,6 +299,10 @@ struct Sizer {
 };
 
 // ALS descriptor scalars and tiles for nrep summaries of shape n[3] (no memory)
+// element kind the ALS kernels see: float8 summaries run the float-factor ALS
+// of the tensor-core path, as bfloat16 ones do
+static int als_elem(const sbt_ctx *c) { return c->elem == 3 ? 2 : c->elem; }
+
 static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
                       int max_iters) {
     std::memset(&d, 0, sizeof(d));
@@ -387,12 +405,12 @@ static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, i
     int P = 0;
     if (mode == 0)
         return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
     if (mode == 1)
         return launch_mttkrp_tc(tc->m2, tc->split ? &tc->m2lo : nullptr, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
     return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
-                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, c->num_sms, &P, c->stream);
+                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
 }
 
 // partial counts of the tensor-core kernels, fixed by the shapes
@@ -560,7 +578,7 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     c->K = X0->K;
     c->sdtype = X0->dtype;
     c->lds = round8(c->J);
-    c->elem = opt->prec == SBT_PREC_F64 ? 0 : (opt->prec == SBT_PREC_F32 ? 1 : 2);
+    c->elem = opt->prec == SBT_PREC_F64 ? 0 : (opt->prec == SBT_PREC_F32 ? 1 : (opt->prec == SBT_PREC_BF16 ? 2 : 3));
     c->Kcap = std::max<int64_t>(opt->K_capacity > 0 ? opt->K_capacity : 2 * X0->K, X0->K + 1);
     const size_t es = esize_store(c->sdtype);
     TRY(c->store.ensure((size_t)c->Kcap * c->I * c->lds * es));
@@ -576,6 +594,10 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     TRY(c->dxb.ensure((size_t)c->J * 8));
     TRY(c->status.ensure(sizeof(DevStatus)));
     TRY(c->h_status.ensure(sizeof(DevStatus)));
+    if (c->elem == 3) {  // float8 summaries: max |x| of every stored slice, kept by the appends
+        TRY(c->samax.ensure((size_t)c->Kcap * 4));
+        CK(cudaMemsetAsync(c->samax.p, 0, (size_t)c->Kcap * 4, c->stream));
+    }
     TRY(c->prof_bytes.ensure(8));
     CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
@@ -606,7 +628,7 @@ static sbt_status ctx_alloc(sbt_ctx *c, const sbt_tensor *X0, int32_t R, const s
     }
     CK(launch_append(c->store.p, c->sdtype, X0->K, c->I, c->J, c->lds, c->store.p, c->lds, c->S,
                      c->xa.as<unsigned long long>(), c->xb.as<unsigned long long>(),
-                     c->xc.as<unsigned long long>(), c->status.as<DevStatus>(), c->stream));
+                     c->xc.as<unsigned long long>(), c->samax.as<unsigned>(), c->status.as<DevStatus>(), c->stream));
     TRY(read_status(c, &hs));
     TRY(status_error(hs.err));
     // positive-weight counts
@@ -698,10 +720,15 @@ static sbt_status grow_store(sbt_ctx *c, int64_t need) {
     int64_t ncap = std::max<int64_t>(need, c->Kcap * 2);
     const size_t es = esize_store(c->sdtype);
     const size_t slice = (size_t)c->I * c->lds * es;
-    Buf ns, nC, nxc;
+    Buf ns, nC, nxc, nam;
     TRY(ns.ensure(ncap * slice));
     TRY(nC.ensure((size_t)ncap * c->R * 8));
     TRY(nxc.ensure((size_t)ncap * 8));
+    if (c->samax.p) {
+        TRY(nam.ensure((size_t)ncap * 4));
+        CK(cudaMemsetAsync(nam.p, 0, (size_t)ncap * 4, c->stream));
+        CK(cudaMemcpyAsync(nam.p, c->samax.p, (size_t)c->K * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
     CK(cudaMemsetAsync(ns.p, 0, ncap * slice, c->stream));
     CK(cudaMemsetAsync(nxc.p, 0, (size_t)ncap * 8, c->stream));
     CK(cudaMemcpyAsync(ns.p, c->store.p, c->K * slice, cudaMemcpyDeviceToDevice, c->stream));
@@ -714,6 +741,10 @@ static sbt_status grow_store(sbt_ctx *c, int64_t need) {
     std::swap(c->C.cap, nC.cap);
     std::swap(c->xc.p, nxc.p);
     std::swap(c->xc.cap, nxc.cap);
+    if (c->samax.p) {
+        std::swap(c->samax.p, nam.p);
+        std::swap(c->samax.cap, nam.cap);
+    }
     c->Kcap = ncap;
     return SBT_OK;
 }
@@ -738,12 +769,13 @@ static sbt_status update_shape(const sbt_ctx *c, int64_t K_old, int K_new, bool 
     u.nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), pos[2]);
     if (u.nI < 1 || u.nJ < 1 || u.nK < 1) return fail(SBT_E_STATE, "a mode has no positive weight to sample");
     u.Kp = u.nK + K_new;
-    u.ldj = round8(u.nJ);
-    u.ldi = round8(u.nI);
+    u.ldj = summary_ld(u.nJ, c->elem);
+    u.ldi = summary_ld(u.nI, c->elem);
     u.samp_stride = std::max(u.nI, std::max(u.nJ, u.nK));
     u.key_stride = std::max<int64_t>(std::max(c->I, c->J), K_old);
     u.xrs = (long long)u.Kp * u.nI * u.ldj;
-    u.tc = c->elem == 2 && tc_supported(c->R, u.nI) && tc_supported(c->R, u.nJ);
+    u.tc = (c->elem == 2 || c->elem == 3) && tc_supported(c->R, u.nI, c->elem == 3) &&
+           tc_supported(c->R, u.nJ, c->elem == 3);
     return SBT_OK;
 }
 
@@ -755,8 +787,8 @@ static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound)
     for (int Kp = bound ? 1 : u.Kp; Kp <= u.Kp; ++Kp) {
         AlsDesc d;
         const int n[3] = {u.nI, u.nJ, Kp};
-        als_shape(c, d, r, n, u.ldj, u.nK, c->elem, c->opt.max_iters);
-        best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(c->elem));
+        als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
+        best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(als_elem(c)));
         if (u.tc) {
             tc_partials(d, c->num_sms);
             best = std::max<size_t>(best, (size_t)r * d.prs * 4);
@@ -777,9 +809,10 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
     TRY(z.need(c->xc_new, (size_t)u.K_new * 8));
     AlsDesc d;
     const int n[3] = {u.nI, u.nJ, u.Kp};
-    als_shape(c, d, r, n, u.ldj, u.nK, c->elem, c->opt.max_iters);
+    als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
     TRY(als_sizes(c, d, update_part_bytes(c, u, bound), z));
-    if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * 2));
+    if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * esize_elem(c->elem)));
+    if (c->elem == 3) TRY(z.need(c->sscale, (size_t)r * u.Kp * 4));
     if (u.tc && c->opt.refine_sweeps > 0) {
         TRY(z.need(c->Xlo, (size_t)r * u.xrs * 2));
         TRY(z.need(c->Xtlo, (size_t)r * u.Kp * u.nJ * u.ldi * 2));
@@ -809,7 +842,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
-            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main};
+            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale};
 }
 
 // device bytes after the needs of z (every buffer at max(capacity, need))
@@ -882,6 +915,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         Sizer z;
         TRY(size_update(c, u, false, z));
     }
+    if (c->elem == 3 && !u.tc) return fail(SBT_E_INVALID, "float8 summaries need the tensor-core MTTKRP (R <= 32)");
     const int nI = u.nI, nJ = u.nJ, nK = u.nK, Kp = u.Kp, ldj = u.ldj;
     const long long samp_stride = u.samp_stride, key_stride = u.key_stride, xrs = u.xrs;
     // 1. append + marginal deltas
@@ -889,6 +923,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     CK(cudaMemsetAsync(c->dxa.p, 0, (size_t)c->I * 8, c->stream));
     CK(cudaMemsetAsync(c->dxb.p, 0, (size_t)c->J * 8, c->stream));
     CK(cudaMemsetAsync(c->xc_new.p, 0, (size_t)K_new * 8, c->stream));
+    if (c->samax.p) CK(cudaMemsetAsync(c->samax.as<unsigned>() + K_old, 0, (size_t)K_new * 4, c->stream));
     TRY(append_slices(c, X, K_old, c->dxa.as<unsigned long long>(), c->dxb.as<unsigned long long>(),
                       c->xc_new.as<unsigned long long>()));
     // 2. sampling from the marginals of the tensor before the update
@@ -941,7 +976,11 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         g.Xt = c->Xt.p;
         g.ldi = u.ldi;
         g.xtrs = (long long)Kp * nJ * u.ldi;
-        if (c->opt.refine_sweeps > 0) {  // and the lo parts of the split summary
+        if (c->elem == 3) {  // float8: per-slice scales from the stored slices' max |x|
+            g.samax = c->samax.as<unsigned>();
+            g.sscale = c->sscale.as<float>();
+        }
+        if (c->opt.refine_sweeps > 0 && c->elem == 2) {  // and the lo parts of the split summary
             g.Xlo = c->Xlo.p;
             g.Xtlo = c->Xtlo.p;
             g.rowsq2 = c->rowsq2.as<double>();
@@ -951,15 +990,16 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     // 4. CP-ALS on the r summaries
     AlsDesc d;
     const int n[3] = {nI, nJ, Kp};
-    als_shape(c, d, r, n, ldj, nK, c->elem, c->opt.max_iters);
+    als_shape(c, d, r, n, ldj, nK, als_elem(c), c->opt.max_iters);
     TRY(als_bind(c, d, c->Xs.p, xrs));
     // bfloat16 summaries: tensor-core MTTKRP over the summary and its transposed copy
     TcPlan &tc = c->tc;
     tc.on = u.tc;
     if (tc.on) {
         const int ldi = u.ldi;
-        CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp));
-        CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp));
+        CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp, c->elem == 3));
+        CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp, c->elem == 3));
+        tc.sscale = c->elem == 3 ? c->sscale.as<float>() : nullptr;
         tc_partials(d, c->num_sms);
     }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
@@ -972,8 +1012,8 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         if (!tc.on) {
             no_refine = true;
         } else {
-            CK(make_summary_tmap(&tc.m1lo, c->Xlo.p, nJ, nI, ldj, (long long)r * Kp));
-            CK(make_summary_tmap(&tc.m2lo, c->Xtlo.p, nI, nJ, u.ldi, (long long)r * Kp));
+            CK(make_summary_tmap(&tc.m1lo, c->Xlo.p, nJ, nI, ldj, (long long)r * Kp, false));
+            CK(make_summary_tmap(&tc.m2lo, c->Xtlo.p, nI, nJ, u.ldi, (long long)r * Kp, false));
             CK(cudaMemcpyAsync(c->iters_main.p, d.iters, (size_t)r * 4, cudaMemcpyDeviceToDevice, c->stream));
             CK(launch_refine_start(d, c->rowsq2.as<double>(), c->stream));
             AlsDesc dr = d;
@@ -1163,6 +1203,9 @@ extern "C" sbt_status sbt_last_summary(const sbt_ctx *c, int32_t rep, double *ou
     std::vector<unsigned char> h((size_t)xrs * es);
     CK(cudaMemcpy(h.data(), c->Xs.as<unsigned char>() + (size_t)rep * xrs * es, (size_t)xrs * es,
                   cudaMemcpyDeviceToHost));
+    std::vector<float> sc(c->elem == 3 ? Kp : 0);
+    if (c->elem == 3)
+        CK(cudaMemcpy(sc.data(), c->sscale.as<float>() + (size_t)rep * Kp, (size_t)Kp * 4, cudaMemcpyDeviceToHost));
     for (int64_t row = 0; row < (int64_t)Kp * nI; ++row)
         for (int jj = 0; jj < nJ; ++jj) {
             const size_t idx = (size_t)row * ldj + jj;
@@ -1172,10 +1215,12 @@ extern "C" sbt_status sbt_last_summary(const sbt_ctx *c, int32_t rep, double *ou
                 float f;
                 std::memcpy(&f, &h[idx * 4], 4);
                 v = f;
-            } else {
+            } else if (c->elem == 2) {
                 uint16_t b;
                 std::memcpy(&b, &h[idx * 2], 2);
                 v = bf16_bits_to_float(b);
+            } else {
+                v = e4m3_value(h[idx]) * (double)sc[row / nI];
             }
             out[row * nJ + jj] = v;
         }
@@ -1301,7 +1346,7 @@ extern "C" sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64
 static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J, int64_t ld, const void *A,
                                  const void *B, const void *C, int32_t R, int32_t mode, void *M, cudaStream_t st) {
     const int NP = (int)(mode == 1 ? J : I), NC = (int)(mode == 1 ? I : J);
-    if (!tc_supported(R, NC)) return fail(SBT_E_INVALID, "R or the contraction length exceeds the tensor-core plan");
+    if (!tc_supported(R, NC, false)) return fail(SBT_E_INVALID, "R or the contraction length exceeds the tensor-core plan");
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1335,21 +1380,21 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     if (e == cudaSuccess) {
         if (mode == 1) {
             e = launch_transpose_bf16(X, scr + off_xt, (int)I, (int)J, (int)ld, ldi, K, st);
-            if (e == cudaSuccess) e = make_summary_tmap(&map, scr + off_xt, (int)I, (int)J, ldi, K);
+            if (e == cudaSuccess) e = make_summary_tmap(&map, scr + off_xt, (int)I, (int)J, ldi, K, false);
         } else {
-            e = make_summary_tmap(&map, X, (int)J, (int)I, (int)ld, K);
+            e = make_summary_tmap(&map, X, (int)J, (int)I, (int)ld, K, false);
         }
     }
     if (e == cudaSuccess) {
         if (mode == 0)
             e = launch_mttkrp_tc(map, nullptr, 0, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)C, 0,
-                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, nullptr, sms, &Pk, st);
         else if (mode == 1)
             e = launch_mttkrp_tc(map, nullptr, 0, 1, R, (int)J, (int)I, (int)K, (const float *)A, 0, (const float *)C, 0,
-                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, nullptr, sms, &Pk, st);
         else
             e = launch_mttkrp_tc(map, nullptr, 1, 1, R, (int)I, (int)J, (int)K, (const float *)B, 0, (const float *)A, 0,
-                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, sms, &Pk, st);
+                                 (float *)d.part, d.prs, d.pr, d.conv, nullptr, err, nullptr, sms, &Pk, st);
     }
     if (e == cudaSuccess) e = launch_reduce_only(d, mode, st);
     if (e == cudaSuccess) e = launch_store_m(d, mode, M, st);

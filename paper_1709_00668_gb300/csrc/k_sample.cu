@@ -111,7 +111,8 @@ template <typename T>
 __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long long nrows, int I, int J, int ldin,
                                                            T *store, int lds, int S, int vec_ok,
                                                            unsigned long long *dxa, unsigned long long *dxb,
-                                                           unsigned long long *xc_new, DevStatus *status) {
+                                                           unsigned long long *xc_new, unsigned *samax,
+                                                           DevStatus *status) {
     constexpr int V = 16 / sizeof(T);
     constexpr int NW = APPEND_THREADS / 32;
     const long long r0 = (long long)blockIdx.x * APPEND_ROWS;
@@ -120,10 +121,15 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ unsigned long long rowp[APPEND_ROWS][NW];
     __shared__ unsigned long long slice_acc[APPEND_ROWS + 1];
+    __shared__ unsigned slice_max[APPEND_ROWS + 1];  // max |x| per slice (float bits: ordered as integers)
     __shared__ int range_flag;
     if (threadIdx.x == 0) range_flag = 0;
-    for (int t = threadIdx.x; t <= APPEND_ROWS; t += APPEND_THREADS) slice_acc[t] = 0;
+    for (int t = threadIdx.x; t <= APPEND_ROWS; t += APPEND_THREADS) {
+        slice_acc[t] = 0;
+        slice_max[t] = 0;
+    }
     __syncthreads();
+    const long long k_first = r0 / I;
     unsigned long long cs[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) cs[v] = 0;
@@ -132,6 +138,7 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
     for (int t = 0; t < rows; ++t) {
         const long long r = r0 + t;
         unsigned long long rp = 0;
+        float am = 0.f;
         if (jc < J) {
             const T *src = Xin + r * ldin + jc;
             T *dst = store + r * lds + jc;
@@ -149,6 +156,7 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 unsigned long long q = 0;
+                if (samax) am = fmaxf(am, fabsf((float)x[v]));
                 if (!isfinite(x[v])) bad = true;
                 else if (!qsquare(x[v], S, &q)) range = true;
                 if (cs[v] + q < cs[v]) range = true;
@@ -164,12 +172,16 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
             rp += other;
         }
         if (lane == 0) rowp[t][warp] = rp;
+        if (samax) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+            if (lane == 0 && am > 0.f) atomicMax(&slice_max[r / I - k_first], __float_as_uint(am));
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&status->err, ERR_NONFINITE);
     if (range) range_flag = 1;
     __syncthreads();
     // rows: x_a[i] += row sum; slice sums gathered per slice in shared memory
-    const long long k_first = r0 / I;
     for (int t = threadIdx.x; t < rows; t += APPEND_THREADS) {
         unsigned long long s = 0;
         bool ov = false;
@@ -190,7 +202,10 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
     }
     __syncthreads();
     const int nslices = (int)((r0 + rows - 1) / I - k_first) + 1;
-    for (int t = threadIdx.x; t < nslices; t += APPEND_THREADS) add_checked(&xc_new[k_first + t], slice_acc[t], status);
+    for (int t = threadIdx.x; t < nslices; t += APPEND_THREADS) {
+        add_checked(&xc_new[k_first + t], slice_acc[t], status);
+        if (samax && slice_max[t]) atomicMax(&samax[k_first + t], slice_max[t]);
+    }
     // columns: x_b[j] += column sums of this CTA's rows
 #pragma unroll
     for (int v = 0; v < V; ++v)
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
 
 cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
                           int lds, int S, unsigned long long *dxa, unsigned long long *dxb,
-                          unsigned long long *xc_new, DevStatus *status, cudaStream_t st) {
+                          unsigned long long *xc_new, unsigned *samax, DevStatus *status, cudaStream_t st) {
     if (K_new <= 0) return cudaSuccess;
     const long long nrows = K_new * I;
     const int V = dtype == 0 ? 2 : 4;
@@ -209,10 +224,10 @@ cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, in
     count_launches(1);
     if (dtype == 0)
         k_append<double><<<grid, APPEND_THREADS, 0, st>>>((const double *)Xin, nrows, I, J, ldin, (double *)store, lds,
-                                                          S, vec_ok, dxa, dxb, xc_new, status);
+                                                          S, vec_ok, dxa, dxb, xc_new, samax, status);
     else
         k_append<float><<<grid, APPEND_THREADS, 0, st>>>((const float *)Xin, nrows, I, J, ldin, (float *)store, lds,
-                                                         S, vec_ok, dxa, dxb, xc_new, status);
+                                                         S, vec_ok, dxa, dxb, xc_new, samax, status);
     return cudaGetLastError();
 }
 
@@ -566,9 +581,86 @@ __global__ void __launch_bounds__(256) k_gather_bf16_t(GatherParams g) {
     }
 }
 
+// float8 e4m3 summaries with their transposed copy (the same tiling as
+// k_gather_bf16_t): summary slice kk of stored slice k gets the scale
+// amax_k / 448 and codes e4m3(x * (448 / amax_k)), all in float32 with round
+// to nearest; the row sums of squares are sum(q^2) * scale^2.
+template <typename TS>
+__global__ void __launch_bounds__(256) k_gather_fp8_t(GatherParams g) {
+    const int tiles_i = (g.nI + GT_ROWS - 1) / GT_ROWS;
+    const int rep = (int)(blockIdx.x % g.nrep);
+    const long long tix = blockIdx.x / g.nrep;
+    const int kk = (int)(tix / tiles_i), ii0 = (int)(tix % tiles_i) * GT_ROWS;
+    const int Kp = g.nK + g.K_new;
+    if (kk >= Kp) return;
+    const int rows = min(GT_ROWS, g.nI - ii0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int *Is = g.samples + (long long)(rep * 3 + 0) * g.samp_stride;
+    const int *Js = g.samples + (long long)(rep * 3 + 1) * g.samp_stride;
+    const int *Ks = g.samples + (long long)(rep * 3 + 2) * g.samp_stride;
+    const int gk = kk < g.nK ? Ks[kk] : g.K_old + (kk - g.nK);
+    const float amax = __uint_as_float(g.samax[gk]);
+    const float inv = amax > 0.f ? __fdiv_rn(448.f, amax) : 0.f;
+    const float scale = __fdiv_rn(amax, 448.f);
+    if (ii0 == 0 && threadIdx.x == 0) g.sscale[(long long)rep * Kp + kk] = scale;
+    __shared__ unsigned char tile[GT_ROWS][GT_COLS + 4];
+    SqF acc[GT_ROWS / 8];
+    unsigned char *xs = (unsigned char *)g.Xs + rep * g.xrs + (long long)kk * g.nI * g.ldj;
+    unsigned char *xt = (unsigned char *)g.Xt + rep * g.xtrs + (long long)kk * g.nJ * g.ldi;
+    for (int j0 = 0; j0 < g.ldj; j0 += GT_COLS) {
+#pragma unroll
+        for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
+            const int r = warp + 8 * rr;
+            if (r < rows) {
+                const TS *src = (const TS *)g.store + ((long long)gk * g.I + Is[ii0 + r]) * g.lds;
+                unsigned char *dst = xs + (long long)(ii0 + r) * g.ldj;
+                for (int c = lane; c < GT_COLS && j0 + c < g.ldj; c += 32) {
+                    const int jj = j0 + c;
+                    const float x = jj < g.nJ ? (float)src[Js[jj]] : 0.f;
+                    const unsigned char q = to_e4m3(__fmul_rn(x, inv));
+                    dst[jj] = q;
+                    tile[r][c] = q;
+                    acc[rr].add(from_e4m3(q));
+                }
+            }
+        }
+        __syncthreads();
+        // Xt[kk][jj][ii0 + r]: 16 threads per column jj, two rows each
+        const int jn = min(GT_COLS, g.nJ - j0);
+        for (int e = threadIdx.x; e < jn * 16; e += blockDim.x) {
+            const int c = e >> 4, r = (e & 15) * 2;
+            if (r < rows) {
+                unsigned char *o = xt + (long long)(j0 + c) * g.ldi + ii0 + r;
+                if (r + 1 < rows) {
+                    *reinterpret_cast<uchar2 *>(o) = make_uchar2(tile[r][c], tile[r + 1][c]);
+                } else {
+                    o[0] = tile[r][c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < GT_ROWS / 8; ++rr) {
+        const int r = warp + 8 * rr;
+        if (r < rows) {
+            const double t = acc[rr].total() * (double)scale * (double)scale;
+            if (lane == 0) g.rowsq[(long long)rep * Kp * g.nI + (long long)kk * g.nI + ii0 + r] = t;
+        }
+    }
+}
+
 cudaError_t launch_gather(const GatherParams &g, int sdtype, int xelem, cudaStream_t st) {
     const long long rows = (long long)(g.nK + g.K_new) * g.nI;
     if (rows <= 0 || g.nrep <= 0) return cudaSuccess;
+    if (xelem == 3) {
+        if (!g.Xt || !g.samax || !g.sscale) return cudaErrorInvalidValue;
+        const long long tiles = (long long)(g.nK + g.K_new) * ((g.nI + GT_ROWS - 1) / GT_ROWS) * g.nrep;
+        count_launches(1);
+        if (sdtype == 0) k_gather_fp8_t<double><<<(unsigned)tiles, 256, 0, st>>>(g);
+        else k_gather_fp8_t<float><<<(unsigned)tiles, 256, 0, st>>>(g);
+        return cudaGetLastError();
+    }
     if (xelem == 2 && g.Xt) {
         const long long tiles = (long long)(g.nK + g.K_new) * ((g.nI + GT_ROWS - 1) / GT_ROWS) * g.nrep;
         count_launches(1);

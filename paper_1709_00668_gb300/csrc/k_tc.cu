@@ -83,24 +83,37 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16, A and B bfloat16, D float32, both K-major.
+// Instruction descriptor, D float32, A and B K-major: kind::f16 with A and B
+// bfloat16 (format 1), or kind::f8f6f4 with A and B float8 e4m3 (format 0).
+template <bool FP8>
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
-    return (1u << 4)                     // D format: float32
-           | (1u << 7)                   // A format: bfloat16
-           | (1u << 10)                  // B format: bfloat16
-           | ((uint32_t)(N >> 3) << 17)  // N / 8
-           | ((uint32_t)(M >> 4) << 24); // M / 16
+    return (1u << 4)                                  // D format: float32
+           | ((FP8 ? 0u : 1u) << 7)                   // A format
+           | ((FP8 ? 0u : 1u) << 10)                  // B format
+           | ((uint32_t)(N >> 3) << 17)               // N / 8
+           | ((uint32_t)(M >> 4) << 24);              // M / 16
 }
 
+template <bool FP8>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
 }
+
 
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -132,6 +145,7 @@ struct TcParams {
     int nkb, npb, spc, nks;
     int br;                  // summary rows per tile (tiles of equal height, a multiple of 8, <= 128)
     int split;               // 1: add the lo part of a split summary (second tensor map) into each product
+    const float *sscale;     // float8 summaries: scale of every summary slice [rep][Kp]; else null
     int epi;                 // 0 ROWSUM (weights C(kk)), 1 COLSUM (weights A(p))
     const float *F;          // contraction factor [rep][NC][R]
     long long frs;
@@ -167,10 +181,17 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
-template <int N>
+// N columns: NT terms of RH columns each.  bfloat16 summaries: the factor
+// as bf16 hi and lo (NT = 2); float8 summaries: the factor as three e4m3
+// terms at fixed scales, F = 2^-8 (e1 + 2^-4 e2 + 2^-8 e3) (NT = 3; factor
+// entries are at most 1 in magnitude: unit columns or uniforms in [0, 1)).
+template <int N, bool FP8>
 __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap,
                                                    const __grid_constant__ CUtensorMap tmap_lo, TcParams p) {
-    constexpr int RH = N / 2;
+    constexpr int NT = FP8 ? 3 : 2;
+    constexpr int RH = N / NT;
+    constexpr int TS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);  // tensor-memory columns per accumulator
+    constexpr int KE = FP8 ? 128 : 64;                        // contraction elements per 128-byte row
     const int rep = blockIdx.y;
     // programmatic dependent launch: the next kernel of the stream may be
     // scheduled now.  This grid reads the previous kernel's results (the
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "r"(2 * N));
+                     "r"(2 * TS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -233,28 +254,46 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         asm volatile("griddepcontrol.wait;" ::: "memory");
         if (threadIdx.x == 32 && p.conv[rep]) *abort_flag = 2;  // converged just before: skip, no error
         // warps 1-5 (160 threads), while warp 0 already streams X: the B operand
-        // (rows n < RH: bf16(F), rows RH..: bf16(F - bf16(F)); K-major, swizzled),
-        // one thread per contraction index j, and the epilogue weights C(kk, :)
+        // (row n of term q holds column n - q RH of the factor; K-major,
+        // 128-byte swizzled), one thread per contraction index j, and the
+        // epilogue weights C(kk, :) (times the slice scale for float8)
         const float *F = p.F + rep * p.frs;
         const int t = threadIdx.x - 32;
-        for (int j = t; j < p.nkb * 64; j += 160) {
-            const int kb = j >> 6, k = j & 63;
-            unsigned char *col = btile + (size_t)kb * N * 128 + (k & 7) * 2;
+        for (int j = t; j < p.nkb * KE; j += 160) {
+            const int kb = j / KE, k = j % KE;
+            unsigned char *blk = btile + (size_t)kb * N * 128;
 #pragma unroll 4
             for (int r = 0; r < RH; ++r) {
                 const float f = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-                const int nh = r, nl = RH + r;
-                *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
-                *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
+                if constexpr (!FP8) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+                    const int nh = r, nl = RH + r;
+                    unsigned char *col = blk + (k & 7) * 2;
+                    *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
+                    *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
+                } else {
+                    const unsigned char e1 = to_e4m3(f * 256.f);
+                    const float r1 = f - from_e4m3(e1) * 0.00390625f;
+                    const unsigned char e2 = to_e4m3(r1 * 4096.f);
+                    const float r2 = r1 - from_e4m3(e2) * 0.000244140625f;
+                    const unsigned char e3 = to_e4m3(r2 * 65536.f);
+                    const unsigned char ev[3] = {e1, e2, e3};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int n = q * RH + r;
+                        blk[n * 128 + (((k >> 4) ^ (n & 7)) << 4) + (k & 15)] = ev[q];
+                    }
+                }
             }
         }
         if (p.epi == 0) {
             const float *W = p.W + rep * p.wrs;
             for (int e = t; e < nsl * RH; e += 160) {
                 const int tt = e / RH, r = e % RH;
-                wst[e] = r < R ? W[(long long)(k0 + tt) * R + r] : 0.f;
+                float w = r < R ? W[(long long)(k0 + tt) * R + r] : 0.f;
+                if (FP8) w *= p.sscale[(long long)rep * p.Kp + k0 + tt];
+                wst[e] = w;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -298,7 +337,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = tc_idesc(TC_M, N);
+            constexpr uint32_t idesc = tc_idesc<FP8>(TC_M, N);
             int stage = 0;
             uint32_t phase = 0;
             const uint32_t bbase = smem_u32(btile);
@@ -307,7 +346,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 const uint32_t aph = (uint32_t)(t >> 1) & 1u;
                 if (!tc_wait(&sh->acce[a], aph ^ 1u, abort_flag, p.err)) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(a * N);
+                const uint32_t d = tmem + (uint32_t)(a * TS);
                 bool ok = true;
                 const int nkb2 = p.nkb * (1 + p.split);
                 for (int kb2 = 0; kb2 < nkb2; ++kb2) {
@@ -320,8 +359,8 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                     const uint32_t abase = smem_u32(ring + (size_t)stage * TC_BOX_BYTES);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        tc_mma(d, sw128_desc(abase + k * 32), sw128_desc(bbase + kb * N * 128 + k * 32), idesc,
-                               (kb2 | k) != 0);
+                        tc_mma<FP8>(d, sw128_desc(abase + k * 32), sw128_desc(bbase + kb * N * 128 + k * 32), idesc,
+                                    (kb2 | k) != 0);
                     }
                     tc_commit(&sh->empty[stage]);
                     if (++stage == S) {
@@ -356,16 +395,23 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             float z[RH];
             if (got) {
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * N);
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TS);
                 float v[32];
+#pragma unroll
+                for (int r = 0; r < RH; ++r) z[r] = 0.f;
 #pragma unroll
                 for (int c = 0; c < N; c += 32) {
                     tmem_ld32(taddr + c, v);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int col = c + i;
-                        if (col < RH) z[col] = v[i];
-                        else z[col - RH] += v[i];
+                        if (col < N) {
+                            const int q = col / RH;
+                            // bf16: hi + lo; e4m3: 2^-8 (t1 + 2^-4 t2 + 2^-8 t3)
+                            const float tw = FP8 ? (q == 0 ? 0.00390625f : (q == 1 ? 0.000244140625f : 1.52587890625e-05f))
+                                                 : 1.f;
+                            z[col - q * RH] = FP8 ? fmaf(v[i], tw, z[col - q * RH]) : z[col - q * RH] + v[i];
+                        }
                     }
                 }
                 tc_fence_before();
@@ -393,6 +439,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 epi_bar();
                 if (etid < R && *abort_flag != 2) {
                     float s = ((sh->red[0][etid] + sh->red[1][etid]) + sh->red[2][etid]) + sh->red[3][etid];
+                    if (FP8) s *= p.sscale[(long long)rep * p.Kp + kk];
                     part[((long long)pb * p.Kp + kk) * p.pr + etid] = s;
                 }
                 epi_bar();
@@ -406,14 +453,14 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
         if (p.bytes_ctr && etid == 0 && !skipped) {
             const int rows = min(p.br, p.NP - pb * p.br);
-            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * 2ull * nsl * (1 + p.split));
+            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * (FP8 ? 1ull : 2ull) * nsl * (1 + p.split));
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TS));
     }
 }
 
@@ -461,33 +508,37 @@ int tc_box_rows(int NP) {
     return std::min(TC_M, (br + 7) / 8 * 8);
 }
 
-// 3-D map over [slices][NP][ld] bfloat16, box 64 x tc_box_rows(NP) x 1,
-// 128-byte swizzle, zero fill outside (columns >= NC, rows >= NP).
-cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices) {
+// 3-D map over [slices][NP][ld] bfloat16 (or float8 codes), box of one
+// 128-byte row (64 or 128 elements) x tc_box_rows(NP) x 1, 128-byte swizzle,
+// zero fill outside (columns >= NC, rows >= NP).
+cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices,
+                              bool fp8) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    if (((uintptr_t)base & 15) || (ld * 2) % 16) return cudaErrorInvalidValue;
+    const int es = fp8 ? 1 : 2;
+    if (((uintptr_t)base & 15) || (ld * es) % 16) return cudaErrorInvalidValue;
     cuuint64_t dims[3] = {(cuuint64_t)NC, (cuuint64_t)NP, (cuuint64_t)nslices};
-    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)NP * ld * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)tc_box_rows(NP), 1};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)NP * ld * es};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)tc_box_rows(NP), 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static int tc_n_of(int R) { return R <= 16 ? 32 : 64; }
+// B operand columns: two bf16 terms or three e4m3 terms of RH = 16 or 32 columns
+static int tc_rh_of(int R) { return R <= 16 ? 16 : 32; }
+static int tc_n_of(int R, bool fp8) { return (fp8 ? 3 : 2) * tc_rh_of(R); }
+static int tc_nkb_of(int NC, bool fp8) { return (NC + (fp8 ? 127 : 63)) / (fp8 ? 128 : 64); }
 
-static size_t tc_smem_bytes(int nkb, int N, int stages) {
-    return 1024 + (size_t)stages * TC_BOX_BYTES + (size_t)nkb * N * 128 + sizeof(TcShared) +
-           (size_t)TC_MAX_SPC * (N / 2) * sizeof(float);
+static size_t tc_fixed_smem(int nkb, int N, int RH) {
+    return 1024 + (size_t)nkb * N * 128 + sizeof(TcShared) + (size_t)TC_MAX_SPC * RH * sizeof(float);
 }
 
-bool tc_supported(int R, int NC) {
-    const int N = tc_n_of(R);
-    const int nkb = (NC + 63) / 64;
-    return R <= 32 && (size_t)nkb * N * 128 <= 96 * 1024;
+bool tc_supported(int R, int NC, bool fp8) {
+    return R <= 32 && (size_t)tc_nkb_of(NC, fp8) * tc_n_of(R, fp8) * 128 <= 96 * 1024;
 }
 
 // Work split for one mode: CTAs = nrep x npb x nks, about two per SM.
@@ -507,15 +558,17 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
                              int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
-                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
-                             int *P_out, cudaStream_t st) {
+                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
+                             int num_sms, int *P_out, cudaStream_t st) {
+    const bool fp8 = sscale != nullptr;
     TcParams p{};
     p.nrep = nrep;
     p.R = R;
     p.NP = NP;
     p.NC = NC;
     p.Kp = Kp;
-    p.nkb = (NC + 63) / 64;
+    p.nkb = tc_nkb_of(NC, fp8);
+    p.sscale = sscale;
     tc_tiles(nrep, NP, Kp, num_sms, &p.npb, &p.nks, &p.spc);
     p.br = tc_box_rows(NP);
     p.split = tmap_lo ? 1 : 0;
@@ -531,12 +584,12 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     p.conv = conv;
     p.bytes_ctr = bytes_ctr;
     p.err = err;
-    const int N = tc_n_of(R);
+    const int N = tc_n_of(R, fp8);
     const size_t budget = 110 * 1024;
-    const size_t fixed = 1024 + (size_t)p.nkb * N * 128 + sizeof(TcShared) + (size_t)TC_MAX_SPC * (N / 2) * 4;
+    const size_t fixed = tc_fixed_smem(p.nkb, N, tc_rh_of(R));
     int stages = (int)std::min<size_t>(8, (budget > fixed ? (budget - fixed) : 0) / TC_BOX_BYTES);
     p.stages = std::max(2, stages);
-    const size_t smem = tc_smem_bytes(p.nkb, N, p.stages);
+    const size_t smem = fixed + (size_t)p.stages * TC_BOX_BYTES;
     *P_out = epi == 0 ? p.nks : p.npb;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p.npb * p.nks, nrep);
@@ -549,15 +602,20 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launches(1);
-    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32>, tmap, lo, p);
-    return cudaLaunchKernelEx(&cfg, k_mtt_tc<64>, tmap, lo, p);
+    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32, false>, tmap, lo, p);
+    if (N == 64) return cudaLaunchKernelEx(&cfg, k_mtt_tc<64, false>, tmap, lo, p);
+    if (N == 48) return cudaLaunchKernelEx(&cfg, k_mtt_tc<48, true>, tmap, lo, p);
+    return cudaLaunchKernelEx(&cfg, k_mtt_tc<96, true>, tmap, lo, p);
 }
 
 // Raise the dynamic shared-memory limit of the tensor-core kernels once,
 // outside any stream capture.
 cudaError_t set_tc_kernel_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<32, false>, a, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<64, false>, a, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<48, true>, a, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<96, true>, a, 200 * 1024);
     return e;
 }
 

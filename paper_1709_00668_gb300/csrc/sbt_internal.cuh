@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include <string>
@@ -98,6 +99,14 @@ __device__ __forceinline__ float widen_elem(__nv_bfloat16 v) { return __bfloat16
 // Double-float accumulation on the float32 pipes (float64 is a slow unit on
 // this part): a value is the unevaluated sum hi + lo, sums use Knuth's
 // two-sum, products of squares are split exactly with an FMA.
+// float8 e4m3 code of x (nearest, ties to even, saturating at +-448) and its value
+__device__ __forceinline__ unsigned char to_e4m3(float x) {
+    return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(unsigned char c) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3)));
+}
+
 struct DF {
     float hi, lo;
 };
@@ -201,6 +210,8 @@ struct GatherParams {
     long long xtrs;
     void *Xlo, *Xtlo;         // bfloat16 with Xt only, may be null: lo parts bf16(x - hi), same layouts
     double *rowsq2;           // with Xlo: row sums of (hi + lo)^2
+    const unsigned *samax;    // float8: max |x| of every stored slice (float bits)
+    float *sscale;            // float8: scale of every summary slice [rep][Kp] (written here)
 };
 
 // rows of one tail CTA (float32 / bfloat16 summaries): the partial-sum
@@ -253,9 +264,10 @@ cudaError_t launch_absmax(const void *X, int dtype, long long n, DevStatus *stat
 
 // Copy K_new slices (row pitch ldin; may alias the store) into the store and
 // add their fixed-point squares to the marginals: dxa (I), dxb (J), xc_new (K_new).
+// samax: null, or the max |x| of every new slice (float bits, atomically maxed; zero it first)
 cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, int J, int ldin, void *store,
                           int lds, int S, unsigned long long *dxa, unsigned long long *dxb,
-                          unsigned long long *xc_new, DevStatus *status, cudaStream_t st);
+                          unsigned long long *xc_new, unsigned *samax, DevStatus *status, cudaStream_t st);
 
 cudaError_t launch_sample(const SampleParams &sp, cudaStream_t st);
 
@@ -287,16 +299,19 @@ void choose_tiles(AlsDesc &d, int num_sms);
 long long partial_elems(const AlsDesc &d);  // per repetition
 
 // tcgen05 MTTKRP of bfloat16 summaries (k_tc.cu)
-bool tc_supported(int R, int NC);
+bool tc_supported(int R, int NC, bool fp8);
 void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc);
-cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices);
-// tmap_lo: null, or the map of the lo part of a split summary (added into every product)
+cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices,
+                              bool fp8);
+// tmap_lo: null, or the map of the lo part of a split summary (added into
+// every product); sscale: null for bfloat16 summaries, else float8 e4m3
+// summaries with one scale per summary slice [rep][Kp]
 cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo, int epi, int nrep, int R, int NP,
                              int NC, int Kp,
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
-                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, int num_sms,
-                             int *P_out, cudaStream_t st);
+                             const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
+                             int num_sms, int *P_out, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
                                   cudaStream_t st);
 // reduction of d.P[mode] partials into d.M, then the tail

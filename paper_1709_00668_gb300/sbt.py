@@ -38,7 +38,8 @@ SBT_BF16 = 2
 SBT_PREC_F64 = 0
 SBT_PREC_F32 = 1
 SBT_PREC_BF16 = 2
-PREC = {"f64": SBT_PREC_F64, "f32": SBT_PREC_F32, "bf16": SBT_PREC_BF16}
+SBT_PREC_FP8 = 3
+PREC = {"f64": SBT_PREC_F64, "f32": SBT_PREC_F32, "bf16": SBT_PREC_BF16, "fp8": SBT_PREC_FP8}
 
 SBT_FLAG_CHOL_REGULARIZED = 1
 SBT_FLAG_ZERO_COLUMN = 2

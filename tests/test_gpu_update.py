@@ -104,6 +104,23 @@ def test_update_bf16_summary_bits_and_factors(sbt):
     _check_update(ctx, ost2, traces, ftol=1e-3)
 
 
+@pytest.mark.parametrize("R", [6, 20])
+def test_update_fp8_summary_bits_and_factors(sbt, R):
+    """float8 e4m3 summaries (one scale per stored slice): the scaled codes
+    bit-exact against the oracle, factors within the tolerance of a 4-bit
+    summary ALS run both sides with the same codes."""
+    X, A, B, C = planted(120, 96, 70, R, dtype=torch.float32, seed=22)
+    fac = unit_factors(A, B, C[:60])
+    ctx, ost = _pair(sbt, X, 60, R, fac, prec="fp8", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15)
+    ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[60:70]).cuda())
+    errs = [rel_err(a, b) for a, b in zip(ctx.factors(), (ost2.lam, ost2.A, ost2.B, ost2.C))]
+    print("fp8 R", R, "factor errors vs oracle (lam, A, B, C):", errs)
+    _check_update(ctx, ost2, traces, ftol=2e-3)
+    p = ctx.profile()
+    assert p["updates"] == 1
+
+
 def test_update_bf16_refinement_matches_oracle(sbt):
     """bf16 ALS, then refinement sweeps on the split summary, against the
     oracle doing the same: samples and summaries bit-exact, main iteration
@@ -123,8 +140,9 @@ def test_update_bf16_refinement_matches_oracle(sbt):
 
 def test_refinement_moves_bf16_towards_float32(sbt):
     """The refined bf16 update is closer to the float32 oracle than the plain
-    bf16 update (same samples, same start, 50 ALS iterations in all three)."""
-    X, A, B, C = planted(120, 96, 70, 6, dtype=torch.float32, seed=12)
+    bf16 update (same samples, same start, 50 ALS iterations in all three).
+    Noiseless planted data, so that the summary's rounding is what differs."""
+    X, A, B, C = planted(120, 96, 70, 6, noise=0.0, dtype=torch.float32, seed=12, dist="normal")
     fac = unit_factors(A, B, C[:60])
     kw = dict(s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1)
     c16, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", max_iters=50, **kw)
