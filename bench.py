@@ -45,6 +45,7 @@ TRAFFIC = {
                                    "capture": "k_mtt_tc<32> grid 36x8, 17.8-18.6 us, --small --steps 1 --warmup 1"},
 }
 KERNEL_NAME = {"bf16": "k_mtt_tc (tcgen05 MTTKRP, bf16 summaries)",
+               "fp8": "k_mtt_tc (tcgen05 kind::f8f6f4 MTTKRP, e4m3 summaries)",
                "f32": "k_mtt_row / k_mtt_col (CUDA-core MTTKRP, f32 summaries)"}
 
 
@@ -59,7 +60,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "f32", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -71,6 +72,9 @@ def parse():
     ap.add_argument("--duration", type=float, default=30.0, help="--serve: seconds of arrivals")
     ap.add_argument("--streams", type=int, default=64, help="--serve: live streams")
     ap.add_argument("--slots", type=int, default=8, help="--serve: concurrent updates")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep on the 2000x2000x(1000+10x100), R=20 workload: f32, bf16, "
+                         "bf16 + refinement, fp8; throughput and error against the FP64 oracle (one JSON line)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same summary shapes, 200 initial slices (a few GB on the device)")
     args = ap.parse_args()
@@ -617,10 +621,113 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+SWEEP = dict(I=2000, J=2000, K0=1000, batch=100, nbatch=10, R=20, s=5, r=8, noise=1e-3, cond=1e3, iters=30,
+             refine=10, seed=0)
+SWEEP_NAME = ("dense-fp32 2000x2000x(1000+100/batch) planted R=20, cond(Gram)~1e3, noise 1e-3, s=5, r=8, "
+              "30 fixed ALS iterations")
+
+
+def run_sweep(args):
+    """Per precision: slices/s over the 10 batches (device-resident, no
+    per-launch timing), MTTKRP bandwidth from a profiling pass over the first
+    batch, the full-tensor fit, and the error of repetition 0's summary
+    factors (after the shared-row normalisation) after the first batch against
+    the FP64 oracle's ALS on the same summary (the oracle draws its own
+    samples from its own marginals)."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import sambaten as O
+    from paper_1709_00668_gb300 import sbt, synth
+    w = SWEEP
+    K0, b, nb = w["K0"], w["batch"], w["nbatch"]
+    p = synth.planted_dense(w["I"], w["J"], K0 + nb * b, w["R"], noise=w["noise"], seed=w["seed"],
+                            dtype=torch.float32, device=device, cond=w["cond"])
+    X0 = p.X[:K0]
+    batches = [p.X[K0 + i * b:K0 + (i + 1) * b] for i in range(nb)]
+    stream = torch.cuda.current_stream(device)
+    sptr = stream.cuda_stream
+    # every arm runs w["iters"] ALS iterations in all (refinement included)
+    arms = [("f32", "f32", 0), ("bf16", "bf16", 0), ("bf16+refine", "bf16", w["refine"]), ("fp8", "fp8", 0)]
+    res = []
+    for name, prec, refine in arms:
+        o = dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=0.0, max_iters=w["iters"] - refine, fixed_iters=1,
+                 max_iters_init=50, seed=w["seed"], prec=prec, refine_sweeps=refine, cuda_stream=sptr,
+                 K_capacity=K0 + nb * b, max_batch=b)
+        # first batch on its own context: summary factors of repetition 0, MTTKRP bandwidth
+        c1 = sbt.SamBaTen(X0, w["R"], **o)
+        c1.profile_reset(timing=True)
+        c1.update(batches[0])
+        prof = c1.profile()
+        lam_s, As, Bs, Cs = c1.last_summary_factors(0)
+        fit0 = c1.stats()["fit"][0]
+        c1.close()
+        # throughput over all batches
+        ct = sbt.SamBaTen(X0, w["R"], **o)
+        ct.profile_reset(timing=False)
+        torch.cuda.synchronize()
+        secs, per, _ = time_updates(ct, batches, torch, stream)
+        fit = ct.fit()
+        ct.close()
+        ach = prof["mttkrp_bytes"] / (prof["mttkrp_ms"] / 1e3) / 1e9 if prof["mttkrp_ms"] > 0 else None
+        res.append({"arm": name, "value": nb * b / secs, "unit": "slices/s", "ms_per_step": 1e3 * secs / nb,
+                    "full_tensor_fit": fit, "mttkrp_GBps_first_batch": ach,
+                    "mttkrp_us_per_launch_first_batch": 1e3 * prof["mttkrp_ms"] / max(1, prof["mttkrp_launches"]),
+                    "_summary": (lam_s, As, Bs, Cs), "_fit0": fit0})
+        torch.cuda.synchronize()
+    # the FP64 oracle on repetition 0 of the first batch
+    t0 = time.perf_counter()
+    Xh = p.X[:K0 + b].cpu().numpy()
+    oo = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], seed=w["seed"])
+    S = O.marginal_shift(Xh[:K0])
+    xa, xb, xc = O.marginals(Xh[:K0], S)
+    nI, nJ, nK = (O.sample_size(N, w["s"], m) for N, m in ((w["I"], xa), (w["J"], xb), (K0, xc)))
+    Is = O.sample_mode(xa, nI, oo, 0, 0, 0)
+    Js = O.sample_mode(xb, nJ, oo, 1, 0, 0)
+    Ks = O.sample_mode(xc, nK, oo, 2, 0, 0)
+    Kp = np.concatenate([Ks.astype(np.int64), np.arange(K0, K0 + b)])
+    Xs = O.summary(Xh, Is, Js, Kp).astype(np.float64)
+    U0 = [O.init_factor(Is, w["R"], 0, 0, 0, oo), O.init_factor(Js, w["R"], 1, 0, 0, oo),
+          O.init_factor(Kp, w["R"], 2, 0, 0, oo)]
+    ref = O.cp_als(Xs, U0, 0.0, w["iters"], fixed_iters=True)
+    Us_ref, lam_ref, _ = O.normalize_shared(ref.U, ref.lam, nK)
+    oracle_s = time.perf_counter() - t0
+    for r_ in res:
+        lam_s, As, Bs, Cs = r_.pop("_summary")
+        fit0 = r_.pop("_fit0")
+        err = max(float(np.max(np.abs(g - o_)) / max(float(np.max(np.abs(o_))), 1e-300))
+                  for g, o_ in zip((As, Bs, Cs), Us_ref))
+        # the ALS of an ill-conditioned problem is still moving after 30
+        # iterations, so components may differ in order or sign: FMS (after
+        # the best matching) and the summary fit are the order-free measures
+        r_["err_vs_fp64_oracle"] = {
+            "summary_fit_rep0_abs_diff": abs(fit0 - ref.fit),
+            "summary_fms_rep0": O.fms(lam_s, [As, Bs, Cs], lam_ref, Us_ref),
+            "summary_factors_rep0_max_rel_same_order": err,
+            "lambda_rep0_max_rel_same_order": float(np.max(np.abs(lam_s - lam_ref) / np.abs(lam_ref)))}
+    line = {"metric": "precision sweep: slices absorbed/sec and error against the FP64 oracle",
+            "unit": "slices/s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": SWEEP_NAME, **w}, "arms": res,
+            "oracle": {"seconds": oracle_s, "summary_fit_rep0": ref.fit,
+                       "what": "FP64 CP-ALS of repetition 0's summary of batch 1 "
+                               "(own marginals and samples), shared-row normalised"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.serve:
         return run_serve(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

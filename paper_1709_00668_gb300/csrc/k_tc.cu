@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                     const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
                     if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
                     mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
-                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * 64,
+                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * KE,
                                 pb * p.br, rep * p.Kp + k0 + t, &sh->full[stage]);
                     ++issued;
                     if (++stage == S) {

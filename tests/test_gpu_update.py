@@ -104,18 +104,20 @@ def test_update_bf16_summary_bits_and_factors(sbt):
     _check_update(ctx, ost2, traces, ftol=1e-3)
 
 
-@pytest.mark.parametrize("R", [6, 20])
-def test_update_fp8_summary_bits_and_factors(sbt, R):
+@pytest.mark.parametrize("shape", [(120, 96, 6, 3), (120, 96, 20, 3), (330, 290, 10, 2)])
+def test_update_fp8_summary_bits_and_factors(sbt, shape):
     """float8 e4m3 summaries (one scale per stored slice): the scaled codes
     bit-exact against the oracle, factors within the tolerance of a 4-bit
-    summary ALS run both sides with the same codes."""
-    X, A, B, C = planted(120, 96, 70, R, dtype=torch.float32, seed=22)
+    summary ALS run both sides with the same codes.  The last shape has
+    summaries wider than one 128-element box (165 x 145)."""
+    I, J, R, s = shape
+    X, A, B, C = planted(I, J, 70, R, dtype=torch.float32, seed=22)
     fac = unit_factors(A, B, C[:60])
-    ctx, ost = _pair(sbt, X, 60, R, fac, prec="fp8", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15)
+    ctx, ost = _pair(sbt, X, 60, R, fac, prec="fp8", s_I=s, s_J=s, s_K=3, r=4, fixed_iters=1, max_iters=15)
     ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
     ctx.update(torch.from_numpy(X[60:70]).cuda())
     errs = [rel_err(a, b) for a, b in zip(ctx.factors(), (ost2.lam, ost2.A, ost2.B, ost2.C))]
-    print("fp8 R", R, "factor errors vs oracle (lam, A, B, C):", errs)
+    print("fp8", shape, "factor errors vs oracle (lam, A, B, C):", errs)
     _check_update(ctx, ost2, traces, ftol=2e-3)
     p = ctx.profile()
     assert p["updates"] == 1
