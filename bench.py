@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "f32", "fp8"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the tensor-core MTTKRP tiles in an untimed pass over the same batches first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -324,6 +326,13 @@ def run_ours(args):
     batches = [p.X[K0 + i * b:K0 + (i + 1) * b] for i in range(nb)]
     torch.cuda.synchronize()
 
+    if args.autotune:
+        # tuning pass: every launch shape of the timed batches gets its tile
+        # choice here, outside the timed region
+        ctx_t = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr, args.steps), autotune=1)
+        for i in range(args.steps):
+            ctx_t.update(batches[i % nb])
+        ctx_t.close()
     # warm-up on a separate context (same shapes, first batches)
     ctx_w = sbt.SamBaTen(X0, w["R"], **opts_for(args.prec, sptr, args.warmup))
     for i in range(args.warmup):
@@ -430,7 +439,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec,
+            "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec, "autotuned_tiles": bool(args.autotune),
                        "l2": "inputs larger than L2 (200 MB batch per step, 4 GB resident store)",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},

@@ -98,6 +98,9 @@ typedef struct {
                               MTTKRP reads the split summary x ~ hi + lo (hi = bf16(x), lo =
                               bf16(x - hi), ~16 significant bits); 0: none.  Needs the
                               tensor-core MTTKRP (R <= 32); otherwise flagged and skipped */
+    int32_t autotune;      /* 1: before the ALS of an update, time the tile candidates of every
+                              tensor-core MTTKRP launch shape not in the tile table and record
+                              the fastest (see sbt_tile_table); 0: use the table / default rule */
 } sbt_options;
 
 typedef struct {
@@ -207,6 +210,31 @@ sbt_status sbt_profile_read(sbt_ctx *ctx, sbt_profile *out);
 
 /* Free every device and host resource of the context.  NULL is a no-op. */
 void sbt_destroy(sbt_ctx *ctx);
+
+/* ---- MTTKRP tile table ----------------------------------------------------
+ * No counterpart in the paper.  Process-wide choices for the tensor-core
+ * MTTKRP (bf16 / fp8 summaries): per launch shape, CTAs per SM (1 or 2) and
+ * pipeline stages (0: as many as fit).  Shapes without an entry use 2 CTAs
+ * per SM and as many stages as fit.  Filled by the autotuner
+ * (sbt_options.autotune) or imported (a tuning run can be saved and
+ * reloaded).  Results depend on the choice only through the order in which
+ * partial sums are added. */
+typedef struct {
+    int32_t fp8;          /* 0: bfloat16 summaries, 1: float8 */
+    int32_t R;
+    int32_t NP;           /* summary rows of the launch (n_I for modes 1 and 3, n_J for mode 2) */
+    int32_t NC;           /* contraction length (n_J for modes 1 and 3, n_I for mode 2) */
+    int32_t Kp_bucket;    /* ceil(summary slices / 32) */
+    int32_t nrep;         /* repetitions in the launch */
+    int32_t epi;          /* 0: rows of M (modes 1, 2), 1: M3 (mode 3) */
+    int32_t ctas_per_sm;  /* 1 or 2 */
+    int32_t stages;       /* 0..8 */
+} sbt_tile_entry;
+
+/* op 0: copy up to cap entries into entries, *n = number in the table;
+ * op 1: merge cap entries from entries (same key: replaced);
+ * op 2: clear.  SBT_E_INVALID on bad arguments or choices. */
+sbt_status sbt_tile_table(int32_t op, sbt_tile_entry *entries, int32_t cap, int32_t *n);
 
 /* ---- serving loop ---------------------------------------------------------
  * No counterpart in the paper, which absorbs one stream.  A server owns many

@@ -124,6 +124,7 @@ struct TcPlan {
     CUtensorMap m2;      // [slice][jj][ii]: contraction over ii
     CUtensorMap m1lo, m2lo;
     const float *sscale = nullptr;  // float8 summaries: scale of every summary slice
+    const TileChoice *force = nullptr;  // autotuning: the candidate being timed
 };
 
 }  // namespace
@@ -405,26 +406,76 @@ static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, i
     int P = 0;
     if (mode == 0)
         return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
+                                tc->force);
     if (mode == 1)
         return launch_mttkrp_tc(tc->m2, tc->split ? &tc->m2lo : nullptr, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
+                                tc->force);
     return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
-                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream);
+                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
+                                tc->force);
 }
 
-// partial counts of the tensor-core kernels, fixed by the shapes
-static void tc_partials(AlsDesc &d, int num_sms) {
+// partial counts of the tensor-core kernels, fixed by the shapes and the tile choices
+static void tc_partials(AlsDesc &d, int num_sms, bool fp8) {
     int npb, nks, spc;
-    tc_tiles(d.nrep, d.n[0], d.n[2], num_sms, &npb, &nks, &spc);
+    tc_plan(fp8, d.R, d.nrep, d.n[0], d.n[1], d.n[2], 0, num_sms, &npb, &nks, &spc);
     d.P[0] = nks;
     const long long e0 = (long long)nks * d.n[0];
-    const long long e2 = (long long)npb * d.n[2];
+    tc_plan(fp8, d.R, d.nrep, d.n[0], d.n[1], d.n[2], 1, num_sms, &npb, &nks, &spc);
     d.P[2] = npb;
-    tc_tiles(d.nrep, d.n[1], d.n[2], num_sms, &npb, &nks, &spc);
+    const long long e2 = (long long)npb * d.n[2];
+    tc_plan(fp8, d.R, d.nrep, d.n[1], d.n[0], d.n[2], 0, num_sms, &npb, &nks, &spc);
     d.P[1] = nks;
     const long long e1 = (long long)nks * d.n[1];
     d.prs = std::max(e0, std::max(e1, e2)) * d.pr;
+}
+
+// Autotuning of the tensor-core MTTKRP tiles: for every launch shape of this
+// update that has no recorded choice, time each candidate (CTAs per SM,
+// pipeline stages) on the live summaries with CUDA events and keep the
+// fastest.  Runs before the ALS; the passes it times count no bytes and
+// their partial sums are overwritten by the ALS.
+static sbt_status autotune_tiles(sbt_ctx *c, const AlsDesc &d, TcPlan &tc) {
+    const bool fp8 = c->elem == 3;
+    const int R = d.R, nrep = d.nrep, Kp = d.n[2];
+    static const TileChoice cands[] = {{2, 3}, {2, 4}, {2, 6}, {2, 0}, {1, 6}, {1, 0}};
+    AlsDesc dq = d;
+    dq.bytes_ctr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    sbt_status st = SBT_OK;
+    for (int mode = 0; mode < 3 && st == SBT_OK; ++mode) {
+        const int NP = mode == 1 ? d.n[1] : d.n[0], NC = mode == 1 ? d.n[0] : d.n[1], epi = mode == 2 ? 1 : 0;
+        if (tile_known(fp8, R, NP, NC, Kp, nrep, epi)) continue;
+        TileChoice best{2, 0};
+        float best_ms = 1e30f;
+        for (const TileChoice &cand : cands) {
+            tc.force = &cand;
+            cudaError_t e = mttkrp_mode(c, dq, &tc, mode);  // warm
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = mttkrp_mode(c, dq, &tc, mode);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = fail(SBT_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        tc.force = nullptr;
+        if (st == SBT_OK) tile_store(fp8, R, NP, NC, Kp, nrep, epi, best);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 // The kernels of G ALS iterations on the library's stream: per mode, V^-1 on
@@ -790,7 +841,7 @@ static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound)
         als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
         best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(als_elem(c)));
         if (u.tc) {
-            tc_partials(d, c->num_sms);
+            tc_partials(d, c->num_sms, c->elem == 3);
             best = std::max<size_t>(best, (size_t)r * d.prs * 4);
         }
     }
@@ -872,6 +923,30 @@ static sbt_status reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max) {
     TRY(update_shape(c, K_max - K_new_max, (int)K_new_max, true, u));
     TRY(size_update(c, u, true, z));
     return SBT_OK;
+}
+
+extern "C" sbt_status sbt_tile_table(int32_t op, sbt_tile_entry *entries, int32_t cap, int32_t *n) {
+    static_assert(sizeof(sbt_tile_entry) == 9 * sizeof(int32_t), "sbt_tile_entry layout");
+    if (op == 0) {
+        if (!n || (cap > 0 && !entries)) return fail(SBT_E_INVALID, "sbt_tile_table: bad arguments");
+        *n = tile_table_read(reinterpret_cast<int *>(entries), cap);
+        return SBT_OK;
+    }
+    if (op == 1) {
+        if (cap < 0 || (cap > 0 && !entries)) return fail(SBT_E_INVALID, "sbt_tile_table: bad arguments");
+        for (int q = 0; q < cap; ++q) {
+            const sbt_tile_entry &e = entries[q];
+            if ((e.ctas_per_sm != 1 && e.ctas_per_sm != 2) || e.stages < 0 || e.stages > 8)
+                return fail(SBT_E_INVALID, "sbt_tile_table: ctas_per_sm must be 1 or 2, stages 0..8");
+        }
+        tile_table_merge(reinterpret_cast<const int *>(entries), cap);
+        return SBT_OK;
+    }
+    if (op == 2) {
+        tile_table_clear();
+        return SBT_OK;
+    }
+    return fail(SBT_E_INVALID, "sbt_tile_table: op must be 0 (read), 1 (merge) or 2 (clear)");
 }
 
 extern "C" sbt_status sbt_device_bytes(sbt_ctx *c, uint64_t *bytes) {
@@ -1000,10 +1075,14 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp, c->elem == 3));
         CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp, c->elem == 3));
         tc.sscale = c->elem == 3 ? c->sscale.as<float>() : nullptr;
-        tc_partials(d, c->num_sms);
+        tc_partials(d, c->num_sms, c->elem == 3);
     }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
                           c->batch, c->rowsq.as<double>(), c->stream));
+    if (tc.on && c->opt.autotune) {  // tile choices for shapes not seen before, then the partial counts they give
+        TRY(autotune_tiles(c, d, tc));
+        tc_partials(d, c->num_sms, c->elem == 3);
+    }
     TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
     // refinement sweeps: the same ALS continued for refine_sweeps iterations
     // with every MTTKRP on the split summary (hi + lo)
@@ -1360,7 +1439,7 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     d.elem = 2;
     d.pr = R;
     int npb, nks, spc;
-    tc_tiles(1, NP, (int)K, sms, &npb, &nks, &spc);
+    tc_plan(false, R, 1, NP, NC, (int)K, mode == 2 ? 1 : 0, sms, &npb, &nks, &spc);
     const int P = mode == 2 ? npb : nks;
     d.P[mode] = P;
     d.prs = (long long)P * (mode == 2 ? K : NP) * R;

@@ -23,6 +23,9 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace sbt {
 
@@ -541,17 +544,86 @@ bool tc_supported(int R, int NC, bool fp8) {
     return R <= 32 && (size_t)tc_nkb_of(NC, fp8) * tc_n_of(R, fp8) * 128 <= 96 * 1024;
 }
 
-// Work split for one mode: CTAs = nrep x npb x nks, about two per SM.
-void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc) {
+// ---------------------------------------------------------------------------
+// Tile choices: CTAs per SM (1 or 2) and pipeline stages for one launch shape,
+// process-wide; filled by the autotuner (or imported), else the default rule.
+namespace {
+struct TileKey {
+    int fp8, R, NP, NC, Kb, nrep, epi;
+    bool operator<(const TileKey &o) const {
+        return std::tie(fp8, R, NP, NC, Kb, nrep, epi) < std::tie(o.fp8, o.R, o.NP, o.NC, o.Kb, o.nrep, o.epi);
+    }
+};
+std::mutex g_tile_mu;
+std::map<TileKey, TileChoice> g_tiles;
+TileKey tile_key(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi) {
+    return TileKey{fp8 ? 1 : 0, R, NP, NC, (Kp + 31) / 32, nrep, epi};
+}
+}  // namespace
+
+TileChoice tile_choice(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi) {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    auto it = g_tiles.find(tile_key(fp8, R, NP, NC, Kp, nrep, epi));
+    return it == g_tiles.end() ? TileChoice{2, 0} : it->second;
+}
+
+bool tile_known(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi) {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    return g_tiles.count(tile_key(fp8, R, NP, NC, Kp, nrep, epi)) != 0;
+}
+
+void tile_store(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi, TileChoice c) {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tiles[tile_key(fp8, R, NP, NC, Kp, nrep, epi)] = c;
+}
+
+// entries [fp8, R, NP, NC, Kb, nrep, epi, per_sm, stages] x n
+int tile_table_read(int *out, int cap) {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    int n = 0;
+    for (const auto &kv : g_tiles) {
+        if (n < cap) {
+            int *e = out + 9 * n;
+            const TileKey &k = kv.first;
+            e[0] = k.fp8; e[1] = k.R; e[2] = k.NP; e[3] = k.NC; e[4] = k.Kb; e[5] = k.nrep; e[6] = k.epi;
+            e[7] = kv.second.per_sm;
+            e[8] = kv.second.stages;
+        }
+        ++n;
+    }
+    return n;
+}
+
+void tile_table_merge(const int *in, int n) {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    for (int q = 0; q < n; ++q) {
+        const int *e = in + 9 * q;
+        g_tiles[TileKey{e[0], e[1], e[2], e[3], e[4], e[5], e[6]}] = TileChoice{e[7], e[8]};
+    }
+}
+
+void tile_table_clear() {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tiles.clear();
+}
+
+// Work split for one mode: CTAs = nrep x npb x nks, about per_sm per SM.
+void tc_tiles(int nrep, int NP, int Kp, int num_sms, int per_sm, int *npb, int *nks, int *spc) {
     *npb = (NP + TC_M - 1) / TC_M;
-    // one wave at two CTAs per SM, less one slot per repetition for the V^-1
-    // kernel that runs beside the pass (a full grid would push CTAs into a
-    // second wave behind it)
-    long long target = 2LL * num_sms - nrep;
+    // one wave at per_sm CTAs per SM, less one slot per repetition for the
+    // V^-1 kernel that runs beside the pass (a full grid would push CTAs
+    // into a second wave behind it)
+    long long target = (long long)per_sm * num_sms - nrep;
     long long n = target / std::max(1LL, (long long)nrep * *npb);
     n = std::max(1LL, std::min<long long>(n, Kp));
     *spc = std::min(TC_MAX_SPC, (int)((Kp + n - 1) / n));
     *nks = (Kp + *spc - 1) / *spc;
+}
+
+void tc_plan(bool fp8, int R, int nrep, int NP, int NC, int Kp, int epi, int num_sms, int *npb, int *nks,
+             int *spc) {
+    const TileChoice c = tile_choice(fp8, R, NP, NC, Kp, nrep, epi);
+    tc_tiles(nrep, NP, Kp, num_sms, c.per_sm, npb, nks, spc);
 }
 
 cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo, int epi, int nrep, int R, int NP,
@@ -559,8 +631,9 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
-                             int num_sms, int *P_out, cudaStream_t st) {
+                             int num_sms, int *P_out, cudaStream_t st, const TileChoice *force) {
     const bool fp8 = sscale != nullptr;
+    const TileChoice tch = force ? *force : tile_choice(fp8, R, NP, NC, Kp, nrep, epi);
     TcParams p{};
     p.nrep = nrep;
     p.R = R;
@@ -569,7 +642,7 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     p.Kp = Kp;
     p.nkb = tc_nkb_of(NC, fp8);
     p.sscale = sscale;
-    tc_tiles(nrep, NP, Kp, num_sms, &p.npb, &p.nks, &p.spc);
+    tc_tiles(nrep, NP, Kp, num_sms, tch.per_sm, &p.npb, &p.nks, &p.spc);
     p.br = tc_box_rows(NP);
     p.split = tmap_lo ? 1 : 0;
     const CUtensorMap &lo = tmap_lo ? *tmap_lo : tmap;
@@ -585,9 +658,10 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     p.bytes_ctr = bytes_ctr;
     p.err = err;
     const int N = tc_n_of(R, fp8);
-    const size_t budget = 110 * 1024;
+    const size_t budget = tch.per_sm == 1 ? 220 * 1024 : 110 * 1024;
     const size_t fixed = tc_fixed_smem(p.nkb, N, tc_rh_of(R));
     int stages = (int)std::min<size_t>(8, (budget > fixed ? (budget - fixed) : 0) / TC_BOX_BYTES);
+    if (tch.stages > 0) stages = std::min(stages, tch.stages);
     p.stages = std::max(2, stages);
     const size_t smem = fixed + (size_t)p.stages * TC_BOX_BYTES;
     *P_out = epi == 0 ? p.nks : p.npb;

@@ -300,7 +300,19 @@ long long partial_elems(const AlsDesc &d);  // per repetition
 
 // tcgen05 MTTKRP of bfloat16 summaries (k_tc.cu)
 bool tc_supported(int R, int NC, bool fp8);
-void tc_tiles(int nrep, int NP, int Kp, int num_sms, int *npb, int *nks, int *spc);
+// tile choice of one tensor-core MTTKRP launch shape: CTAs per SM (1 or 2),
+// pipeline stages (0: as many as fit)
+struct TileChoice {
+    int per_sm, stages;
+};
+TileChoice tile_choice(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi);
+bool tile_known(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi);
+void tile_store(bool fp8, int R, int NP, int NC, int Kp, int nrep, int epi, TileChoice c);
+int tile_table_read(int *out, int cap);
+void tile_table_merge(const int *in, int n);
+void tile_table_clear();
+void tc_tiles(int nrep, int NP, int Kp, int num_sms, int per_sm, int *npb, int *nks, int *spc);
+void tc_plan(bool fp8, int R, int nrep, int NP, int NC, int Kp, int epi, int num_sms, int *npb, int *nks, int *spc);
 cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, int ld, long long nslices,
                               bool fp8);
 // tmap_lo: null, or the map of the lo part of a split summary (added into
@@ -311,7 +323,7 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
-                             int num_sms, int *P_out, cudaStream_t st);
+                             int num_sms, int *P_out, cudaStream_t st, const TileChoice *force = nullptr);
 cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
                                   cudaStream_t st);
 // reduction of d.P[mode] partials into d.M, then the tail

@@ -51,7 +51,7 @@ EXPORTS = [
     "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
     "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
-    "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve",
+    "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve", "sbt_tile_table",
     "sbt_server_default_options", "sbt_server_create", "sbt_server_open_stream", "sbt_server_submit",
     "sbt_server_wait", "sbt_server_stream_ctx", "sbt_server_close_stream", "sbt_server_stats",
     "sbt_server_stats_reset", "sbt_server_destroy",
@@ -73,7 +73,7 @@ class SbtOptions(ctypes.Structure):
                 ("lambda_mode", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
                 ("K_capacity", ctypes.c_int64), ("max_batch", ctypes.c_int64),
                 ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32),
-                ("refine_sweeps", ctypes.c_int32)]
+                ("refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class SbtStats(ctypes.Structure):
@@ -90,6 +90,13 @@ class SbtProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
                 ("mttkrp_bytes", ctypes.c_double)]
+
+
+TILE_FIELDS = ("fp8", "R", "NP", "NC", "Kp_bucket", "nrep", "epi", "ctas_per_sm", "stages")
+
+
+class SbtTileEntry(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in TILE_FIELDS]
 
 
 class SbtServerOptions(ctypes.Structure):
@@ -155,6 +162,7 @@ def lib() -> ctypes.CDLL:
     L.sbt_device_bytes.argtypes = [P, ctypes.POINTER(U64)]
     L.sbt_update_bytes.argtypes = [P, I64, ctypes.POINTER(U64)]
     L.sbt_reserve.argtypes = [P, I64, I64]
+    L.sbt_tile_table.argtypes = [I32, P, I32, ctypes.POINTER(I32)]
     L.sbt_server_default_options.argtypes = [ctypes.POINTER(SbtServerOptions)]
     L.sbt_server_create.argtypes = [ctypes.POINTER(SbtServerOptions), ctypes.POINTER(P)]
     L.sbt_server_open_stream.argtypes = [P, ctypes.POINTER(SbtTensor), I32, ctypes.POINTER(SbtOptions),
@@ -182,6 +190,30 @@ def _check(status: int, where: str):
 
 def version() -> str:
     return lib().sbt_version().decode()
+
+
+def tile_table() -> list:
+    """The MTTKRP tile table as a list of dicts (TILE_FIELDS)."""
+    n = ctypes.c_int32()
+    _check(lib().sbt_tile_table(0, None, 0, ctypes.byref(n)), "sbt_tile_table")
+    arr = (SbtTileEntry * max(1, n.value))()
+    _check(lib().sbt_tile_table(0, ctypes.cast(arr, ctypes.c_void_p), n.value, ctypes.byref(n)), "sbt_tile_table")
+    return [{f: getattr(arr[q], f) for f in TILE_FIELDS} for q in range(n.value)]
+
+
+def tile_table_merge(entries: list):
+    arr = (SbtTileEntry * max(1, len(entries)))()
+    for q, e in enumerate(entries):
+        for f in TILE_FIELDS:
+            setattr(arr[q], f, int(e[f]))
+    n = ctypes.c_int32()
+    _check(lib().sbt_tile_table(1, ctypes.cast(arr, ctypes.c_void_p), len(entries), ctypes.byref(n)),
+           "sbt_tile_table")
+
+
+def tile_table_clear():
+    n = ctypes.c_int32()
+    _check(lib().sbt_tile_table(2, None, 0, ctypes.byref(n)), "sbt_tile_table")
 
 
 # ---------------------------------------------------------------------------

@@ -105,3 +105,27 @@ def test_server_host_logic_without_gpu(lib):
     lib.sbt_server_destroy(srv)
     slots_bad = sbt.SbtServerOptions(65, 1, 0)
     assert lib.sbt_server_create(ctypes.byref(slots_bad), ctypes.byref(srv)) == sbt.SBT_E_INVALID
+
+
+def test_tile_table_host_logic(lib):
+    """The MTTKRP tile table: merge, read back, replace by key, reject bad
+    choices, clear (host only)."""
+    from paper_1709_00668_gb300 import sbt
+    sbt.tile_table_clear()
+    assert sbt.tile_table() == []
+    e1 = dict(fp8=0, R=10, NP=200, NC=200, Kp_bucket=6, nrep=8, epi=0, ctas_per_sm=1, stages=6)
+    e2 = dict(e1, epi=1, ctas_per_sm=2, stages=0)
+    sbt.tile_table_merge([e1, e2])
+    got = sbt.tile_table()
+    assert len(got) == 2 and e1 in got and e2 in got
+    sbt.tile_table_merge([dict(e1, stages=3)])
+    got = sbt.tile_table()
+    assert len(got) == 2 and dict(e1, stages=3) in got
+    with pytest.raises(sbt.SbtError):
+        sbt.tile_table_merge([dict(e1, ctas_per_sm=3)])
+    with pytest.raises(sbt.SbtError):
+        sbt.tile_table_merge([dict(e1, stages=9)])
+    n = ctypes.c_int32()
+    assert lib.sbt_tile_table(7, None, 0, ctypes.byref(n)) == sbt.SBT_E_INVALID
+    sbt.tile_table_clear()
+    assert sbt.tile_table() == []

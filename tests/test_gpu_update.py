@@ -357,3 +357,28 @@ def test_device_loop_equals_directly_launched_iterations(sbt):
                 assert p1["mttkrp_launches"] % 12 == 0 and p1["mttkrp_launches"] > 0
             assert p1["mttkrp_bytes"] == p2["mttkrp_bytes"]
             assert p1["mttkrp_ms"] == 0 and p2["mttkrp_ms"] > 0
+
+
+def test_autotune_records_choices_and_keeps_parity(sbt):
+    """Autotuned tile choices: one table entry per tensor-core launch shape,
+    parity with the oracle kept, and a second context of the same shapes
+    reuses the entries (no new tuning) with bit-identical results."""
+    sbt.tile_table_clear()
+    X, A, B, C = planted(200, 200, 120, 10, dtype=torch.float32, seed=1)
+    fac = unit_factors(A, B, C[:100])
+    kw = dict(prec="bf16", s_I=5, s_J=5, s_K=5, r=8, fixed_iters=1, max_iters=20)
+    ctx, ost = _pair(sbt, X, 100, 10, fac, autotune=1, **kw)
+    ost2, traces = O.update(ost, X[100:120], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[100:120]).cuda())
+    _check_update(ctx, ost2, traces, ftol=1e-3)
+    tab = sbt.tile_table()
+    st = ctx.stats()
+    shapes = {(st["n_I"], st["n_J"], 0), (st["n_J"], st["n_I"], 0), (st["n_I"], st["n_J"], 1)}  # modes 1, 2, 3
+    assert {(e["NP"], e["NC"], e["epi"]) for e in tab} == shapes and len(tab) == len(shapes)
+    assert all(e["ctas_per_sm"] in (1, 2) and 0 <= e["stages"] <= 8 for e in tab)
+    ctx2, _ = _pair(sbt, X, 100, 10, fac, autotune=1, **kw)
+    ctx2.update(torch.from_numpy(X[100:120]).cuda())
+    assert sbt.tile_table() == tab
+    for a, b in zip(ctx.factors(), ctx2.factors()):
+        assert np.array_equal(a, b)
+    sbt.tile_table_clear()
