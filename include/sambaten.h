@@ -154,6 +154,37 @@ sbt_status sbt_fit(sbt_ctx *ctx, double *fit);
 /* Statistics of the last sbt_update. */
 sbt_status sbt_stats(const sbt_ctx *ctx, sbt_update_stats *st);
 
+/* ---- sparse (COO) tensors -------------------------------------------------
+ * The same method (Alg. 1) on tensors stored as nonzeros (the sparse
+ * workloads of Section 5.1).  The context keeps the nonzeros grouped by time
+ * slice; summaries are the lists of nonzeros of the sampled slices whose row
+ * and column were sampled.  Results equal the dense definitions applied to the
+ * densified tensor; the MTTKRP adds its float32 products in 64-bit fixed point,
+ * so results do not depend on the order of the input nonzeros.  Coordinates
+ * must be unique (duplicates are not merged).  Options: prec must be
+ * SBT_PREC_F32; refine_sweeps, autotune, max_batch do not apply. */
+typedef struct {
+    int64_t I, J, K;           /* shape (K: slices of this tensor or batch) */
+    int64_t nnz;               /* nonzeros, < 2^31 */
+    const int32_t *ii, *jj, *kk;  /* coordinates; kk relative to this tensor (batch): 0 <= kk < K */
+    const float *val;
+    int32_t on_device;         /* arrays in device memory (ordered on opts.cuda_stream) or host */
+} sbt_coo;
+
+/* CP-ALS of X0 (max_iters_init iterations) and a context for updates.
+ * SBT_E_SHAPE: a coordinate outside the shape; SBT_E_NONFINITE; SBT_E_INVALID. */
+sbt_status sbt_init_coo(const sbt_coo *X0, int32_t R, const sbt_options *opts, sbt_ctx **out);
+
+/* As sbt_init_coo with the decomposition of X0 given (host, row-major, as
+ * sbt_init_factors). */
+sbt_status sbt_init_coo_factors(const sbt_coo *X0, int32_t R, const double *lambda, const double *A,
+                                const double *B, const double *C, const sbt_options *opts, sbt_ctx **out);
+
+/* One batch of K_new new slices given as nonzeros (kk relative to the batch);
+ * transactional like sbt_update.  sbt_factors, sbt_fit, sbt_stats,
+ * sbt_last_samples and sbt_last_summary_factors apply to COO contexts too. */
+sbt_status sbt_update_coo(sbt_ctx *ctx, const sbt_coo *X_new);
+
 /* ---- device memory of a context ------------------------------------------
  * No counterpart in the paper: these let a caller (the server below) admit
  * work by a device-memory budget and keep allocation out of the update path. */

@@ -166,6 +166,16 @@ struct sbt_ctx {
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
+    // COO contexts (sbt_init_coo): nonzeros grouped by slice, and the summary workspace
+    bool coo = false;
+    int64_t nnz = 0;
+    Buf si, sj, sv, sptr;                   // store [nnz cap] x 3, slice offsets [K cap + 1]
+    Buf cin_i, cin_j, cin_k, cin_v;         // host input staged on the device
+    Buf ccnt, cfill, cmax;                  // per new slice counts / fill; max |v| of the input
+    Buf posI, posJ, gcnt, goff, gtot, vmax, fexp;
+    Buf eii, ejj, ekk, ev, perm1, perm2, rp1, rp2, gc1, gc2, gf1, gf2;
+    HBuf h_tot;
+    CooDesc cd{};
     cudaStream_t side = nullptr;  // runs V^-1 of a mode beside its MTTKRP pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TcPlan tc;
@@ -283,6 +293,7 @@ static sbt_status status_error(unsigned err) {
     if (err & ERR_RANGE) return fail(SBT_E_RANGE, "fixed-point marginal would overflow 64 bits");
     if (err & ERR_SAMPLE) return fail(SBT_E_STATE, "sample size above the number of positive weights");
     if (err & ERR_TIMEOUT) return fail(SBT_E_TIMEOUT, "a bounded device wait gave up");
+    if (err & ERR_INDEX) return fail(SBT_E_SHAPE, "a COO coordinate lies outside the tensor");
     return SBT_OK;
 }
 
@@ -399,6 +410,7 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
 // Run ALS iterations until every repetition converged (polled every
 // check_every iterations) or max_iters.
 static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode) {
+    if (c->coo) return launch_mttkrp_coo(d, c->cd, mode, c->stream);
     if (!tc || !tc->on) return launch_mttkrp(d, mode, c->stream);
     const int R = d.R, NI = d.n[0], NJ = d.n[1], Kp = d.n[2];
     const float *U0 = (const float *)d.U[0], *U1 = (const float *)d.U[1], *U2 = (const float *)d.U[2];
@@ -893,7 +905,10 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
-            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale};
+            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale,
+            &c->si, &c->sj, &c->sv, &c->sptr, &c->cin_i, &c->cin_j, &c->cin_k, &c->cin_v, &c->ccnt, &c->cfill,
+            &c->cmax, &c->posI, &c->posJ, &c->gcnt, &c->goff, &c->gtot, &c->vmax, &c->fexp, &c->eii, &c->ejj,
+            &c->ekk, &c->ev, &c->perm1, &c->perm2, &c->rp1, &c->rp2, &c->gc1, &c->gc2, &c->gf1, &c->gf2};
 }
 
 // device bytes after the needs of z (every buffer at max(capacity, need))
@@ -958,6 +973,7 @@ extern "C" sbt_status sbt_device_bytes(sbt_ctx *c, uint64_t *bytes) {
 
 extern "C" sbt_status sbt_update_bytes(sbt_ctx *c, int64_t K_new, uint64_t *bytes) {
     if (!c || !bytes || K_new < 1 || K_new > INT32_MAX) return fail(SBT_E_INVALID, "sbt_update_bytes: bad arguments");
+    if (c->coo) return fail(SBT_E_INVALID, "sbt_update_bytes: dense contexts only");
     UpdShape u;
     TRY(update_shape(c, c->K, (int)K_new, false, u));
     Sizer z;
@@ -969,12 +985,122 @@ extern "C" sbt_status sbt_update_bytes(sbt_ctx *c, int64_t K_new, uint64_t *byte
 
 extern "C" sbt_status sbt_reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max) {
     if (!c) return fail(SBT_E_INVALID, "null context");
+    if (c->coo) return fail(SBT_E_INVALID, "sbt_reserve: dense contexts only");
     DeviceGuard dg(c->device);
     return reserve(c, K_max, K_new_max);
 }
 
+// Steps 5 and 6 of an update (shared-row normalisation, matching, project
+// back, commit) and its statistics; shared by the dense and the COO updates.
+static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int K_new, int nI, int nJ, int nK,
+                               long long samp_stride, int ldj, bool refined, bool no_refine) {
+    const int R = c->R, r = c->opt.r;
+    // 5. normalise, match, project back; 6. commit
+    const int pmax = (int)samp_stride;
+    MergeDesc m;
+    std::memset(&m, 0, sizeof(m));
+    m.nrep = r;
+    m.R = R;
+    m.I = c->I;
+    m.J = c->J;
+    m.K_old = (int)K_old;
+    m.K_new = K_new;
+    m.nI = nI;
+    m.nJ = nJ;
+    m.nK = nK;
+    m.samples = c->samples.as<int>();
+    m.samp_stride = samp_stride;
+    for (int q = 0; q < 3; ++q) m.U[q] = c->U[q].p;
+    m.elem = c->elem == 0 ? 0 : 1;
+    m.lam_s = c->lam_s.as<double>();
+    m.A = c->A.as<double>();
+    m.B = c->B.as<double>();
+    m.C = c->C.as<double>();
+    m.lam = c->lam.as<double>();
+    m.nu = c->nu.as<double>();
+    m.cnew = c->cnew.as<double>();
+    m.prop = c->prop.as<double>();
+    m.pmax = pmax;
+    m.lam_est = c->lam_est.as<double>();
+    m.perm = c->perm.as<int>();
+    m.min_score = c->min_score.as<double>();
+    m.flags = c->flags.as<int>();
+    m.lambda_mode = c->opt.lambda_mode;
+    m.xa = c->xa.as<unsigned long long>();
+    m.xb = c->xb.as<unsigned long long>();
+    m.xc = c->xc.as<unsigned long long>();
+    m.dxa = c->dxa.as<unsigned long long>();
+    m.dxb = c->dxb.as<unsigned long long>();
+    m.xc_new = c->xc_new.as<unsigned long long>();
+    m.status = c->status.as<DevStatus>();
+    CK(launch_match(m, c->stream));
+    CK(launch_precommit(m, c->stream));
+    CK(launch_commit(m, c->stream));
+    // 7. one synchronisation: status and statistics
+    const size_t stat_bytes = sizeof(DevStatus) + (size_t)r * (4 + 8 + 8 + 4 + 4 * R);
+    TRY(c->h_stats.ensure(stat_bytes));
+    char *hb = c->h_stats.as<char>();
+    CK(cudaMemcpyAsync(hb, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    size_t off = sizeof(DevStatus);
+    CK(cudaMemcpyAsync(hb + off, refined ? c->iters_main.p : (void *)d.iters, (size_t)r * 4,
+                       cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 4;
+    CK(cudaMemcpyAsync(hb + off, d.fit, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 8;
+    CK(cudaMemcpyAsync(hb + off, m.min_score, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 8;
+    CK(cudaMemcpyAsync(hb + off, d.flags, (size_t)r * 4, cudaMemcpyDeviceToHost, c->stream));
+    off += (size_t)r * 4;
+    CK(cudaMemcpyAsync(hb + off, m.perm, (size_t)r * R * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
+    DevStatus hs;
+    std::memcpy(&hs, hb, sizeof(DevStatus));
+    if (hs.err) return status_error(hs.err);
+    // the update is committed
+    c->updates += 1;
+    c->K = K_old + K_new;
+    c->batch += 1;
+    for (int q = 0; q < 3; ++q) c->npos[q] = (int64_t)hs.npos[q];
+    sbt_update_stats &st = c->stats;
+    std::memset(&st, 0, sizeof(st));
+    st.K = c->K;
+    st.r = r;
+    st.R = R;
+    st.n_I = nI;
+    st.n_J = nJ;
+    st.n_K = nK;
+    off = sizeof(DevStatus);
+    const int *it = (const int *)(hb + off);
+    off += (size_t)r * 4;
+    const double *ft = (const double *)(hb + off);
+    off += (size_t)r * 8;
+    const double *ms = (const double *)(hb + off);
+    off += (size_t)r * 8;
+    const int *fl = (const int *)(hb + off);
+    off += (size_t)r * 4;
+    const int *pm = (const int *)(hb + off);
+    if (no_refine) st.flags |= SBT_FLAG_NO_REFINE;
+    for (int q = 0; q < r; ++q) {
+        st.iters[q] = it[q];
+        st.fit[q] = ft[q];
+        st.min_score[q] = ms[q];
+        st.flags |= fl[q];
+        for (int a = 0; a < R; ++a) st.perm[q][a] = pm[q * R + a];
+    }
+    c->have_last = true;
+    c->last_nI = nI;
+    c->last_nJ = nJ;
+    c->last_nK = nK;
+    c->last_Knew = K_new;
+    c->last_ldj = ldj;
+    c->last_samp_stride = samp_stride;
+    return SBT_OK;
+}
+
 extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     if (!c) return fail(SBT_E_INVALID, "null context");
+    if (c->coo) return fail(SBT_E_INVALID, "a COO context takes sbt_update_coo");
     TRY(check_tensor(X));
     if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
     if (X->dtype != c->sdtype) return fail(SBT_E_INVALID, "dtype must match the initial tensor");
@@ -1105,107 +1231,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
             refined = true;
         }
     }
-    // 5. normalise, match, project back; 6. commit
-    const int pmax = (int)samp_stride;
-    MergeDesc m;
-    std::memset(&m, 0, sizeof(m));
-    m.nrep = r;
-    m.R = R;
-    m.I = c->I;
-    m.J = c->J;
-    m.K_old = (int)K_old;
-    m.K_new = K_new;
-    m.nI = nI;
-    m.nJ = nJ;
-    m.nK = nK;
-    m.samples = c->samples.as<int>();
-    m.samp_stride = samp_stride;
-    for (int q = 0; q < 3; ++q) m.U[q] = c->U[q].p;
-    m.elem = c->elem == 0 ? 0 : 1;
-    m.lam_s = c->lam_s.as<double>();
-    m.A = c->A.as<double>();
-    m.B = c->B.as<double>();
-    m.C = c->C.as<double>();
-    m.lam = c->lam.as<double>();
-    m.nu = c->nu.as<double>();
-    m.cnew = c->cnew.as<double>();
-    m.prop = c->prop.as<double>();
-    m.pmax = pmax;
-    m.lam_est = c->lam_est.as<double>();
-    m.perm = c->perm.as<int>();
-    m.min_score = c->min_score.as<double>();
-    m.flags = c->flags.as<int>();
-    m.lambda_mode = c->opt.lambda_mode;
-    m.xa = c->xa.as<unsigned long long>();
-    m.xb = c->xb.as<unsigned long long>();
-    m.xc = c->xc.as<unsigned long long>();
-    m.dxa = c->dxa.as<unsigned long long>();
-    m.dxb = c->dxb.as<unsigned long long>();
-    m.xc_new = c->xc_new.as<unsigned long long>();
-    m.status = c->status.as<DevStatus>();
-    CK(launch_match(m, c->stream));
-    CK(launch_precommit(m, c->stream));
-    CK(launch_commit(m, c->stream));
-    // 7. one synchronisation: status and statistics
-    const size_t stat_bytes = sizeof(DevStatus) + (size_t)r * (4 + 8 + 8 + 4 + 4 * R);
-    TRY(c->h_stats.ensure(stat_bytes));
-    char *hb = c->h_stats.as<char>();
-    CK(cudaMemcpyAsync(hb, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
-    size_t off = sizeof(DevStatus);
-    CK(cudaMemcpyAsync(hb + off, refined ? c->iters_main.p : (void *)d.iters, (size_t)r * 4,
-                       cudaMemcpyDeviceToHost, c->stream));
-    off += (size_t)r * 4;
-    CK(cudaMemcpyAsync(hb + off, d.fit, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
-    off += (size_t)r * 8;
-    CK(cudaMemcpyAsync(hb + off, m.min_score, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
-    off += (size_t)r * 8;
-    CK(cudaMemcpyAsync(hb + off, d.flags, (size_t)r * 4, cudaMemcpyDeviceToHost, c->stream));
-    off += (size_t)r * 4;
-    CK(cudaMemcpyAsync(hb + off, m.perm, (size_t)r * R * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    settle_als_counts(c);
-    DevStatus hs;
-    std::memcpy(&hs, hb, sizeof(DevStatus));
-    if (hs.err) return status_error(hs.err);
-    // the update is committed
-    c->updates += 1;
-    c->K = K_old + K_new;
-    c->batch += 1;
-    for (int q = 0; q < 3; ++q) c->npos[q] = (int64_t)hs.npos[q];
-    sbt_update_stats &st = c->stats;
-    std::memset(&st, 0, sizeof(st));
-    st.K = c->K;
-    st.r = r;
-    st.R = R;
-    st.n_I = nI;
-    st.n_J = nJ;
-    st.n_K = nK;
-    off = sizeof(DevStatus);
-    const int *it = (const int *)(hb + off);
-    off += (size_t)r * 4;
-    const double *ft = (const double *)(hb + off);
-    off += (size_t)r * 8;
-    const double *ms = (const double *)(hb + off);
-    off += (size_t)r * 8;
-    const int *fl = (const int *)(hb + off);
-    off += (size_t)r * 4;
-    const int *pm = (const int *)(hb + off);
-    if (no_refine) st.flags |= SBT_FLAG_NO_REFINE;
-    for (int q = 0; q < r; ++q) {
-        st.iters[q] = it[q];
-        st.fit[q] = ft[q];
-        st.min_score[q] = ms[q];
-        st.flags |= fl[q];
-        for (int a = 0; a < R; ++a) st.perm[q][a] = pm[q * R + a];
-    }
-    c->have_last = true;
-    c->last_nI = nI;
-    c->last_nJ = nJ;
-    c->last_nK = nK;
-    c->last_Knew = K_new;
-    c->last_ldj = ldj;
-    c->last_samp_stride = samp_stride;
-    return SBT_OK;
+    return match_commit(c, d, K_old, K_new, nI, nJ, nK, samp_stride, ldj, refined, no_refine);
 }
 
 extern "C" sbt_status sbt_factors(const sbt_ctx *c, double *lambda, double *A, double *B, double *C, int64_t *K_out) {
@@ -1220,9 +1246,12 @@ extern "C" sbt_status sbt_factors(const sbt_ctx *c, double *lambda, double *A, d
     return SBT_OK;
 }
 
+static sbt_status coo_fit(sbt_ctx *c, double *fit);
+
 extern "C" sbt_status sbt_fit(sbt_ctx *c, double *fit) {
     if (!c || !fit) return fail(SBT_E_INVALID, "null argument");
     DeviceGuard dg(c->device);
+    if (c->coo) return coo_fit(c, fit);
     const long long need = fit_scratch_doubles((int)c->K, c->I, c->J, c->R) + 2;
     TRY(c->fitscr.ensure((size_t)need * 8));
     double *scr = c->fitscr.as<double>();
@@ -1268,6 +1297,7 @@ static inline float bf16_bits_to_float(uint16_t b) {
 extern "C" sbt_status sbt_last_summary(const sbt_ctx *c, int32_t rep, double *out, int64_t cap, int64_t dims[3]) {
     if (!c || !dims) return fail(SBT_E_INVALID, "null argument");
     if (!c->have_last) return fail(SBT_E_STATE, "no update has run");
+    if (c->coo) return fail(SBT_E_STATE, "COO summaries are lists of nonzeros, not dense arrays");
     if (rep < 0 || rep >= c->opt.r) return fail(SBT_E_INVALID, "rep out of range");
     DeviceGuard dg(c->device);
     const int nI = c->last_nI, nJ = c->last_nJ, Kp = c->last_nK + c->last_Knew, ldj = c->last_ldj;
@@ -1363,6 +1393,505 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
     out->mttkrp_launches = c->mtt_launches;
     out->mttkrp_ms = ms;
     out->mttkrp_bytes = (double)bytes;
+    return SBT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// COO tensors: the same method (Alg. 1) on a store of nonzeros grouped by
+// time slice; the sparse workloads of Section 5.1.
+
+static sbt_status check_coo(const sbt_coo *X) {
+    if (!X) return fail(SBT_E_INVALID, "null tensor");
+    if (X->I < 1 || X->J < 1 || X->K < 1) return fail(SBT_E_SHAPE, "tensor dimensions must be >= 1");
+    if (X->I > INT32_MAX || X->J > INT32_MAX || X->K > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
+    if (X->nnz < 0 || X->nnz > INT32_MAX) return fail(SBT_E_SHAPE, "nnz out of range");
+    if (X->nnz > 0 && (!X->ii || !X->jj || !X->kk || !X->val)) return fail(SBT_E_INVALID, "null COO array");
+    return SBT_OK;
+}
+
+// device arrays of a COO input: host arrays are copied to staging buffers
+static sbt_status coo_device(sbt_ctx *c, const sbt_coo *X, const int **ii, const int **jj, const int **kk,
+                             const float **v) {
+    if (X->on_device || X->nnz == 0) {
+        *ii = X->ii;
+        *jj = X->jj;
+        *kk = X->kk;
+        *v = X->val;
+        return SBT_OK;
+    }
+    const size_t n = (size_t)X->nnz;
+    TRY(c->cin_i.ensure(n * 4));
+    TRY(c->cin_j.ensure(n * 4));
+    TRY(c->cin_k.ensure(n * 4));
+    TRY(c->cin_v.ensure(n * 4));
+    CK(cudaMemcpyAsync(c->cin_i.p, X->ii, n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->cin_j.p, X->jj, n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->cin_k.p, X->kk, n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->cin_v.p, X->val, n * 4, cudaMemcpyHostToDevice, c->stream));
+    *ii = c->cin_i.as<int>();
+    *jj = c->cin_j.as<int>();
+    *kk = c->cin_k.as<int>();
+    *v = c->cin_v.as<float>();
+    return SBT_OK;
+}
+
+// room for `need` stored nonzeros (doubling; the first nnz are kept)
+static sbt_status coo_grow_nnz(sbt_ctx *c, int64_t need) {
+    const int64_t cap = (int64_t)(c->sv.cap / 4);
+    if (need <= cap && c->sv.p) return SBT_OK;
+    const int64_t ncap = std::max<int64_t>(std::max<int64_t>(need, 2 * cap), 1024);
+    Buf ni, nj, nv;
+    TRY(ni.ensure((size_t)ncap * 4));
+    TRY(nj.ensure((size_t)ncap * 4));
+    TRY(nv.ensure((size_t)ncap * 4));
+    if (c->nnz > 0) {
+        CK(cudaMemcpyAsync(ni.p, c->si.p, (size_t)c->nnz * 4, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(nj.p, c->sj.p, (size_t)c->nnz * 4, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(nv.p, c->sv.p, (size_t)c->nnz * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    std::swap(c->si.p, ni.p);
+    std::swap(c->si.cap, ni.cap);
+    std::swap(c->sj.p, nj.p);
+    std::swap(c->sj.cap, nj.cap);
+    std::swap(c->sv.p, nv.p);
+    std::swap(c->sv.cap, nv.cap);
+    return SBT_OK;
+}
+
+// room for `need` slices: C, x_c and the slice offsets
+static sbt_status coo_grow_slices(sbt_ctx *c, int64_t need) {
+    if (need <= c->Kcap) return SBT_OK;
+    const int64_t ncap = std::max<int64_t>(need, c->Kcap * 2);
+    Buf nC, nxc, nsp;
+    TRY(nC.ensure((size_t)ncap * c->R * 8));
+    TRY(nxc.ensure((size_t)ncap * 8));
+    TRY(nsp.ensure((size_t)(ncap + 1) * 8));
+    CK(cudaMemsetAsync(nxc.p, 0, (size_t)ncap * 8, c->stream));
+    CK(cudaMemcpyAsync(nC.p, c->C.p, (size_t)c->K * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(nxc.p, c->xc.p, (size_t)c->K * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(nsp.p, c->sptr.p, (size_t)(c->K + 1) * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::swap(c->C.p, nC.p);
+    std::swap(c->C.cap, nC.cap);
+    std::swap(c->xc.p, nxc.p);
+    std::swap(c->xc.cap, nxc.cap);
+    std::swap(c->sptr.p, nsp.p);
+    std::swap(c->sptr.cap, nsp.cap);
+    c->Kcap = ncap;
+    return SBT_OK;
+}
+
+// Context of a COO tensor: the store of X0's nonzeros and its marginals (Eq. 1)
+static sbt_status coo_begin(const sbt_coo *X0, int32_t R, const sbt_options *opt, sbt_ctx *c) {
+    TRY(check_coo(X0));
+    TRY(check_options(opt, R));
+    if (opt->prec != SBT_PREC_F32)
+        return fail(SBT_E_INVALID, "COO tensors take SBT_PREC_F32 (float32 values, fixed-point MTTKRP sums)");
+    c->opt = *opt;
+    c->coo = true;
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    CK(ensure_kernel_attributes(c->device));
+    c->user = (cudaStream_t)opt->cuda_stream;
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming));
+    TRY(order_after_user(c));
+    c->I = (int)X0->I;
+    c->J = (int)X0->J;
+    c->R = R;
+    c->K = X0->K;
+    c->sdtype = SBT_F32;
+    c->elem = 1;
+    c->Kcap = std::max<int64_t>(opt->K_capacity > 0 ? opt->K_capacity : 2 * X0->K, X0->K + 1);
+    TRY(c->A.ensure((size_t)c->I * R * 8));
+    TRY(c->B.ensure((size_t)c->J * R * 8));
+    TRY(c->C.ensure((size_t)c->Kcap * R * 8));
+    TRY(c->lam.ensure((size_t)R * 8));
+    TRY(c->xa.ensure((size_t)c->I * 8));
+    TRY(c->xb.ensure((size_t)c->J * 8));
+    TRY(c->xc.ensure((size_t)c->Kcap * 8));
+    TRY(c->dxa.ensure((size_t)c->I * 8));
+    TRY(c->dxb.ensure((size_t)c->J * 8));
+    TRY(c->sptr.ensure((size_t)(c->Kcap + 1) * 8));
+    TRY(c->status.ensure(sizeof(DevStatus)));
+    TRY(c->h_status.ensure(sizeof(DevStatus)));
+    TRY(c->prof_bytes.ensure(8));
+    TRY(c->cmax.ensure(4));
+    CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
+    CK(cudaMemsetAsync(c->xa.p, 0, (size_t)c->I * 8, c->stream));
+    CK(cudaMemsetAsync(c->xb.p, 0, (size_t)c->J * 8, c->stream));
+    CK(cudaMemsetAsync(c->xc.p, 0, (size_t)c->Kcap * 8, c->stream));
+    CK(cudaMemsetAsync(c->cmax.p, 0, 4, c->stream));
+    TRY(coo_grow_nnz(c, std::max<int64_t>(X0->nnz, 1)));
+    const int *ii, *jj, *kk;
+    const float *v;
+    TRY(coo_device(c, X0, &ii, &jj, &kk, &v));
+    // the shift S from max |x| (zeros do not matter), as for dense tensors
+    CK(launch_abs_max_f(v, X0->nnz, c->cmax.as<unsigned>(), c->stream));
+    unsigned mb = 0;
+    CK(cudaMemcpyAsync(c->h_status.p, c->cmax.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(&mb, c->h_status.p, 4);
+    float mf;
+    std::memcpy(&mf, &mb, 4);
+    const double M = (double)mf;
+    if (M == 0.0) {
+        c->S = 0;
+    } else {
+        int e2;
+        std::frexp(M * M, &e2);
+        c->S = 32 - e2;
+    }
+    // nonzeros into the store by slice; marginals straight into x_a, x_b, x_c
+    const int K = (int)c->K;
+    TRY(c->ccnt.ensure((size_t)K * 4));
+    TRY(c->cfill.ensure((size_t)K * 4));
+    CK(cudaMemsetAsync(c->ccnt.p, 0, (size_t)K * 4, c->stream));
+    CK(cudaMemsetAsync(c->cfill.p, 0, (size_t)K * 4, c->stream));
+    CK(launch_coo_count(kk, X0->nnz, K, c->ccnt.as<int>(), c->status.as<DevStatus>(), c->stream));
+    CK(launch_exscan(c->ccnt.as<int>(), 0, c->sptr.as<long long>(), 0, K, 1, 0, c->stream));
+    CK(launch_coo_scatter(ii, jj, kk, v, X0->nnz, c->I, c->J, K, c->S, c->sptr.as<long long>(), c->cfill.as<int>(),
+                          c->si.as<int>(), c->sj.as<int>(), c->sv.as<float>(), c->xa.as<unsigned long long>(),
+                          c->xb.as<unsigned long long>(), c->xc.as<unsigned long long>(), c->status.as<DevStatus>(),
+                          c->stream));
+    DevStatus hs;
+    TRY(read_status(c, &hs));
+    TRY(status_error(hs.err));
+    c->nnz = X0->nnz;
+    std::vector<unsigned long long> h(std::max<int64_t>(std::max(c->I, c->J), c->K));
+    const unsigned long long *src[3] = {c->xa.as<unsigned long long>(), c->xb.as<unsigned long long>(),
+                                        c->xc.as<unsigned long long>()};
+    const int64_t len[3] = {c->I, c->J, c->K};
+    for (int m = 0; m < 3; ++m) {
+        CK(cudaMemcpy(h.data(), src[m], (size_t)len[m] * 8, cudaMemcpyDeviceToHost));
+        int64_t cnt = 0;
+        for (int64_t x = 0; x < len[m]; ++x) cnt += h[x] != 0;
+        c->npos[m] = cnt;
+    }
+    return SBT_OK;
+}
+
+// entries of every repetition grouped by ii (mode 1) and jj (mode 2), and the
+// fixed-point exponents; the MTTKRP descriptor of the summaries
+static sbt_status coo_groups(sbt_ctx *c, int nrep, int nI, int nJ, long long ecap, long long max_total,
+                             const int *eii, const int *ejj) {
+    TRY(c->gc1.ensure((size_t)nrep * (nI + 1) * 4));
+    TRY(c->gc2.ensure((size_t)nrep * (nJ + 1) * 4));
+    TRY(c->gf1.ensure((size_t)nrep * nI * 4));
+    TRY(c->gf2.ensure((size_t)nrep * nJ * 4));
+    TRY(c->rp1.ensure((size_t)nrep * (nI + 1) * 8));
+    TRY(c->rp2.ensure((size_t)nrep * (nJ + 1) * 8));
+    TRY(c->perm1.ensure((size_t)nrep * std::max(1LL, ecap) * 4));
+    TRY(c->perm2.ensure((size_t)nrep * std::max(1LL, ecap) * 4));
+    TRY(c->fexp.ensure((size_t)nrep * 4));
+    CK(cudaMemsetAsync(c->gc1.p, 0, (size_t)nrep * (nI + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(c->gc2.p, 0, (size_t)nrep * (nJ + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(c->gf1.p, 0, (size_t)nrep * nI * 4, c->stream));
+    CK(cudaMemsetAsync(c->gf2.p, 0, (size_t)nrep * nJ * 4, c->stream));
+    const long long *tot = c->gtot.as<long long>();
+    CK(launch_coo_group(eii, ecap, tot, max_total, nI, nrep, c->gc1.as<int>(), c->rp1.as<long long>(),
+                        c->gf1.as<int>(), c->perm1.as<int>(), c->stream));
+    CK(launch_coo_group(ejj, ecap, tot, max_total, nJ, nrep, c->gc2.as<int>(), c->rp2.as<long long>(),
+                        c->gf2.as<int>(), c->perm2.as<int>(), c->stream));
+    CK(launch_coo_fexp(c->vmax.as<unsigned>(), tot, nrep, c->fexp.as<int>(), c->stream));
+    return SBT_OK;
+}
+
+// ALS descriptor of COO summaries: one partial per mode (the MTTKRP writes
+// whole rows)
+static void coo_partials(AlsDesc &d) {
+    d.P[0] = d.P[1] = d.P[2] = 1;
+    d.prs = (long long)std::max(d.n[0], std::max(d.n[1], d.n[2])) * d.pr;
+}
+
+// CP-ALS of the whole stored tensor (the identity summary), or nothing when
+// the factors are given
+static sbt_status coo_init_als(sbt_ctx *c) {
+    const int K = (int)c->K;
+    const long long nnz = c->nnz;
+    TRY(c->ekk.ensure((size_t)std::max(1LL, nnz) * 4));
+    CK(launch_coo_expand_k(c->sptr.as<long long>(), K, c->ekk.as<int>(), c->stream));
+    TRY(c->gtot.ensure(8));
+    TRY(c->vmax.ensure(4));
+    CK(cudaMemcpy(c->gtot.p, &nnz, 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c->vmax.p, c->cmax.p, 4, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(coo_groups(c, 1, c->I, c->J, nnz, nnz, c->si.as<int>(), c->sj.as<int>()));
+    c->cd = CooDesc{nnz, c->si.as<int>(), c->sj.as<int>(), c->ekk.as<int>(), c->sv.as<float>(),
+                    c->sptr.as<long long>(), c->rp1.as<long long>(), c->rp2.as<long long>(), c->perm1.as<int>(),
+                    c->perm2.as<int>(), c->fexp.as<int>()};
+    AlsDesc d;
+    const int n[3] = {c->I, c->J, K};
+    TRY(setup_als(c, d, 1, n, 0, K, 1, nullptr, 0, c->opt.max_iters_init));
+    coo_partials(d);
+    d.rq_rows = K;
+    // ||X||^2 per slice from the exact marginals: x_c(k) 2^-S
+    std::vector<unsigned long long> hx(K);
+    CK(cudaMemcpy(hx.data(), c->xc.p, (size_t)K * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> rq(K);
+    for (int k = 0; k < K; ++k) rq[k] = std::ldexp((double)hx[k], -c->S);
+    TRY(c->rowsq.ensure((size_t)K * 8));
+    CK(cudaMemcpy(c->rowsq.p, rq.data(), (size_t)K * 8, cudaMemcpyHostToDevice));
+    CK(launch_als_prepare(d, nullptr, 0, K, true, c->opt.seed, c->opt.stream_id, 0xFFFFFFFFu, c->rowsq.as<double>(),
+                          c->stream));
+    TRY(run_als(c, d, c->opt.max_iters_init));
+    CK(launch_canonicalize(d, c->A.as<double>(), c->B.as<double>(), c->C.as<double>(), c->lam.as<double>(),
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_init_coo(const sbt_coo *X0, int32_t R, const sbt_options *opt, sbt_ctx **out) {
+    if (!out) return fail(SBT_E_INVALID, "null output pointer");
+    *out = nullptr;
+    sbt_ctx *c = new sbt_ctx();
+    sbt_status s = coo_begin(X0, R, opt, c);
+    if (s == SBT_OK) s = coo_init_als(c);
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_init_coo_factors(const sbt_coo *X0, int32_t R, const double *lambda, const double *A,
+                                           const double *B, const double *C, const sbt_options *opt, sbt_ctx **out) {
+    if (!out) return fail(SBT_E_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!lambda || !A || !B || !C) return fail(SBT_E_INVALID, "null factor pointer");
+    sbt_ctx *c = new sbt_ctx();
+    sbt_status s = coo_begin(X0, R, opt, c);
+    if (s == SBT_OK) {
+        cudaError_t e = cudaMemcpy(c->A.p, A, (size_t)c->I * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->B.p, B, (size_t)c->J * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->C.p, C, (size_t)c->K * R * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->lam.p, lambda, (size_t)R * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(SBT_E_CUDA, std::string("factor upload: ") + cudaGetErrorString(e));
+    }
+    if (s != SBT_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SBT_OK;
+}
+
+extern "C" sbt_status sbt_update_coo(sbt_ctx *c, const sbt_coo *X) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    if (!c->coo) return fail(SBT_E_INVALID, "not a COO context (sbt_update takes dense slices)");
+    TRY(check_coo(X));
+    if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
+    DeviceGuard dg(c->device);
+    TRY(order_after_user(c));
+    const int R = c->R, r = c->opt.r;
+    const int K_new = (int)X->K;
+    const int64_t K_old = c->K;
+    // sample sizes (Section 4.1): ceil(N / s), clamped to the positive weights
+    const int nI = (int)std::min<int64_t>(ceil_div(c->I, c->opt.s_I), c->npos[0]);
+    const int nJ = (int)std::min<int64_t>(ceil_div(c->J, c->opt.s_J), c->npos[1]);
+    const int nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), c->npos[2]);
+    if (nI < 1 || nJ < 1 || nK < 1) return fail(SBT_E_STATE, "a mode has no positive weight to sample");
+    const int Kp = nK + K_new;
+    const long long samp_stride = std::max(nI, std::max(nJ, nK));
+    const long long key_stride = std::max<int64_t>(std::max(c->I, c->J), K_old);
+    TRY(coo_grow_slices(c, K_old + K_new));
+    TRY(coo_grow_nnz(c, c->nnz + X->nnz));
+    const int *ii, *jj, *kk;
+    const float *v;
+    TRY(coo_device(c, X, &ii, &jj, &kk, &v));
+    TRY(c->samples.ensure((size_t)r * 3 * samp_stride * 4));
+    TRY(c->khi.ensure((size_t)r * 3 * key_stride * 8));
+    TRY(c->klo.ensure((size_t)r * 3 * key_stride * 8));
+    TRY(c->xc_new.ensure((size_t)K_new * 8));
+    TRY(c->ccnt.ensure((size_t)K_new * 4));
+    TRY(c->cfill.ensure((size_t)K_new * 4));
+    // 1. append the nonzeros and their marginal deltas
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
+    CK(cudaMemsetAsync(c->dxa.p, 0, (size_t)c->I * 8, c->stream));
+    CK(cudaMemsetAsync(c->dxb.p, 0, (size_t)c->J * 8, c->stream));
+    CK(cudaMemsetAsync(c->xc_new.p, 0, (size_t)K_new * 8, c->stream));
+    CK(cudaMemsetAsync(c->ccnt.p, 0, (size_t)K_new * 4, c->stream));
+    CK(cudaMemsetAsync(c->cfill.p, 0, (size_t)K_new * 4, c->stream));
+    long long *sptr_new = c->sptr.as<long long>() + K_old;
+    CK(launch_coo_count(kk, X->nnz, K_new, c->ccnt.as<int>(), c->status.as<DevStatus>(), c->stream));
+    CK(launch_exscan(c->ccnt.as<int>(), 0, sptr_new, 0, K_new, 1, c->nnz, c->stream));
+    CK(launch_coo_scatter(ii, jj, kk, v, X->nnz, c->I, c->J, K_new, c->S, sptr_new, c->cfill.as<int>(),
+                          c->si.as<int>(), c->sj.as<int>(), c->sv.as<float>(), c->dxa.as<unsigned long long>(),
+                          c->dxb.as<unsigned long long>(), c->xc_new.as<unsigned long long>(),
+                          c->status.as<DevStatus>(), c->stream));
+    // 2. sampling from the marginals of the tensor before the update
+    SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.w[0] = c->xa.as<unsigned long long>();
+    sp.w[1] = c->xb.as<unsigned long long>();
+    sp.w[2] = c->xc.as<unsigned long long>();
+    sp.N[0] = c->I;
+    sp.N[1] = c->J;
+    sp.N[2] = (int)K_old;
+    sp.n[0] = nI;
+    sp.n[1] = nJ;
+    sp.n[2] = nK;
+    sp.mode_id[0] = 0;
+    sp.mode_id[1] = 1;
+    sp.mode_id[2] = 2;
+    sp.nmodes = 3;
+    sp.nrep = r;
+    sp.out = c->samples.as<int>();
+    sp.out_stride = samp_stride;
+    sp.khi = c->khi.as<unsigned long long>();
+    sp.klo = c->klo.as<unsigned long long>();
+    sp.key_stride = key_stride;
+    sp.seed = c->opt.seed;
+    sp.stream_id = c->opt.stream_id;
+    sp.batch = c->batch;
+    sp.status = c->status.as<DevStatus>();
+    CK(launch_sample(sp, c->stream));
+    // 3. the summaries: sampled nonzeros of the sampled and the new slices
+    TRY(c->posI.ensure((size_t)r * c->I * 4));
+    TRY(c->posJ.ensure((size_t)r * c->J * 4));
+    CK(cudaMemsetAsync(c->posI.p, 0xFF, (size_t)r * c->I * 4, c->stream));
+    CK(cudaMemsetAsync(c->posJ.p, 0xFF, (size_t)r * c->J * 4, c->stream));
+    CK(launch_coo_pos(c->samples.as<int>(), samp_stride, nI, nJ, c->I, c->J, r, c->posI.as<int>(), c->posJ.as<int>(),
+                      c->stream));
+    TRY(c->gcnt.ensure((size_t)r * (Kp + 1) * 4));
+    TRY(c->goff.ensure((size_t)r * (Kp + 1) * 8));
+    TRY(c->gtot.ensure((size_t)r * 8));
+    TRY(c->vmax.ensure((size_t)r * 4));
+    TRY(c->rowsq.ensure((size_t)r * Kp * 8));
+    CK(cudaMemsetAsync(c->gcnt.p, 0, (size_t)r * (Kp + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(c->vmax.p, 0, (size_t)r * 4, c->stream));
+    CooGather g;
+    std::memset(&g, 0, sizeof(g));
+    g.si = c->si.as<int>();
+    g.sj = c->sj.as<int>();
+    g.sv = c->sv.as<float>();
+    g.sptr = c->sptr.as<long long>();
+    g.samples = c->samples.as<int>();
+    g.samp_stride = samp_stride;
+    g.posI = c->posI.as<int>();
+    g.posJ = c->posJ.as<int>();
+    g.I = c->I;
+    g.J = c->J;
+    g.nK = nK;
+    g.K_old = (int)K_old;
+    g.K_new = K_new;
+    g.nrep = r;
+    g.S = c->S;
+    g.cnt = c->gcnt.as<int>();
+    g.off = c->goff.as<long long>();
+    g.rowsq = c->rowsq.as<double>();
+    g.vmax = c->vmax.as<unsigned>();
+    CK(launch_coo_gather(g, 0, c->stream));
+    CK(launch_exscan(c->gcnt.as<int>(), Kp + 1, c->goff.as<long long>(), Kp + 1, Kp, r, 0, c->stream));
+    CK(cudaMemcpy2DAsync(c->gtot.p, 8, c->goff.as<long long>() + Kp, (size_t)(Kp + 1) * 8, 8, r,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    TRY(c->h_tot.ensure((size_t)r * 8));
+    CK(cudaMemcpyAsync(c->h_tot.p, c->gtot.p, (size_t)r * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    long long max_total = 0;
+    for (int q = 0; q < r; ++q) max_total = std::max(max_total, c->h_tot.as<long long>()[q]);
+    const long long ecap = std::max(1LL, max_total);
+    TRY(c->eii.ensure((size_t)r * ecap * 4));
+    TRY(c->ejj.ensure((size_t)r * ecap * 4));
+    TRY(c->ekk.ensure((size_t)r * ecap * 4));
+    TRY(c->ev.ensure((size_t)r * ecap * 4));
+    g.ecap = ecap;
+    g.eii = c->eii.as<int>();
+    g.ejj = c->ejj.as<int>();
+    g.ekk = c->ekk.as<int>();
+    g.ev = c->ev.as<float>();
+    CK(launch_coo_gather(g, 1, c->stream));
+    TRY(coo_groups(c, r, nI, nJ, ecap, max_total, c->eii.as<int>(), c->ejj.as<int>()));
+    c->cd = CooDesc{ecap, c->eii.as<int>(), c->ejj.as<int>(), c->ekk.as<int>(), c->ev.as<float>(),
+                    c->goff.as<long long>(), c->rp1.as<long long>(), c->rp2.as<long long>(), c->perm1.as<int>(),
+                    c->perm2.as<int>(), c->fexp.as<int>()};
+    // 4. CP-ALS on the r summaries
+    AlsDesc d;
+    const int n[3] = {nI, nJ, Kp};
+    als_shape(c, d, r, n, 0, nK, 1, c->opt.max_iters);
+    {
+        Sizer z;
+        TRY(als_sizes(c, d, (size_t)r * std::max(nI, std::max(nJ, Kp)) * d.pr * 4 + (size_t)r * d.prs * 4, z));
+    }
+    TRY(als_bind(c, d, nullptr, 0));
+    coo_partials(d);
+    d.rq_rows = Kp;
+    CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
+                          c->batch, c->rowsq.as<double>(), c->stream));
+    TRY(run_als(c, d, c->opt.max_iters));
+    // 5-6. normalise, match, project back, commit
+    const size_t pmax = (size_t)samp_stride;
+    TRY(c->nu.ensure((size_t)r * 3 * R * 8));
+    TRY(c->cnew.ensure((size_t)r * K_new * R * 8));
+    TRY(c->prop.ensure((size_t)r * 3 * pmax * R * 8));
+    TRY(c->lam_est.ensure((size_t)r * R * 8));
+    TRY(c->perm.ensure((size_t)r * R * 4));
+    TRY(c->min_score.ensure((size_t)r * 8));
+    const int64_t nnz_in = X->nnz;
+    TRY(match_commit(c, d, K_old, K_new, nI, nJ, nK, samp_stride, 0, false, false));
+    c->nnz += nnz_in;
+    return SBT_OK;
+}
+
+// Full-tensor fit of a COO context: ||X||^2 from the exact marginals,
+// ||X_hat||^2 from the Grams, <X, X_hat> over the nonzeros in fixed point.
+static sbt_status coo_fit(sbt_ctx *c, double *fit) {
+    const int R = c->R, I = c->I, J = c->J, K = (int)c->K;
+    std::vector<double> lam(R), A((size_t)I * R), B((size_t)J * R), C((size_t)K * R);
+    std::vector<unsigned long long> xc(K);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(lam.data(), c->lam.p, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(A.data(), c->A.p, A.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(B.data(), c->B.p, B.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(C.data(), c->C.p, C.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(xc.data(), c->xc.p, (size_t)K * 8, cudaMemcpyDeviceToHost));
+    double nx2 = 0.0;
+    for (int k = 0; k < K; ++k) nx2 += std::ldexp((double)xc[k], -c->S);
+    auto gram = [R](const std::vector<double> &U, int n) {
+        std::vector<double> G((size_t)R * R, 0.0);
+        for (int x = 0; x < n; ++x)
+            for (int a = 0; a < R; ++a)
+                for (int b = 0; b < R; ++b) G[a * R + b] += U[(size_t)x * R + a] * U[(size_t)x * R + b];
+        return G;
+    };
+    const std::vector<double> GA = gram(A, I), GB = gram(B, J), GC = gram(C, K);
+    double nh2 = 0.0;
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) nh2 += lam[a] * lam[b] * GA[a * R + b] * GB[a * R + b] * GC[a * R + b];
+    // a bound on |v * model| over the nonzeros picks the fixed-point exponent
+    auto colmax = [R](const std::vector<double> &U, int r) {
+        double m = 0.0;
+        for (size_t x = r; x < U.size(); x += R) m = std::max(m, std::fabs(U[x]));
+        return m;
+    };
+    double mb = 0.0;
+    for (int a = 0; a < R; ++a) mb += std::fabs(lam[a]) * colmax(A, a) * colmax(B, a) * colmax(C, a);
+    CK(cudaMemsetAsync(c->cmax.p, 0, 4, c->stream));
+    CK(launch_abs_max_f(c->sv.as<float>(), c->nnz, c->cmax.as<unsigned>(), c->stream));
+    unsigned vb = 0;
+    CK(cudaMemcpyAsync(c->h_status.p, c->cmax.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(&vb, c->h_status.p, 4);
+    float vf;
+    std::memcpy(&vf, &vb, 4);
+    int e2 = 0;
+    std::frexp((double)vf * mb * (double)std::max<int64_t>(1, c->nnz) + 1.0, &e2);
+    const int F = std::max(0, std::min(100, 61 - e2));
+    TRY(c->fitscr.ensure(16));
+    CK(cudaMemsetAsync(c->fitscr.p, 0, 8, c->stream));
+    CK(launch_coo_inner(c->si.as<int>(), c->sj.as<int>(), c->sv.as<float>(), c->sptr.as<long long>(), K,
+                        c->A.as<double>(), c->B.as<double>(), c->C.as<double>(), c->lam.as<double>(), R, F,
+                        c->fitscr.as<unsigned long long>(), c->stream));
+    unsigned long long acc = 0;
+    CK(cudaMemcpyAsync(c->h_status.p, c->fitscr.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(&acc, c->h_status.p, 8);
+    const double inner = std::ldexp((double)(long long)acc, -F);
+    const double resid2 = std::max(nx2 + nh2 - 2.0 * inner, 0.0);
+    *fit = nx2 > 0.0 ? 1.0 - std::sqrt(resid2) / std::sqrt(nx2) : 0.0;
     return SBT_OK;
 }
 

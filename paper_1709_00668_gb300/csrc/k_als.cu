@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
     }
     // ||X_s||^2 from the row sums, fixed order
     __shared__ double red[256];
-    const long long rows = (long long)d.n[2] * d.n[0];
+    const long long rows = d.rq_rows ? d.rq_rows : (long long)d.n[2] * d.n[0];
     const double *rq = rowsq + rep * rows;
     double a = 0.0;
     for (long long e = threadIdx.x; e < rows; e += blockDim.x) a += rq[e];

@@ -51,52 +51,6 @@ cudaError_t launch_absmax(const void *X, int dtype, long long n, DevStatus *stat
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Append + marginals (Eq. 1).  q(x) = floor((x*x) * 2^S): one correctly rounded
-// float64 product (never contracted), exact power-of-two scaling, truncation.
-__device__ __forceinline__ bool qsquare(double x, int S, unsigned long long *q) {
-    double sq = ldexp(__dmul_rn(x, x), S);
-    if (!(sq < 18446744073709551616.0)) return false;
-    *q = __double2ull_rz(sq);
-    return true;
-}
-
-// The same q for a float32 x without float64 arithmetic: x = m * 2^e with a
-// 24-bit integer m, so x*x = m^2 * 2^(2e) exactly and q = floor(m^2 * 2^(2e+S))
-// is an integer shift of the 48-bit m^2.  Returns false on overflow (q >= 2^64).
-__device__ __forceinline__ bool qsquare(float x, int S, unsigned long long *q) {
-    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
-    const int be = (int)(b >> 23);
-    uint32_t m = b & 0x7FFFFFu;
-    int e;
-    if (be == 0) {
-        e = -149;  // subnormal: no implicit bit
-    } else {
-        m |= 0x800000u;
-        e = be - 150;
-    }
-    const unsigned long long m2 = (unsigned long long)m * (unsigned long long)m;  // < 2^48
-    const int sh = 2 * e + S;
-    if (m2 == 0) {
-        *q = 0;
-        return true;
-    }
-    if (sh >= 0) {
-        if (sh >= 64 || (m2 >> (63 - sh)) >> 1) return false;  // m2 * 2^sh >= 2^64
-        *q = m2 << sh;
-    } else {
-        *q = sh <= -64 ? 0ull : (m2 >> (-sh));
-    }
-    return true;
-}
-
-__device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
-                                            DevStatus *status) {
-    if (v == 0) return;
-    unsigned long long old = atomicAdd(dst, v);
-    if (old + v < old) atomicOr(&status->err, ERR_RANGE);
-}
-
 constexpr int APPEND_ROWS = 128;  // rows (k, i) of the new slices per CTA
 constexpr int APPEND_THREADS = 256;
 

@@ -32,6 +32,7 @@ enum : unsigned {
     ERR_RANGE = 2u,      // fixed-point marginal overflow
     ERR_SAMPLE = 4u,     // sample size above the number of positive weights
     ERR_TIMEOUT = 8u,    // a bounded device wait gave up
+    ERR_INDEX = 16u,     // a coordinate outside the tensor (COO input)
 };
 
 // Device status block (mirrored to pinned host memory once per call).
@@ -41,6 +42,56 @@ struct DevStatus {
     unsigned long long npos[3];  // positive-weight counts of x_a, x_b, x_c after commit
     unsigned long long amax_bits;  // max |x| of a tensor, as ordered double bits
 };
+
+
+// ---------------------------------------------------------------------------
+// Fixed-point squares of the marginals (Eq. 1).  q(x) = floor((x*x) * 2^S): one correctly rounded
+// float64 product (never contracted), exact power-of-two scaling, truncation.
+__device__ __forceinline__ bool qsquare(double x, int S, unsigned long long *q) {
+    double sq = ldexp(__dmul_rn(x, x), S);
+    if (!(sq < 18446744073709551616.0)) return false;
+    *q = __double2ull_rz(sq);
+    return true;
+}
+
+// The same q for a float32 x without float64 arithmetic: x = m * 2^e with a
+// 24-bit integer m, so x*x = m^2 * 2^(2e) exactly and q = floor(m^2 * 2^(2e+S))
+// is an integer shift of the 48-bit m^2.  Returns false on overflow (q >= 2^64).
+__device__ __forceinline__ bool qsquare(float x, int S, unsigned long long *q) {
+    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+    const int be = (int)(b >> 23);
+    uint32_t m = b & 0x7FFFFFu;
+    int e;
+    if (be == 0) {
+        e = -149;  // subnormal: no implicit bit
+    } else {
+        m |= 0x800000u;
+        e = be - 150;
+    }
+    const unsigned long long m2 = (unsigned long long)m * (unsigned long long)m;  // < 2^48
+    const int sh = 2 * e + S;
+    if (m2 == 0) {
+        *q = 0;
+        return true;
+    }
+    if (sh >= 0) {
+        if (sh >= 64 || (m2 >> (63 - sh)) >> 1) return false;  // m2 * 2^sh >= 2^64
+        *q = m2 << sh;
+    } else {
+        *q = sh <= -64 ? 0ull : (m2 >> (-sh));
+    }
+    return true;
+}
+
+__device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
+                                            DevStatus *status) {
+    if (v == 0) return;
+    unsigned long long old = atomicAdd(dst, v);
+    if (old + v < old) atomicOr(&status->err, ERR_RANGE);
+}
+
+
+
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
@@ -214,6 +265,36 @@ struct GatherParams {
     float *sscale;            // float8: scale of every summary slice [rep][Kp] (written here)
 };
 
+// COO summaries: gather of the sampled nonzeros
+struct CooGather {
+    const int *si, *sj;       // store: row, column of every nonzero, grouped by slice
+    const float *sv;
+    const long long *sptr;    // slice k at [sptr[k], sptr[k+1])
+    const int *samples;       // [rep][3][samp_stride]
+    long long samp_stride;
+    const int *posI, *posJ;   // [rep][I], [rep][J]: position in the sample or -1
+    int I, J, nK, K_old, K_new, nrep, S;
+    int *cnt;                 // [rep][Kp + 1] kept nonzeros per summary slice (pass 0)
+    const long long *off;     // [rep][Kp + 1] their offsets (pass 1)
+    double *rowsq;            // [rep][Kp] sum of squares per summary slice
+    unsigned *vmax;           // [rep] max |v| (float bits)
+    long long ecap;           // entries capacity per repetition
+    int *eii, *ejj, *ekk;     // [rep][ecap] summary coordinates
+    float *ev;
+};
+
+// COO summaries as the MTTKRP reads them
+struct CooDesc {
+    long long ecap;
+    const int *eii, *ejj, *ekk;
+    const float *ev;
+    const long long *off;     // [rep][Kp + 1]: entries of summary slice kk (mode 3 rows)
+    const long long *rp1;     // [rep][nI + 1]: row offsets into perm1 (mode 1 rows)
+    const long long *rp2;     // [rep][nJ + 1]
+    const int *perm1, *perm2; // [rep][ecap]: entries grouped by ii / by jj
+    const int *fexp;          // [rep]: fixed-point exponent F of the sums
+};
+
 // rows of one tail CTA (float32 / bfloat16 summaries): the partial-sum
 // reduction after each MTTKRP pass is spread over ceil(n / TAIL_ROWS) CTAs
 // per repetition
@@ -250,6 +331,7 @@ struct AlsDesc {
     DF *nx2f, *fitpf;      // ||X_s||^2 and the previous fit in double-float [rep]
     int *tail_cnt;         // [rep] chunk CTAs finished (the last one completes the mode; zero between uses)
     int tchunks;           // row chunks of TAIL_ROWS for the largest mode
+    long long rq_rows;     // row sums of squares per repetition (0: n[2] * n[0], the dense summary rows)
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -293,6 +375,26 @@ cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
 cudaError_t launch_refine_start(const AlsDesc &d, const double *rowsq2, cudaStream_t st);
+// COO path
+cudaError_t launch_coo_count(const int *kk, long long nnz, int K, int *cnt, DevStatus *status, cudaStream_t st);
+cudaError_t launch_exscan(const int *in, long long in_stride, long long *out, long long out_stride, int n, int nseg,
+                          long long base, cudaStream_t st);
+cudaError_t launch_coo_scatter(const int *ii, const int *jj, const int *kk, const float *val, long long nnz, int I,
+                               int J, int K_new, int S, const long long *sptr_new, int *fill, int *si, int *sj,
+                               float *sv, unsigned long long *dxa, unsigned long long *dxb,
+                               unsigned long long *xc_new, DevStatus *status, cudaStream_t st);
+cudaError_t launch_abs_max_f(const float *v, long long n, unsigned *out, cudaStream_t st);
+cudaError_t launch_coo_pos(const int *samples, long long samp_stride, int nI, int nJ, int I, int J, int nrep,
+                           int *posI, int *posJ, cudaStream_t st);
+cudaError_t launch_coo_gather(const CooGather &g, int pass, cudaStream_t st);
+cudaError_t launch_coo_fexp(const unsigned *vmax, const long long *total, int nrep, int *fexp, cudaStream_t st);
+cudaError_t launch_coo_group(const int *key, long long ecap, const long long *total, long long max_total, int nrows,
+                             int nrep, int *cnt, long long *rowptr, int *fill, int *perm, cudaStream_t st);
+cudaError_t launch_coo_expand_k(const long long *sptr, int K, int *ekk, cudaStream_t st);
+cudaError_t launch_mttkrp_coo(const AlsDesc &d, const CooDesc &s, int mode, cudaStream_t st);
+cudaError_t launch_coo_inner(const int *si, const int *sj, const float *sv, const long long *sptr, int K,
+                             const double *A, const double *B, const double *C, const double *lam, int R, int F,
+                             unsigned long long *acc, cudaStream_t st);
 cudaError_t launch_als_continue(cudaGraphConditionalHandle h, const int *conv, int nrep, int *passes,
                                 int max_passes, cudaStream_t st);
 void choose_tiles(AlsDesc &d, int num_sms);

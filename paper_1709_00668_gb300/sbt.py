@@ -52,6 +52,7 @@ EXPORTS = [
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
     "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
     "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve", "sbt_tile_table",
+    "sbt_init_coo", "sbt_init_coo_factors", "sbt_update_coo",
     "sbt_server_default_options", "sbt_server_create", "sbt_server_open_stream", "sbt_server_submit",
     "sbt_server_wait", "sbt_server_stream_ctx", "sbt_server_close_stream", "sbt_server_stats",
     "sbt_server_stats_reset", "sbt_server_destroy",
@@ -90,6 +91,12 @@ class SbtProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
                 ("mttkrp_bytes", ctypes.c_double)]
+
+
+class SbtCoo(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int64), ("J", ctypes.c_int64), ("K", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("ii", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("kk", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32)]
 
 
 TILE_FIELDS = ("fp8", "R", "NP", "NC", "Kp_bucket", "nrep", "epi", "ctas_per_sm", "stages")
@@ -163,6 +170,10 @@ def lib() -> ctypes.CDLL:
     L.sbt_update_bytes.argtypes = [P, I64, ctypes.POINTER(U64)]
     L.sbt_reserve.argtypes = [P, I64, I64]
     L.sbt_tile_table.argtypes = [I32, P, I32, ctypes.POINTER(I32)]
+    L.sbt_init_coo.argtypes = [ctypes.POINTER(SbtCoo), I32, ctypes.POINTER(SbtOptions), ctypes.POINTER(P)]
+    L.sbt_init_coo_factors.argtypes = [ctypes.POINTER(SbtCoo), I32, P, P, P, P, ctypes.POINTER(SbtOptions),
+                                       ctypes.POINTER(P)]
+    L.sbt_update_coo.argtypes = [P, ctypes.POINTER(SbtCoo)]
     L.sbt_server_default_options.argtypes = [ctypes.POINTER(SbtServerOptions)]
     L.sbt_server_create.argtypes = [ctypes.POINTER(SbtServerOptions), ctypes.POINTER(P)]
     L.sbt_server_open_stream.argtypes = [P, ctypes.POINTER(SbtTensor), I32, ctypes.POINTER(SbtOptions),
@@ -248,6 +259,28 @@ def _tensor_desc(X, keep: list) -> SbtTensor:
     return SbtTensor(dt, 1 if X.is_cuda else 0, I, J, K, ctypes.c_void_p(X.data_ptr()))
 
 
+def _coo_desc(ii, jj, kk, val, shape, keep: list) -> SbtCoo:
+    """SbtCoo for coordinate arrays (torch tensors on one device, or numpy)."""
+    import torch
+
+    def as_t(x, dt):
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x))
+        return x.to(dt).contiguous()
+    ii, jj, kk = (as_t(x, torch.int32) for x in (ii, jj, kk))
+    val = as_t(val, torch.float32)
+    n = int(val.numel())
+    if not (ii.numel() == jj.numel() == kk.numel() == n):
+        raise ValueError("coordinate and value arrays differ in length")
+    devs = {t.device for t in (ii, jj, kk, val)}
+    if len(devs) != 1:
+        raise ValueError("COO arrays on different devices")
+    keep.extend([ii, jj, kk, val])
+    I, J, K = (int(x) for x in shape)
+    ptr = (lambda t: ctypes.c_void_p(t.data_ptr()) if n else None)
+    return SbtCoo(I, J, K, n, ptr(ii), ptr(jj), ptr(kk), ptr(val), 1 if val.is_cuda else 0)
+
+
 def _current_stream():
     import torch
     if torch.cuda.is_available():
@@ -276,6 +309,41 @@ class SamBaTen:
                                           B.ctypes.data, C.ctypes.data, ctypes.byref(self.opts),
                                           ctypes.byref(h)), "sbt_init_factors")
         self._h = h
+
+    @classmethod
+    def from_coo(cls, ii, jj, kk, val, shape, R: int, *, factors=None, **opts) -> "SamBaTen":
+        """A stream whose initial tensor is given by its nonzeros (float32 values,
+        unique coordinates, kk in [0, K)); CP-ALS init unless factors are given."""
+        if "cuda_stream" not in opts:
+            opts["cuda_stream"] = _current_stream()
+        opts.setdefault("prec", "f32")
+        obj = cls.__new__(cls)
+        obj.opts = sbt_default_options(**opts)
+        obj.R = int(R)
+        keep: list = []
+        desc = _coo_desc(ii, jj, kk, val, shape, keep)
+        obj.I, obj.J = int(desc.I), int(desc.J)
+        h = ctypes.c_void_p()
+        if factors is None:
+            _check(lib().sbt_init_coo(ctypes.byref(desc), obj.R, ctypes.byref(obj.opts), ctypes.byref(h)),
+                   "sbt_init_coo")
+        else:
+            lam, A, B, C = (np.ascontiguousarray(np.asarray(f, dtype=np.float64)) for f in factors)
+            _check(lib().sbt_init_coo_factors(ctypes.byref(desc), obj.R, lam.ctypes.data, A.ctypes.data,
+                                              B.ctypes.data, C.ctypes.data, ctypes.byref(obj.opts),
+                                              ctypes.byref(h)), "sbt_init_coo_factors")
+        obj._h = h
+        return obj
+
+    def update_coo(self, ii, jj, kk, val, K_new: int):
+        keep: list = []
+        desc = _coo_desc(ii, jj, kk, val, (self.I, self.J, K_new), keep)
+        _check(lib().sbt_update_coo(self._h, ctypes.byref(desc)), "sbt_update_coo")
+
+    def update_coo_status(self, ii, jj, kk, val, K_new: int) -> int:
+        keep: list = []
+        desc = _coo_desc(ii, jj, kk, val, (self.I, self.J, K_new), keep)
+        return int(lib().sbt_update_coo(self._h, ctypes.byref(desc)))
 
     @classmethod
     def _borrow(cls, h, R: int, I: int, J: int) -> "SamBaTen":

@@ -114,3 +114,64 @@ def poisson_arrivals(n: int, rate: float, seed: int = 0) -> list[float]:
     gaps = torch.empty(n, dtype=torch.float64).exponential_(1.0, generator=g)
     t = torch.cumsum(gaps / float(rate), 0)
     return [float(x) for x in t]
+
+
+@dataclass
+class SparsePlanted:
+    k: torch.Tensor          # (nnz,) int32 time slice, sorted (time-major order)
+    i: torch.Tensor          # (nnz,) int32
+    j: torch.Tensor          # (nnz,) int32
+    v: torch.Tensor          # (nnz,) float32: planted model + noise at the coordinate
+    A: torch.Tensor          # (I, R) float64, zero off the component supports
+    B: torch.Tensor          # (J, R)
+    C: torch.Tensor          # (K, R)
+    sigma: float
+
+    def batch(self, k0: int, k1: int):
+        """Nonzeros of slices [k0, k1) with k relative to k0."""
+        lo = int(torch.searchsorted(self.k, torch.tensor(k0, dtype=self.k.dtype, device=self.k.device)))
+        hi = int(torch.searchsorted(self.k, torch.tensor(k1, dtype=self.k.dtype, device=self.k.device)))
+        return self.i[lo:hi], self.j[lo:hi], self.k[lo:hi] - k0, self.v[lo:hi]
+
+    def dense(self, k0: int = 0, k1: int = None) -> torch.Tensor:
+        """The slices [k0, k1) as a dense (K, I, J) float32 array on the CPU (small tensors only)."""
+        k1 = self.C.shape[0] if k1 is None else k1
+        I, J = self.A.shape[0], self.B.shape[0]
+        ii, jj, kk, vv = (t.cpu() for t in self.batch(k0, k1))
+        X = torch.zeros(k1 - k0, I, J, dtype=torch.float32)
+        X[kk.long(), ii.long(), jj.long()] = vv
+        return X
+
+
+def planted_sparse(I: int, J: int, K: int, R: int, *, support: int, coords: int, noise: float = 0.01,
+                   seed: int = 0, device="cpu") -> SparsePlanted:
+    """Planted sparse CP tensor, seeded: component r has `support` random
+    indices in each mode with factor values U[0, 1) there (0 elsewhere);
+    `coords` coordinates are drawn uniformly from its support box; the value
+    at a coordinate is the full planted model plus N(0, noise^2); coordinates
+    drawn more than once are kept once.  Time-sorted."""
+    dev = torch.device(device)
+    g = _gen(seed, dev)
+    U = []
+    sup = []
+    for n in (I, J, K):
+        Un = torch.zeros(n, R, dtype=torch.float64, device=dev)
+        Sn = torch.stack([torch.randperm(n, generator=g, device=dev)[:support] for _ in range(R)])  # (R, support)
+        vals = torch.rand(R, support, generator=g, device=dev, dtype=torch.float64)
+        for r in range(R):
+            Un[Sn[r], r] = vals[r]
+        U.append(Un)
+        sup.append(Sn)
+    keys = []
+    for r in range(R):
+        t = [sup[m][r][torch.randint(0, support, (coords,), generator=g, device=dev)].long() for m in range(3)]
+        keys.append((t[2] * I + t[0]) * J + t[1])
+    key = torch.unique(torch.cat(keys))  # sorted: time-major
+    k = key // (I * J)
+    i = (key // J) % I
+    j = key % J
+    A, B, C = U
+    model = (A[i] * B[j] * C[k]).sum(dim=1)
+    v = (model + noise * torch.randn(model.shape, generator=g, device=dev, dtype=torch.float64)).to(torch.float32)
+    return SparsePlanted(k=k.to(torch.int32), i=i.to(torch.int32), j=j.to(torch.int32), v=v, A=A, B=B, C=C,
+                         sigma=noise)
