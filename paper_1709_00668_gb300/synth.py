@@ -171,7 +171,12 @@ def planted_sparse(I: int, J: int, K: int, R: int, *, support: int, coords: int,
     i = (key // J) % I
     j = key % J
     A, B, C = U
-    model = (A[i] * B[j] * C[k]).sum(dim=1)
-    v = (model + noise * torch.randn(model.shape, generator=g, device=dev, dtype=torch.float64)).to(torch.float32)
+    v = torch.empty(key.shape[0], dtype=torch.float32, device=dev)
+    step = 1 << 22
+    for a in range(0, key.shape[0], step):
+        b = min(a + step, key.shape[0])
+        model = (A[i[a:b]] * B[j[a:b]] * C[k[a:b]]).sum(dim=1)
+        v[a:b] = (model + noise * torch.randn(model.shape, generator=g, device=dev, dtype=torch.float64)).to(
+            torch.float32)
     return SparsePlanted(k=k.to(torch.int32), i=i.to(torch.int32), j=j.to(torch.int32), v=v, A=A, B=B, C=C,
                          sigma=noise)
