@@ -576,7 +576,7 @@ __device__ void warp_inverse_f(const float (*L)[33], float (*Y)[33], float (*X)[
     __syncwarp();
 }
 
-__device__ void tail_finish(const AlsDesc &d, int mode, int rep);
+__device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_bytes);
 
 // dynamic shared memory of k_tail_rows
 struct TailSmem {
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    tail_finish(d, mode, rep);
+    tail_finish(d, mode, rep, tail_smem_bytes<RP>());
 }
 
 // Finish of one mode for one repetition (the last chunk CTA), in double-float:
@@ -752,7 +752,7 @@ __device__ __forceinline__ DF ldcg_df(const DF *p) {
     return DF{v.x, v.y};
 }
 
-__device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
+__device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_bytes) {
     const int R = d.R, n = d.n[mode];
     const int npairs = R * (R + 1) / 2;
     const int nch = (n + TAIL_ROWS - 1) / TAIL_ROWS;
@@ -764,13 +764,27 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
     __shared__ int zero_flag;
     DF *Gf = d.Gf + (long long)rep * 3 * R * R;
     const DF *tp = d.tpart + (long long)rep * d.tchunks * (npairs + 1);
-    for (int pq = threadIdx.x; pq <= npairs; pq += blockDim.x) {
-        DF a{0.f, 0.f};
-        for (int c = 0; c < nch; ++c) a = df_add(a, ldcg_df(&tp[(long long)c * (npairs + 1) + pq]));
-        graw[pq] = a;
-    }
+    // chunk shares: as many as the CTA's dynamic shared memory holds (free
+    // now: this CTA's own chunk is done) loaded with all loads in flight,
+    // then added per pair in chunk order
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
+    DF *shr = reinterpret_cast<DF *>(tsm_raw);
+    const int blk = max(1, (int)(smem_bytes / ((size_t)(npairs + 1) * sizeof(DF))));
     if (threadIdx.x == 0) zero_flag = 0;
-    __syncthreads();
+    for (int pq = threadIdx.x; pq <= npairs; pq += blockDim.x) graw[pq] = DF{0.f, 0.f};
+    for (int c0 = 0; c0 < nch; c0 += blk) {
+        const int cn = min(blk, nch - c0);
+        const int items = cn * (npairs + 1);
+        for (int e = threadIdx.x; e < items; e += blockDim.x)
+            shr[e] = ldcg_df(&tp[(long long)c0 * (npairs + 1) + e]);
+        __syncthreads();
+        for (int pq = threadIdx.x; pq <= npairs; pq += blockDim.x) {
+            DF a = graw[pq];
+            for (int c = 0; c < cn; ++c) a = df_add(a, shr[c * (npairs + 1) + pq]);
+            graw[pq] = a;
+        }
+        __syncthreads();
+    }
     if (threadIdx.x < R) {
         const int r = threadIdx.x;
         DF l = df_sqrt(graw[r * R - r * (r - 1) / 2]);  // diagonal pair (r, r)
@@ -798,13 +812,25 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
     }
     float *U = (float *)d.U[mode] + (long long)rep * n * R;
     {
-        // column index tracked incrementally (no division per element)
+        // U /= lambda column-wise: eight loads in flight per thread, then the
+        // stores (column index tracked incrementally, no division per element)
+        const long long total = (long long)n * R;
         const int step = (int)(blockDim.x % R);
         int r = (int)(threadIdx.x % R);
-        for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x) {
-            U[e] = __ldcg(&U[e]) * inv_lam[r];
-            r += step;
-            if (r >= R) r -= R;
+        for (long long e0 = threadIdx.x; e0 < total; e0 += 8LL * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long e = e0 + (long long)u * blockDim.x;
+                v[u] = e < total ? __ldcg(&U[e]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long e = e0 + (long long)u * blockDim.x;
+                if (e < total) U[e] = v[u] * inv_lam[r];
+                r += step;
+                if (r >= R) r -= R;
+            }
         }
     }
     __syncthreads();
@@ -821,8 +847,7 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep) {
         if (threadIdx.x == 0) {
             DF xh{0.f, 0.f};
             for (int t = 0; t < (int)(blockDim.x >> 5); ++t) xh = df_add(xh, xh_part[t]);
-            DF in{0.f, 0.f};  // <X, X_hat> = sum_r lambda_r <M(:,r), U(:,r)> = <M, U_raw>
-            for (int c = 0; c < nch; ++c) in = df_add(in, ldcg_df(&tp[(long long)c * (npairs + 1) + npairs]));
+            const DF in = graw[npairs];  // <X, X_hat> = sum_r lambda_r <M(:,r), U(:,r)> = <M, U_raw>
             const DF nx2 = d.nx2f[rep];
             DF res2 = df_sub(df_add(nx2, xh), df_add(in, in));
             if (!(res2.hi > 0.f)) res2 = DF{0.f, 0.f};

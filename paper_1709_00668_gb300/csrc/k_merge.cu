@@ -9,10 +9,16 @@ namespace sbt {
 // Maximum-weight perfect matching of an R x R score matrix (Hungarian method,
 // shortest augmenting paths with potentials; Kuhn 1955, Munkres 1957), single
 // thread.  perm[row] = column.  Ties resolve to the lower column index.
-__device__ void hungarian_max(const double *score, int ld, int R, int *perm) {
+struct HungarianWork {
     double u[33], v[33], minv[33];
     int p[33], way[33];
     bool used[33];
+};
+
+__device__ void hungarian_max(const double *score, int ld, int R, int *perm, HungarianWork &w) {
+    double *u = w.u, *v = w.v, *minv = w.minv;
+    int *p = w.p, *way = w.way;
+    bool *used = w.used;
     for (int j = 0; j <= R; ++j) {
         u[j] = 0.0;
         v[j] = 0.0;
@@ -106,7 +112,9 @@ template <> struct MatchAcc<float> {
     __device__ __forceinline__ double value() const { return df_value(v); }
 };
 
-constexpr int MATCH_TS = 16;                                      // rows staged per tile
+// rows staged per tile (the float64 path has twice the bytes per row and
+// stays within 48 KB of static shared memory with 16)
+template <typename TF> constexpr int match_ts() { return sizeof(TF) == 8 ? 16 : 32; }
 constexpr int MATCH_ITEMS = (32 * 32 + 2 * 32 + 255) / 256;      // accumulators per thread
 
 // One CTA per repetition: shared-row norms (Alg. 1 step 6), cosines and the
@@ -121,10 +129,12 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     const int n[3] = {m.nI, m.nJ, Kp};
     const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
     __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32], scale[3][32];
+    constexpr int MATCH_TS = match_ts<TF>();
     __shared__ TF su[MATCH_TS * 32];
     __shared__ Anchor sa[MATCH_TS * 32];
     __shared__ int perm[32];
     __shared__ int zflag;
+    __shared__ HungarianWork hw;  // in shared memory rather than the thread's stack
     const TF *U[3];
     const int *S[3];
     const double *old[3] = {m.A, m.B, m.C};
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
             for (int r = 0; r < R; ++r)
                 score[rp * 32 + r] = fabs(gam[0][rp][r]) * fabs(gam[1][rp][r]) * fabs(gam[2][rp][r]);
         }
-        hungarian_max(score, 32, R, perm);
+        hungarian_max(score, 32, R, perm, hw);
         double mn = INFINITY;
         for (int rp = 0; rp < R; ++rp) {
             mn = fmin(mn, score[rp * 32 + perm[rp]]);

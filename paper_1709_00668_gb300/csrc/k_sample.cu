@@ -63,7 +63,7 @@ constexpr int APPEND_THREADS = 256;
 // exact 64-bit integers, so the atomics may land in any order.
 template <typename T>
 __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long long nrows, int I, int J, int ldin,
-                                                           T *store, int lds, int S, int vec_ok,
+                                                           T *store, int lds, int S, int vec_ok, int inplace,
                                                            unsigned long long *dxa, unsigned long long *dxb,
                                                            unsigned long long *xc_new, unsigned *samax,
                                                            DevStatus *status) {
@@ -89,47 +89,76 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
     for (int v = 0; v < V; ++v) cs[v] = 0;
     bool bad = false, range = false;
     const bool vec = vec_ok && jc + V <= J;
-    for (int t = 0; t < rows; ++t) {
-        const long long r = r0 + t;
-        unsigned long long rp = 0;
-        float am = 0.f;
-        if (jc < J) {
-            const T *src = Xin + r * ldin + jc;
-            T *dst = store + r * lds + jc;
-            T x[V];
-            if (vec) {
-                *reinterpret_cast<uint4 *>(x) = *reinterpret_cast<const uint4 *>(src);
-                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(x);
+    // rows in groups of AU: the loads of a group are issued before any of
+    // its rows is processed (several vectors in flight per thread)
+    constexpr int AU = 4;
+    for (int t0 = 0; t0 < rows; t0 += AU) {
+        T xs[AU][V];
+#pragma unroll
+        for (int u = 0; u < AU; ++u) {
+            const long long r = r0 + t0 + u;
+            if (t0 + u < rows && jc < J) {
+                const T *src = Xin + r * ldin + jc;
+                if (vec) {
+                    *reinterpret_cast<uint4 *>(xs[u]) = *reinterpret_cast<const uint4 *>(src);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) xs[u][v] = jc + v < J ? src[v] : T(0);
+                }
             } else {
 #pragma unroll
+                for (int v = 0; v < V; ++v) xs[u][v] = T(0);
+            }
+        }
+        if (!inplace) {
+#pragma unroll
+            for (int u = 0; u < AU; ++u) {
+                const long long r = r0 + t0 + u;
+                if (t0 + u < rows && jc < J) {
+                    T *dst = store + r * lds + jc;
+                    if (vec) {
+                        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(xs[u]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            if (jc + v < J) dst[v] = xs[u][v];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < AU; ++u) {
+            const int t = t0 + u;
+            if (t >= rows) break;
+            const long long r = r0 + t;
+            unsigned long long rp = 0;
+            float am = 0.f;
+            if (jc < J) {
+#pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    x[v] = jc + v < J ? src[v] : T(0);
-                    if (jc + v < J) dst[v] = x[v];
+                    const T x = xs[u][v];
+                    unsigned long long q = 0;
+                    if (samax) am = fmaxf(am, fabsf((float)x));
+                    if (!isfinite(x)) bad = true;
+                    else if (!qsquare(x, S, &q)) range = true;
+                    if (cs[v] + q < cs[v]) range = true;
+                    cs[v] += q;
+                    if (rp + q < rp) range = true;
+                    rp += q;
                 }
             }
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                unsigned long long q = 0;
-                if (samax) am = fmaxf(am, fabsf((float)x[v]));
-                if (!isfinite(x[v])) bad = true;
-                else if (!qsquare(x[v], S, &q)) range = true;
-                if (cs[v] + q < cs[v]) range = true;
-                cs[v] += q;
-                if (rp + q < rp) range = true;
-                rp += q;
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, rp, o);
+                if (rp + other < rp) range = true;
+                rp += other;
             }
-        }
+            if (lane == 0) rowp[t][warp] = rp;
+            if (samax) {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, rp, o);
-            if (rp + other < rp) range = true;
-            rp += other;
-        }
-        if (lane == 0) rowp[t][warp] = rp;
-        if (samax) {
-#pragma unroll
-            for (int o = 16; o; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
-            if (lane == 0 && am > 0.f) atomicMax(&slice_max[r / I - k_first], __float_as_uint(am));
+                for (int o = 16; o; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+                if (lane == 0 && am > 0.f) atomicMax(&slice_max[r / I - k_first], __float_as_uint(am));
+            }
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&status->err, ERR_NONFINITE);
@@ -175,13 +204,14 @@ cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, in
     const int V = dtype == 0 ? 2 : 4;
     dim3 grid((unsigned)((nrows + APPEND_ROWS - 1) / APPEND_ROWS), (J + APPEND_THREADS * V - 1) / (APPEND_THREADS * V));
     const int vec_ok = ldin % V == 0 && lds % V == 0 && ((uintptr_t)Xin & 15) == 0 && ((uintptr_t)store & 15) == 0;
+    const int inplace = Xin == store && ldin == lds;  // the initial tensor is already in the store
     count_launches(1);
     if (dtype == 0)
         k_append<double><<<grid, APPEND_THREADS, 0, st>>>((const double *)Xin, nrows, I, J, ldin, (double *)store, lds,
-                                                          S, vec_ok, dxa, dxb, xc_new, samax, status);
+                                                          S, vec_ok, inplace, dxa, dxb, xc_new, samax, status);
     else
         k_append<float><<<grid, APPEND_THREADS, 0, st>>>((const float *)Xin, nrows, I, J, ldin, (float *)store, lds,
-                                                         S, vec_ok, dxa, dxb, xc_new, samax, status);
+                                                         S, vec_ok, inplace, dxa, dxb, xc_new, samax, status);
     return cudaGetLastError();
 }
 
