@@ -41,8 +41,10 @@ UNIT = "slices/s"
 # (same summary shapes, 90 slices per summary, 57.6 MB per launch), where
 # traffic scales with the slices processed; scaled here to the full launch.
 TRAFFIC = {
-    ("4327738099107878", "bf16"): {"ratio": (57.7376e6 + 0.013056e6) / 57.6e6,
-                                   "capture": "k_mtt_tc<32> grid 36x8, 17.8-18.6 us, --small --steps 1 --warmup 1"},
+    ("186d37ccb5bcc318", "bf16"): {"ratio": (57.737728e6 + 0.04416e6) / 57.6e6,
+                                   "capture": "k_mtt_tc<32, bf16> grid 36x8, 18.5-18.9 us, --small --steps 1 --warmup 1"},
+    ("186d37ccb5bcc318", "fp8"): {"ratio": 30.094592e6 / 28.8e6,
+                                  "capture": "k_mtt_tc<48, e4m3> grid 36x8, 14.1-14.8 us, --small --prec fp8"},
 }
 KERNEL_NAME = {"bf16": "k_mtt_tc (tcgen05 MTTKRP, bf16 summaries)",
                "fp8": "k_mtt_tc (tcgen05 kind::f8f6f4 MTTKRP, e4m3 summaries)",
