@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "f32", "fp8"])
     ap.add_argument("--autotune", action="store_true",
                     help="tune the tensor-core MTTKRP tiles in an untimed pass over the same batches first")
+    ap.add_argument("--mode3-pass", action="store_true",
+                    help="mode 3 reads the summary in its own MTTKRP pass (default: formed from the mode-2 pass)")
+    ap.add_argument("--als-groups", type=int, default=0,
+                    help="groups the repetitions' ALS runs in (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -87,6 +91,9 @@ def parse():
     args = ap.parse_args()
     if args.small:
         WORKLOAD["K0"] = 200
+    global MODE3_PASS, ALS_GROUPS
+    MODE3_PASS = int(args.mode3_pass)
+    ALS_GROUPS = args.als_groups
     return args
 
 
@@ -201,12 +208,16 @@ def make_data(steps: int, warmup: int, device):
     return p, nb
 
 
+MODE3_PASS = 0
+ALS_GROUPS = 0
+
+
 def opts_for(prec: str, stream, nb: int):
     """Options of one context that will absorb nb batches (store sized for exactly that)."""
     w = WORKLOAD
     return dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
                 max_iters_init=50, seed=w["seed"], prec=prec, cuda_stream=stream,
-                K_capacity=w["K0"] + nb * w["batch"])
+                K_capacity=w["K0"] + nb * w["batch"], mode3_pass=MODE3_PASS, als_groups=ALS_GROUPS)
 
 
 def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
@@ -445,6 +456,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec, "autotuned_tiles": bool(args.autotune),
+                       "mode3_pass": bool(MODE3_PASS), "als_groups": ALS_GROUPS or "default",
                        "l2": "inputs larger than L2 (200 MB batch per step, 4 GB resident store)",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},

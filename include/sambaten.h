@@ -101,6 +101,18 @@ typedef struct {
     int32_t autotune;      /* 1: before the ALS of an update, time the tile candidates of every
                               tensor-core MTTKRP launch shape not in the tile table and record
                               the fastest (see sbt_tile_table); 0: use the table / default rule */
+    int32_t mode3_pass;    /* tensor-core MTTKRP (bf16 / fp8 summaries) only.  0 (default): the
+                              mode-2 pass keeps every slice's product Y_k = X_k^T A (float32,
+                              K_s' x n_J x R per repetition) and the mode-3 MTTKRP is formed from
+                              it and the new B, M3(k, r) = sum_j Y_k(j, r) B(j, r): two passes
+                              over the summary per ALS iteration instead of three (the same sums
+                              as the definition, in another order).  1: mode 3 reads the summary
+                              in its own pass */
+    int32_t als_groups;    /* tensor-core MTTKRP only: the r independent summary ALS run as this
+                              many groups of repetitions, each its own chain of kernels on its
+                              own stream, so that one group's MTTKRP pass overlaps another
+                              group's latency-bound tail; 0: 2 (1 when r = 1).  Results depend
+                              on it only through the order of partial sums */
 } sbt_options;
 
 typedef struct {

@@ -125,6 +125,28 @@ struct TcPlan {
     CUtensorMap m1lo, m2lo;
     const float *sscale = nullptr;  // float8 summaries: scale of every summary slice
     const TileChoice *force = nullptr;  // autotuning: the candidate being timed
+    int sms = 0;                    // SMs a launch sizes its grid for (0: all; a group of the ALS: its share)
+    // the summaries the maps cover, so that a group of repetitions gets maps of its own
+    const void *xs = nullptr, *xt = nullptr, *xlo = nullptr, *xtlo = nullptr;
+    int nI = 0, nJ = 0, ldj = 0, ldi = 0, Kp = 0;
+    bool fp8 = false;
+};
+
+// The ALS of the repetitions as independent groups, each its own chain of
+// kernels on its own stream: one group's MTTKRP pass streams the summaries
+// while another group's tail (a latency-bound chain of small steps) runs.
+struct AlsGroupRt {
+    cudaStream_t st = nullptr, side = nullptr;   // the group's chain; V^-1 beside its passes
+    cudaEvent_t fork = nullptr, join = nullptr;  // around V^-1
+    cudaEvent_t done = nullptr;                  // end of the group's chain in a loop body
+};
+
+// one group: its descriptor (per-repetition pointers offset to its first
+// repetition) and its tensor-core plan
+struct AlsPlan {
+    AlsDesc d;
+    TcPlan tc;
+    bool has_tc = false;
 };
 
 }  // namespace
@@ -165,6 +187,7 @@ struct sbt_ctx {
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
+    Buf ymem;                           // mode-2 pass products for the mode-3 MTTKRP (mode3_pass 0)
     Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
     // COO contexts (sbt_init_coo): nonzeros grouped by slice, and the summary workspace
     bool coo = false;
@@ -179,6 +202,8 @@ struct sbt_ctx {
     cudaStream_t side = nullptr;  // runs V^-1 of a mode beside its MTTKRP pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TcPlan tc;
+    std::vector<AlsGroupRt> grt;   // groups 1.. of the ALS (group 0 runs on stream / side)
+    cudaEvent_t ev_groups = nullptr;  // start of a loop body, for the groups' streams
     // profiling
     Buf prof_bytes;  // unsigned long long, device
     Buf passes;      // pass counter of the device-side ALS loop
@@ -190,6 +215,7 @@ struct sbt_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
     double mtt_ms = 0.0;
     long long launch_base = 0, updates = 0, mtt_launches = 0;
+    int mtt_per_iter = 3;  // MTTKRP launches per ALS iteration of the last loop (2 with the memoised mode 3)
     ~sbt_ctx() {
         for (auto &e : gev) {
             cudaEventDestroy(e.first);
@@ -198,6 +224,14 @@ struct sbt_ctx {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
+        for (auto &g : grt) {
+            if (g.fork) cudaEventDestroy(g.fork);
+            if (g.join) cudaEventDestroy(g.join);
+            if (g.done) cudaEventDestroy(g.done);
+            if (g.side) cudaStreamDestroy(g.side);
+            if (g.st) cudaStreamDestroy(g.st);
+        }
+        if (ev_groups) cudaEventDestroy(ev_groups);
         if (ev_user) cudaEventDestroy(ev_user);
         if (stream) cudaStreamDestroy(stream);
     }
@@ -243,6 +277,8 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (o->prec < SBT_PREC_F64 || o->prec > SBT_PREC_FP8) return fail(SBT_E_INVALID, "unknown precision");
     if (o->lambda_mode != 0 && o->lambda_mode != 1) return fail(SBT_E_INVALID, "lambda_mode must be 0 or 1");
     if (o->refine_sweeps < 0 || o->refine_sweeps > 1000) return fail(SBT_E_INVALID, "refine_sweeps out of [0, 1000]");
+    if (o->mode3_pass != 0 && o->mode3_pass != 1) return fail(SBT_E_INVALID, "mode3_pass must be 0 or 1");
+    if (o->als_groups < 0 || o->als_groups > SBT_MAX_REPS) return fail(SBT_E_INVALID, "als_groups out of [0, SBT_MAX_REPS]");
     return SBT_OK;
 }
 
@@ -409,24 +445,26 @@ static sbt_status setup_als(sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
 
 // Run ALS iterations until every repetition converged (polled every
 // check_every iterations) or max_iters.
-static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode) {
-    if (c->coo) return launch_mttkrp_coo(d, c->cd, mode, c->stream);
-    if (!tc || !tc->on) return launch_mttkrp(d, mode, c->stream);
+static cudaError_t mttkrp_mode(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int mode, cudaStream_t st) {
+    if (c->coo) return launch_mttkrp_coo(d, c->cd, mode, st);
+    if (!tc || !tc->on) return launch_mttkrp(d, mode, st);
     const int R = d.R, NI = d.n[0], NJ = d.n[1], Kp = d.n[2];
+    const int sms = tc->sms > 0 ? tc->sms : c->num_sms;
     const float *U0 = (const float *)d.U[0], *U1 = (const float *)d.U[1], *U2 = (const float *)d.U[2];
     unsigned *err = &c->status.as<DevStatus>()->err;
     int P = 0;
     if (mode == 0)
         return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 0, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
-                                tc->force);
-    if (mode == 1)
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, sms, &P, st,
+                                nullptr, 0, tc->force);
+    if (mode == 1)  // keeps Y_kk = X_kk^T A for the memoised mode 3
         return launch_mttkrp_tc(tc->m2, tc->split ? &tc->m2lo : nullptr, 0, d.nrep, R, NJ, NI, Kp, U0, (long long)NI * R, U2, (long long)Kp * R,
-                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
-                                tc->force);
+                                (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, sms, &P, st,
+                                d.ymem, d.yrs, tc->force);
+    if (d.ymem) return launch_mtt_memo(d, st);  // mode 3 from Y and the new B (one partial), and its V^-1
     return launch_mttkrp_tc(tc->m1, tc->split ? &tc->m1lo : nullptr, 1, d.nrep, R, NI, NJ, Kp, U1, (long long)NJ * R, U0, (long long)NI * R,
-                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, c->num_sms, &P, c->stream,
-                                tc->force);
+                            (float *)d.part, d.prs, d.pr, d.conv, d.bytes_ctr, err, tc->sscale, sms, &P, st,
+                            nullptr, 0, tc->force);
 }
 
 // partial counts of the tensor-core kernels, fixed by the shapes and the tile choices
@@ -461,14 +499,14 @@ static sbt_status autotune_tiles(sbt_ctx *c, const AlsDesc &d, TcPlan &tc) {
     sbt_status st = SBT_OK;
     for (int mode = 0; mode < 3 && st == SBT_OK; ++mode) {
         const int NP = mode == 1 ? d.n[1] : d.n[0], NC = mode == 1 ? d.n[0] : d.n[1], epi = mode == 2 ? 1 : 0;
-        if (tile_known(fp8, R, NP, NC, Kp, nrep, epi)) continue;
+        if (tile_known(fp8, R, NP, NC, Kp, nrep, epi) || (mode == 2 && d.ymem)) continue;
         TileChoice best{2, 0};
         float best_ms = 1e30f;
         for (const TileChoice &cand : cands) {
             tc.force = &cand;
-            cudaError_t e = mttkrp_mode(c, dq, &tc, mode);  // warm
+            cudaError_t e = mttkrp_mode(c, dq, &tc, mode, c->stream);  // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = mttkrp_mode(c, dq, &tc, mode);
+            for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = mttkrp_mode(c, dq, &tc, mode, c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -490,26 +528,155 @@ static sbt_status autotune_tiles(sbt_ctx *c, const AlsDesc &d, TcPlan &tc) {
     return st;
 }
 
-// The kernels of G ALS iterations on the library's stream: per mode, V^-1 on
-// the side stream beside the MTTKRP pass, then the tail.  With timing, CUDA
-// events bracket every MTTKRP launch (slots from `slot`).
-static cudaError_t launch_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G, bool timed) {
+// Groups the ALS of nrep repetitions runs in: the tensor-core path splits
+// them (default 2 groups, option als_groups) so that the groups' passes and
+// tails overlap; every other path runs one group.
+static int als_group_count(const sbt_ctx *c, int nrep, bool tc) {
+    if (!tc || nrep < 2) return 1;
+    const int g = c->opt.als_groups > 0 ? c->opt.als_groups : 2;
+    return std::min(g, nrep);
+}
+
+// Partial counts of a tensor-core ALS of nrep repetitions in G groups, and
+// the per-repetition stride of the partials that covers every group (the
+// smallest group splits its slices most).
+static void tc_group_partials(const sbt_ctx *c, AlsDesc &d, int G) {
+    AlsDesc dm = d;
+    dm.nrep = d.nrep / G;
+    tc_partials(dm, c->num_sms / G, c->elem == 3);
+    d.prs = dm.prs;
+    for (int m = 0; m < 3; ++m) d.P[m] = dm.P[m];
+}
+
+// descriptor of repetitions [rep0, rep0 + ng): every per-repetition pointer
+// offset to rep0 (the kernels index repetitions from blockIdx)
+static AlsDesc group_desc(const AlsDesc &d, int rep0, int ng, size_t xbytes_per_rep) {
+    AlsDesc s = d;
+    const int R = d.R;
+    const size_t tfs = esize_tf(d.elem);
+    const long long r0 = rep0;
+    s.nrep = ng;
+    if (d.X) s.X = (const char *)d.X + r0 * xbytes_per_rep;
+    for (int m = 0; m < 3; ++m) s.U[m] = (char *)d.U[m] + r0 * d.n[m] * R * tfs;
+    if (d.M) s.M = d.M + r0 * d.mrs;
+    s.part = (char *)d.part + r0 * d.prs * tfs;
+    s.G = d.G + r0 * 3 * R * R;
+    s.lam = d.lam + r0 * R;
+    s.fit = d.fit + r0;
+    s.fit_prev = d.fit_prev + r0;
+    s.normX2 = d.normX2 + r0;
+    s.iters = d.iters + r0;
+    s.conv = d.conv + r0;
+    s.flags = d.flags + r0;
+    s.tpart = d.tpart + r0 * d.tchunks * (R * (R + 1) / 2 + 1);
+    if (d.xinv) s.xinv = d.xinv + r0 * 2048;
+    if (d.Gf) s.Gf = d.Gf + r0 * 3 * R * R;
+    if (d.nx2f) s.nx2f = d.nx2f + r0;
+    if (d.fitpf) s.fitpf = d.fitpf + r0;
+    s.tail_cnt = d.tail_cnt + r0;
+    if (d.ymem) s.ymem = d.ymem + r0 * d.yrs;
+    return s;
+}
+
+// the groups of one ALS run (one group unless the tensor-core path splits)
+static sbt_status als_plans(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, std::vector<AlsPlan> &out) {
+    out.clear();
+    const bool on = tc && tc->on;
+    const int G = als_group_count(c, d.nrep, on);
+    if (G == 1) {
+        AlsPlan p;
+        p.d = d;
+        if (tc) {
+            p.tc = *tc;
+            p.has_tc = true;
+            p.tc.sms = c->num_sms;
+        }
+        out.push_back(p);
+        return SBT_OK;
+    }
+    const size_t es = tc->fp8 ? 1 : 2;
+    const size_t xb = (size_t)tc->Kp * tc->nI * tc->ldj * es, xtb = (size_t)tc->Kp * tc->nJ * tc->ldi * es;
+    const size_t xlb = (size_t)tc->Kp * tc->nI * tc->ldj * 2, xtlb = (size_t)tc->Kp * tc->nJ * tc->ldi * 2;
+    for (int g = 0; g < G; ++g) {
+        const int rep0 = g * d.nrep / G, ng = (g + 1) * d.nrep / G - rep0;
+        AlsPlan p;
+        p.d = group_desc(d, rep0, ng, xb);
+        p.tc = *tc;
+        p.has_tc = true;
+        p.tc.sms = c->num_sms / G;
+        const long long ns = (long long)ng * tc->Kp;
+        CK(make_summary_tmap(&p.tc.m1, (const char *)tc->xs + rep0 * xb, tc->nJ, tc->nI, tc->ldj, ns, tc->fp8));
+        CK(make_summary_tmap(&p.tc.m2, (const char *)tc->xt + rep0 * xtb, tc->nI, tc->nJ, tc->ldi, ns, tc->fp8));
+        if (tc->split) {
+            CK(make_summary_tmap(&p.tc.m1lo, (const char *)tc->xlo + rep0 * xlb, tc->nJ, tc->nI, tc->ldj, ns, false));
+            CK(make_summary_tmap(&p.tc.m2lo, (const char *)tc->xtlo + rep0 * xtlb, tc->nI, tc->nJ, tc->ldi, ns, false));
+        }
+        if (tc->sscale) p.tc.sscale = tc->sscale + (long long)rep0 * tc->Kp;
+        tc_partials(p.d, p.tc.sms, tc->fp8);
+        p.d.prs = d.prs;  // the stride of the shared buffer (covers this group's partials)
+        out.push_back(p);
+    }
+    return SBT_OK;
+}
+
+// streams and events of groups 1 .. G-1 (created outside any capture)
+static sbt_status ensure_group_rt(sbt_ctx *c, int G) {
+    if (G > 1 && !c->ev_groups) CK(cudaEventCreateWithFlags(&c->ev_groups, cudaEventDisableTiming));
+    while ((int)c->grt.size() < G - 1) {
+        AlsGroupRt g;
+        CK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+        c->grt.push_back(g);
+    }
+    return SBT_OK;
+}
+
+// The kernels of G ALS iterations: group 0 on the library's stream, group g
+// on its own stream, forked from and joined back to the library's stream.
+// Per mode and group: V^-1 on the group's side stream beside its MTTKRP
+// pass, then the tail.  With timing, CUDA events bracket every MTTKRP launch
+// on the stream it runs on (slots from 0).
+static cudaError_t launch_iterations(sbt_ctx *c, const std::vector<AlsPlan> &plans, int G, bool timed) {
     cudaError_t e = cudaSuccess;
+    const int ng = (int)plans.size();
+    if (ng > 1) {
+        e = cudaEventRecord(c->ev_groups, c->stream);
+        for (int g = 1; g < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(c->grt[g - 1].st, c->ev_groups, 0);
+    }
     int slot = 0;
     for (int it = 0; it < G && e == cudaSuccess; ++it) {
-        for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode, ++slot) {
-            if (d.xinv) {
-                e = cudaEventRecord(c->ev_fork, c->stream);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-                if (e == cudaSuccess) e = launch_xinv(d, mode, c->side);
-                if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+        for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+            for (int g = 0; g < ng && e == cudaSuccess; ++g, ++slot) {
+                const AlsDesc &d = plans[g].d;
+                const TcPlan *tc = plans[g].has_tc ? &plans[g].tc : nullptr;
+                cudaStream_t st = g == 0 ? c->stream : c->grt[g - 1].st;
+                cudaStream_t side = g == 0 ? c->side : c->grt[g - 1].side;
+                cudaEvent_t fork = g == 0 ? c->ev_fork : c->grt[g - 1].fork;
+                cudaEvent_t join = g == 0 ? c->ev_join : c->grt[g - 1].join;
+                // V^-1 beside the pass; a memoised mode 3 has no pass over the
+                // summary, and k_mtt_memo forms its inverse
+                const bool xinv = d.xinv && !(mode == 2 && d.ymem);
+                if (xinv) {
+                    e = cudaEventRecord(fork, st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+                    if (e == cudaSuccess) e = launch_xinv(d, mode, side);
+                    if (e == cudaSuccess) e = cudaEventRecord(join, side);
+                }
+                const bool pass = !(mode == 2 && d.ymem);  // a memoised mode 3 launches no pass
+                if (e == cudaSuccess && timed && pass) e = cudaEventRecord(c->gev[slot].first, st);
+                if (e == cudaSuccess) e = mttkrp_mode(c, d, tc, mode, st);
+                if (e == cudaSuccess && timed && pass) e = cudaEventRecord(c->gev[slot].second, st);
+                if (e == cudaSuccess && xinv) e = cudaStreamWaitEvent(st, join, 0);
+                if (e == cudaSuccess) e = launch_reduce_tail(d, mode, st);
             }
-            if (e == cudaSuccess && timed) e = cudaEventRecord(c->gev[slot].first, c->stream);
-            if (e == cudaSuccess) e = mttkrp_mode(c, d, tc, mode);
-            if (e == cudaSuccess && timed) e = cudaEventRecord(c->gev[slot].second, c->stream);
-            if (e == cudaSuccess && d.xinv) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-            if (e == cudaSuccess) e = launch_reduce_tail(d, mode, c->stream);
         }
+    }
+    for (int g = 1; g < ng && e == cudaSuccess; ++g) {
+        e = cudaEventRecord(c->grt[g - 1].done, c->grt[g - 1].st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->grt[g - 1].done, 0);
     }
     return e;
 }
@@ -518,8 +685,8 @@ static cudaError_t launch_iterations(sbt_ctx *c, const AlsDesc &d, const TcPlan 
 // and then k_als_continue, which keeps the loop going while a repetition has
 // not converged, for at most ceil(max_iters / G) passes.  The convergence
 // test runs on the device: no host round trip inside the ALS.
-static sbt_status build_als_loop(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, int G, int max_passes,
-                                 cudaGraphExec_t *exec, long long *launches_per_pass) {
+static sbt_status build_als_loop(sbt_ctx *c, const AlsDesc &d, const std::vector<AlsPlan> &plans, int G,
+                                 int max_passes, cudaGraphExec_t *exec, long long *launches_per_pass) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaGraphCreate(&graph, 0);
     cudaGraphConditionalHandle h = 0;
@@ -536,7 +703,7 @@ static sbt_status build_als_loop(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc,
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t el = launch_iterations(c, d, tc, G, false);
+            cudaError_t el = launch_iterations(c, plans, G, false);
             if (el == cudaSuccess)
                 el = launch_als_continue(h, d.conv, d.nrep, c->passes.as<int>(), max_passes, c->stream);
             cudaGraph_t got = nullptr;
@@ -558,7 +725,7 @@ static void settle_als_counts(sbt_ctx *c) {
     if (!c->passes_pending) return;
     const int passes = *c->h_passes.as<int>();
     count_launches((int)(passes * c->launches_per_pass));
-    c->mtt_launches += 3LL * c->pass_iters * passes;
+    c->mtt_launches += (long long)c->mtt_per_iter * c->pass_iters * passes;
     c->passes_pending = false;
 }
 
@@ -566,13 +733,20 @@ static void settle_als_counts(sbt_ctx *c) {
 // Throughput path: one graph launch of the device-side loop; the pass count
 // is read back with the caller's next synchronisation.  Timing path (CUDA
 // events around every MTTKRP launch): the same kernels issued directly on the
-// stream, convergence polled every check_every iterations.  Kernels of
+// streams, convergence polled every check_every iterations.  Kernels of
 // converged repetitions exit at once, so iterations past convergence cost
 // only their launches.
 static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcPlan *tc = nullptr) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     const int G = std::max(1, std::min(every, max_iters));
     const int nl = (max_iters + G - 1) / G;
+    std::vector<AlsPlan> plans;
+    TRY(als_plans(c, d, tc, plans));
+    for (AlsPlan &pl : plans)
+        if (pl.d.ymem) pl.d.P[2] = 1;  // the memoised mode 3 writes one partial
+    const int ngr = (int)plans.size();
+    TRY(ensure_group_rt(c, ngr));
+    c->mtt_per_iter = (d.ymem ? 2 : 3) * ngr;
     if (c->passes_pending) {  // an earlier loop's count not read yet (its call failed before syncing)
         CK(cudaStreamSynchronize(c->stream));
         settle_als_counts(c);
@@ -582,7 +756,7 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
         TRY(c->h_passes.ensure(sizeof(int)));
         cudaGraphExec_t exec = nullptr;
         long long lpp = 0;
-        TRY(build_als_loop(c, d, tc, G, nl, &exec, &lpp));
+        TRY(build_als_loop(c, d, plans, G, nl, &exec, &lpp));
         cudaError_t e = cudaMemsetAsync(c->passes.p, 0, sizeof(int), c->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
         if (e == cudaSuccess)
@@ -594,21 +768,23 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
         c->pass_iters = G;
         return SBT_OK;
     }
-    while ((int)c->gev.size() < 3 * G) {
+    const int nslots = 3 * G * ngr;
+    while ((int)c->gev.size() < nslots) {
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
         c->gev.emplace_back(a, b);
     }
     for (int k = 0; k < nl; ++k) {
-        cudaError_t e = launch_iterations(c, d, tc, G, true);
-        c->mtt_launches += 3LL * G;
+        cudaError_t e = launch_iterations(c, plans, G, true);
+        c->mtt_launches += (long long)c->mtt_per_iter * G;
         const bool poll = (k == nl - 1) || !c->opt.fixed_iters;
         if (e == cudaSuccess && poll)
             e = cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS (timed): ") + cudaGetErrorString(e));
-        for (int q = 0; q < 3 * G; ++q) {
+        for (int q = 0; q < nslots; ++q) {
+            if ((q / ngr) % 3 == 2 && d.ymem) continue;
             float t = 0.f;
             if (cudaEventElapsedTime(&t, c->gev[q].first, c->gev[q].second) == cudaSuccess) c->mtt_ms += t;
         }
@@ -853,7 +1029,7 @@ static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound)
         als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
         best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(als_elem(c)));
         if (u.tc) {
-            tc_partials(d, c->num_sms, c->elem == 3);
+            tc_group_partials(c, d, als_group_count(c, r, true));
             best = std::max<size_t>(best, (size_t)r * d.prs * 4);
         }
     }
@@ -875,6 +1051,7 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
     als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
     TRY(als_sizes(c, d, update_part_bytes(c, u, bound), z));
     if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * esize_elem(c->elem)));
+    if (u.tc && !c->opt.mode3_pass) TRY(z.need(c->ymem, (size_t)r * u.Kp * u.nJ * d.pr * 4));
     if (c->elem == 3) TRY(z.need(c->sscale, (size_t)r * u.Kp * 4));
     if (u.tc && c->opt.refine_sweeps > 0) {
         TRY(z.need(c->Xlo, (size_t)r * u.xrs * 2));
@@ -905,7 +1082,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
-            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale,
+            &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale, &c->ymem,
             &c->si, &c->sj, &c->sv, &c->sptr, &c->cin_i, &c->cin_j, &c->cin_k, &c->cin_v, &c->ccnt, &c->cfill,
             &c->cmax, &c->posI, &c->posJ, &c->gcnt, &c->goff, &c->gtot, &c->vmax, &c->fexp, &c->eii, &c->ejj,
             &c->ekk, &c->ev, &c->perm1, &c->perm2, &c->rp1, &c->rp2, &c->gc1, &c->gc2, &c->gf1, &c->gf2};
@@ -1201,13 +1378,26 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp, c->elem == 3));
         CK(make_summary_tmap(&tc.m2, c->Xt.p, nI, nJ, ldi, (long long)r * Kp, c->elem == 3));
         tc.sscale = c->elem == 3 ? c->sscale.as<float>() : nullptr;
-        tc_partials(d, c->num_sms, c->elem == 3);
+        tc.xs = c->Xs.p;
+        tc.xt = c->Xt.p;
+        tc.nI = nI;
+        tc.nJ = nJ;
+        tc.ldj = ldj;
+        tc.ldi = ldi;
+        tc.Kp = Kp;
+        tc.fp8 = c->elem == 3;
+        tc_group_partials(c, d, als_group_count(c, r, true));
+        if (!c->opt.mode3_pass) {
+            d.ymem = c->ymem.as<float>();
+            d.yrs = (long long)Kp * nJ * d.pr;
+        }
     }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
                           c->batch, c->rowsq.as<double>(), c->stream));
-    if (tc.on && c->opt.autotune) {  // tile choices for shapes not seen before, then the partial counts they give
-        TRY(autotune_tiles(c, d, tc));
-        tc_partials(d, c->num_sms, c->elem == 3);
+    if (tc.on && c->opt.autotune) {  // tile choices for the groups' launch shapes not seen before
+        std::vector<AlsPlan> plans;
+        TRY(als_plans(c, d, &tc, plans));
+        for (AlsPlan &pl : plans) TRY(autotune_tiles(c, pl.d, pl.tc));
     }
     TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
     // refinement sweeps: the same ALS continued for refine_sweeps iterations
@@ -1219,6 +1409,8 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         } else {
             CK(make_summary_tmap(&tc.m1lo, c->Xlo.p, nJ, nI, ldj, (long long)r * Kp, false));
             CK(make_summary_tmap(&tc.m2lo, c->Xtlo.p, nI, nJ, u.ldi, (long long)r * Kp, false));
+            tc.xlo = c->Xlo.p;
+            tc.xtlo = c->Xtlo.p;
             CK(cudaMemcpyAsync(c->iters_main.p, d.iters, (size_t)r * 4, cudaMemcpyDeviceToDevice, c->stream));
             CK(launch_refine_start(d, c->rowsq2.as<double>(), c->stream));
             AlsDesc dr = d;

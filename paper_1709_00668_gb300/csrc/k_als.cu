@@ -440,141 +440,17 @@ __global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
 }
 
 // ---------------------------------------------------------------------------
-// Tail of one mode for float32 factors, in two kernels.  float64 is a slow
-// unit here, so only the R x R work (Hadamard of Grams, Cholesky, inverse,
-// fit) is float64; the n x R work runs in double-float on the float32 pipes.
+// Tail of one mode for float32 factors.  float64 is a slow unit here, so the
+// R x R work (Hadamard of Grams, inverse, fit) runs in double-float like the
+// n x R work, on the float32 pipes.
 //
-// V^-1 for mode `mode` from the Grams of the other two modes, by Gauss-Jordan
-// elimination on [V | I] in double-float, all R x 2R entries updated in
-// parallel (R pivot steps).  For symmetric V the pivots are the squared
-// Cholesky diagonals, so a non-positive pivot means V is not positive
-// definite: then V + 1e-12 tr(V)/R I is used and `reg` is set; if that fails
-// too, X = 0 and `reg` is set.  Called by a whole CTA; W holds 32 x 64 values.
-// X is written as two float planes (hi, lo) of 32 x 32.
-__device__ void block_inverse_df(const DF *Gf, int R, int mode, DF *W, float *X, int *reg) {
-    const int ld = 64;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        for (int e = threadIdx.x; e < R * 2 * R; e += blockDim.x) {
-            const int i = e / (2 * R), j = e % (2 * R);
-            DF v;
-            if (j < R) {
-                v = DF{1.f, 0.f};
-                for (int m = 0; m < 3; ++m)
-                    if (m != mode) v = df_mul(v, Gf[m * R * R + i * R + j]);
-            } else {
-                v = DF{(j - R == i) ? 1.f : 0.f, 0.f};
-            }
-            W[i * ld + j] = v;
-        }
-        __syncthreads();
-        if (attempt == 1) {
-            if (threadIdx.x == 0) {
-                DF tr{0.f, 0.f};
-                for (int i = 0; i < R; ++i) tr = df_add(tr, W[i * ld + i]);
-                const DF shift = df_mul(tr, DF{1e-12f / (float)R, 0.f});
-                for (int i = 0; i < R; ++i) W[i * ld + i] = df_add(W[i * ld + i], shift);
-            }
-            __syncthreads();
-        }
-        bool ok = true;
-        for (int k = 0; k < R; ++k) {
-            const DF piv = W[k * ld + k];
-            if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
-                ok = false;
-                break;
-            }
-            const DF inv = df_div(DF{1.f, 0.f}, piv);
-            DF rowk[8], colk[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int e = threadIdx.x + c * blockDim.x;
-                if (e < R * 2 * R) {
-                    const int i = e / (2 * R), j = e % (2 * R);
-                    rowk[c] = W[k * ld + j];
-                    colk[c] = W[i * ld + k];
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int e = threadIdx.x + c * blockDim.x;
-                if (e < R * 2 * R) {
-                    const int i = e / (2 * R), j = e % (2 * R);
-                    const DF t = df_mul(rowk[c], inv);
-                    if (i == k) W[i * ld + j] = t;
-                    else W[i * ld + j] = df_sub(W[i * ld + j], df_mul(colk[c], t));
-                }
-            }
-            __syncthreads();
-        }
-        if (ok) {
-            for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-                const int i = e / 32, j = e % 32;
-                const DF v = (i < R && j < R) ? W[i * ld + R + j] : DF{0.f, 0.f};
-                X[e] = v.hi;
-                X[1024 + e] = v.lo;
-            }
-            if (attempt == 1 && threadIdx.x == 0) *reg = 1;
-            __syncthreads();
-            return;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < 2 * 32 * 32; e += blockDim.x) X[e] = 0.f;
-    if (threadIdx.x == 0) *reg = 1;
-    __syncthreads();
-}
-
-// k_tail_rows: grid (row chunks of TAIL_ROWS, repetitions).  Every CTA
-// solves the R x R system itself (it keeps the chunks independent): a float32
-// Cholesky factorisation and inverse X0 of V (one warp), then Newton steps
-// X <- X (2I - V X) in double-float, which carry X0 to float64-level accuracy
-// (iterative refinement of the normal equations); float64 factorisation only
-// if the float32 one breaks down.  It sums the MTTKRP partials of its rows in
-// fixed order, forms U_raw = M V^-1 (written unnormalised) and the chunk's
-// share of U_raw^T U_raw and of <M, U_raw>.
+// k_tail_rows: grid (row chunks of TAIL_ROWS, repetitions).  V^-1 of the
+// mode comes from k_xinv (beside the MTTKRP pass) or k_mtt_memo.  Every CTA
+// sums the MTTKRP partials of its rows in fixed order, forms U_raw = M V^-1
+// (written unnormalised) and the chunk's share of U_raw^T U_raw and of
+// <M, U_raw>; the last CTA to finish combines the shares (tail_finish).
 constexpr int TAIL_PB = 32;        // partials staged per block
 constexpr int TAIL_THREADS = 256;
-
-// float32 Cholesky (one warp, lane per row): V = L L^T; false if not positive definite
-__device__ bool warp_cholesky_f(const float (*V)[33], float (*L)[33], int R, int lane) {
-    for (int j = 0; j < R; ++j) {
-        if (lane == j) {
-            float s = V[j][j];
-            for (int k = 0; k < j; ++k) s = fmaf(-L[j][k], L[j][k], s);
-            L[j][j] = s > 0.f ? sqrtf(s) : -1.f;
-        }
-        __syncwarp();
-        const float djj = L[j][j];
-        if (!(djj > 0.f)) return false;
-        const float inv = 1.f / djj;
-        if (lane > j && lane < R) {
-            float s = V[lane][j];
-            for (int k = 0; k < j; ++k) s = fmaf(-L[lane][k], L[j][k], s);
-            L[lane][j] = s * inv;
-        }
-        __syncwarp();
-    }
-    return true;
-}
-
-// X = (L L^T)^-1 in float32: lane c solves for column c, working column in Y
-__device__ void warp_inverse_f(const float (*L)[33], float (*Y)[33], float (*X)[33], int R, int lane) {
-    if (lane < R) {
-        for (int i = 0; i < R; ++i) {
-            float s = (i == lane) ? 1.f : 0.f;
-            for (int k = 0; k < i; ++k) s = fmaf(-L[i][k], Y[k][lane], s);
-            Y[i][lane] = s / L[i][i];
-        }
-        for (int i = R - 1; i >= 0; --i) {
-            float s = Y[i][lane];
-            for (int k = i + 1; k < R; ++k) s = fmaf(-L[k][i], Y[k][lane], s);
-            Y[i][lane] = s / L[i][i];
-        }
-        for (int i = 0; i < R; ++i) X[i][lane] = Y[i][lane];
-    }
-    __syncwarp();
-}
 
 __device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_bytes);
 
@@ -600,7 +476,6 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (d.conv[rep]) return;
     const int R = d.R, n = d.n[mode], P = d.P[mode];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ __align__(16) unsigned char tsm_raw[];
     TailSmem &S = *reinterpret_cast<TailSmem *>(tsm_raw);
     auto xh = S.xh, xl = S.xl, nh = S.nh, nl = S.nl;
@@ -609,7 +484,6 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
     float (*ml)[RP + 1] = mh + TAIL_ROWS;
     float (*ur)[RP + 1] = ml + TAIL_ROWS;
     const float *part = (const float *)d.part + rep * d.prs;
-    const long long pstride = (long long)n * R;
     float *U = (float *)d.U[mode] + (long long)rep * n * R;
     const int x0 = chunk * TAIL_ROWS;
     const int rows = min(TAIL_ROWS, n - x0);
@@ -867,17 +741,164 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_byt
     if (threadIdx.x == 0 && zero_flag) d.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
 }
 
-// V^-1 of mode `mode` (its Grams are final): one CTA per repetition, run on a
-// side stream while the mode's MTTKRP pass runs.
-__global__ void __launch_bounds__(256) k_xinv(AlsDesc d, int mode) {
+// V^-1 for mode `mode` from the Grams of the other two modes, by Gauss-Jordan
+// elimination on [V | I] in double-float (R pivot steps).  For symmetric V
+// the pivots are the squared Cholesky diagonals, so a non-positive pivot
+// means V is not positive definite: then V + 1e-12 tr(V)/R I is used and
+// `reg` is set; if that fails too, X = 0 and `reg` is set.  Called by
+// INV_THREADS threads, each holding up to INV_EPT entries (e = t + 128 u,
+// row-major over R x 2R; EPT >= 2 R^2 / 128) with straight-line code per
+// pivot step; W (shared memory, 32 x 64 values) exchanges the pivot row and
+// column.  X is written as two float planes (hi, lo) of 32 x 32.
+constexpr int INV_THREADS = 128;
+template <int EPT>
+__device__ void cta_inverse_df_t(const DF *Gf, int R, int mode, float *X, int *reg, DF *W) {
+    constexpr int INV_EPT = EPT;
+    const int t = threadIdx.x, ld = 64;
+    const int m0 = mode == 0 ? 1 : 0, m1 = mode == 2 ? 1 : 2;  // the two other modes, in order
+    const int ne = 2 * R * R;
+    int ei[INV_EPT], ej[INV_EPT];
+    DF init[INV_EPT];
+#pragma unroll
+    for (int u = 0; u < INV_EPT; ++u) {
+        const int e = t + INV_THREADS * u;
+        const int ec = e < ne ? e : 0;
+        ei[u] = ec / (2 * R);
+        ej[u] = ec % (2 * R);
+        const int jc = ej[u] < R ? ej[u] : 0;
+        const DF v = df_mul(df_mul(DF{1.f, 0.f}, Gf[m0 * R * R + ei[u] * R + jc]), Gf[m1 * R * R + ei[u] * R + jc]);
+        init[u] = ej[u] < R ? v : DF{(ej[u] - R == ei[u]) ? 1.f : 0.f, 0.f};
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+        for (int u = 0; u < INV_EPT; ++u)
+            if (t + INV_THREADS * u < ne) W[ei[u] * ld + ej[u]] = init[u];
+        __syncthreads();
+        if (attempt == 1) {
+            if (t == 0) {
+                DF tr{0.f, 0.f};
+                for (int i = 0; i < R; ++i) tr = df_add(tr, W[i * ld + i]);
+                const DF shift = df_mul(tr, DF{1e-12f / (float)R, 0.f});
+                for (int i = 0; i < R; ++i) W[i * ld + i] = df_add(W[i * ld + i], shift);
+            }
+            __syncthreads();
+        }
+        bool ok = true;
+        for (int k = 0; k < R; ++k) {
+            const DF piv = W[k * ld + k];
+            const DF inv = df_div(DF{1.f, 0.f}, piv);
+            DF nv[INV_EPT];
+#pragma unroll
+            for (int u = 0; u < INV_EPT; ++u) {
+                const DF rk = W[k * ld + ej[u]];
+                const DF ck = W[ei[u] * ld + k];
+                const DF tt = df_mul(rk, inv);
+                nv[u] = ei[u] == k ? tt : df_sub(W[ei[u] * ld + ej[u]], df_mul(ck, tt));
+            }
+            ok = ok && piv.hi > 0.f && isfinite(piv.hi);
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < INV_EPT; ++u)
+                if (t + INV_THREADS * u < ne) W[ei[u] * ld + ej[u]] = nv[u];
+            __syncthreads();
+        }
+        if (ok) {
+            for (int e = t; e < 32 * 32; e += INV_THREADS) {
+                const int i = e / 32, j = e % 32;
+                const DF v = (i < R && j < R) ? W[i * ld + R + j] : DF{0.f, 0.f};
+                X[e] = v.hi;
+                X[1024 + e] = v.lo;
+            }
+            if (attempt == 1 && t == 0) *reg = 1;
+            return;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < 2 * 32 * 32; e += INV_THREADS) X[e] = 0.f;
+    if (t == 0) *reg = 1;
+}
+
+// R <= 8: one entry per thread; R <= 16: four; R <= 32: sixteen
+__device__ void cta_inverse_df(const DF *Gf, int R, int mode, float *X, int *reg, DF *W) {
+    if (R <= 8) cta_inverse_df_t<1>(Gf, R, mode, X, reg, W);
+    else if (R <= 16) cta_inverse_df_t<4>(Gf, R, mode, X, reg, W);
+    else cta_inverse_df_t<16>(Gf, R, mode, X, reg, W);
+}
+
+// V^-1 of mode `mode` (its Grams are final): one CTA per repetition, run on
+// a side stream while the mode's MTTKRP pass runs.
+__global__ void __launch_bounds__(INV_THREADS) k_xinv(AlsDesc d, int mode) {
     const int rep = blockIdx.x;
     if (d.conv[rep]) return;
     __shared__ DF W[32 * 64];
-    __shared__ int reg;
-    if (threadIdx.x == 0) reg = 0;
-    __syncthreads();
-    block_inverse_df(d.Gf + (long long)rep * 3 * d.R * d.R, d.R, mode, W, d.xinv + (long long)rep * 2048, &reg);
+    int reg = 0;
+    cta_inverse_df(d.Gf + (long long)rep * 3 * d.R * d.R, d.R, mode, d.xinv + (long long)rep * 2048, &reg, W);
     if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
+}
+
+// Mode 3 after a memoised mode-2 pass: M3(kk, r) = sum_j Y_kk(j, r) B(j, r)
+// with the new B, one warp per summary slice (lanes over j, MJ rows of Y in
+// flight per lane, a fixed lane-order tree per r), written as the single
+// partial sum of the mode-3 tail; the first CTA of each repetition forms
+// V^-1 of mode 3 (the Grams of A and B are final) meanwhile.
+constexpr int MEMO_WARPS = INV_THREADS / 32;
+template <int RP>
+__global__ void __launch_bounds__(MEMO_WARPS * 32) k_mtt_memo(AlsDesc d) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int rep = blockIdx.y;
+    if (d.conv[rep]) return;
+    const int R = d.R, nj = d.n[1], Kp = d.n[2], pr = d.pr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x == 0) {
+        __shared__ DF W[32 * 64];
+        int reg = 0;
+        cta_inverse_df(d.Gf + (long long)rep * 3 * R * R, R, 2, d.xinv + (long long)rep * 2048, &reg, W);
+        if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
+        return;
+    }
+    const int kk = (blockIdx.x - 1) * MEMO_WARPS + warp;
+    if (kk >= Kp) return;
+    constexpr int NQ = RP / 4;             // float4 per row of Y (pr <= RP)
+    constexpr int MJ = RP <= 16 ? 4 : 2;   // rows of Y per lane in flight
+    const int pq = pr / 4;
+    const float4 *y = reinterpret_cast<const float4 *>(d.ymem + rep * d.yrs + (long long)kk * nj * pr);
+    const float *Bf = (const float *)d.U[1] + (long long)rep * nj * R;
+    float a[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) a[r] = 0.f;
+    for (int jb = lane; jb < nj; jb += 32 * MJ) {
+        float4 v[MJ][NQ];
+#pragma unroll
+        for (int u = 0; u < MJ; ++u) {
+            const int j = jb + 32 * u;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                v[u][q] = (j < nj && q < pq) ? __ldcg(y + (long long)j * pq + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < MJ; ++u) {
+            const int j = jb + 32 * u;
+            if (j < nj) {
+                const float *b = Bf + (long long)j * R;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float e[4] = {v[u][q].x, v[u][q].y, v[u][q].z, v[u][q].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (4 * q + c < R) a[4 * q + c] = fmaf(e[c], __ldg(b + 4 * q + c), a[4 * q + c]);
+                }
+            }
+        }
+    }
+    float *out = (float *)d.part + rep * d.prs + (long long)kk * pr;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+        if (r < R) {
+            const float sr = warp_sum(a[r]);
+            if (lane == 0) out[r] = sr;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1222,9 +1243,24 @@ cudaError_t launch_als_continue(cudaGraphConditionalHandle h, const int *conv, i
 }
 
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st) {
-    k_xinv<<<d.nrep, 256, 0, st>>>(d, mode);
+    k_xinv<<<d.nrep, INV_THREADS, 0, st>>>(d, mode);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mtt_memo(const AlsDesc &d, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((d.n[2] + MEMO_WARPS - 1) / MEMO_WARPS + 1, d.nrep);
+    cfg.blockDim = dim3(MEMO_WARPS * 32);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launches(1);
+    if (d.R <= 16) return cudaLaunchKernelEx(&cfg, k_mtt_memo<16>, d);
+    return cudaLaunchKernelEx(&cfg, k_mtt_memo<32>, d);
 }
 
 cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st) {

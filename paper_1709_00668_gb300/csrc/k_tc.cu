@@ -64,12 +64,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// tiled 3-d load with an L2 eviction policy (`policy` from createpolicy)
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                            uint64_t *bar) {
+                                            uint64_t *bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
+}
+
+// L2 policy for data read once per pass: evicted before other lines, so the
+// pass's outputs (partials, kept products) and the factors stay in L2
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -161,6 +171,8 @@ struct TcParams {
     unsigned long long *bytes_ctr;
     unsigned *err;           // device status word (ERR_TIMEOUT on a wait that gave up)
     int stages;
+    float *Y;                // ROWSUM only, nullable: every slice's product Z = X_kk F, [rep][Kp][NP][pr]
+    long long yrs;
 };
 
 constexpr int TC_MAX_SPC = 64;  // slices per CTA (epilogue weights staged in shared memory)
@@ -310,13 +322,14 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             uint32_t phase = 0;
             int issued = 0;
             const int nkb2 = p.nkb * (1 + p.split);
+            const uint64_t pol = l2_evict_first_policy();
             for (int t = 0; t < nsl && !*abort_flag; ++t) {
                 for (int kb2 = 0; kb2 < nkb2; ++kb2) {
                     const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
                     if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
                     mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
                     tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * KE,
-                                pb * p.br, rep * p.Kp + k0 + t, &sh->full[stage]);
+                                pb * p.br, rep * p.Kp + k0 + t, &sh->full[stage], pol);
                     ++issued;
                     if (++stage == S) {
                         stage = 0;
@@ -352,6 +365,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 const uint32_t d = tmem + (uint32_t)(a * TS);
                 bool ok = true;
                 const int nkb2 = p.nkb * (1 + p.split);
+            const uint64_t pol = l2_evict_first_policy();
                 for (int kb2 = 0; kb2 < nkb2; ++kb2) {
                     const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
                     if (!tc_wait(&sh->full[stage], phase, abort_flag, p.err)) {
@@ -424,6 +438,14 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             }
             mbar_arrive(&sh->acce[a]);
             const int kk = k0 + t;
+            if (p.Y && got && valid) {
+                // keep Z_kk (the slice scale applied): the mode-3 tail contracts it with the new factor
+                const float sc = FP8 ? p.sscale[(long long)rep * p.Kp + kk] : 1.f;
+                float4 *y = reinterpret_cast<float4 *>(p.Y + rep * p.yrs + ((long long)kk * p.NP + pidx) * p.pr);
+#pragma unroll
+                for (int r4 = 0; r4 < RH; r4 += 4)
+                    if (r4 < p.pr) y[r4 / 4] = make_float4(z[r4] * sc, z[r4 + 1] * sc, z[r4 + 2] * sc, z[r4 + 3] * sc);
+            }
             // after an abort every remaining wait returns at once; the loop
             // runs to its end so that all 128 threads meet the same barriers
             if (p.epi == 0) {
@@ -456,7 +478,10 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
         if (p.bytes_ctr && etid == 0 && !skipped) {
             const int rows = min(p.br, p.NP - pb * p.br);
-            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * (FP8 ? 1ull : 2ull) * nsl * (1 + p.split));
+            // summary bytes read, plus the products kept for the memoised mode 3
+            atomicAdd(p.bytes_ctr, (unsigned long long)rows * nsl *
+                                       ((unsigned long long)p.NC * (FP8 ? 1ull : 2ull) * (1 + p.split) +
+                                        (p.Y ? 4ull * R : 0ull)));
         }
     }
     tc_fence_before();
@@ -631,7 +656,8 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
-                             int num_sms, int *P_out, cudaStream_t st, const TileChoice *force) {
+                             int num_sms, int *P_out, cudaStream_t st, float *Y, long long yrs,
+                             const TileChoice *force) {
     const bool fp8 = sscale != nullptr;
     const TileChoice tch = force ? *force : tile_choice(fp8, R, NP, NC, Kp, nrep, epi);
     TcParams p{};
@@ -657,6 +683,8 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     p.conv = conv;
     p.bytes_ctr = bytes_ctr;
     p.err = err;
+    p.Y = epi == 0 ? Y : nullptr;
+    p.yrs = yrs;
     const int N = tc_n_of(R, fp8);
     const size_t budget = tch.per_sm == 1 ? 220 * 1024 : 110 * 1024;
     const size_t fixed = tc_fixed_smem(p.nkb, N, tc_rh_of(R));

@@ -332,6 +332,9 @@ struct AlsDesc {
     int *tail_cnt;         // [rep] chunk CTAs finished (the last one completes the mode; zero between uses)
     int tchunks;           // row chunks of TAIL_ROWS for the largest mode
     long long rq_rows;     // row sums of squares per repetition (0: n[2] * n[0], the dense summary rows)
+    float *ymem;           // nullable: Y_kk = X_kk^T A of the mode-2 pass, [rep][n[2]][n[1]][pr]; the
+                           // mode-3 MTTKRP is then M3(kk, r) = sum_j Y_kk(j, r) B(j, r) (k_mtt_memo)
+    long long yrs;         // floats per repetition of ymem
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -374,6 +377,9 @@ cudaError_t set_als_kernel_attributes();
 cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
+// mode 3 after a memoised mode-2 pass: M3 from d.ymem and the new B as the
+// single partial of the mode-3 tail, and V^-1 of mode 3 (PDL launch)
+cudaError_t launch_mtt_memo(const AlsDesc &d, cudaStream_t st);
 cudaError_t launch_refine_start(const AlsDesc &d, const double *rowsq2, cudaStream_t st);
 // COO path
 cudaError_t launch_coo_count(const int *kk, long long nnz, int K, int *cnt, DevStatus *status, cudaStream_t st);
@@ -425,7 +431,8 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
                              const float *F, long long frs, const float *W, long long wrs, float *part, long long prs,
                              int pr,
                              const int *conv, unsigned long long *bytes_ctr, unsigned *err, const float *sscale,
-                             int num_sms, int *P_out, cudaStream_t st, const TileChoice *force = nullptr);
+                             int num_sms, int *P_out, cudaStream_t st, float *Y = nullptr, long long yrs = 0,
+                             const TileChoice *force = nullptr);
 cudaError_t launch_transpose_bf16(const void *X, void *Y, int NI, int NJ, int ldx, int ldy, long long nslices,
                                   cudaStream_t st);
 // reduction of d.P[mode] partials into d.M, then the tail

@@ -95,25 +95,33 @@ def test_update_f32_matches_oracle_scaled_c2(sbt):
     assert abs(f - O.full_fit(ost2.X, ost2.lam, ost2.A, ost2.B, ost2.C)) < 1e-5
 
 
-def test_update_bf16_summary_bits_and_factors(sbt):
+@pytest.mark.parametrize("mode3_pass,groups", [(0, 0), (1, 1), (0, 3)])
+def test_update_bf16_summary_bits_and_factors(sbt, mode3_pass, groups):
+    """mode3_pass 0: the mode-3 MTTKRP formed from the mode-2 pass's
+    products; 1: its own pass over the summary.  The 4 repetitions' ALS in
+    the default 2 groups, in 1, and in 3 uneven groups (1, 1, 2).  All within
+    the bar."""
     X, A, B, C = planted(120, 96, 70, 6, dtype=torch.float32, seed=2)
     fac = unit_factors(A, B, C[:60])
-    ctx, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15)
+    ctx, ost = _pair(sbt, X, 60, 6, fac, prec="bf16", s_I=3, s_J=3, s_K=3, r=4, fixed_iters=1, max_iters=15,
+                     mode3_pass=mode3_pass, als_groups=groups)
     ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
     ctx.update(torch.from_numpy(X[60:70]).cuda())
     _check_update(ctx, ost2, traces, ftol=1e-3)
 
 
-@pytest.mark.parametrize("shape", [(120, 96, 6, 3), (120, 96, 20, 3), (330, 290, 10, 2)])
+@pytest.mark.parametrize("shape", [(120, 96, 6, 3, 0), (120, 96, 20, 3, 0), (330, 290, 10, 2, 0),
+                                   (330, 290, 10, 2, 1)])
 def test_update_fp8_summary_bits_and_factors(sbt, shape):
     """float8 e4m3 summaries (one scale per stored slice): the scaled codes
     bit-exact against the oracle, factors within the tolerance of a 4-bit
     summary ALS run both sides with the same codes.  The last shape has
     summaries wider than one 128-element box (165 x 145)."""
-    I, J, R, s = shape
+    I, J, R, s, m3 = shape
     X, A, B, C = planted(I, J, 70, R, dtype=torch.float32, seed=22)
     fac = unit_factors(A, B, C[:60])
-    ctx, ost = _pair(sbt, X, 60, R, fac, prec="fp8", s_I=s, s_J=s, s_K=3, r=4, fixed_iters=1, max_iters=15)
+    ctx, ost = _pair(sbt, X, 60, R, fac, prec="fp8", s_I=s, s_J=s, s_K=3, r=4, fixed_iters=1, max_iters=15,
+                     mode3_pass=m3)
     ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
     ctx.update(torch.from_numpy(X[60:70]).cuda())
     errs = [rel_err(a, b) for a, b in zip(ctx.factors(), (ost2.lam, ost2.A, ost2.B, ost2.C))]
@@ -286,11 +294,15 @@ def test_init_als_f32_fit(sbt):
     assert abs(ctx.fit() - O.full_fit(X, st.lam, st.A, st.B, st.C)) < 1e-4
 
 
-def test_profile_counters(sbt):
-    """MTTKRP bytes counted = passes x repetitions x summary bytes (fixed iterations)."""
+@pytest.mark.parametrize("mode3_pass", [0, 1])
+def test_profile_counters(sbt, mode3_pass):
+    """MTTKRP bytes counted = passes x repetitions x summary bytes (fixed
+    iterations), plus the products the mode-2 pass keeps when mode 3 is
+    formed from them (two passes per iteration instead of three)."""
     X, A, B, C = planted(64, 48, 40, 4, dtype=torch.float32, seed=13)
     fac = unit_factors(A, B, C[:30])
-    ctx, _ = _pair(sbt, X, 30, 4, fac, prec="bf16", r=3, fixed_iters=1, max_iters=7)
+    ctx, _ = _pair(sbt, X, 30, 4, fac, prec="bf16", r=3, fixed_iters=1, max_iters=7, mode3_pass=mode3_pass,
+                   als_groups=2)
     ctx.profile_reset(timing=True)
     ctx.update(torch.from_numpy(X[30:40]).cuda())
     p = ctx.profile()
@@ -298,9 +310,11 @@ def test_profile_counters(sbt):
     Kp = st["n_K"] + 10
     assert p["updates"] == 1
     # the ALS runs as a graph of 4 iterations (the poll interval): 2 graph launches
-    assert p["mttkrp_launches"] == 3 * 8
+    passes = 3 if mode3_pass else 2
+    assert p["mttkrp_launches"] == passes * 8 * 2  # 8 iterations (2 loop bodies of 4), 2 groups
     # only passes of repetitions still iterating read the summary: 7 iterations
-    assert p["mttkrp_bytes"] == 3 * 7 * 3 * Kp * st["n_I"] * st["n_J"] * 2
+    keep = 0 if mode3_pass else Kp * st["n_J"] * 4 * 4
+    assert p["mttkrp_bytes"] == 3 * 7 * (passes * Kp * st["n_I"] * st["n_J"] * 2 + keep)
     assert p["mttkrp_ms"] > 0 and p["launches"] > p["mttkrp_launches"]
 
 
@@ -350,11 +364,13 @@ def test_device_loop_equals_directly_launched_iterations(sbt):
             s1, s2 = c_loop.stats(), c_timed.stats()
             assert s1["iters"] == s2["iters"] and s1["fit"] == s2["fit"]
             p1, p2 = c_loop.profile(), c_timed.profile()
+            # bf16: mode 3 formed from the mode-2 pass, the 3 repetitions in 2 groups
+            per_iter = 2 * 2 if prec == "bf16" else 3
             if kw["fixed_iters"]:
-                assert p1["mttkrp_launches"] == p2["mttkrp_launches"] == 2 * 3 * 8
+                assert p1["mttkrp_launches"] == p2["mttkrp_launches"] == 2 * per_iter * 8
             else:
                 assert max(s1["iters"]) < kw["max_iters"]
-                assert p1["mttkrp_launches"] % 12 == 0 and p1["mttkrp_launches"] > 0
+                assert p1["mttkrp_launches"] % (4 * per_iter) == 0 and p1["mttkrp_launches"] > 0
             assert p1["mttkrp_bytes"] == p2["mttkrp_bytes"]
             assert p1["mttkrp_ms"] == 0 and p2["mttkrp_ms"] > 0
 
@@ -373,7 +389,8 @@ def test_autotune_records_choices_and_keeps_parity(sbt):
     _check_update(ctx, ost2, traces, ftol=1e-3)
     tab = sbt.tile_table()
     st = ctx.stats()
-    shapes = {(st["n_I"], st["n_J"], 0), (st["n_J"], st["n_I"], 0), (st["n_I"], st["n_J"], 1)}  # modes 1, 2, 3
+    # modes 1 and 2 (mode 3 is formed from the mode-2 pass and launches none)
+    shapes = {(st["n_I"], st["n_J"], 0), (st["n_J"], st["n_I"], 0)}
     assert {(e["NP"], e["NC"], e["epi"]) for e in tab} == shapes and len(tab) == len(shapes)
     assert all(e["ctas_per_sm"] in (1, 2) and 0 <= e["stages"] <= 8 for e in tab)
     ctx2, _ = _pair(sbt, X, 100, 10, fac, autotune=1, **kw)
