@@ -18,6 +18,8 @@
 // Every reduction runs in a fixed order, so results do not depend on timing.
 #include "sbt_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <atomic>
 
@@ -451,6 +453,7 @@ __global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
 // <M, U_raw>; the last CTA to finish combines the shares (tail_finish).
 constexpr int TAIL_PB = 32;        // partials staged per block
 constexpr int TAIL_THREADS = 256;
+constexpr int TAIL_MAX_CLUSTER = 16;  // chunks of one repetition in one cluster (non-portable size)
 
 __device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_bytes);
 
@@ -468,6 +471,10 @@ __host__ __device__ constexpr size_t tail_smem_bytes() {
 }
 
 template <int RP>
+__device__ void tail_finish_cluster(const AlsDesc &d, int mode, int rep, const DF *csh, int nch, int rows, int x0,
+                                    const float (*ur)[RP + 1]);
+
+template <int RP, bool CL>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode) {
     const int rep = blockIdx.y, chunk = blockIdx.x;
     // programmatic dependent launch: let the next MTTKRP pass be scheduled,
@@ -488,11 +495,27 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
     const int x0 = chunk * TAIL_ROWS;
     const int rows = min(TAIL_ROWS, n - x0);
 
-    // V^-1 of this mode (double-float planes, computed beside the MTTKRP pass)
-    const float *Xg = d.xinv + (long long)rep * 2048;
-    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-        xh[e / 32][e % 32] = Xg[e];
-        xl[e / 32][e % 32] = Xg[1024 + e];
+    // V^-1 of this mode (double-float planes, computed beside the MTTKRP
+    // pass): its R x R entries, all loads in flight before the stores
+    {
+        const float *Xg = d.xinv + (long long)rep * 2048;
+        constexpr int XPT = 32 * 32 / TAIL_THREADS;
+        float vh[XPT], vl[XPT];
+#pragma unroll
+        for (int u = 0; u < XPT; ++u) {
+            const int e = threadIdx.x + u * TAIL_THREADS;
+            const int k = e / R, r = e % R;
+            vh[u] = e < R * R ? Xg[k * 32 + r] : 0.f;
+            vl[u] = e < R * R ? Xg[1024 + k * 32 + r] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < XPT; ++u) {
+            const int e = threadIdx.x + u * TAIL_THREADS;
+            if (e < R * R) {
+                xh[e / R][e % R] = vh[u];
+                xl[e / R][e % R] = vl[u];
+            }
+        }
     }
     // partial sums in fixed order per (row, r) item.  The chunk's share of
     // each partial is one contiguous, 16-byte aligned run of rows*pr floats
@@ -560,7 +583,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
         for (int k = 0; k < R; ++k) a = df_fma(a, DF{mh[t][k], ml[t][k]}, DF{xh[k][r], xl[k][r]});
         const float uf = __fadd_rn(a.hi, a.lo);
         ur[t][r] = uf;
-        U[(long long)(x0 + t) * R + r] = uf;
+        if (!CL) U[(long long)(x0 + t) * R + r] = uf;  // a cluster writes its rows once, normalised
         inner = df_fma(inner, DF{mh[t][r], ml[t][r]}, DF{uf, 0.f});
     }
     inner = warp_df_sum(inner);
@@ -595,25 +618,37 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_rows(AlsDesc d, int mode)
         (&nl[0][0])[w0] = a.lo;
     }
     __syncthreads();
-    for (int pq = threadIdx.x; pq < slots; pq += blockDim.x) {
-        DF a{0.f, 0.f};
-        for (int sub = 0; sub < tps; ++sub) a = df_add(a, DF{(&nh[0][0])[pq * tps + sub], (&nl[0][0])[pq * tps + sub]});
-        tp[pq] = a;
-    }
-    // the last chunk CTA of this repetition to finish completes the mode
-    __shared__ int is_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if constexpr (CL) {
+        // the repetition's chunk CTAs are one cluster: shares stay in shared
+        // memory and every CTA completes the mode for its own rows
+        __shared__ DF csh[32 * 33 / 2 + 1];
+        for (int pq = threadIdx.x; pq < slots; pq += blockDim.x) {
+            DF a{0.f, 0.f};
+            for (int sub = 0; sub < tps; ++sub) a = df_add(a, DF{(&nh[0][0])[pq * tps + sub], (&nl[0][0])[pq * tps + sub]});
+            csh[pq] = a;
+        }
+        tail_finish_cluster<RP>(d, mode, rep, csh, (int)gridDim.x, rows, x0, ur);
+    } else {
+        for (int pq = threadIdx.x; pq < slots; pq += blockDim.x) {
+            DF a{0.f, 0.f};
+            for (int sub = 0; sub < tps; ++sub) a = df_add(a, DF{(&nh[0][0])[pq * tps + sub], (&nl[0][0])[pq * tps + sub]});
+            tp[pq] = a;
+        }
+        // the last chunk CTA of this repetition to finish completes the mode
+        __shared__ int is_last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int nch = (n + TAIL_ROWS - 1) / TAIL_ROWS;
+            const int old = atomicAdd(&d.tail_cnt[rep], 1);
+            is_last = (old == nch - 1);
+            if (is_last) d.tail_cnt[rep] = 0;
+        }
+        __syncthreads();
+        if (!is_last) return;
         __threadfence();
-        const int nch = (n + TAIL_ROWS - 1) / TAIL_ROWS;
-        const int old = atomicAdd(&d.tail_cnt[rep], 1);
-        is_last = (old == nch - 1);
-        if (is_last) d.tail_cnt[rep] = 0;
+        tail_finish(d, mode, rep, tail_smem_bytes<RP>());
     }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    tail_finish(d, mode, rep, tail_smem_bytes<RP>());
 }
 
 // Finish of one mode for one repetition (the last chunk CTA), in double-float:
@@ -739,6 +774,109 @@ __device__ void tail_finish(const AlsDesc &d, int mode, int rep, size_t smem_byt
         if (threadIdx.x < R) d.lam[rep * R + threadIdx.x] = df_value(lam_s[threadIdx.x]);
     }
     if (threadIdx.x == 0 && zero_flag) d.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
+}
+
+// tail_finish for a cluster of the repetition's chunk CTAs (rank = chunk):
+// after a cluster barrier every CTA adds the shares of all chunks in chunk
+// order from their shared memory (the same sums as tail_finish), forms
+// lambda and the normalised Gram, and writes its own rows of U divided by
+// lambda; rank 0 writes the repetition's state (Gram, lambda, fit,
+// convergence).  A second barrier keeps every CTA's shares readable until
+// all have been read.
+template <int RP>
+__device__ void tail_finish_cluster(const AlsDesc &d, int mode, int rep, const DF *csh, int nch, int rows, int x0,
+                                    const float (*ur)[RP + 1]) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int R = d.R, n = d.n[mode];
+    const int npairs = R * (R + 1) / 2;
+    const bool lead = cluster.block_rank() == 0;
+    __shared__ DF graw[32 * 33 / 2 + 1];
+    __shared__ DF lam_s[32], inv_l[32];
+    __shared__ float inv_lam[32];
+    __shared__ DF gm[32 * 32];
+    __shared__ DF xh_part[32];
+    __shared__ int zero_flag;
+    if (threadIdx.x == 0) zero_flag = 0;
+    cluster.sync();
+    for (int pq = threadIdx.x; pq <= npairs; pq += blockDim.x) {
+        DF v[TAIL_MAX_CLUSTER];
+#pragma unroll
+        for (int c = 0; c < TAIL_MAX_CLUSTER; ++c)
+            v[c] = c < nch ? cluster.map_shared_rank(csh, c)[pq] : DF{0.f, 0.f};
+        DF a{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < TAIL_MAX_CLUSTER; ++c)
+            if (c < nch) a = df_add(a, v[c]);
+        graw[pq] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        DF l = df_sqrt(graw[r * R - r * (r - 1) / 2]);  // diagonal pair (r, r)
+        if (l.hi == 0.f) {
+            l = DF{1.f, 0.f};
+            zero_flag = 1;
+        }
+        lam_s[r] = l;
+        inv_l[r] = df_div(DF{1.f, 0.f}, l);
+        inv_lam[r] = __fadd_rn(inv_l[r].hi, inv_l[r].lo);
+    }
+    __syncthreads();
+    DF *Gf = d.Gf + (long long)rep * 3 * R * R;
+    for (int pq = threadIdx.x; pq < npairs; pq += blockDim.x) {
+        int r = 0, rem = pq;
+        while (rem >= R - r) {
+            rem -= R - r;
+            ++r;
+        }
+        const int s2 = r + rem;
+        const DF g = df_mul(df_mul(graw[pq], inv_l[r]), inv_l[s2]);
+        if (lead) {
+            Gf[mode * R * R + r * R + s2] = g;
+            Gf[mode * R * R + s2 * R + r] = g;
+        }
+        gm[r * R + s2] = g;
+        gm[s2 * R + r] = g;
+    }
+    float *U = (float *)d.U[mode] + (long long)rep * n * R;
+    for (int it = threadIdx.x; it < rows * R; it += blockDim.x) {
+        const int t = it / R, r = it % R;
+        U[(long long)(x0 + t) * R + r] = ur[t][r] * inv_lam[r];
+    }
+    __syncthreads();
+    if (mode == 2 && lead) {
+        DF a{0.f, 0.f};
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+            const int r = e / R, s2 = e % R;
+            DF t = df_mul(df_mul(lam_s[r], lam_s[s2]), df_mul(df_mul(Gf[e], Gf[R * R + e]), gm[e]));
+            a = df_add(a, t);
+        }
+        a = warp_df_sum(a);
+        if ((threadIdx.x & 31) == 0) xh_part[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DF xh{0.f, 0.f};
+            for (int t = 0; t < (int)(blockDim.x >> 5); ++t) xh = df_add(xh, xh_part[t]);
+            const DF in = graw[npairs];  // <X, X_hat> = sum_r lambda_r <M(:,r), U(:,r)> = <M, U_raw>
+            const DF nx2 = d.nx2f[rep];
+            DF res2 = df_sub(df_add(nx2, xh), df_add(in, in));
+            if (!(res2.hi > 0.f)) res2 = DF{0.f, 0.f};
+            const DF ratio = nx2.hi > 0.f ? df_div(df_sqrt(res2), df_sqrt(nx2)) : DF{1.f, 0.f};
+            const DF fit = df_sub(DF{1.f, 0.f}, ratio);
+            const DF diff = df_sub(fit, d.fitpf[rep]);
+            const int it = d.iters[rep] + 1;
+            d.iters[rep] = it;
+            d.fit[rep] = df_value(fit);
+            bool stop = it >= d.max_iters;
+            if (!d.fixed_iters && fabsf(__fadd_rn(diff.hi, diff.lo)) < (float)d.tol) stop = true;
+            d.fitpf[rep] = fit;
+            if (stop) d.conv[rep] = 1;
+        }
+        if (threadIdx.x < R) d.lam[rep * R + threadIdx.x] = df_value(lam_s[threadIdx.x]);
+    }
+    if (lead && threadIdx.x == 0 && zero_flag) d.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
+    cluster.sync();
 }
 
 // V^-1 for mode `mode` from the Grams of the other two modes, by Gauss-Jordan
@@ -1169,16 +1307,31 @@ cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         count_launches(1);
+        // a repetition's chunks as one cluster (up to 16 CTAs) when they fit
+        const int nch = (d.n[mode] + TAIL_ROWS - 1) / TAIL_ROWS;
+        const bool cl = nch <= TAIL_MAX_CLUSTER;
+        cudaLaunchAttribute attr2[2] = {attr[0], {}};
+        if (cl) {
+            attr2[1].id = cudaLaunchAttributeClusterDimension;
+            attr2[1].val.clusterDim.x = (unsigned)nch;
+            attr2[1].val.clusterDim.y = 1;
+            attr2[1].val.clusterDim.z = 1;
+            cfg.attrs = attr2;
+            cfg.numAttrs = 2;
+        }
         if (RP == 8) {
             cfg.dynamicSmemBytes = tail_smem_bytes<8>();
-            return cudaLaunchKernelEx(&cfg, k_tail_rows<8>, d, mode);
+            return cl ? cudaLaunchKernelEx(&cfg, k_tail_rows<8, true>, d, mode)
+                      : cudaLaunchKernelEx(&cfg, k_tail_rows<8, false>, d, mode);
         }
         if (RP == 16) {
             cfg.dynamicSmemBytes = tail_smem_bytes<16>();
-            return cudaLaunchKernelEx(&cfg, k_tail_rows<16>, d, mode);
+            return cl ? cudaLaunchKernelEx(&cfg, k_tail_rows<16, true>, d, mode)
+                      : cudaLaunchKernelEx(&cfg, k_tail_rows<16, false>, d, mode);
         }
         cfg.dynamicSmemBytes = tail_smem_bytes<32>();
-        return cudaLaunchKernelEx(&cfg, k_tail_rows<32>, d, mode);
+        return cl ? cudaLaunchKernelEx(&cfg, k_tail_rows<32, true>, d, mode)
+                  : cudaLaunchKernelEx(&cfg, k_tail_rows<32, false>, d, mode);
     }
     cudaError_t e = reduce_dispatch(d, mode, st);
     if (e != cudaSuccess) return e;
@@ -1199,6 +1352,17 @@ static cudaError_t raise_smem_limits() {
 
 // Raise the dynamic shared-memory limits of every ALS kernel once, outside any
 // stream capture.
+
+// dynamic shared memory of both tail variants; clusters of up to 16 CTAs
+template <int RP>
+static cudaError_t tail_attributes() {
+    const int smem = (int)tail_smem_bytes<RP>();
+    cudaError_t e = cudaFuncSetAttribute(k_tail_rows<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
 cudaError_t set_als_kernel_attributes() {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = raise_smem_limits<double, 8>();
@@ -1210,14 +1374,9 @@ cudaError_t set_als_kernel_attributes() {
     if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 8>();
     if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 16>();
     if (e == cudaSuccess) e = raise_smem_limits<__nv_bfloat16, 32>();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tail_rows<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_bytes<8>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tail_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tail_smem_bytes<16>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tail_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tail_smem_bytes<32>());
+    if (e == cudaSuccess) e = tail_attributes<8>();
+    if (e == cudaSuccess) e = tail_attributes<16>();
+    if (e == cudaSuccess) e = tail_attributes<32>();
     return e;
 }
 

@@ -274,41 +274,61 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         // epilogue weights C(kk, :) (times the slice scale for float8)
         const float *F = p.F + rep * p.frs;
         const int t = threadIdx.x - 32;
-        for (int j = t; j < p.nkb * KE; j += 160) {
-            const int kb = j / KE, k = j % KE;
-            unsigned char *blk = btile + (size_t)kb * N * 128;
-#pragma unroll 4
-            for (int r = 0; r < RH; ++r) {
-                const float f = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
-                if constexpr (!FP8) {
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-                    const int nh = r, nl = RH + r;
-                    unsigned char *col = blk + (k & 7) * 2;
-                    *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
-                    *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
-                } else {
-                    const unsigned char e1 = to_e4m3(f * 256.f);
-                    const float r1 = f - from_e4m3(e1) * 0.00390625f;
-                    const unsigned char e2 = to_e4m3(r1 * 4096.f);
-                    const float r2 = r1 - from_e4m3(e2) * 0.000244140625f;
-                    const unsigned char e3 = to_e4m3(r2 * 65536.f);
-                    const unsigned char ev[3] = {e1, e2, e3};
+        // two contraction indices per thread and round, all loads of a round
+        // in flight before the conversions
+        for (int j0 = t; j0 < p.nkb * KE; j0 += 2 * 160) {
+            float fv[2][RH];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const int n = q * RH + r;
-                        blk[n * 128 + (((k >> 4) ^ (n & 7)) << 4) + (k & 15)] = ev[q];
+            for (int u = 0; u < 2; ++u) {
+                const int j = j0 + u * 160;
+#pragma unroll
+                for (int r = 0; r < RH; ++r) fv[u][r] = (j < p.NC && r < R) ? F[(long long)j * R + r] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = j0 + u * 160;
+                if (j >= p.nkb * KE) break;
+                const int kb = j / KE, k = j % KE;
+                unsigned char *blk = btile + (size_t)kb * N * 128;
+#pragma unroll
+                for (int r = 0; r < RH; ++r) {
+                    const float f = fv[u][r];
+                    if constexpr (!FP8) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+                        const int nh = r, nl = RH + r;
+                        unsigned char *col = blk + (k & 7) * 2;
+                        *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
+                        *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
+                    } else {
+                        const unsigned char e1 = to_e4m3(f * 256.f);
+                        const float r1 = f - from_e4m3(e1) * 0.00390625f;
+                        const unsigned char e2 = to_e4m3(r1 * 4096.f);
+                        const float r2 = r1 - from_e4m3(e2) * 0.000244140625f;
+                        const unsigned char e3 = to_e4m3(r2 * 65536.f);
+                        const unsigned char ev[3] = {e1, e2, e3};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const int n = q * RH + r;
+                            blk[n * 128 + (((k >> 4) ^ (n & 7)) << 4) + (k & 15)] = ev[q];
+                        }
                     }
                 }
             }
         }
         if (p.epi == 0) {
             const float *W = p.W + rep * p.wrs;
-            for (int e = t; e < nsl * RH; e += 160) {
-                const int tt = e / RH, r = e % RH;
-                float w = r < R ? W[(long long)(k0 + tt) * R + r] : 0.f;
-                if (FP8) w *= p.sscale[(long long)rep * p.Kp + k0 + tt];
-                wst[e] = w;
+            for (int e0 = t; e0 < nsl * RH; e0 += 2 * 160) {
+                float w[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = e0 + u * 160, tt = e / RH, r = e % RH;
+                    w[u] = (e < nsl * RH && r < R) ? W[(long long)(k0 + tt) * R + r] : 0.f;
+                    if (FP8 && e < nsl * RH) w[u] *= p.sscale[(long long)rep * p.Kp + k0 + tt];
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (e0 + u * 160 < nsl * RH) wst[e0 + u * 160] = w[u];
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
