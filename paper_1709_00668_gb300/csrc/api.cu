@@ -1018,6 +1018,10 @@ static sbt_status update_shape(const sbt_ctx *c, int64_t K_old, int K_new, bool 
     return SBT_OK;
 }
 
+// mode 3 formed from the mode-2 pass's products (tensor-core path) unless
+// the option asks for its own pass
+static bool memo_mode3(const sbt_ctx *c, int) { return !c->opt.mode3_pass; }
+
 // bytes of MTTKRP partial sums for an update of this shape; with `bound`, the
 // largest over all summary lengths up to u.Kp (tile counts are not monotone)
 static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound) {
@@ -1051,7 +1055,7 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
     als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
     TRY(als_sizes(c, d, update_part_bytes(c, u, bound), z));
     if (u.tc) TRY(z.need(c->Xt, (size_t)r * u.Kp * u.nJ * u.ldi * esize_elem(c->elem)));
-    if (u.tc && !c->opt.mode3_pass) TRY(z.need(c->ymem, (size_t)r * u.Kp * u.nJ * d.pr * 4));
+    if (u.tc && memo_mode3(c, u.nJ)) TRY(z.need(c->ymem, (size_t)r * u.Kp * u.nJ * d.pr * 4));
     if (c->elem == 3) TRY(z.need(c->sscale, (size_t)r * u.Kp * 4));
     if (u.tc && c->opt.refine_sweeps > 0) {
         TRY(z.need(c->Xlo, (size_t)r * u.xrs * 2));
@@ -1387,7 +1391,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         tc.Kp = Kp;
         tc.fp8 = c->elem == 3;
         tc_group_partials(c, d, als_group_count(c, r, true));
-        if (!c->opt.mode3_pass) {
+        if (memo_mode3(c, nJ)) {
             d.ymem = c->ymem.as<float>();
             d.yrs = (long long)Kp * nJ * d.pr;
         }

@@ -956,9 +956,10 @@ __device__ void cta_inverse_df_t(const DF *Gf, int R, int mode, float *X, int *r
     if (t == 0) *reg = 1;
 }
 
-// R <= 8: one entry per thread; R <= 16: four; R <= 32: sixteen
+// entries per thread: 2 R^2 <= 128 EPT
 __device__ void cta_inverse_df(const DF *Gf, int R, int mode, float *X, int *reg, DF *W) {
     if (R <= 8) cta_inverse_df_t<1>(Gf, R, mode, X, reg, W);
+    else if (R <= 11) cta_inverse_df_t<2>(Gf, R, mode, X, reg, W);
     else if (R <= 16) cta_inverse_df_t<4>(Gf, R, mode, X, reg, W);
     else cta_inverse_df_t<16>(Gf, R, mode, X, reg, W);
 }
@@ -975,18 +976,19 @@ __global__ void __launch_bounds__(INV_THREADS) k_xinv(AlsDesc d, int mode) {
 }
 
 // Mode 3 after a memoised mode-2 pass: M3(kk, r) = sum_j Y_kk(j, r) B(j, r)
-// with the new B, one warp per summary slice (lanes over j, MJ rows of Y in
-// flight per lane, a fixed lane-order tree per r), written as the single
-// partial sum of the mode-3 tail; the first CTA of each repetition forms
-// V^-1 of mode 3 (the Grams of A and B are final) meanwhile.
-constexpr int MEMO_WARPS = INV_THREADS / 32;
+// with the new B, one CTA per summary slice: every thread loads its rows of
+// Y and of B together (two rows per round), then a fixed-order reduction
+// (lane tree, then the warps in order) gives the single partial sum of the
+// mode-3 tail.  CTA 0 of each repetition forms V^-1 of mode 3 (the Grams of
+// A and B are final) meanwhile.
+constexpr int MEMO_THREADS = INV_THREADS;
 template <int RP>
-__global__ void __launch_bounds__(MEMO_WARPS * 32) k_mtt_memo(AlsDesc d) {
+__global__ void __launch_bounds__(MEMO_THREADS) k_mtt_memo(AlsDesc d) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int rep = blockIdx.y;
     if (d.conv[rep]) return;
-    const int R = d.R, nj = d.n[1], Kp = d.n[2], pr = d.pr;
+    const int R = d.R, nj = d.n[1], pr = d.pr;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x == 0) {
         __shared__ DF W[32 * 64];
@@ -995,47 +997,47 @@ __global__ void __launch_bounds__(MEMO_WARPS * 32) k_mtt_memo(AlsDesc d) {
         if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
         return;
     }
-    const int kk = (blockIdx.x - 1) * MEMO_WARPS + warp;
-    if (kk >= Kp) return;
-    constexpr int NQ = RP / 4;             // float4 per row of Y (pr <= RP)
-    constexpr int MJ = RP <= 16 ? 4 : 2;   // rows of Y per lane in flight
+    const int kk = blockIdx.x - 1;
+    constexpr int NQ = RP / 4;  // float4 per row of Y (pr <= RP)
     const int pq = pr / 4;
     const float4 *y = reinterpret_cast<const float4 *>(d.ymem + rep * d.yrs + (long long)kk * nj * pr);
     const float *Bf = (const float *)d.U[1] + (long long)rep * nj * R;
     float a[RP];
 #pragma unroll
     for (int r = 0; r < RP; ++r) a[r] = 0.f;
-    for (int jb = lane; jb < nj; jb += 32 * MJ) {
-        float4 v[MJ][NQ];
+    for (int jb = threadIdx.x; jb < nj; jb += 2 * MEMO_THREADS) {
+        float4 v[2][NQ];
+        float b[2][RP];
 #pragma unroll
-        for (int u = 0; u < MJ; ++u) {
-            const int j = jb + 32 * u;
+        for (int u = 0; u < 2; ++u) {
+            const int j = jb + u * MEMO_THREADS;
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
                 v[u][q] = (j < nj && q < pq) ? __ldcg(y + (long long)j * pq + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < RP; ++r) b[u][r] = (j < nj && r < R) ? __ldg(Bf + (long long)j * R + r) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < MJ; ++u) {
-            const int j = jb + 32 * u;
-            if (j < nj) {
-                const float *b = Bf + (long long)j * R;
+        for (int u = 0; u < 2; ++u) {
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const float e[4] = {v[u][q].x, v[u][q].y, v[u][q].z, v[u][q].w};
+            for (int q = 0; q < NQ; ++q) {
+                const float e[4] = {v[u][q].x, v[u][q].y, v[u][q].z, v[u][q].w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (4 * q + c < R) a[4 * q + c] = fmaf(e[c], __ldg(b + 4 * q + c), a[4 * q + c]);
-                }
+                for (int c = 0; c < 4; ++c) a[4 * q + c] = fmaf(e[c], b[u][4 * q + c], a[4 * q + c]);
             }
         }
     }
-    float *out = (float *)d.part + rep * d.prs + (long long)kk * pr;
+    __shared__ float red[MEMO_THREADS / 32][RP];
 #pragma unroll
     for (int r = 0; r < RP; ++r) {
-        if (r < R) {
-            const float sr = warp_sum(a[r]);
-            if (lane == 0) out[r] = sr;
-        }
+        const float v = warp_sum(a[r]);
+        if (lane == 0) red[warp][r] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        float sum = red[0][threadIdx.x];
+        for (int w = 1; w < MEMO_THREADS / 32; ++w) sum += red[w][threadIdx.x];
+        ((float *)d.part + rep * d.prs + (long long)kk * pr)[threadIdx.x] = sum;
     }
 }
 
@@ -1409,8 +1411,8 @@ cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st) {
 
 cudaError_t launch_mtt_memo(const AlsDesc &d, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((d.n[2] + MEMO_WARPS - 1) / MEMO_WARPS + 1, d.nrep);
-    cfg.blockDim = dim3(MEMO_WARPS * 32);
+    cfg.gridDim = dim3(d.n[2] + 1, d.nrep);
+    cfg.blockDim = dim3(MEMO_THREADS);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
