@@ -237,15 +237,20 @@ sbt_status sbt_last_summary_factors(const sbt_ctx *ctx, int32_t rep, double *lam
 typedef struct {
     int64_t launches;        /* kernels launched by the library (process-wide) since the reset */
     int64_t updates;         /* sbt_update calls committed since the reset */
-    int64_t mttkrp_launches; /* MTTKRP pass launches (one per mode per ALS iteration) */
-    double mttkrp_ms;        /* their summed device time from CUDA events (timing enabled), else 0 */
-    double mttkrp_bytes;     /* algorithmic bytes they read: each summary element of every
-                                repetition still iterating, once per pass */
+    int64_t mttkrp_launches; /* MTTKRP kernel launches over the summaries (one per group of
+                                repetitions per pass) */
+    double mttkrp_ms;        /* device time of the passes from CUDA events (timing enabled), else
+                                0: per pass, from the first group's launch start to the last
+                                group's launch end (the groups' launches run concurrently) */
+    double mttkrp_bytes;     /* algorithmic bytes of the passes: each summary element of every
+                                repetition still iterating read once per pass */
+    int64_t mttkrp_passes;   /* timed passes (mttkrp_ms covers these) */
 } sbt_profile;
 
 /* Zero the counters; timing = 1 also brackets every MTTKRP launch of this
- * context with CUDA events on its stream (event nodes in the ALS graphs: a
- * few microseconds per MTTKRP launch, so leave it off for throughput). */
+ * context with CUDA events on the stream it runs on (the ALS then runs its
+ * kernels directly, polling convergence from the host, rather than as one
+ * graph: leave it off for throughput). */
 sbt_status sbt_profile_reset(sbt_ctx *ctx, int32_t timing);
 
 /* Read the counters (synchronises the context's stream). */

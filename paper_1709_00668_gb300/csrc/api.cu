@@ -214,7 +214,7 @@ struct sbt_ctx {
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
     double mtt_ms = 0.0;
-    long long launch_base = 0, updates = 0, mtt_launches = 0;
+    long long launch_base = 0, updates = 0, mtt_launches = 0, mtt_passes = 0;
     int mtt_per_iter = 3;  // MTTKRP launches per ALS iteration of the last loop (2 with the memoised mode 3)
     ~sbt_ctx() {
         for (auto &e : gev) {
@@ -537,13 +537,18 @@ static int als_group_count(const sbt_ctx *c, int nrep, bool tc) {
     return std::min(g, nrep);
 }
 
+// SMs a group's MTTKRP launch sizes its grid for: its share, so that the
+// groups' concurrent passes fit the GPU together in one wave (a group's
+// pass alone, one CTA per SM, streams at about half the HBM bandwidth)
+static int group_sms(const sbt_ctx *c, int G) { return c->num_sms / G; }
+
 // Partial counts of a tensor-core ALS of nrep repetitions in G groups, and
 // the per-repetition stride of the partials that covers every group (the
 // smallest group splits its slices most).
 static void tc_group_partials(const sbt_ctx *c, AlsDesc &d, int G) {
     AlsDesc dm = d;
     dm.nrep = d.nrep / G;
-    tc_partials(dm, c->num_sms / G, c->elem == 3);
+    tc_partials(dm, group_sms(c, G), c->elem == 3);
     d.prs = dm.prs;
     for (int m = 0; m < 3; ++m) d.P[m] = dm.P[m];
 }
@@ -603,7 +608,7 @@ static sbt_status als_plans(sbt_ctx *c, const AlsDesc &d, const TcPlan *tc, std:
         p.d = group_desc(d, rep0, ng, xb);
         p.tc = *tc;
         p.has_tc = true;
-        p.tc.sms = c->num_sms / G;
+        p.tc.sms = group_sms(c, G);
         const long long ns = (long long)ng * tc->Kp;
         CK(make_summary_tmap(&p.tc.m1, (const char *)tc->xs + rep0 * xb, tc->nJ, tc->nI, tc->ldj, ns, tc->fp8));
         CK(make_summary_tmap(&p.tc.m2, (const char *)tc->xt + rep0 * xtb, tc->nI, tc->nJ, tc->ldi, ns, tc->fp8));
@@ -783,10 +788,24 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
             e = cudaMemcpyAsync(c->h_poll.p, d.conv, sizeof(int) * d.nrep, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS (timed): ") + cudaGetErrorString(e));
-        for (int q = 0; q < nslots; ++q) {
-            if ((q / ngr) % 3 == 2 && d.ymem) continue;
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, c->gev[q].first, c->gev[q].second) == cudaSuccess) c->mtt_ms += t;
+        // a pass (one launch per group, concurrent on the groups' streams)
+        // lasts from the earliest start to the latest end, taken relative
+        // to the first start event of the batch
+        for (int q0 = 0; q0 < nslots; q0 += ngr) {
+            if ((q0 / ngr) % 3 == 2 && d.ymem) continue;
+            float t0 = 0.f, t1 = 0.f;
+            bool okp = true;
+            for (int g = 0; g < ngr; ++g) {
+                float a = 0.f, b = 0.f;
+                okp = okp && cudaEventElapsedTime(&a, c->gev[0].first, c->gev[q0 + g].first) == cudaSuccess &&
+                      cudaEventElapsedTime(&b, c->gev[0].first, c->gev[q0 + g].second) == cudaSuccess;
+                t0 = g == 0 ? a : std::min(t0, a);
+                t1 = g == 0 ? b : std::max(t1, b);
+            }
+            if (okp) {
+                c->mtt_ms += t1 - t0;
+                ++c->mtt_passes;
+            }
         }
         if (poll) {
             const int *h = c->h_poll.as<int>();
@@ -1573,6 +1592,7 @@ extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     c->launch_base = launch_count();
     c->updates = 0;
     c->mtt_launches = 0;
+    c->mtt_passes = 0;
     return SBT_OK;
 }
 
@@ -1589,6 +1609,7 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
     out->mttkrp_launches = c->mtt_launches;
     out->mttkrp_ms = ms;
     out->mttkrp_bytes = (double)bytes;
+    out->mttkrp_passes = c->mtt_passes;
     return SBT_OK;
 }
 

@@ -498,10 +498,9 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
         if (p.bytes_ctr && etid == 0 && !skipped) {
             const int rows = min(p.br, p.NP - pb * p.br);
-            // summary bytes read, plus the products kept for the memoised mode 3
-            atomicAdd(p.bytes_ctr, (unsigned long long)rows * nsl *
-                                       ((unsigned long long)p.NC * (FP8 ? 1ull : 2ull) * (1 + p.split) +
-                                        (p.Y ? 4ull * R : 0ull)));
+            // summary bytes read (the products a memoised mode-2 pass keeps
+            // are an intermediate that stays in L2, not counted)
+            atomicAdd(p.bytes_ctr, (unsigned long long)rows * p.NC * (FP8 ? 1ull : 2ull) * nsl * (1 + p.split));
         }
     }
     tc_fence_before();

@@ -91,7 +91,7 @@ class SbtStats(ctypes.Structure):
 class SbtProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
-                ("mttkrp_bytes", ctypes.c_double)]
+                ("mttkrp_bytes", ctypes.c_double), ("mttkrp_passes", ctypes.c_int64)]
 
 
 class SbtCoo(ctypes.Structure):
@@ -431,7 +431,7 @@ class SamBaTen:
         p = SbtProfile()
         _check(lib().sbt_profile_read(self._h, ctypes.byref(p)), "sbt_profile_read")
         return {"launches": p.launches, "updates": p.updates, "mttkrp_launches": p.mttkrp_launches,
-                "mttkrp_ms": p.mttkrp_ms, "mttkrp_bytes": p.mttkrp_bytes}
+                "mttkrp_ms": p.mttkrp_ms, "mttkrp_bytes": p.mttkrp_bytes, "mttkrp_passes": p.mttkrp_passes}
 
     def last_samples(self, rep: int, mode: int) -> np.ndarray:
         n = ctypes.c_int64()
