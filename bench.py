@@ -66,6 +66,10 @@ def parse():
                     help="tune the tensor-core MTTKRP tiles in an untimed pass over the same batches first")
     ap.add_argument("--mode3-pass", action="store_true",
                     help="mode 3 reads the summary in its own MTTKRP pass (default: formed from the mode-2 pass)")
+    ap.add_argument("--max-iters", type=int, default=0,
+                    help="ALS iteration cap of every update (0: the workload's 50)")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="start every summary ALS from the old factors at the sampled rows (default: random start)")
     ap.add_argument("--als-groups", type=int, default=0,
                     help="groups the repetitions' ALS runs in (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,9 +94,12 @@ def parse():
     args = ap.parse_args()
     if args.small:
         WORKLOAD["K0"] = 200
-    global MODE3_PASS, ALS_GROUPS
+    if args.max_iters > 0:
+        WORKLOAD["max_iters"] = args.max_iters
+    global MODE3_PASS, ALS_GROUPS, WARM_START
     MODE3_PASS = int(args.mode3_pass)
     ALS_GROUPS = args.als_groups
+    WARM_START = int(args.warm_start)
     return args
 
 
@@ -209,6 +216,7 @@ def make_data(steps: int, warmup: int, device):
 
 MODE3_PASS = 0
 ALS_GROUPS = 0
+WARM_START = 0
 
 
 def opts_for(prec: str, stream, nb: int):
@@ -216,7 +224,8 @@ def opts_for(prec: str, stream, nb: int):
     w = WORKLOAD
     return dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
                 max_iters_init=50, seed=w["seed"], prec=prec, cuda_stream=stream,
-                K_capacity=w["K0"] + nb * w["batch"], mode3_pass=MODE3_PASS, als_groups=ALS_GROUPS)
+                K_capacity=w["K0"] + nb * w["batch"], mode3_pass=MODE3_PASS, als_groups=ALS_GROUPS,
+                warm_start=WARM_START)
 
 
 def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
@@ -259,7 +268,7 @@ def cpu_baseline(p, nb_used: int, reps_sample: int = 2) -> dict:
     A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
     na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
     opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=reps_sample, tol=w["tol"], max_iters=w["max_iters"],
-                     seed=w["seed"], prec="bf16")
+                     seed=w["seed"], prec="bf16", warm_start=bool(WARM_START))
     st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
     t0 = time.perf_counter()
     _, traces = O.update(st, X[K0:K0 + b])
@@ -293,7 +302,7 @@ def run_reference(args):
     A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
     na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
     opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=1, tol=w["tol"], max_iters=w["max_iters"],
-                     seed=w["seed"], prec=args.prec)
+                     seed=w["seed"], prec=args.prec, warm_start=bool(WARM_START))
     st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
     # each step: one batch update of the oracle with one of the 8 repetitions
     # (a bounded sample); the batch time is the shared part + 8 x repetition
@@ -462,6 +471,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec, "autotuned_tiles": bool(args.autotune),
                        "mode3_pass": bool(MODE3_PASS), "als_groups": ALS_GROUPS or "default",
+                       "warm_start": bool(WARM_START),
                        "l2": "inputs larger than L2 (200 MB batch per step, 4 GB resident store)",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},

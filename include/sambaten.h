@@ -113,6 +113,11 @@ typedef struct {
                               own stream, so that one group's MTTKRP pass overlaps another
                               group's latency-bound tail; 0: 2 (1 when r = 1).  Results depend
                               on it only through the order of partial sums */
+    int32_t warm_start;    /* 0 (default): the summary ALS starts from Philox uniforms keyed by the
+                              global index (the paper leaves the start open).  1: it starts from
+                              the old factors at the sampled rows, A(I_s), B(J_s), C(K_s), with
+                              the new slices' rows of C' zero; it then converges in a few
+                              iterations and keeps the component order */
 } sbt_options;
 
 typedef struct {

@@ -81,6 +81,7 @@ class Options:
     fixed_iters: bool = False
     prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16 | fp8
     refine_sweeps: int = 0     # bf16 only: ALS iterations on the split summary after the bf16 ALS
+    warm_start: bool = False   # start the summary ALS from the old factors at the sampled rows
 
 
 @dataclass
@@ -517,10 +518,16 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
             Xs = fp8_summary_values(summary(X_all, Is, Js, Kp), slice_amax(X_all)[Kp])
         else:
             Xs = summary_values(summary(X_all, Is, Js, Kp), opts.prec)
-        # step 5: CP of the summary
-        U0 = [init_factor(Is, R, 0, rho, state.batch, opts),
-              init_factor(Js, R, 1, rho, state.batch, opts),
-              init_factor(Kp, R, 2, rho, state.batch, opts)]
+        # step 5: CP of the summary, from random factors (the paper leaves
+        # the start open), or warm: the old factors at the sampled rows, the
+        # new slices' rows of C' zero (their first mode-3 update fills them)
+        if opts.warm_start:
+            U0 = [state.A[Is].copy(), state.B[Js].copy(),
+                  np.concatenate([state.C[Ks], np.zeros((K_new, R))], axis=0)]
+        else:
+            U0 = [init_factor(Is, R, 0, rho, state.batch, opts),
+                  init_factor(Js, R, 1, rho, state.batch, opts),
+                  init_factor(Kp, R, 2, rho, state.batch, opts)]
         res = cp_als(Xs, U0, opts.tol, opts.max_iters, opts.fixed_iters)
         if opts.prec == "bf16" and opts.refine_sweeps > 0:
             # refinement: continue the same ALS from its factors for a fixed

@@ -279,6 +279,7 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (o->refine_sweeps < 0 || o->refine_sweeps > 1000) return fail(SBT_E_INVALID, "refine_sweeps out of [0, 1000]");
     if (o->mode3_pass != 0 && o->mode3_pass != 1) return fail(SBT_E_INVALID, "mode3_pass must be 0 or 1");
     if (o->als_groups < 0 || o->als_groups > SBT_MAX_REPS) return fail(SBT_E_INVALID, "als_groups out of [0, SBT_MAX_REPS]");
+    if (o->warm_start != 0 && o->warm_start != 1) return fail(SBT_E_INVALID, "warm_start must be 0 or 1");
     return SBT_OK;
 }
 
@@ -1037,6 +1038,18 @@ static sbt_status update_shape(const sbt_ctx *c, int64_t K_old, int K_new, bool 
     return SBT_OK;
 }
 
+// start of the summary ALS: the old factors at the sampled rows (option
+// warm_start), else Philox uniforms
+static WarmStart warm_start_of(const sbt_ctx *c) {
+    WarmStart w;
+    if (c->opt.warm_start) {
+        w.F[0] = c->A.as<double>();
+        w.F[1] = c->B.as<double>();
+        w.F[2] = c->C.as<double>();
+    }
+    return w;
+}
+
 // mode 3 formed from the mode-2 pass's products (tensor-core path) unless
 // the option asks for its own pass
 static bool memo_mode3(const sbt_ctx *c, int) { return !c->opt.mode3_pass; }
@@ -1416,7 +1429,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         }
     }
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
-                          c->batch, c->rowsq.as<double>(), c->stream));
+                          c->batch, c->rowsq.as<double>(), c->stream, warm_start_of(c)));
     if (tc.on && c->opt.autotune) {  // tile choices for the groups' launch shapes not seen before
         std::vector<AlsPlan> plans;
         TRY(als_plans(c, d, &tc, plans));
@@ -2037,7 +2050,7 @@ extern "C" sbt_status sbt_update_coo(sbt_ctx *c, const sbt_coo *X) {
     coo_partials(d);
     d.rq_rows = Kp;
     CK(launch_als_prepare(d, c->samples.as<int>(), samp_stride, (int)K_old, false, c->opt.seed, c->opt.stream_id,
-                          c->batch, c->rowsq.as<double>(), c->stream));
+                          c->batch, c->rowsq.as<double>(), c->stream, warm_start_of(c)));
     TRY(run_als(c, d, c->opt.max_iters));
     // 5-6. normalise, match, project back, commit
     const size_t pmax = (size_t)samp_stride;

@@ -1047,7 +1047,7 @@ template <typename TF>
 __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, long long samp_stride,
                                                  int K_old, int identity, uint64_t seed,
                                                  uint32_t stream_id, uint32_t batch,
-                                                 const double *rowsq) {
+                                                 const double *rowsq, WarmStart ws) {
     const int rep = blockIdx.x;
     const int R = d.R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1062,7 +1062,10 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
             if (identity) gx = (uint32_t)x;
             else if (m < 2) gx = (uint32_t)S[x];
             else gx = (uint32_t)(x < d.nK ? S[x] : K_old + (x - d.nK));
-            U[e] = (TF)init_value(key, gx, r, m, rep, batch);
+            if (ws.F[0])  // warm: the old factor at the sampled row; new slices' rows zero
+                U[e] = (m < 2 || x < d.nK) ? (TF)ws.F[m][(long long)gx * R + r] : (TF)0;
+            else
+                U[e] = (TF)init_value(key, gx, r, m, rep, batch);
         }
     }
     __syncthreads();
@@ -1442,13 +1445,13 @@ cudaError_t launch_als_iteration(const AlsDesc &d, cudaStream_t st) {
 
 cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long samp_stride, int K_old,
                                bool identity, uint64_t seed, uint32_t stream_id, uint32_t batch,
-                               const double *rowsq, cudaStream_t st) {
+                               const double *rowsq, cudaStream_t st, const WarmStart &ws) {
     if (d.elem == 0)
         k_prepare<double><<<d.nrep, 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
-                                                  stream_id, batch, rowsq);
+                                                  stream_id, batch, rowsq, ws);
     else
         k_prepare<float><<<d.nrep, 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
-                                                 stream_id, batch, rowsq);
+                                                 stream_id, batch, rowsq, ws);
     count_launches(1);
     return cudaGetLastError();
 }

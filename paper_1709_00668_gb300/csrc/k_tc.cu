@@ -2,9 +2,10 @@
 //
 // Per slice kk of a summary, Z = X_kk . F is a dense product: 128 rows of
 // X_kk (an M = 128 tile, rows beyond the summary zero-filled by TMA) times the
-// contraction factor F (K = the other summary dimension, N = 2 * RH columns:
-// F rounded to bfloat16 and the bfloat16 rounding error of F, so that
-// bf16 x (hi + lo) keeps ~16 bits of the float32 factor).  The accumulators
+// contraction factor F (K = the other summary dimension, N = NT * RH
+// columns: F as NT bfloat16 terms, each the rounding of what the previous
+// ones left, so that bf16 x (sum of the terms) keeps ~24 bits (three terms)
+// or ~16 bits (two) of the float32 factor).  The accumulators
 // live in tensor memory; four epilogue warps read them back and fold the
 // ALS weights in:
 //   ROWSUM (modes 1 and 2): M(p, r) += Z(p, r) C(kk, r), summed over the
@@ -197,13 +198,16 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
 }
 
 // N columns: NT terms of RH columns each.  bfloat16 summaries: the factor
-// as bf16 hi and lo (NT = 2); float8 summaries: the factor as three e4m3
-// terms at fixed scales, F = 2^-8 (e1 + 2^-4 e2 + 2^-8 e3) (NT = 3; factor
-// entries are at most 1 in magnitude: unit columns or uniforms in [0, 1)).
+// as bf16 terms, hi + mid + lo (NT = 3, the float32 factor to ~24 bits) up
+// to R = 16 and hi + lo (NT = 2, ~16 bits) above, where a third term would
+// not leave room for two CTAs per SM; float8 summaries: the factor as three
+// e4m3 terms at fixed scales, F = 2^-8 (e1 + 2^-4 e2 + 2^-8 e3) (NT = 3;
+// factor entries are at most 1 in magnitude: unit columns or uniforms in
+// [0, 1)).
 template <int N, bool FP8>
 __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUtensorMap tmap,
                                                    const __grid_constant__ CUtensorMap tmap_lo, TcParams p) {
-    constexpr int NT = FP8 ? 3 : 2;
+    constexpr int NT = (FP8 || N == 48) ? 3 : 2;
     constexpr int RH = N / NT;
     constexpr int TS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);  // tensor-memory columns per accumulator
     constexpr int KE = FP8 ? 128 : 64;                        // contraction elements per 128-byte row
@@ -294,12 +298,20 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                 for (int r = 0; r < RH; ++r) {
                     const float f = fv[u][r];
                     if constexpr (!FP8) {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-                        const int nh = r, nl = RH + r;
+                        // successive bf16 roundings of the remainder (exact differences)
+                        __nv_bfloat16 t[NT];
+                        float rem = f;
+#pragma unroll
+                        for (int q = 0; q < NT; ++q) {
+                            t[q] = __float2bfloat16_rn(rem);
+                            rem -= __bfloat162float(t[q]);
+                        }
                         unsigned char *col = blk + (k & 7) * 2;
-                        *reinterpret_cast<__nv_bfloat16 *>(col + nh * 128 + (((k >> 3) ^ (nh & 7)) << 4)) = hi;
-                        *reinterpret_cast<__nv_bfloat16 *>(col + nl * 128 + (((k >> 3) ^ (nl & 7)) << 4)) = lo;
+#pragma unroll
+                        for (int q = 0; q < NT; ++q) {
+                            const int n = q * RH + r;
+                            *reinterpret_cast<__nv_bfloat16 *>(col + n * 128 + (((k >> 3) ^ (n & 7)) << 4)) = t[q];
+                        }
                     } else {
                         const unsigned char e1 = to_e4m3(f * 256.f);
                         const float r1 = f - from_e4m3(e1) * 0.00390625f;
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
                         const int col = c + i;
                         if (col < N) {
                             const int q = col / RH;
-                            // bf16: hi + lo; e4m3: 2^-8 (t1 + 2^-4 t2 + 2^-8 t3)
+                            // bf16: sum of the terms; e4m3: 2^-8 (t1 + 2^-4 t2 + 2^-8 t3)
                             const float tw = FP8 ? (q == 0 ? 0.00390625f : (q == 1 ? 0.000244140625f : 1.52587890625e-05f))
                                                  : 1.f;
                             z[col - q * RH] = FP8 ? fmaf(v[i], tw, z[col - q * RH]) : z[col - q * RH] + v[i];
@@ -575,9 +587,10 @@ cudaError_t make_summary_tmap(CUtensorMap *m, const void *base, int NC, int NP, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// B operand columns: two bf16 terms or three e4m3 terms of RH = 16 or 32 columns
+// B operand columns: terms of RH = 16 or 32 columns; three (e4m3, or bf16 up
+// to R = 16) or two (bf16 above R = 16)
 static int tc_rh_of(int R) { return R <= 16 ? 16 : 32; }
-static int tc_n_of(int R, bool fp8) { return (fp8 ? 3 : 2) * tc_rh_of(R); }
+static int tc_n_of(int R, bool fp8) { return (fp8 || R <= 16 ? 3 : 2) * tc_rh_of(R); }
 static int tc_nkb_of(int NC, bool fp8) { return (NC + (fp8 ? 127 : 63)) / (fp8 ? 128 : 64); }
 
 static size_t tc_fixed_smem(int nkb, int N, int RH) {
@@ -723,17 +736,17 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launches(1);
-    if (N == 32) return cudaLaunchKernelEx(&cfg, k_mtt_tc<32, false>, tmap, lo, p);
-    if (N == 64) return cudaLaunchKernelEx(&cfg, k_mtt_tc<64, false>, tmap, lo, p);
-    if (N == 48) return cudaLaunchKernelEx(&cfg, k_mtt_tc<48, true>, tmap, lo, p);
-    return cudaLaunchKernelEx(&cfg, k_mtt_tc<96, true>, tmap, lo, p);
+    if (!fp8) return N == 48 ? cudaLaunchKernelEx(&cfg, k_mtt_tc<48, false>, tmap, lo, p)
+                             : cudaLaunchKernelEx(&cfg, k_mtt_tc<64, false>, tmap, lo, p);
+    return N == 48 ? cudaLaunchKernelEx(&cfg, k_mtt_tc<48, true>, tmap, lo, p)
+                   : cudaLaunchKernelEx(&cfg, k_mtt_tc<96, true>, tmap, lo, p);
 }
 
 // Raise the dynamic shared-memory limit of the tensor-core kernels once,
 // outside any stream capture.
 cudaError_t set_tc_kernel_attributes() {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<32, false>, a, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<48, false>, a, 200 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<64, false>, a, 200 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<48, true>, a, 200 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<96, true>, a, 200 * 1024);

@@ -341,6 +341,13 @@ struct AlsDesc {
     int nrs, cols;         // column kernel: row splits, columns per lane
 };
 
+// Start of a summary ALS: F[0] null -> Philox uniforms; else the old factors
+// A, B, C (float64, row-major, R columns) at the sampled rows, the new
+// slices' rows of C' zero
+struct WarmStart {
+    const double *F[3] = {nullptr, nullptr, nullptr};
+};
+
 // ---------------------------------------------------------------------------
 // Launchers (all asynchronous on `st`)
 cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint32_t *out, long long n, cudaStream_t st);
@@ -365,7 +372,8 @@ cudaError_t launch_rowsq(const void *X, int sdtype, long long rows, int J, int l
 // ALS: start values, Grams, ||X_s||^2; then the iterations.
 cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long samp_stride, int K_old,
                                bool identity, uint64_t seed, uint32_t stream_id, uint32_t batch,
-                               const double *rowsq, cudaStream_t st);
+                               const double *rowsq, cudaStream_t st,
+                               const WarmStart &ws = WarmStart{});
 cudaError_t launch_als_iteration(const AlsDesc &d, cudaStream_t st);
 cudaError_t launch_als_mode(const AlsDesc &d, int mode, cudaStream_t st);
 // the two halves of launch_als_mode: the MTTKRP pass, then reduction + tail

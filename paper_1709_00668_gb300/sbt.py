@@ -75,7 +75,8 @@ class SbtOptions(ctypes.Structure):
                 ("K_capacity", ctypes.c_int64), ("max_batch", ctypes.c_int64),
                 ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32),
                 ("refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("mode3_pass", ctypes.c_int32), ("als_groups", ctypes.c_int32)]
+                ("mode3_pass", ctypes.c_int32), ("als_groups", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32)]
 
 
 class SbtStats(ctypes.Structure):

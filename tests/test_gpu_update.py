@@ -30,7 +30,7 @@ def _pair(sbt, X, K0, R, fac, *, prec="f32", **kw):
     oo = O.Options(s_I=opts["s_I"], s_J=opts["s_J"], s_K=opts["s_K"], r=opts["r"], tol=opts["tol"],
                    max_iters=opts["max_iters"], seed=opts["seed"], fixed_iters=bool(opts.get("fixed_iters", 0)),
                    lambda_mode=opts.get("lambda_mode", 0), stream_id=opts.get("stream_id", 0), prec=prec,
-                   refine_sweeps=opts.get("refine_sweeps", 0))
+                   refine_sweeps=opts.get("refine_sweeps", 0), warm_start=bool(opts.get("warm_start", 0)))
     ost = O.init_state_from_factors(X[:K0], *fac, oo)
     return ctx, ost
 
@@ -129,6 +129,36 @@ def test_update_fp8_summary_bits_and_factors(sbt, shape):
     _check_update(ctx, ost2, traces, ftol=2e-3)
     p = ctx.profile()
     assert p["updates"] == 1
+
+
+@pytest.mark.parametrize("prec,ftol,fixed", [("f64", 1e-8, 0), ("f32", 1e-4, 1), ("bf16", 1e-3, 1),
+                                             ("bf16", 2e-3, 0)])
+def test_update_warm_start_matches_oracle(sbt, prec, ftol, fixed):
+    """Warm-started summary ALS (the old factors at the sampled rows, the new
+    rows of C' zero) against the oracle doing the same: samples bit-exact, the
+    identity match, factors within the bar of the arithmetic; float64 and one
+    bf16 case with the tolerance stop (a few iterations; float64 the oracle's
+    count), the float32 and bf16 trajectories over 6 fixed iterations."""
+    dt = torch.float64 if prec == "f64" else torch.float32
+    X, A, B, C = planted(120, 96, 70, 6, dtype=dt, seed=31, noise=0.01)
+    fac = unit_factors(A, B, C[:60])
+    ctx, ost = _pair(sbt, X, 60, 6, fac, prec=prec, s_I=3, s_J=3, s_K=3, r=4, tol=1e-6,
+                     max_iters=6 if fixed else 50, fixed_iters=fixed, warm_start=1)
+    ost2, traces = O.update(ost, X[60:70], keep_summaries=True)
+    ctx.update(torch.from_numpy(X[60:70]).cuda())
+    _check_update(ctx, ost2, traces, ftol=ftol)
+    st = ctx.stats()
+    for rep, t in enumerate(traces):
+        assert list(t.match.perm) == list(range(6))
+        if not fixed:
+            assert t.als.iters <= 10
+            if prec == "f64":
+                assert st["iters"][rep] == t.als.iters
+    if not fixed and prec == "bf16":
+        # float32 accumulation puts a small floor under the fit change, so the
+        # stop may come an iteration or two after the oracle's
+        its = st["iters"][:4]
+        assert max(its) <= 8, (its, [t.als.iters for t in traces])
 
 
 def test_update_bf16_refinement_matches_oracle(sbt):

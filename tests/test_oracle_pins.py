@@ -441,6 +441,34 @@ def test_update_noiseless_projects_back_exactly():
         assert len(t.Is) == 12 and len(t.Js) == 11 and len(t.Ks) == 10
 
 
+def test_warm_start_projects_back_exactly_in_few_iterations():
+    """Warm start (the old factors at the sampled rows, new rows of C' zero):
+    in the noiseless case the same project-back relation holds, the matching
+    is the identity (the start keeps the component order), and the summary ALS
+    stops after far fewer iterations than from the random start."""
+    R = 3
+    base = dict(s_I=2, s_J=2, s_K=2, r=3, tol=1e-12, max_iters=3000, seed=0)
+    st, X, (A, B, Cn, lam) = _planted_state(24, 22, 20, R, O.Options(**base, warm_start=True), Ktot=30)
+    st2, traces = O.update(st, X[20:30])
+    np.testing.assert_allclose(st2.C[20:30], Cn[20:30], rtol=1e-5, atol=1e-7)
+    assert O.full_fit(st2.X, st2.lam, st2.A, st2.B, st2.C) > 1 - 1e-6
+    st_r, X_r, _ = _planted_state(24, 22, 20, R, O.Options(**base), Ktot=30)
+    _, traces_r = O.update(st_r, X_r[20:30])
+    for t, tr in zip(traces, traces_r):
+        assert list(t.match.perm) == list(range(R))
+        assert t.als.iters <= 10 and t.als.iters * 5 < tr.als.iters
+
+
+def test_warm_start_first_mode1_update_ignores_new_slices():
+    """With the new rows of C' zero, the first mode-1 MTTKRP is that of the old
+    slices alone: the start's new rows carry no weight (checked against the
+    MTTKRP of the summary with the new slices cut off)."""
+    rng = np.random.default_rng(5)
+    X = rng.random((7, 5, 6))
+    U = [rng.random((5, 3)), rng.random((6, 3)), np.concatenate([rng.random((4, 3)), np.zeros((3, 3))])]
+    np.testing.assert_allclose(O.mttkrp(X, U, 0), O.mttkrp(X[:4], [U[0], U[1], U[2][:4]], 0), rtol=1e-14)
+
+
 def test_update_stream_keeps_fit_noiseless():
     R = 2
     opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-15, max_iters=3000, seed=4)
