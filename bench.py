@@ -66,6 +66,8 @@ def parse():
                     help="tune the tensor-core MTTKRP tiles in an untimed pass over the same batches first")
     ap.add_argument("--mode3-pass", action="store_true",
                     help="mode 3 reads the summary in its own MTTKRP pass (default: formed from the mode-2 pass)")
+    ap.add_argument("--no-recompute", action="store_true",
+                    help="skip the recomputed CP-ALS of the final tensor (Relative Fitness)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="ALS iteration cap of every update (0: the workload's 50)")
     ap.add_argument("--warm-start", action="store_true",
@@ -383,6 +385,9 @@ def run_ours(args):
     head_launches = ctx.profile()["launches"]
     stats = ctx.stats()
     fit_gpu = ctx.fit()
+    # Relative Fitness against CP-ALS recomputed on the whole final tensor
+    # (after the timed region)
+    fit_cp = None if args.no_recompute else ctx.recompute(max_iters=w["max_iters"], tol=w["tol"], seed=w["seed"])[0]
     ctx.close()
 
     # profiling pass: the same batches on a fresh context, with CUDA events
@@ -476,6 +481,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},
             "fit": {"full_tensor_fit_after_steps": fit_gpu,
+                    "recomputed_cp_als_fit": fit_cp,
+                    "relative_fitness": (1.0 - fit_gpu) / (1.0 - fit_cp) if fit_cp is not None and fit_cp < 1.0
+                    else None,
                     "planted_noise_floor": 1.0 - w["noise"],
                     "summary_fit_last_batch": stats["fit"], "als_iters_last_batch": stats["iters"]},
             "plain_f32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,

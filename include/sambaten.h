@@ -168,6 +168,19 @@ sbt_status sbt_factors(const sbt_ctx *ctx, double *lambda, double *A, double *B,
  * 1 - ||X - X_hat||_F / ||X||_F (Section 5.2, relative error = 1 - fit). */
 sbt_status sbt_fit(sbt_ctx *ctx, double *fit);
 
+/* The recompute comparator of Section 5.2 (Relative Fitness): CP-ALS of the
+ * whole resident tensor from scratch, as sbt_init runs it (the store's
+ * precision, Philox start with `seed` and the context's stream id, at most
+ * max_iters iterations, stop when the fit changes by less than tol), without
+ * touching the context's factors.  Outputs are caller-owned host buffers,
+ * each nullable: lambda (R), A (I x R), B (J x R), C (K x R), row-major; *fit
+ * = 1 - ||X - X_cp|| / ||X|| of the recomputed model.  Relative Fitness =
+ * ||X - X_sbt|| / ||X - X_cp|| = (1 - sbt_fit) / (1 - *fit).  Dense
+ * contexts only (SBT_E_STATE for COO).  Synchronises the context's stream;
+ * may grow the context's ALS workspace. */
+sbt_status sbt_recompute(sbt_ctx *ctx, int32_t max_iters, double tol, uint64_t seed, double *lambda, double *A,
+                         double *B, double *C, double *fit);
+
 /* Statistics of the last sbt_update. */
 sbt_status sbt_stats(const sbt_ctx *ctx, sbt_update_stats *st);
 

@@ -604,6 +604,15 @@ def full_fit(X: np.ndarray, lam, A, B, C) -> float:
 # --------------------------------------------------------------------------
 # Test utilities: core consistency (Bro & Kiers 2003) and FMS (Section 5.4)
 # --------------------------------------------------------------------------
+def relative_fitness(X: np.ndarray, model, baseline) -> float:
+    """Relative Fitness (Section 5.2): ||X - X_model|| / ||X - X_baseline||,
+    each model a tuple (lam, A, B, C); the baseline is the decomposition
+    recomputed on the whole tensor."""
+    ra = np.linalg.norm((X - reconstruct(*model)).ravel())
+    rb = np.linalg.norm((X - reconstruct(*baseline)).ravel())
+    return float(ra / rb) if rb > 0 else float("inf")
+
+
 def core_consistency(X: np.ndarray, lam, A, B, C) -> float:
     """100 (1 - ||G - T||^2 / R): G the least-squares Tucker core for the fixed
     CP factors (lambda absorbed into C), T the superdiagonal of ones."""

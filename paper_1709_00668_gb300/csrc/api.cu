@@ -1492,6 +1492,49 @@ extern "C" sbt_status sbt_fit(sbt_ctx *c, double *fit) {
     return SBT_OK;
 }
 
+extern "C" sbt_status sbt_recompute(sbt_ctx *c, int32_t max_iters, double tol, uint64_t seed, double *lambda,
+                                    double *A, double *B, double *C, double *fit) {
+    if (!c) return fail(SBT_E_INVALID, "null context");
+    if (c->coo) return fail(SBT_E_STATE, "sbt_recompute takes dense contexts");
+    if (max_iters < 1 || !(tol >= 0.0)) return fail(SBT_E_INVALID, "max_iters >= 1 and tol >= 0 required");
+    DeviceGuard dg(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
+    const int R = c->R, K = (int)c->K;
+    // the same CP-ALS as sbt_init, on the whole store
+    AlsDesc d;
+    const int n[3] = {c->I, c->J, K};
+    const int elem = c->sdtype == SBT_F64 ? 0 : 1;
+    TRY(setup_als(c, d, 1, n, c->lds, K, elem, c->store.p, 0, max_iters));
+    d.tol = tol;
+    TRY(c->rowsq.ensure((size_t)K * c->I * 8));
+    Buf tA, tB, tC, tl, scr;
+    TRY(tA.ensure((size_t)c->I * R * 8));
+    TRY(tB.ensure((size_t)c->J * R * 8));
+    TRY(tC.ensure((size_t)K * R * 8));
+    TRY(tl.ensure((size_t)R * 8));
+    CK(launch_rowsq(c->store.p, c->sdtype, (long long)K * c->I, c->J, c->lds, c->rowsq.as<double>(), c->stream));
+    CK(launch_als_prepare(d, nullptr, 0, K, true, seed, c->opt.stream_id, 0xFFFFFFFFu, c->rowsq.as<double>(),
+                          c->stream));
+    TRY(run_als(c, d, max_iters));
+    CK(launch_canonicalize(d, tA.as<double>(), tB.as<double>(), tC.as<double>(), tl.as<double>(), c->stream));
+    const long long need = fit_scratch_doubles(K, c->I, c->J, R) + 2;
+    TRY(scr.ensure((size_t)need * 8));
+    double *sp = scr.as<double>();
+    CK(launch_full_fit(c->store.p, c->sdtype, K, c->I, c->J, c->lds, tA.as<double>(), tB.as<double>(),
+                       tC.as<double>(), tl.as<double>(), R, sp + need - 2, sp, c->stream));
+    double h[2];
+    CK(cudaMemcpyAsync(h, sp + need - 2, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
+    if (lambda) CK(cudaMemcpy(lambda, tl.p, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    if (A) CK(cudaMemcpy(A, tA.p, (size_t)c->I * R * 8, cudaMemcpyDeviceToHost));
+    if (B) CK(cudaMemcpy(B, tB.p, (size_t)c->J * R * 8, cudaMemcpyDeviceToHost));
+    if (C) CK(cudaMemcpy(C, tC.p, (size_t)K * R * 8, cudaMemcpyDeviceToHost));
+    if (fit) *fit = h[1] > 0.0 ? 1.0 - std::sqrt(h[0]) / std::sqrt(h[1]) : 0.0;
+    return SBT_OK;
+}
+
 extern "C" sbt_status sbt_stats(const sbt_ctx *c, sbt_update_stats *st) {
     if (!c || !st) return fail(SBT_E_INVALID, "null argument");
     if (!c->have_last) return fail(SBT_E_STATE, "no update has run");

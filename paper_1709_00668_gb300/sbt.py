@@ -48,7 +48,7 @@ SBT_FLAG_NO_REFINE = 8
 
 EXPORTS = [
     "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
-    "sbt_update", "sbt_factors", "sbt_fit", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
+    "sbt_update", "sbt_factors", "sbt_fit", "sbt_recompute", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
     "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
     "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve", "sbt_tile_table",
@@ -156,6 +156,7 @@ def lib() -> ctypes.CDLL:
     L.sbt_update.argtypes = [P, ctypes.POINTER(SbtTensor)]
     L.sbt_factors.argtypes = [P, P, P, P, P, ctypes.POINTER(I64)]
     L.sbt_fit.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    L.sbt_recompute.argtypes = [P, I32, ctypes.c_double, ctypes.c_uint64, P, P, P, P, ctypes.POINTER(ctypes.c_double)]
     L.sbt_stats.argtypes = [P, ctypes.POINTER(SbtStats)]
     L.sbt_last_samples.argtypes = [P, I32, I32, P, I64, ctypes.POINTER(I64)]
     L.sbt_last_summary.argtypes = [P, I32, P, I64, P]
@@ -415,6 +416,24 @@ class SamBaTen:
         f = ctypes.c_double()
         _check(lib().sbt_fit(self._h, ctypes.byref(f)), "sbt_fit")
         return float(f.value)
+
+    def recompute(self, max_iters: int = 50, tol: float = 1e-6, seed: int = 0):
+        """CP-ALS of the whole resident tensor from scratch (the comparator of
+        Relative Fitness): (fit, lambda, A, B, C); the context is unchanged."""
+        lam = np.empty(self.R)
+        A = np.empty((self.I, self.R))
+        B = np.empty((self.J, self.R))
+        C = np.empty((self.K, self.R))
+        f = ctypes.c_double()
+        _check(lib().sbt_recompute(self._h, max_iters, tol, seed, lam.ctypes.data, A.ctypes.data, B.ctypes.data,
+                                   C.ctypes.data, ctypes.byref(f)), "sbt_recompute")
+        return float(f.value), lam, A, B, C
+
+    def relative_fitness(self, max_iters: int = 50, tol: float = 1e-6, seed: int = 0) -> float:
+        """Relative Fitness (Section 5.2): ||X - X_sbt|| / ||X - X_cp|| with X_cp
+        the recomputed CP-ALS of the whole tensor; 1 = as good as recomputing."""
+        f_cp = self.recompute(max_iters, tol, seed)[0]
+        return (1.0 - self.fit()) / (1.0 - f_cp) if f_cp < 1.0 else float("inf")
 
     def stats(self) -> dict:
         st = SbtStats()

@@ -317,6 +317,31 @@ def test_init_als_matches_oracle(sbt):
     assert rel_err(A, st.A) < 1e-8 and rel_err(B, st.B) < 1e-8 and rel_err(C, st.C) < 1e-8
 
 
+def test_recompute_is_the_init_als_of_the_whole_tensor(sbt):
+    """The Relative Fitness comparator: after two updates, sbt_recompute is
+    the oracle's CP-ALS of the whole tensor from the same Philox start
+    (float64, fixed iterations), leaves the context's model unchanged, and
+    Relative Fitness = (1 - fit) / (1 - recomputed fit) agrees with the
+    oracle's definition on the oracle's models."""
+    X, A, B, C = planted(50, 40, 46, 4, dtype=torch.float64, seed=17)
+    fac = unit_factors(A, B, C[:30])
+    ctx, ost = _pair(sbt, X, 30, 4, fac, prec="f64", fixed_iters=1, max_iters=20)
+    for k0 in (30, 38):
+        ost, _ = O.update(ost, X[k0:k0 + 8])
+        ctx.update(torch.from_numpy(X[k0:k0 + 8]).cuda())
+    before = ctx.factors()
+    f_cp, lam, A2, B2, C2 = ctx.recompute(max_iters=25, tol=1e-6, seed=3)
+    st_cp, _ = O.init_decomposition(X, 4, O.Options(max_iters_init=25, fixed_iters=True, seed=3))
+    assert rel_err(lam, st_cp.lam) < 1e-8 and rel_err(A2, st_cp.A) < 1e-8
+    assert rel_err(B2, st_cp.B) < 1e-8 and rel_err(C2, st_cp.C) < 1e-8
+    assert abs(f_cp - O.full_fit(X, st_cp.lam, st_cp.A, st_cp.B, st_cp.C)) < 1e-10
+    for a, b in zip(before, ctx.factors()):
+        assert np.array_equal(a, b)
+    rf = ctx.relative_fitness(max_iters=25, seed=3)
+    rf_o = O.relative_fitness(X, (ost.lam, ost.A, ost.B, ost.C), (st_cp.lam, st_cp.A, st_cp.B, st_cp.C))
+    assert abs(rf - rf_o) < 1e-6 * rf_o
+
+
 def test_init_als_f32_fit(sbt):
     X, *_ = planted(80, 70, 60, 5, dtype=torch.float32, seed=12)
     ctx = sbt.SamBaTen(torch.from_numpy(X).cuda(), 5, max_iters_init=40, fixed_iters=1, seed=1)

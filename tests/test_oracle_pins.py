@@ -469,6 +469,25 @@ def test_warm_start_first_mode1_update_ignores_new_slices():
     np.testing.assert_allclose(O.mttkrp(X, U, 0), O.mttkrp(X[:4], [U[0], U[1], U[2][:4]], 0), rtol=1e-14)
 
 
+def test_relative_fitness_definition():
+    """Relative Fitness: 1 for the baseline itself; the ratio of the (1 - fit)
+    values; and 2 for a model whose residual is exactly twice the baseline's
+    (data = baseline + a rank-one D, model = baseline - D as a rank R+1 CP)."""
+    rng = np.random.default_rng(9)
+    A, B, C = rng.random((6, 2)), rng.random((5, 2)), rng.random((4, 2))
+    lam = np.array([2.0, 1.0])
+    base = (lam, A, B, C)
+    a, b, c = rng.random((6, 1)), rng.random((5, 1)), rng.random((4, 1))
+    eps = 0.01
+    X = O.reconstruct(*base) + O.reconstruct(np.array([eps]), a, b, c)
+    assert O.relative_fitness(X, base, base) == 1.0
+    other = (lam * 1.01, A, B, C)
+    ratio = (1 - O.full_fit(X, *other)) / (1 - O.full_fit(X, *base))
+    assert abs(O.relative_fitness(X, other, base) - ratio) < 1e-12
+    twice = (np.concatenate([lam, [-eps]]), np.hstack([A, a]), np.hstack([B, b]), np.hstack([C, c]))
+    assert abs(O.relative_fitness(X, twice, base) - 2.0) < 1e-12
+
+
 def test_update_stream_keeps_fit_noiseless():
     R = 2
     opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-15, max_iters=3000, seed=4)
