@@ -1,6 +1,8 @@
 // C ABI of libsambaten: context management and the per-batch pipeline of
 // Algorithm 1 (sample -> gather -> CP-ALS -> normalise/match -> project back ->
-// commit), all on one CUDA stream, one host synchronisation per update.
+// commit) on the context's stream (the ALS forks side streams for V^-1 and
+// for groups of repetitions, and joins them), one host synchronisation per
+// update.
 #include "sambaten.h"
 #include "sbt_internal.cuh"
 
@@ -133,8 +135,9 @@ struct TcPlan {
 };
 
 // The ALS of the repetitions as independent groups, each its own chain of
-// kernels on its own stream: one group's MTTKRP pass streams the summaries
-// while another group's tail (a latency-bound chain of small steps) runs.
+// kernels on its own stream; each group's launches size their grids for its
+// share of the SMs, so the groups' passes run side by side and the kernel
+// boundaries of one chain overlap the other's work.
 struct AlsGroupRt {
     cudaStream_t st = nullptr, side = nullptr;   // the group's chain; V^-1 beside its passes
     cudaEvent_t fork = nullptr, join = nullptr;  // around V^-1

@@ -10,11 +10,15 @@
 // float32 / bfloat16 summaries (float32 factors): float64 is a slow unit on
 // this GPU, so the R x R work is done in double-float (pairs of floats with
 // error-free sums and products, ~44 significant bits).  V^-1 (Gauss-Jordan)
-// is computed by k_xinv on a side stream while the MTTKRP runs; k_tail_rows
-// then reduces the partials of 64 rows per CTA, forms U = M V^-1 and the
-// chunk's share of the new Gram, and the last CTA of a repetition to finish
-// (an atomic ticket, no waiting) combines the shares in chunk order, takes
-// lambda, rescales U and computes the fit.
+// is computed by k_xinv on a side stream while the MTTKRP runs (for a mode 3
+// formed from the mode-2 pass's products, by k_mtt_memo beside that
+// contraction); k_tail_rows then reduces the partials of 16 rows per CTA,
+// forms U = M V^-1 and the chunk's share of the new Gram.  The chunks of a
+// repetition form one thread-block cluster (up to 16 CTAs): every CTA adds
+// the shares from distributed shared memory in chunk order, takes lambda and
+// writes its rows of U normalised.  Larger modes use an atomic ticket: the
+// last CTA to finish combines the shares, takes lambda, rescales U and, after
+// mode 3, computes the fit.
 // Every reduction runs in a fixed order, so results do not depend on timing.
 #include "sbt_internal.cuh"
 
