@@ -59,6 +59,7 @@ from . import csampling
 
 DOMAIN_SAMPLE = 1
 DOMAIN_INIT = 2
+DOMAIN_GETRANK = 3
 INIT_BATCH = 0xFFFFFFFF  # batch number used by the initial decomposition
 
 FLAG_CHOL_REGULARIZED = 1
@@ -82,6 +83,9 @@ class Options:
     prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16 | fp8
     refine_sweeps: int = 0     # bf16 only: ALS iterations on the split summary after the bf16 ALS
     warm_start: bool = False   # start the summary ALS from the old factors at the sampled rows
+    get_rank: bool = False     # Section 4.2: estimate R_new per summary (Algorithm 2) and match R_new components
+    get_rank_trials: int = 2   # Algorithm 2's `it`: decompositions per candidate rank
+    get_rank_threshold: float = 90.0  # CorConDia a candidate rank must reach
 
 
 @dataclass
@@ -232,16 +236,17 @@ def summary_values(Xs: np.ndarray, prec: str) -> np.ndarray:
 # Algorithm 1 step 5: CP(X_s, R) by alternating least squares
 # --------------------------------------------------------------------------
 def init_factor(global_idx: np.ndarray, R: int, mode: int, rep: int, batch: int,
-                opts: Options) -> np.ndarray:
-    """U(x, r) = (Philox word 0 >> 8) * 2^-24 with counter (x, r | mode<<8 | rep<<12, batch, 2)."""
+                opts: Options, trial: int = -1) -> np.ndarray:
+    """U(x, r) = (Philox word 0 >> 8) * 2^-24 with counter (x, r | mode<<8 | rep<<12, batch, 2);
+    GetRank's trial t (>= 0) uses (x, r | mode<<8 | rep<<12 | t<<20, batch, 3)."""
     gi = np.asarray(global_idx, dtype=np.uint64)
     n = gi.shape[0]
     ctr = np.zeros((n, R, 4), np.uint32)
     ctr[:, :, 0] = gi[:, None].astype(np.uint32)
     ctr[:, :, 1] = (np.arange(R, dtype=np.uint32)[None, :] | np.uint32(mode << 8)
-                    | np.uint32((rep << 12) & 0xFFFFFFFF))
+                    | np.uint32((rep << 12) & 0xFFFFFFFF) | np.uint32((max(trial, 0) << 20) & 0xFFFFFFFF))
     ctr[:, :, 2] = np.uint32(batch & 0xFFFFFFFF)
-    ctr[:, :, 3] = DOMAIN_INIT
+    ctr[:, :, 3] = DOMAIN_INIT if trial < 0 else DOMAIN_GETRANK
     key = [opts.seed & 0xFFFFFFFF, ((opts.seed >> 32) & 0xFFFFFFFF) ^ (opts.stream_id & 0xFFFFFFFF)]
     out = csampling.philox4x32_10(ctr.reshape(-1, 4), key)
     return np.ldexp((out[:, 0] >> 8).astype(np.float64), -24).reshape(n, R)
@@ -406,13 +411,19 @@ def project_coef(mt: Match, lam_s, lam_old, skip_mode: int) -> np.ndarray:
 
 def project_back(Us_full, lam_s, lam_old, mt: Match, nK: int, K_new: int,
                  old_rows, sampled):
-    """Returns (C_new in old scale (K_new x R), zero-fill proposals per mode:
-    dict {(row, r): value} for old entries that are exactly 0)."""
+    """Returns (C_new in old scale (K_new x R_old), zero-fill proposals per
+    mode: dict {(row, r): value} for old entries that are exactly 0, the
+    summary's estimate of lambda, and the mask of old components matched).
+    With GetRank the summary has R_new <= R_old components; old components
+    no summary component matched get no new rows from this repetition."""
     R = lam_s.shape[0]
+    R_old = lam_old.shape[0]
     c3 = project_coef(mt, lam_s, lam_old, 2)
-    Cnew = np.zeros((K_new, R))
+    Cnew = np.zeros((K_new, R_old))
+    matched = np.zeros(R_old, bool)
     for rp in range(R):
         Cnew[:, mt.perm[rp]] = c3[rp] * Us_full[2][nK:nK + K_new, rp]
+        matched[mt.perm[rp]] = True
     props = []
     for n in range(3):
         cn = project_coef(mt, lam_s, lam_old, n)
@@ -424,13 +435,13 @@ def project_back(Us_full, lam_s, lam_old, mt: Match, nK: int, K_new: int,
                 if old_rows[n][t, r] == 0.0:
                     d[(int(x), int(r))] = cn[rp] * Us_full[n][t, rp]
         props.append(d)
-    lam_est = np.zeros(R)
+    lam_est = np.zeros(R_old)
     for rp in range(R):
         r = mt.perm[rp]
         den = mt.norms[0][r] * mt.norms[1][r] * mt.norms[2][r]
         lam_est[r] = (lam_s[rp] * mt.gamma[0][rp, r] * mt.gamma[1][rp, r]
                       * mt.gamma[2][rp, r] / den) if den != 0.0 else 0.0
-    return Cnew, props, lam_est
+    return Cnew, props, lam_est, matched
 
 
 # --------------------------------------------------------------------------
@@ -472,6 +483,24 @@ def init_decomposition(X0: np.ndarray, R: int, opts: Options):
     res = cp_als(Xv, U0, opts.tol, opts.max_iters_init, opts.fixed_iters)
     A, B, C, lam = canonicalize(res.U, res.lam)
     return init_state_from_factors(X0, lam, A, B, C, opts), res
+
+
+def get_rank(X: np.ndarray, R_max: int, idx, opts: Options, rep: int, batch: int):
+    """Algorithm 2 (GetRank): for every candidate rank i = 1..R_max and trial
+    j = 1..it, a CP decomposition of X at rank i (from trial j's start) and its
+    CorConDia p(i, j).  The algorithm's last step (sort p, take the top index)
+    is read as: R_new = the largest rank whose best trial reaches the
+    threshold (CorConDia of a rank-1 model is 100, so the literal top entry
+    would always be rank 1); 1 if none does.  idx: the global indices of the
+    summary's rows per mode (they key the starts).  Returns (R_new, p)."""
+    p = np.zeros((R_max, opts.get_rank_trials))
+    for i in range(1, R_max + 1):
+        for j in range(opts.get_rank_trials):
+            U0 = [init_factor(idx[m], i, m, rep, batch, opts, trial=j) for m in range(3)]
+            res = cp_als(X, U0, opts.tol, opts.max_iters, opts.fixed_iters)
+            p[i - 1, j] = core_consistency(X, res.lam, res.U[0], res.U[1], res.U[2])
+    ok = [i for i in range(1, R_max + 1) if np.max(p[i - 1]) >= opts.get_rank_threshold]
+    return (max(ok) if ok else 1), p
 
 
 @dataclass
@@ -521,13 +550,17 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         # step 5: CP of the summary, from random factors (the paper leaves
         # the start open), or warm: the old factors at the sampled rows, the
         # new slices' rows of C' zero (their first mode-3 update fills them)
-        if opts.warm_start:
+        # GetRank (Section 4.2, Algorithm 2): the summary's rank R_new <= R
+        R_s, p_rank = R, None
+        if opts.get_rank:
+            R_s, p_rank = get_rank(Xs, R, (Is, Js, Kp), opts, rho, state.batch)
+        if opts.warm_start and not opts.get_rank:
             U0 = [state.A[Is].copy(), state.B[Js].copy(),
                   np.concatenate([state.C[Ks], np.zeros((K_new, R))], axis=0)]
         else:
-            U0 = [init_factor(Is, R, 0, rho, state.batch, opts),
-                  init_factor(Js, R, 1, rho, state.batch, opts),
-                  init_factor(Kp, R, 2, rho, state.batch, opts)]
+            U0 = [init_factor(Is, R_s, 0, rho, state.batch, opts),
+                  init_factor(Js, R_s, 1, rho, state.batch, opts),
+                  init_factor(Kp, R_s, 2, rho, state.batch, opts)]
         res = cp_als(Xs, U0, opts.tol, opts.max_iters, opts.fixed_iters)
         if opts.prec == "bf16" and opts.refine_sweeps > 0:
             # refinement: continue the same ALS from its factors for a fixed
@@ -543,20 +576,26 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         old_rows = [state.A[Is], state.B[Js], state.C[Ks]]
         mt = match([Us[0], Us[1], Us[2][:nK]], old_rows)
         # steps 8-9: project back
-        Cnew, props, lam_est = project_back(Us, lam_s, state.lam, mt, nK, K_new,
-                                            old_rows, [Is, Js, Ks])
+        Cnew, props, lam_est, matched = project_back(Us, lam_s, state.lam, mt, nK, K_new,
+                                                     old_rows, [Is, Js, Ks])
         traces.append(RepTrace(Is=Is, Js=Js, Ks=Ks, als=res, Us=Us, lam_s=lam_s,
                                match=mt, Cnew=Cnew, flags=flags))
         traces[-1].props = props
         traces[-1].lam_est = lam_est
+        traces[-1].matched = matched
+        traces[-1].R_new = R_s
+        traces[-1].p_rank = p_rank
         if keep_summaries:
             traces[-1].Xs = Xs
         traces[-1].seconds = time.perf_counter() - t_rep
-    # step 10 and 12: average C_new over the repetitions, append to C
+    # step 10 and 12: average C_new over the repetitions (with GetRank, over
+    # those that matched the component; none: zero rows), append to C
     Cnew = np.zeros((K_new, R))
+    cnt = np.zeros(R)
     for t in traces:
         Cnew = Cnew + t.Cnew
-    Cnew = Cnew / opts.r
+        cnt = cnt + t.matched
+    Cnew = Cnew / np.where(cnt > 0, cnt, 1.0)
     # step 8 (commit): zero entries of the old factors take the mean of the proposals
     A, B, C = state.A.copy(), state.B.copy(), state.C.copy()
     for n, F in enumerate((A, B, C)):
@@ -572,7 +611,7 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         est = np.zeros(R)
         for t in traces:
             est = est + t.lam_est
-        lam = 0.5 * (lam + est / opts.r)
+        lam = np.where(cnt > 0, 0.5 * (lam + est / np.where(cnt > 0, cnt, 1.0)), lam)
     # fold the new slices into the measure of importance
     qa, qb, qc = marginals(X_new, state.S)
     new = State(X=X_all, A=A, B=B, C=np.concatenate([C, Cnew], axis=0), lam=lam, S=state.S,

@@ -488,6 +488,47 @@ def test_relative_fitness_definition():
     assert abs(O.relative_fitness(X, twice, base) - 2.0) < 1e-12
 
 
+@pytest.mark.parametrize("R_true,noise", [(2, 0.0), (3, 0.01)])
+def test_get_rank_finds_the_planted_rank(R_true, noise):
+    """Algorithm 2 with the threshold reading: on a planted rank-R_true tensor
+    the largest candidate rank whose core consistency reaches 90 is R_true
+    (an exact CP scores 100; an over-factored one falls far below)."""
+    p = synth.planted_dense(14, 12, 10, R_true, noise=noise, seed=21, dtype=torch.float64)
+    X = p.X.numpy()
+    opts = O.Options(tol=1e-10, max_iters=400, get_rank=True, get_rank_trials=2)
+    idx = (np.arange(14), np.arange(12), np.arange(10))
+    R_new, pr = O.get_rank(X, 4, idx, opts, rep=0, batch=0)
+    assert R_new == R_true, pr
+    assert np.max(pr[R_true - 1]) > 99.0 - 1000 * noise
+    assert np.all(np.max(pr[R_true:], axis=1) < 90.0)
+
+
+def test_match_of_fewer_summary_components():
+    """Rectangular Lemma-1 matching: a summary with R_new < R components, each
+    an old component at the sampled rows (in another order, unit columns),
+    is matched to exactly those old components."""
+    rng = np.random.default_rng(4)
+    old = [rng.random((8, 4)), rng.random((7, 4)), rng.random((6, 4))]
+    pick = [3, 1]
+    Us = [u[:, pick] / np.linalg.norm(u[:, pick], axis=0) for u in old]
+    mt = O.match(Us, old)
+    assert list(mt.perm) == pick
+
+
+def test_get_rank_full_rank_update_equals_plain_update():
+    """When every summary has the full rank, the GetRank update is the plain
+    update (rank-R ALS from the same start, every component matched by every
+    repetition)."""
+    R = 2
+    base = dict(s_I=2, s_J=2, s_K=2, r=2, tol=1e-10, max_iters=300, seed=0)
+    st, X, _ = _planted_state(16, 14, 10, R, O.Options(**base, get_rank=True), Ktot=14, seed=3)
+    st_g, tr_g = O.update(st, X[10:14])
+    st_p, _ = _planted_state(16, 14, 10, R, O.Options(**base), Ktot=14, seed=3)[:2]
+    st_p2, _ = O.update(st_p, X[10:14])
+    assert all(t.R_new == R and t.matched.all() for t in tr_g)
+    np.testing.assert_array_equal(st_g.C, st_p2.C)
+
+
 def test_update_stream_keeps_fit_noiseless():
     R = 2
     opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-15, max_iters=3000, seed=4)
