@@ -64,6 +64,31 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert b"null" in lib.sbt_last_error()
 
 
+@pytest.mark.parametrize("field,value", [("mode3_pass", 2), ("als_groups", -1), ("als_groups", 65),
+                                         ("warm_start", 3), ("refine_sweeps", -1), ("check_every", 0)])
+def test_invalid_options_rejected_without_gpu(lib, field, value):
+    """Each option's range is checked before any device call (check_every 0
+    is valid: the default poll interval)."""
+    from paper_1709_00668_gb300 import sbt
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_float * 64)()
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 4, 4, 4, ctypes.cast(buf, ctypes.c_void_p))
+    o = sbt.sbt_default_options()
+    setattr(o, field, value)
+    rc = lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(o), ctypes.byref(h))
+    if field == "check_every":
+        assert rc != sbt.SBT_E_INVALID or b"check_every" not in lib.sbt_last_error()
+    else:
+        assert rc == sbt.SBT_E_INVALID, (field, rc)
+        assert field.encode() in lib.sbt_last_error()
+
+
+def test_recompute_rejects_bad_arguments_without_gpu(lib):
+    from paper_1709_00668_gb300 import sbt
+    f = ctypes.c_double()
+    assert lib.sbt_recompute(None, 10, 1e-6, 0, None, None, None, None, ctypes.byref(f)) == sbt.SBT_E_INVALID
+
+
 def test_package_import_does_not_need_the_library():
     import importlib
     m = importlib.import_module("paper_1709_00668_gb300")
