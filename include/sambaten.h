@@ -3,7 +3,7 @@
  * after SamBaTen: "Sampling-based Batch Incremental Tensor Decomposition"
  * (Gujral, Pasricha, Papalexakis; arxiv 1709.00668).
  *
- * The calls follow the paper's problem statement (Section 3.2): given a CP
+ * The calls follow the paper's problem statement (Section 2.2): given a CP
  * decomposition A, B, C, lambda of an I x J x K1 tensor and a batch of K2 new
  * slices along the third (time) mode, return A, B and a C with K1 + K2 rows.
  * One sbt_update runs Algorithm 1 once on the GPU: sample each mode by its
@@ -79,7 +79,7 @@ typedef struct {
 } sbt_tensor;
 
 typedef struct {
-    int32_t s_I, s_J, s_K; /* sampling factors: a sample keeps ceil(N/s) indices (Section 4.1) */
+    int32_t s_I, s_J, s_K; /* sampling factors: a sample keeps ceil(N/s) indices (Section 3.1) */
     int32_t r;             /* repetitions (independent summaries per batch) */
     double tol;            /* ALS stops when |fit - previous fit| < tol */
     int32_t max_iters;     /* ALS iteration cap per summary */
@@ -144,7 +144,7 @@ sbt_status sbt_default_options(sbt_options *opt);
 /* Decompose X0 (I x J x K0) at rank R with CP-ALS on the GPU (Philox-uniform
  * start), sort components by lambda, fix signs (sum A(:,r) >= 0, sum B(:,r)
  * >= 0) and keep X0, the factors and the Eq. 1 marginals resident on the
- * device.  This is the pre-existing decomposition of Section 3.2, (a). */
+ * device.  This is the pre-existing decomposition of Section 2.2, (a). */
 sbt_status sbt_init(const sbt_tensor *X0, int32_t R, const sbt_options *opt, sbt_ctx **out);
 
 /* Same, but the pre-existing decomposition is given: lambda (R), A (I x R),
@@ -165,10 +165,10 @@ sbt_status sbt_factors(const sbt_ctx *ctx, double *lambda, double *A, double *B,
                        int64_t *K_out);
 
 /* Fit of the full model against the full resident tensor:
- * 1 - ||X - X_hat||_F / ||X||_F (Section 5.2, relative error = 1 - fit). */
+ * 1 - ||X - X_hat||_F / ||X||_F (Section 4.2, relative error = 1 - fit). */
 sbt_status sbt_fit(sbt_ctx *ctx, double *fit);
 
-/* The recompute comparator of Section 5.2 (Relative Fitness): CP-ALS of the
+/* The recompute comparator of Section 4.2 (Relative Fitness): CP-ALS of the
  * whole resident tensor from scratch, as sbt_init runs it (the store's
  * precision, Philox start with `seed` and the context's stream id, at most
  * max_iters iterations, stop when the fit changes by less than tol), without
@@ -186,7 +186,7 @@ sbt_status sbt_stats(const sbt_ctx *ctx, sbt_update_stats *st);
 
 /* ---- sparse (COO) tensors -------------------------------------------------
  * The same method (Alg. 1) on tensors stored as nonzeros (the sparse
- * workloads of Section 5.1).  The context keeps the nonzeros grouped by time
+ * workloads of Section 4.1).  The context keeps the nonzeros grouped by time
  * slice; summaries are the lists of nonzeros of the sampled slices whose row
  * and column were sampled.  Results equal the dense definitions applied to the
  * densified tensor; the MTTKRP adds its float32 products in 64-bit fixed point,
@@ -403,7 +403,7 @@ void sbt_server_destroy(sbt_server *srv);
 sbt_status sbt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
                              int64_t n, void *stream);
 
-/* Weighted sampling without replacement of one mode (Section 4.1, Alg. 1
+/* Weighted sampling without replacement of one mode (Section 3.1, Alg. 1
  * step 3): draws n of the N indices with w[x] > 0, probability proportional
  * to w (successive sampling through exponential keys), writes them ascending
  * to out (device, n int32).  Philox key (lo32(seed), hi32(seed) ^ stream_id),

@@ -7,20 +7,20 @@ everything else is plain numpy/scipy in float64, written as the paper's steps
 in the paper's order.
 
 Section map (paper arxiv 1709.00668):
-  * Eq. 1 (Section 4.1, "Sample")      -> marginals()
-  * Section 4.1 + Algorithm 1 step 3   -> sample_sizes(), sample_mode() (oracle/sampling.c)
-  * Section 4.1 + Algorithm 1 step 4   -> summary()
-  * Algorithm 1 step 5, Section 4.1 "Decompose" (ALS, Kolda & Bader 2009)
+  * Eq. 1 (Section 3.1, "Sample")      -> marginals()
+  * Section 3.1 + Algorithm 1 step 3   -> sample_sizes(), sample_mode() (oracle/sampling.c)
+  * Section 3.1 + Algorithm 1 step 4   -> summary()
+  * Algorithm 1 step 5, Section 3.1 "Decompose" (ALS, Kolda & Bader 2009)
                                        -> init_factors(), mttkrp(), cp_als()
-  * Algorithm 1 step 6, Section 4.1 "Project back" (shared-row normalisation)
+  * Algorithm 1 step 6, Section 3.1 "Project back" (shared-row normalisation)
                                        -> normalize_shared()
   * Lemma 1 + Algorithm 1 step 7       -> match()
-  * Section 4.1 "Project back" relation + Algorithm 1 steps 8-10
+  * Section 3.1 "Project back" relation + Algorithm 1 steps 8-10
                                        -> project_back()
   * Algorithm 1 steps 12-13            -> commit inside update()
-  * Section 3.2 problem statement      -> init_decomposition(), update()
-  * Section 5.2 relative error         -> full_fit()
-  * Bro & Kiers 2003 (cited, Section 4.2) core consistency, FMS (Section 5.4)
+  * Section 2.2 problem statement      -> init_decomposition(), update()
+  * Section 4.2 relative error         -> full_fit()
+  * Bro & Kiers 2003 (cited, Section 3.2) core consistency, FMS (Section 4.4)
                                        -> core_consistency(), fms() (test utilities)
 
 Readings where the paper is silent or ambiguous (each is restated in the
@@ -83,7 +83,7 @@ class Options:
     prec: str = "f64"          # values the summary ALS sees: f64 | f32 | bf16 | fp8
     refine_sweeps: int = 0     # bf16 only: ALS iterations on the split summary after the bf16 ALS
     warm_start: bool = False   # start the summary ALS from the old factors at the sampled rows
-    get_rank: bool = False     # Section 4.2: estimate R_new per summary (Algorithm 2) and match R_new components
+    get_rank: bool = False     # Section 3.2: estimate R_new per summary (Algorithm 2) and match R_new components
     get_rank_trials: int = 2   # Algorithm 2's `it`: decompositions per candidate rank
     get_rank_threshold: float = 90.0  # CorConDia a candidate rank must reach
 
@@ -152,7 +152,7 @@ def marginals(X: np.ndarray, S: int):
 
 
 # --------------------------------------------------------------------------
-# Section 4.1 / Algorithm 1 step 3: weighted sampling without replacement
+# Section 3.1 / Algorithm 1 step 3: weighted sampling without replacement
 # --------------------------------------------------------------------------
 def sample_size(N_old: int, s: int, w: np.ndarray) -> int:
     """|I_s| = N/s (rounded up), clamped to the number of positive weights."""
@@ -389,7 +389,7 @@ def match(Us, anchors) -> Match:
 
 
 # --------------------------------------------------------------------------
-# Section 4.1 "Project back" relation + Algorithm 1 steps 8-10
+# Section 3.1 "Project back" relation + Algorithm 1 steps 8-10
 # --------------------------------------------------------------------------
 def project_coef(mt: Match, lam_s, lam_old, skip_mode: int) -> np.ndarray:
     """coef(r') = lam'_{r'} prod_{m != skip} Gamma_m(r', r) / (lam_r prod_{m != skip} N_m(r)),
@@ -445,7 +445,7 @@ def project_back(Us_full, lam_s, lam_old, mt: Match, nK: int, K_new: int,
 
 
 # --------------------------------------------------------------------------
-# Section 3.2: the pre-existing decomposition, and Algorithm 1 as a whole
+# Section 2.2: the pre-existing decomposition, and Algorithm 1 as a whole
 # --------------------------------------------------------------------------
 def canonicalize(U, lam):
     """Sort components by lambda (descending, stable) and fix signs so that
@@ -464,7 +464,7 @@ def canonicalize(U, lam):
 
 
 def init_state_from_factors(X0: np.ndarray, lam, A, B, C, opts: Options) -> State:
-    """State for a given pre-existing decomposition of X0 (Section 3.2, (a))."""
+    """State for a given pre-existing decomposition of X0 (Section 2.2, (a))."""
     S = marginal_shift(X0)
     xa, xb, xc = marginals(X0, S)
     return State(X=np.array(X0, copy=True), A=np.array(A, np.float64), B=np.array(B, np.float64),
@@ -550,7 +550,7 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
         # step 5: CP of the summary, from random factors (the paper leaves
         # the start open), or warm: the old factors at the sampled rows, the
         # new slices' rows of C' zero (their first mode-3 update fills them)
-        # GetRank (Section 4.2, Algorithm 2): the summary's rank R_new <= R
+        # GetRank (Section 3.2, Algorithm 2): the summary's rank R_new <= R
         R_s, p_rank = R, None
         if opts.get_rank:
             R_s, p_rank = get_rank(Xs, R, (Is, Js, Kp), opts, rho, state.batch)
@@ -621,7 +621,7 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
 
 
 # --------------------------------------------------------------------------
-# Section 5.2: relative error / fit of the full model
+# Section 4.2: relative error / fit of the full model
 # --------------------------------------------------------------------------
 def reconstruct(lam, A, B, C) -> np.ndarray:
     return np.einsum("r,ir,jr,kr->kij", lam, A, B, C, optimize=True)
@@ -641,10 +641,10 @@ def full_fit(X: np.ndarray, lam, A, B, C) -> float:
 
 
 # --------------------------------------------------------------------------
-# Test utilities: core consistency (Bro & Kiers 2003) and FMS (Section 5.4)
+# Test utilities: core consistency (Bro & Kiers 2003) and FMS (Section 4.4)
 # --------------------------------------------------------------------------
 def relative_fitness(X: np.ndarray, model, baseline) -> float:
-    """Relative Fitness (Section 5.2): ||X - X_model|| / ||X - X_baseline||,
+    """Relative Fitness (Section 4.2): ||X - X_model|| / ||X - X_baseline||,
     each model a tuple (lam, A, B, C); the baseline is the decomposition
     recomputed on the whole tensor."""
     ra = np.linalg.norm((X - reconstruct(*model)).ravel())

@@ -5,7 +5,7 @@
  * call this file; the tests, the package's smoke check and the benchmark's
  * CPU-baseline leg are its only users.  It shares no code with the CUDA path.
  *
- * Section 4.1 ("Sample") and Algorithm 1, step 3: each mode is sampled
+ * Section 3.1 ("Sample") and Algorithm 1, step 3: each mode is sampled
  * without replacement with probabilities proportional to its measure of
  * importance (Eq. 1).  The oracle realises that draw as successive sampling
  * through exponential keys (Efraimidis & Spirakis, "Weighted random sampling

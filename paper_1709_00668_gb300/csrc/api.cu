@@ -1012,7 +1012,7 @@ static sbt_status grow_store(sbt_ctx *c, int64_t need) {
 }
 
 // Shapes of one update of K_new slices on K_old old ones: the sample sizes of
-// Section 4.1 (ceil(N / s), clamped to the positive weights) and everything
+// Section 3.1 (ceil(N / s), clamped to the positive weights) and everything
 // the workspace depends on.  With `bound` the clamps are replaced by their
 // largest possible values (used to size for future updates).
 struct UpdShape {
@@ -1674,7 +1674,7 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
 
 // ---------------------------------------------------------------------------
 // COO tensors: the same method (Alg. 1) on a store of nonzeros grouped by
-// time slice; the sparse workloads of Section 5.1.
+// time slice; the sparse workloads of Section 4.1.
 
 static sbt_status check_coo(const sbt_coo *X) {
     if (!X) return fail(SBT_E_INVALID, "null tensor");
@@ -1965,7 +1965,7 @@ extern "C" sbt_status sbt_update_coo(sbt_ctx *c, const sbt_coo *X) {
     const int R = c->R, r = c->opt.r;
     const int K_new = (int)X->K;
     const int64_t K_old = c->K;
-    // sample sizes (Section 4.1): ceil(N / s), clamped to the positive weights
+    // sample sizes (Section 3.1): ceil(N / s), clamped to the positive weights
     const int nI = (int)std::min<int64_t>(ceil_div(c->I, c->opt.s_I), c->npos[0]);
     const int nJ = (int)std::min<int64_t>(ceil_div(c->J, c->opt.s_J), c->npos[1]);
     const int nK = (int)std::min<int64_t>(ceil_div(K_old, c->opt.s_K), c->npos[2]);

@@ -375,7 +375,7 @@ cudaError_t launch_commit(const MergeDesc &m, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Full-tensor fit: 1 - ||X - X_hat|| / ||X|| (Section 5.2).  A warp per row
+// Full-tensor fit: 1 - ||X - X_hat|| / ||X|| (Section 4.2).  A warp per row
 // (k, i): x_hat(j) = sum_r lambda_r A(i,r) C(k,r) B(j,r); residual squares and
 // squares accumulate per lane, then per CTA, then in fixed order.
 template <typename TS> struct FitAcc;

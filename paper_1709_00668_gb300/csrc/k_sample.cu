@@ -216,7 +216,7 @@ cudaError_t launch_append(const void *Xin, int dtype, long long K_new, int I, in
 }
 
 // ---------------------------------------------------------------------------
-// Weighted sampling without replacement (Section 4.1, Alg. 1 step 3).
+// Weighted sampling without replacement (Section 3.1, Alg. 1 step 3).
 // Exponential keys: key = floor(L * 2^64 / w), L = -log2(u) in Q.32 with
 // u = (2v+1) / 2^33 and v Philox word 0 on counter (x, mode | rep<<4, batch, 1).
 // The n smallest (key, x) are found by an MSB-first radix select over the

@@ -430,7 +430,7 @@ class SamBaTen:
         return float(f.value), lam, A, B, C
 
     def relative_fitness(self, max_iters: int = 50, tol: float = 1e-6, seed: int = 0) -> float:
-        """Relative Fitness (Section 5.2): ||X - X_sbt|| / ||X - X_cp|| with X_cp
+        """Relative Fitness (Section 4.2): ||X - X_sbt|| / ||X - X_cp|| with X_cp
         the recomputed CP-ALS of the whole tensor; 1 = as good as recomputing."""
         f_cp = self.recompute(max_iters, tol, seed)[0]
         return (1.0 - self.fit()) / (1.0 - f_cp) if f_cp < 1.0 else float("inf")

@@ -2,7 +2,7 @@
 
 This module is the one piece shared by the FP64 oracle's tests and the CUDA
 path's tests and benchmark.  It holds no arithmetic of the method itself: it
-only draws planted CP factors and noise (Section 5.1.1 of the paper: tensors
+only draws planted CP factors and noise (Section 4.1.1 of the paper: tensors
 built from known, randomly generated factors) and hands out the same bytes to
 both sides.
 
