@@ -55,14 +55,15 @@ typedef enum {
 /* Storage type of X.  SBT_BF16 is accepted by sbt_mttkrp only. */
 typedef enum { SBT_F64 = 0, SBT_F32 = 1, SBT_BF16 = 2 } sbt_dtype;
 
-/* Arithmetic of the summary MTTKRP (the hot loop).  F64: float64 throughout
- * (needs an F64 store).  F32: float32 values, float32 accumulation.  BF16:
- * summary rounded to bfloat16 (nearest-even), float32 accumulation.  The R x R
- * Cholesky factorisation, inversion, column norms and the fit stay float64 in
- * every mode. */
-/* Values the summary MTTKRP reads: float64, float32, bfloat16, or float8 e4m3
- * codes with one scale per stored slice (scale = max|x| of the slice / 448,
- * code = e4m3(x * 448 / max|x|), ties to even, saturating; needs R <= 32). */
+/* Arithmetic of the summary ALS.  F64: float64 throughout (needs an F64
+ * store), the R x R solve by a float64 Cholesky factorisation.  F32: float32
+ * values, float32 accumulation.  BF16: summary rounded to bfloat16
+ * (nearest-even), tensor-core MTTKRP with float32 accumulation.  FP8: float8
+ * e4m3 codes with one scale per stored slice (scale = max|x| of the slice /
+ * 448, code = e4m3(x * 448 / max|x|), ties to even, saturating; needs
+ * R <= 32).  For F32, BF16 and FP8 the R x R work (Grams, V^-1, column norms,
+ * the fit) runs in double-float, pairs of floats with ~44 significant bits,
+ * float64 being a slow unit on this GPU. */
 typedef enum { SBT_PREC_F64 = 0, SBT_PREC_F32 = 1, SBT_PREC_BF16 = 2, SBT_PREC_FP8 = 3 } sbt_prec;
 
 /* Update flags (sbt_update_stats.flags), OR-ed over repetitions. */
@@ -420,8 +421,9 @@ sbt_status sbt_sample(const uint64_t *w, int64_t N, int64_t n, uint64_t seed,
  * Alg. 1 step 5.  dtype SBT_F64 or SBT_F32 applies to X, the factors A (I x R),
  * B (J x R), C (K x R) and M (CUDA cores).  dtype SBT_BF16: X is bfloat16, the
  * factors and M are float32, and the product runs on the tensor cores
- * (tcgen05, factors split into two bfloat16 halves); SBT_E_INVALID if R or
- * the contraction length is beyond that kernel's shared-memory plan. */
+ * (tcgen05, factors split into three bfloat16 terms up to R = 16, two
+ * above); SBT_E_INVALID if R or the contraction length is beyond that
+ * kernel's shared-memory plan. */
 sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
                       const void *A, const void *B, const void *C, int32_t R, int32_t mode,
                       void *M, void *stream);
