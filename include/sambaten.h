@@ -428,6 +428,22 @@ sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_
                       const void *A, const void *B, const void *C, int32_t R, int32_t mode,
                       void *M, void *stream);
 
+/* Core consistency diagnostic (CorConDia, Bro & Kiers 2003), the quality
+ * rating GetRank gives each candidate decomposition (Section 3.2, Algorithm
+ * 2): 100 (1 - ||G - T||^2 / R) with G = X x_1 A+ x_2 B+ x_3 (C diag(lambda))+
+ * the least-squares Tucker core for the fixed factors (F+ = (F^T F)^-1 F^T)
+ * and T the superdiagonal of ones; 100 for an exact CP, far below for an
+ * over-factored one.  X: device, slice-major K x I x J, row pitch ld >= J
+ * elements, dtype SBT_F64 or SBT_F32; lambda (R), A (I x R), B (J x R),
+ * C (K x R): device float64, row-major; *cc: host.  Computed in float64 with
+ * fixed-order sums; allocates scratch of about K I R + R (I + J + K) + K R^2
+ * doubles on `stream` and synchronises it.  SBT_E_INVALID for a null
+ * pointer, another dtype or R outside [1, SBT_MAX_RANK]; SBT_E_SHAPE unless
+ * K, I, J >= R; SBT_E_STATE if a factor's Gram is not positive definite. */
+sbt_status sbt_core_consistency(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
+                                const double *lambda, const double *A, const double *B, const double *C,
+                                int32_t R, double *cc, void *stream);
+
 /* The weighted draw of sbt_sample for callers that must not allocate device
  * memory during the call -- for example a serving process that gives the whole
  * device to its own pool at start-up, or a latency-critical loop where a

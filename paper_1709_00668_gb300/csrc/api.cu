@@ -2292,6 +2292,36 @@ static sbt_status mttkrp_bf16_op(const void *X, int64_t K, int64_t I, int64_t J,
     return SBT_OK;
 }
 
+extern "C" sbt_status sbt_core_consistency(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J,
+                                           int64_t ld, const double *lambda, const double *A, const double *B,
+                                           const double *C, int32_t R, double *cc, void *stream) {
+    if (!X || !lambda || !A || !B || !C || !cc) return fail(SBT_E_INVALID, "null pointer");
+    if (dtype != SBT_F64 && dtype != SBT_F32) return fail(SBT_E_INVALID, "dtype must be SBT_F64 or SBT_F32");
+    if (R < 1 || R > SBT_MAX_RANK) return fail(SBT_E_INVALID, "R out of range [1, SBT_MAX_RANK]");
+    if (K < R || I < R || J < R || ld < J) return fail(SBT_E_SHAPE, "need K, I, J >= R and ld >= J");
+    if (K > (1 << 30) || I > (1 << 30) || J > (1 << 30)) return fail(SBT_E_SHAPE, "dimension too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nd = core_consistency_scratch_doubles(K, I, J, R);
+    char *scr = nullptr;
+    CK(cudaMallocAsync((void **)&scr, 16 + (nd + 1) * sizeof(double), st));
+    int *status = (int *)scr;
+    double *out = (double *)(scr + 8), *scratch = out + 1;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = launch_core_consistency(dtype == SBT_F64, X, K, I, J, ld, lambda, A, B, C, R, scratch, status, out, st);
+    double h_out = 0.0;
+    int h_status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_out, out, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t ef = cudaFreeAsync(scr, st);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("core consistency: ") + cudaGetErrorString(e));
+    if (h_status) return fail(SBT_E_STATE, "a factor's Gram is not positive definite");
+    *cc = h_out;
+    return SBT_OK;
+}
+
 extern "C" sbt_status sbt_mttkrp(int32_t dtype, const void *X, int64_t K, int64_t I, int64_t J, int64_t ld,
                                  const void *A, const void *B, const void *C, int32_t R, int32_t mode, void *M,
                                  void *stream) {

@@ -385,6 +385,14 @@ cudaError_t set_als_kernel_attributes();
 cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
+// CorConDia of a CP model (float64; X slice-major f64 when dtype_f64, else
+// f32); scratch: core_consistency_scratch_doubles(K, I, J, R) doubles; status
+// bit 1 when a factor's Gram is not positive definite; *out device double
+cudaError_t launch_core_consistency(int dtype_f64, const void *X, long long K, long long I, long long J, long long ld,
+                                    const double *lam, const double *A, const double *B, const double *C, int R,
+                                    double *scratch, int *status, double *out, cudaStream_t st);
+size_t core_consistency_scratch_doubles(long long K, long long I, long long J, int R);
+
 // mode 3 after a memoised mode-2 pass: M3 from d.ymem and the new B as the
 // single partial of the mode-3 tail, and V^-1 of mode 3 (PDL launch)
 cudaError_t launch_mtt_memo(const AlsDesc &d, cudaStream_t st);

@@ -50,6 +50,7 @@ EXPORTS = [
     "sbt_version", "sbt_last_error", "sbt_default_options", "sbt_init", "sbt_init_factors",
     "sbt_update", "sbt_factors", "sbt_fit", "sbt_recompute", "sbt_stats", "sbt_last_samples", "sbt_last_summary",
     "sbt_last_summary_factors", "sbt_destroy", "sbt_philox4x32_10", "sbt_sample", "sbt_mttkrp",
+    "sbt_core_consistency",
     "sbt_profile_reset", "sbt_profile_read", "sbt_sample_noalloc",
     "sbt_device_bytes", "sbt_update_bytes", "sbt_reserve", "sbt_tile_table",
     "sbt_init_coo", "sbt_init_coo_factors", "sbt_update_coo",
@@ -166,6 +167,8 @@ def lib() -> ctypes.CDLL:
     L.sbt_philox4x32_10.argtypes = [P, U32, U32, P, I64, P]
     L.sbt_sample.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_mttkrp.argtypes = [I32, P, I64, I64, I64, I64, P, P, P, I32, I32, P, P]
+    L.sbt_core_consistency.argtypes = [I32, P, I64, I64, I64, I64, P, P, P, P, I32,
+                                       ctypes.POINTER(ctypes.c_double), P]
     L.sbt_sample_noalloc.argtypes = [P, I64, I64, U64, U32, I32, I32, U32, P, P]
     L.sbt_profile_reset.argtypes = [P, I32]
     L.sbt_profile_read.argtypes = [P, ctypes.POINTER(SbtProfile)]
@@ -568,6 +571,23 @@ def sbt_mttkrp(X, A, B, C, mode, *, stream=None):
     _check(lib().sbt_mttkrp(dt, X.data_ptr(), K, I, J, ld, A.data_ptr(), B.data_ptr(), C.data_ptr(), R,
                             int(mode), out.data_ptr(), _stream_arg(stream)), "sbt_mttkrp")
     return out
+
+
+def sbt_core_consistency(X, lam, A, B, C, *, stream=None) -> float:
+    """CorConDia of the CP model (lam, A, B, C) of a (K, I, ld) CUDA tensor
+    (float64 or float32; J = B.shape[0]); the factors are float64 tensors on
+    the same device."""
+    import torch
+    K, I, ldx = X.shape
+    J = B.shape[0]
+    R = A.shape[1]
+    dt = {torch.float64: SBT_F64, torch.float32: SBT_F32}[X.dtype]
+    lam, A, B, C = (t.to(device=X.device, dtype=torch.float64).contiguous() for t in (lam, A, B, C))
+    cc = ctypes.c_double()
+    _check(lib().sbt_core_consistency(dt, X.data_ptr(), K, I, J, ldx, lam.data_ptr(), A.data_ptr(), B.data_ptr(),
+                                      C.data_ptr(), R, ctypes.byref(cc), _stream_arg(stream)),
+           "sbt_core_consistency")
+    return float(cc.value)
 
 
 # ---------------------------------------------------------------------------

@@ -83,6 +83,21 @@ def test_invalid_options_rejected_without_gpu(lib, field, value):
         assert field.encode() in lib.sbt_last_error()
 
 
+def test_core_consistency_rejects_bad_arguments_without_gpu(lib):
+    from paper_1709_00668_gb300 import sbt
+    cc = ctypes.c_double()
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.sbt_core_consistency(sbt.SBT_F64, None, 4, 4, 4, 4, p, p, p, p, 2, ctypes.byref(cc),
+                                    None) == sbt.SBT_E_INVALID
+    assert lib.sbt_core_consistency(sbt.SBT_BF16, p, 4, 4, 4, 4, p, p, p, p, 2, ctypes.byref(cc),
+                                    None) == sbt.SBT_E_INVALID
+    assert lib.sbt_core_consistency(sbt.SBT_F64, p, 4, 4, 4, 4, p, p, p, p, 0, ctypes.byref(cc),
+                                    None) == sbt.SBT_E_INVALID
+    assert lib.sbt_core_consistency(sbt.SBT_F64, p, 1, 4, 4, 4, p, p, p, p, 2, ctypes.byref(cc),
+                                    None) == sbt.SBT_E_SHAPE
+
+
 def test_recompute_rejects_bad_arguments_without_gpu(lib):
     from paper_1709_00668_gb300 import sbt
     f = ctypes.c_double()
