@@ -529,6 +529,50 @@ def test_get_rank_full_rank_update_equals_plain_update():
     np.testing.assert_array_equal(st_g.C, st_p2.C)
 
 
+def test_nmode_oracle_at_order_three_is_the_three_mode_oracle():
+    """The order-N oracle (NEXT N3) at N = 3: the same samples, the same match
+    and the same appended rows as the 3-mode oracle (only einsum's summation
+    order differs)."""
+    from oracle import nmode
+    R = 3
+    opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-9, max_iters=60, seed=2)
+    st, X, (A, B, Cn, lam) = _planted_state(18, 16, 12, R, opts, noise=0.01, Ktot=16, seed=8)
+    st3, tr3 = O.update(st, X[12:16])
+    stN = nmode.init_state_from_factors(X[:12], lam, [A, B, Cn[:12]], opts)
+    stN2, trN = nmode.update(stN, X[12:16])
+    for a, b in zip(tr3, trN):
+        assert np.array_equal(a.Is, b["idx"][0]) and np.array_equal(a.Js, b["idx"][1])
+        assert np.array_equal(a.Ks, b["idx"][2])
+        assert list(a.match.perm) == list(b["match"].perm)
+        assert a.als.iters == b["als"].iters
+    np.testing.assert_allclose(stN2.U[2], st3.C, rtol=1e-9, atol=1e-12)
+
+
+def test_nmode_update_projects_back_exactly_at_order_four():
+    """Project-back relation at N = 4 (noiseless): the appended time rows equal
+    the planted ones in the old model's scale, and every marginal and mode
+    sample follows Eq. 1 and the sample-size rule."""
+    from oracle import nmode
+    rng = np.random.default_rng(12)
+    R, dims, Ktot, K0 = 2, (9, 8, 7), 14, 10
+    U = [rng.random((d, R)) for d in dims] + [rng.random((Ktot, R))]
+    norms = [np.linalg.norm(u[:K0] if n == 3 else u, axis=0) for n, u in enumerate(U)]
+    Un = [u / nrm for u, nrm in zip(U, norms)]
+    lam = np.prod(norms, axis=0)
+    X = nmode.reconstruct(np.ones(R), U)
+    opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-14, max_iters=2000, seed=0)
+    st = nmode.init_state_from_factors(X[:K0], lam, [Un[0], Un[1], Un[2], Un[3][:K0]], opts)
+    w = nmode.marginals(X[:K0], st.S)
+    q = O.quantized_squares(X[:K0], st.S)
+    assert np.array_equal(w[0], q.sum(axis=(0, 2, 3), dtype=np.uint64))
+    assert np.array_equal(w[3], q.sum(axis=(1, 2, 3), dtype=np.uint64))
+    st2, traces = nmode.update(st, X[K0:])
+    np.testing.assert_allclose(st2.U[3][K0:], Un[3][K0:], rtol=1e-5, atol=1e-7)
+    for t in traces:
+        assert [len(i) for i in t["idx"]] == [5, 4, 4, 5]
+        assert list(t["match"].perm) in ([0, 1], [1, 0])
+
+
 def test_update_stream_keeps_fit_noiseless():
     R = 2
     opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-15, max_iters=3000, seed=4)
