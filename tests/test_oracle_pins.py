@@ -573,6 +573,56 @@ def test_nmode_update_projects_back_exactly_at_order_four():
         assert list(t["match"].perm) in ([0, 1], [1, 0])
 
 
+def test_nmode_mttkrp_bruteforce_order_four():
+    """The order-N MTTKRP against explicit loops on a tiny 4-mode tensor, every mode."""
+    from oracle import nmode
+    rng = np.random.default_rng(6)
+    K, I1, I2, I3, R = 3, 4, 2, 3, 2
+    X = rng.standard_normal((K, I1, I2, I3))
+    U = [rng.standard_normal((I1, R)), rng.standard_normal((I2, R)), rng.standard_normal((I3, R)),
+         rng.standard_normal((K, R))]
+    for mode in range(4):
+        dims = (I1, I2, I3, K)
+        M = np.zeros((dims[mode], R))
+        for k, a, b, c, r in itertools.product(range(K), range(I1), range(I2), range(I3), range(R)):
+            idx = (a, b, c, k)
+            prod = X[k, a, b, c]
+            for m in range(4):
+                if m != mode:
+                    prod *= U[m][idx[m], r]
+            M[idx[mode], r] += prod
+        np.testing.assert_allclose(nmode.mttkrp(X, U, mode), M, rtol=1e-12, atol=1e-12)
+
+
+def test_nmode_cp_als_recovers_planted_order_four():
+    """Noiseless planted rank-2 4-mode tensor: the order-N CP-ALS reaches fit 1
+    and its factors match the planted ones (FMS-style cosines ~1)."""
+    from oracle import nmode
+    rng = np.random.default_rng(7)
+    R = 2
+    U = [rng.random((d, R)) for d in (7, 6, 5, 8)]
+    X = nmode.reconstruct(np.ones(R), U)
+    U0 = [rng.random(u.shape) for u in U]
+    res = nmode.cp_als(X, U0, 1e-14, 3000)
+    assert res.fit > 1 - 1e-6
+    for u, v in zip(res.U, U):
+        cos = np.abs((u / np.linalg.norm(u, axis=0)).T @ (v / np.linalg.norm(v, axis=0)))
+        assert np.allclose(np.sort(cos.max(axis=1)), 1.0, atol=1e-5)
+
+
+def test_cp_als_scale_equivariance():
+    """CP-ALS of c X from the same start: the same unit factors, lambda times c,
+    the same fit (the normal equations are homogeneous in X)."""
+    X = synth.planted_dense(12, 11, 10, 3, noise=0.01, seed=2, dtype=torch.float64).X.numpy()
+    U0 = [O.init_factor(np.arange(n), 3, m, 0, 0, O.Options()) for m, n in enumerate((12, 11, 10))]
+    a = O.cp_als(X, U0, 0.0, 15, fixed_iters=True)
+    b = O.cp_als(4.0 * X, U0, 0.0, 15, fixed_iters=True)
+    for ua, ub in zip(a.U, b.U):
+        np.testing.assert_allclose(ua, ub, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(b.lam, 4.0 * a.lam, rtol=1e-9)
+    assert abs(a.fit - b.fit) < 1e-9
+
+
 def test_update_stream_keeps_fit_noiseless():
     R = 2
     opts = O.Options(s_I=2, s_J=2, s_K=2, r=2, tol=1e-15, max_iters=3000, seed=4)
