@@ -8,8 +8,13 @@ summary MTTKRP in bfloat16 with float32 accumulation (the chosen form), the
 plain float32 path measured beside it.  A step is one sbt_update: append,
 sampling, gather, CP-ALS of the 8 summaries, match, project back and commit.
 
-One JSON line on rank 0.  `python bench.py --impl reference` times the FP64
-CPU oracle (a deliberately slow reference) on the same workload instead.
+One JSON line on rank 0.  After the timed region the FP64 oracle runs the
+first and the last timed batch from the GPU's own pre-update model
+(`oracle_check`: samples bit-exact, full-tensor fit within 1e-3, the metric's
+condition; `valid` says whether it held); its measured batch time is the CPU
+baseline.  `python bench.py --impl reference` times the FP64 CPU oracle (a
+deliberately slow reference) on the same workload instead, every step a full
+batch with its repetitions in parallel processes.
 Multi-GPU (torchrun): independent replicas, one per GPU, no data-path
 collective; value = slices of all ranks / max over ranks of the timed span.
 """
@@ -31,7 +36,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(I=1000, J=1000, K0=500, batch=50, R=10, s=5, r=8, tol=1e-6, max_iters=50, noise=0.01, seed=0)
-WORKLOAD_NAME = "dense-fp32 1000x1000x(500+50/batch) R=10 s=5 r=8"
 METRIC = "slices absorbed/sec at fit within 1e-3 of FP64; p50/p99 batch-update latency"
 UNIT = "slices/s"
 
@@ -74,7 +78,10 @@ def parse():
                     help="start every summary ALS from the old factors at the sampled rows (default: random start)")
     ap.add_argument("--als-groups", type=int, default=0,
                     help="groups the repetitions' ALS runs in (0: the library's default)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the FP64 oracle check of the first and last timed batch (and the CPU baseline it times)")
+    ap.add_argument("--oracle-first-only", action="store_true",
+                    help="check the first timed batch only against the FP64 oracle")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true",
@@ -258,80 +265,148 @@ def percentile(xs, q):
     return xs[f] + (xs[c] - xs[f]) * (k - f)
 
 
-def cpu_baseline(p, nb_used: int, reps_sample: int = 2) -> dict:
-    """The FP64 oracle on the host cores: one batch, `reps_sample` of the 8
-    repetitions timed; the batch time is the shared part plus 8 x the mean
-    repetition time."""
-    import numpy as np
+def oracle_cores():
+    """Host cores for the FP64 oracle: one worker process per repetition (at
+    most one per core), the remaining cores as BLAS threads of each."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    workers = max(1, min(WORKLOAD["r"], cores))
+    return workers, max(1, cores // workers)
+
+
+def host_store(p, K: int, workers: int, threads: int):
+    """The first K stored slices (float32) in the oracle's shared memory,
+    copied from wherever the generator put them, 64 slices at a time."""
+    from oracle.pool import PoolOracle
+    po = PoolOracle(None, workers, threads, shape=(K,) + tuple(p.X.shape[1:]), dtype="float32")
+    for k0 in range(0, K, 64):
+        k1 = min(K, k0 + 64)
+        po.X[k0:k1] = p.X[k0:k1].cpu().numpy()
+    return po
+
+
+def oracle_options(prec: str):
     from oracle import sambaten as O
     w = WORKLOAD
-    K0, b = w["K0"], w["batch"]
-    X = p.X[:K0 + b].cpu().numpy()
-    A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
-    na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
-    opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=reps_sample, tol=w["tol"], max_iters=w["max_iters"],
-                     seed=w["seed"], prec="bf16", warm_start=bool(WARM_START))
-    st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
-    t0 = time.perf_counter()
-    _, traces = O.update(st, X[K0:K0 + b])
-    total = time.perf_counter() - t0
-    rep = [t.seconds for t in traces]
-    common = total - sum(rep)
-    t_batch = common + w["r"] * (sum(rep) / len(rep))
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": b / t_batch, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one batch of {b} slices, {reps_sample} of {w['r']} repetitions timed "
-                      f"({total:.1f} s); batch time = shared part + {w['r']} x mean repetition time "
-                      f"= {t_batch:.1f} s; numpy/BLAS threads on all listed cores",
-            "seconds_per_batch": t_batch}
+    return O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
+                     seed=w["seed"], prec=prec, warm_start=bool(WARM_START))
+
+
+def oracle_check(p, batches, X0, sbt, sptr, args, fit_timed, which):
+    """The metric's gate, checked on the timed run's own batches: for each
+    batch index q in `which`, a fresh context absorbs the batches before q
+    (the same deterministic kernels as the timed context), its model is read
+    back, and then it absorbs batch q; the FP64 oracle runs Algorithm 1 on
+    batch q from that same pre-update model with all r repetitions (one
+    process each).  Reported: samples bit-exact, matches equal, the
+    full-tensor fit after batch q on both sides and its difference, and the
+    oracle's measured batch time (the CPU baseline)."""
+    import numpy as np
+    w = WORKLOAD
+    K0, b, R, r = w["K0"], w["batch"], w["R"], w["r"]
+    workers, threads = oracle_cores()
+    po = host_store(p, K0 + (max(which) + 1) * b, workers, threads)
+    out = []
+    try:
+        for q in which:
+            c = sbt.SamBaTen(X0, R, **opts_for(args.prec, sptr, q + 1))
+            for i in range(q):
+                c.update(batches[i])
+            lam, A, B, C = c.factors()
+            c.update(batches[q])
+            fit_g = c.fit()
+            samples = [[c.last_samples(rep, m) for m in range(3)] for rep in range(r)]
+            st = c.stats()
+            c.close()
+            state = po.state(K0 + q * b, lam, A, B, C, oracle_options("f64"), K_shift=K0, batch=q)
+            t0 = time.perf_counter()
+            new, traces = po.update(state, b)
+            secs = time.perf_counter() - t0
+            fit_o = po.full_fit(new)
+            same = all(np.array_equal(samples[rep][m], (t.Is, t.Js, t.Ks)[m])
+                       for rep, t in enumerate(traces) for m in range(3))
+            perm = sum(int(list(t.match.perm) == st["perm"][rep]) for rep, t in enumerate(traces))
+            rec = {"batch": q, "K_after": K0 + (q + 1) * b, "samples_bit_exact": bool(same),
+                   "matches_equal_reps": perm, "fit_gpu": fit_g, "fit_fp64_oracle": fit_o,
+                   "fit_abs_diff": abs(fit_g - fit_o), "oracle_seconds": secs,
+                   "oracle_iters": [t.als.iters for t in traces], "gpu_iters": st["iters"]}
+            if q == args.steps - 1 and fit_timed is not None:
+                rec["fit_equals_timed_context"] = fit_g == fit_timed
+            out.append(rec)
+            del state, new, traces
+    finally:
+        po.close()
+    ok = all(x["samples_bit_exact"] and x["fit_abs_diff"] <= 1e-3 for x in out)
+    return {"valid": ok, "bar": "samples bit-exact and |fit_gpu - fit_fp64| <= 1e-3 after the batch",
+            "oracle": f"FP64 oracle, {r} repetitions in {workers} processes x {threads} BLAS threads",
+            "cores": workers * threads, "batches": out}
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The FP64 oracle as it stands, timed on the host cores on the same
+    workload: each step one full batch of Algorithm 1 (all r repetitions, one
+    process each), committed, so the steps absorb the same batches as the GPU
+    arm's timed run.  The pre-existing decomposition is the planted one
+    (Section 2.2 allows a given decomposition; the oracle's own CP-ALS of
+    the 1000 x 1000 x 500 initial tensor would dominate the run).  Warm-up
+    steps run the first batch from the initial state and are discarded."""
     world, rank, local = dist_env()
     if rank != 0:
         return 0
     import numpy as np
     import torch
-    from oracle import sambaten as O
     import oracle
     oracle.build()
     w = WORKLOAD
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     p, nb = make_data(args.steps, args.warmup, dev)
     K0, b = w["K0"], w["batch"]
-    X = p.X.cpu().numpy()
+    workers, threads = oracle_cores()
+    po = host_store(p, K0 + args.steps * b, workers, threads)
     A, B, C = p.A.cpu().numpy(), p.B.cpu().numpy(), p.C[:K0].cpu().numpy()
     na, nb_, nc = (np.linalg.norm(u, axis=0) for u in (A, B, C))
-    opts = O.Options(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=1, tol=w["tol"], max_iters=w["max_iters"],
-                     seed=w["seed"], prec=args.prec, warm_start=bool(WARM_START))
-    st = O.init_state_from_factors(X[:K0], na * nb_ * nc, A / na, B / nb_, C / nc, opts)
-    # each step: one batch update of the oracle with one of the 8 repetitions
-    # (a bounded sample); the batch time is the shared part + 8 x repetition
     batch_times = []
-    for i in range(args.warmup + args.steps):
-        k0 = K0 + (i % nb) * b
-        t0 = time.perf_counter()
-        _, traces = O.update(st, X[k0:k0 + b])
-        total = time.perf_counter() - t0
-        rep = traces[0].seconds
-        if i >= args.warmup:
-            batch_times.append((total - rep) + w["r"] * rep)
+    try:
+        st = po.state(K0, na * nb_ * nc, A / na, B / nb_, C / nc, oracle_options("f64"))
+        for _ in range(args.warmup):
+            po.update(st, b)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            st, _ = po.update(st, b)
+            batch_times.append(time.perf_counter() - t0)
+        st = None
+    finally:
+        po.close()
     t = sum(batch_times)
     value = args.steps * b / t
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = workers * threads
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, **w, "prec_values": args.prec},
+            "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step one batch of {b} slices with 1 of {w['r']} repetitions "
-                                       f"run; batch time = shared part + {w['r']} x repetition time"},
+                             "sample": f"every step one full batch of {b} slices, all {w['r']} repetitions "
+                                       f"measured ({workers} processes x {threads} BLAS threads), FP64"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "latency_ms": {"p50": percentile([1e3 * x for x in batch_times], 0.5),
                            "p99": percentile([1e3 * x for x in batch_times], 0.99)}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(args) -> dict:
+    """The workload as run: the dense FP32 single-stream stream of planted
+    rank-10 slices, extended past its 10 batches when --steps asks for more."""
+    w = WORKLOAD
+    K_final = w["K0"] + args.steps * w["batch"]
+    store_gb = K_final * w["I"] * w["J"] * 4 / 1e9
+    name = (f"dense-fp32 {w['I']}x{w['J']}x({w['K0']} + {args.steps} batches of {w['batch']} = {K_final} slices) "
+            f"R={w['R']} s={w['s']} r={w['r']}")
+    if w["K0"] == 500 and args.steps > 10:
+        name += " (the 10-batch stream extended to --steps batches)"
+    return {"workload": name, **w, "batches_absorbed": args.steps, "K_final": K_final,
+            "l2": f"inputs larger than L2 ({w['batch'] * w['I'] * w['J'] * 4 / 1e6:.0f} MB batch per step, "
+                  f"{store_gb:.1f} GB resident store at the end)"}
 
 
 def run_ours(args):
@@ -467,21 +542,29 @@ def run_ours(args):
                                f"{1e3 * secs_prof / args.steps:.2f} ms per step there",
                 "kernel_hash": kh}
 
-    cpu = None
+    # the metric's gate and the CPU baseline: the FP64 oracle on the first
+    # and the last timed batch, from the GPU's own pre-update model
+    cpu, check = None, None
     if not args.no_cpu_baseline and world == 1:
+        which = sorted({0, args.steps - 1}) if not args.oracle_first_only else [0]
         try:
-            cpu = cpu_baseline(p, nb)
+            check = oracle_check(p, batches, X0, sbt, sptr, args, fit_gpu, which)
+            first = check["batches"][0]
+            cpu = {"value": b / first["oracle_seconds"], "unit": UNIT, "cores": check["cores"], "kind": "oracle",
+                   "sample": f"the first timed batch ({b} slices), all {w['r']} repetitions measured "
+                             f"({check['oracle']}), {first['oracle_seconds']:.1f} s",
+                   "seconds_per_batch": first["oracle_seconds"]}
         except Exception as e:  # report, do not fail the benchmark line
+            check = {"valid": None, "failed": f"{type(e).__name__}: {e}"}
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "valid": check.get("valid") if check else None,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, **w, "prec": args.prec, "autotuned_tiles": bool(args.autotune),
+            "config": {**workload_config(args), "prec": args.prec, "autotuned_tiles": bool(args.autotune),
                        "mode3_pass": bool(MODE3_PASS), "als_groups": ALS_GROUPS or "default",
-                       "warm_start": bool(WARM_START),
-                       "l2": "inputs larger than L2 (200 MB batch per step, 4 GB resident store)",
-                       "parallelism": f"replicas x{world}"},
+                       "warm_start": bool(WARM_START), "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},
             "fit": {"full_tensor_fit_after_steps": fit_gpu,
                     "recomputed_cp_als_fit": fit_cp,
@@ -489,7 +572,7 @@ def run_ours(args):
                     else None,
                     "planted_noise_floor": 1.0 - w["noise"],
                     "summary_fit_last_batch": stats["fit"], "als_iters_last_batch": stats["iters"]},
-            "plain_f32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "oracle_check": check, "plain_f32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "gpu_launches": head_launches, "clocks": clk}
     print(json.dumps(line), flush=True)
     if dist is not None:

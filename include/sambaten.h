@@ -456,7 +456,8 @@ sbt_status sbt_core_consistency(int32_t dtype, const void *X, int64_t K, int64_t
  * library's device memory, held by every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress), so make the first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * capture; later calls outside a capture look it up again (a device reset
+ * may move the array), calls inside a capture use the address found last.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (unordered streams or threads) race on it. */
 #define SBT_SAMPLE_NOALLOC_MAX_N 262144
 sbt_status sbt_sample_noalloc(const uint64_t *w, int64_t N, int64_t n, uint64_t seed,

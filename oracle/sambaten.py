@@ -516,78 +516,88 @@ class RepTrace:
     flags: int
 
 
-def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
-    """Algorithm 1 for one batch of new slices X_new (K_new, I, J).
-
-    Returns (new State, list of per-repetition traces)."""
+def batch_sample_sizes(state: State):
+    """Algorithm 1 step 2 on the tensor before the update: the sample sizes
+    (n_I, n_J, n_K) of Section 3.1 from the measure of importance."""
     opts = state.opts
     K_old, I, J = state.X.shape
-    K_new = X_new.shape[0]
+    return (sample_size(I, opts.s_I, state.xa), sample_size(J, opts.s_J, state.xb),
+            sample_size(K_old, opts.s_K, state.xc))
+
+
+def update_rep(state: State, X_all: np.ndarray, sizes, K_new: int, rho: int,
+               keep_summaries: bool = False) -> RepTrace:
+    """Steps 3-9 of Algorithm 1 for repetition rho: sample, gather the
+    summary, CP of the summary, shared-row normalisation, match, project
+    back.  X_all holds the K_old stored slices followed by the K_new new ones
+    (slice-major); every repetition anchors on the pre-update factors of
+    `state`, so repetitions do not depend on one another."""
+    opts = state.opts
+    nI, nJ, nK = sizes
+    K_old = X_all.shape[0] - K_new
     R = state.R
-    if X_new.shape[1:] != (I, J) or K_new < 1:
-        raise ValueError("bad batch shape")
-    if not np.all(np.isfinite(X_new)):
-        raise FloatingPointError("non-finite value in the new slices")
-    # step 2: the measure of importance of X (the tensor before the update)
-    nI = sample_size(I, opts.s_I, state.xa)
-    nJ = sample_size(J, opts.s_J, state.xb)
-    nK = sample_size(K_old, opts.s_K, state.xc)
-    X_all = np.concatenate([state.X, X_new.astype(state.X.dtype)], axis=0)
-    traces = []
-    for rho in range(opts.r):
-        t_rep = time.perf_counter()
-        flags = FLAG_SAMPLE_LT_RANK if min(nI, nJ, nK) < R else 0
-        # step 3: sample each mode without replacement
-        Is = sample_mode(state.xa, nI, opts, 0, rho, state.batch)
-        Js = sample_mode(state.xb, nJ, opts, 1, rho, state.batch)
-        Ks = sample_mode(state.xc, nK, opts, 2, rho, state.batch)
-        Kp = np.concatenate([Ks.astype(np.int64), np.arange(K_old, K_old + K_new)])
-        # step 4: the summary
-        if opts.prec == "fp8":
-            Xs = fp8_summary_values(summary(X_all, Is, Js, Kp), slice_amax(X_all)[Kp])
-        else:
-            Xs = summary_values(summary(X_all, Is, Js, Kp), opts.prec)
-        # step 5: CP of the summary, from random factors (the paper leaves
-        # the start open), or warm: the old factors at the sampled rows, the
-        # new slices' rows of C' zero (their first mode-3 update fills them)
-        # GetRank (Section 3.2, Algorithm 2): the summary's rank R_new <= R
-        R_s, p_rank = R, None
-        if opts.get_rank:
-            R_s, p_rank = get_rank(Xs, R, (Is, Js, Kp), opts, rho, state.batch)
-        if opts.warm_start and not opts.get_rank:
-            U0 = [state.A[Is].copy(), state.B[Js].copy(),
-                  np.concatenate([state.C[Ks], np.zeros((K_new, R))], axis=0)]
-        else:
-            U0 = [init_factor(Is, R_s, 0, rho, state.batch, opts),
-                  init_factor(Js, R_s, 1, rho, state.batch, opts),
-                  init_factor(Kp, R_s, 2, rho, state.batch, opts)]
-        res = cp_als(Xs, U0, opts.tol, opts.max_iters, opts.fixed_iters)
-        if opts.prec == "bf16" and opts.refine_sweeps > 0:
-            # refinement: continue the same ALS from its factors for a fixed
-            # number of iterations on the split (hi + lo) summary
-            Xr = split_bf16(summary(X_all, Is, Js, Kp))
-            ref = cp_als(Xr, res.U, opts.tol, opts.refine_sweeps, fixed_iters=True)
-            res = ALSResult(U=ref.U, lam=ref.lam, iters=res.iters, fit=ref.fit, flags=res.flags | ref.flags)
-        flags |= res.flags
-        # step 6: normalise over shared rows
-        Us, lam_s, f = normalize_shared(res.U, res.lam, nK)
-        flags |= f
-        # step 7: match against the anchors (old factors at the sampled rows)
-        old_rows = [state.A[Is], state.B[Js], state.C[Ks]]
-        mt = match([Us[0], Us[1], Us[2][:nK]], old_rows)
-        # steps 8-9: project back
-        Cnew, props, lam_est, matched = project_back(Us, lam_s, state.lam, mt, nK, K_new,
-                                                     old_rows, [Is, Js, Ks])
-        traces.append(RepTrace(Is=Is, Js=Js, Ks=Ks, als=res, Us=Us, lam_s=lam_s,
-                               match=mt, Cnew=Cnew, flags=flags))
-        traces[-1].props = props
-        traces[-1].lam_est = lam_est
-        traces[-1].matched = matched
-        traces[-1].R_new = R_s
-        traces[-1].p_rank = p_rank
-        if keep_summaries:
-            traces[-1].Xs = Xs
-        traces[-1].seconds = time.perf_counter() - t_rep
+    t_rep = time.perf_counter()
+    flags = FLAG_SAMPLE_LT_RANK if min(nI, nJ, nK) < R else 0
+    # step 3: sample each mode without replacement
+    Is = sample_mode(state.xa, nI, opts, 0, rho, state.batch)
+    Js = sample_mode(state.xb, nJ, opts, 1, rho, state.batch)
+    Ks = sample_mode(state.xc, nK, opts, 2, rho, state.batch)
+    Kp = np.concatenate([Ks.astype(np.int64), np.arange(K_old, K_old + K_new)])
+    # step 4: the summary
+    if opts.prec == "fp8":
+        Xs = fp8_summary_values(summary(X_all, Is, Js, Kp), slice_amax(X_all[Kp]))
+    else:
+        Xs = summary_values(summary(X_all, Is, Js, Kp), opts.prec)
+    # step 5: CP of the summary, from random factors (the paper leaves
+    # the start open), or warm: the old factors at the sampled rows, the
+    # new slices' rows of C' zero (their first mode-3 update fills them)
+    # GetRank (Section 3.2, Algorithm 2): the summary's rank R_new <= R
+    R_s, p_rank = R, None
+    if opts.get_rank:
+        R_s, p_rank = get_rank(Xs, R, (Is, Js, Kp), opts, rho, state.batch)
+    if opts.warm_start and not opts.get_rank:
+        U0 = [state.A[Is].copy(), state.B[Js].copy(),
+              np.concatenate([state.C[Ks], np.zeros((K_new, R))], axis=0)]
+    else:
+        U0 = [init_factor(Is, R_s, 0, rho, state.batch, opts),
+              init_factor(Js, R_s, 1, rho, state.batch, opts),
+              init_factor(Kp, R_s, 2, rho, state.batch, opts)]
+    res = cp_als(Xs, U0, opts.tol, opts.max_iters, opts.fixed_iters)
+    if opts.prec == "bf16" and opts.refine_sweeps > 0:
+        # refinement: continue the same ALS from its factors for a fixed
+        # number of iterations on the split (hi + lo) summary
+        Xr = split_bf16(summary(X_all, Is, Js, Kp))
+        ref = cp_als(Xr, res.U, opts.tol, opts.refine_sweeps, fixed_iters=True)
+        res = ALSResult(U=ref.U, lam=ref.lam, iters=res.iters, fit=ref.fit, flags=res.flags | ref.flags)
+    flags |= res.flags
+    # step 6: normalise over shared rows
+    Us, lam_s, f = normalize_shared(res.U, res.lam, nK)
+    flags |= f
+    # step 7: match against the anchors (old factors at the sampled rows)
+    old_rows = [state.A[Is], state.B[Js], state.C[Ks]]
+    mt = match([Us[0], Us[1], Us[2][:nK]], old_rows)
+    # steps 8-9: project back
+    Cnew, props, lam_est, matched = project_back(Us, lam_s, state.lam, mt, nK, K_new,
+                                                 old_rows, [Is, Js, Ks])
+    t = RepTrace(Is=Is, Js=Js, Ks=Ks, als=res, Us=Us, lam_s=lam_s, match=mt, Cnew=Cnew, flags=flags)
+    t.props = props
+    t.lam_est = lam_est
+    t.matched = matched
+    t.R_new = R_s
+    t.p_rank = p_rank
+    if keep_summaries:
+        t.Xs = Xs
+    t.seconds = time.perf_counter() - t_rep
+    return t
+
+
+def commit(state: State, X_all: np.ndarray, K_new: int, traces) -> State:
+    """Steps 10-13 of Algorithm 1: average the repetitions' new rows of C
+    (in repetition order), fill zero entries of the old factors with the mean
+    of the proposals, keep or average lambda, fold the new slices into the
+    measure of importance.  The new State holds X_all as its slices."""
+    opts = state.opts
+    R = state.R
     # step 10 and 12: average C_new over the repetitions (with GetRank, over
     # those that matched the component; none: zero rows), append to C
     Cnew = np.zeros((K_new, R))
@@ -613,11 +623,29 @@ def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
             est = est + t.lam_est
         lam = np.where(cnt > 0, 0.5 * (lam + est / np.where(cnt > 0, cnt, 1.0)), lam)
     # fold the new slices into the measure of importance
-    qa, qb, qc = marginals(X_new, state.S)
-    new = State(X=X_all, A=A, B=B, C=np.concatenate([C, Cnew], axis=0), lam=lam, S=state.S,
-                xa=state.xa + qa, xb=state.xb + qb, xc=np.concatenate([state.xc, qc]),
-                batch=state.batch + 1, opts=state.opts)
-    return new, traces
+    qa, qb, qc = marginals(X_all[X_all.shape[0] - K_new:], state.S)
+    return State(X=X_all, A=A, B=B, C=np.concatenate([C, Cnew], axis=0), lam=lam, S=state.S,
+                 xa=state.xa + qa, xb=state.xb + qb, xc=np.concatenate([state.xc, qc]),
+                 batch=state.batch + 1, opts=state.opts)
+
+
+def update(state: State, X_new: np.ndarray, keep_summaries: bool = False):
+    """Algorithm 1 for one batch of new slices X_new (K_new, I, J): step 2
+    (sample sizes), steps 3-9 per repetition (update_rep), steps 10-13
+    (commit).
+
+    Returns (new State, list of per-repetition traces)."""
+    K_old, I, J = state.X.shape
+    K_new = X_new.shape[0]
+    if X_new.shape[1:] != (I, J) or K_new < 1:
+        raise ValueError("bad batch shape")
+    if not np.all(np.isfinite(X_new)):
+        raise FloatingPointError("non-finite value in the new slices")
+    # step 2: the measure of importance of X (the tensor before the update)
+    sizes = batch_sample_sizes(state)
+    X_all = np.concatenate([state.X, X_new.astype(state.X.dtype)], axis=0)
+    traces = [update_rep(state, X_all, sizes, K_new, rho, keep_summaries) for rho in range(state.opts.r)]
+    return commit(state, X_all, K_new, traces), traces
 
 
 # --------------------------------------------------------------------------

@@ -13,7 +13,8 @@
 // is only a stand-in for the symbol, not a device address.  The first call on
 // each device therefore looks the address up with cudaGetSymbolAddress (with
 // that device current) and caches it; that first call should come before any
-// stream capture.  All calls share the array and it keeps the last call's
+// stream capture.  Later calls outside a capture look it up again, so the
+// cache never outlives a device reset.  All calls share the array and it keeps the last call's
 // contents, so the status word is cleared before every launch; calls that
 // overlap on the GPU (unordered streams or threads) race on the array.
 #include "sambaten.h"
@@ -34,14 +35,21 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
-cudaError_t scratch_address(unsigned char **out) {
+// Device address of the scratch array on the current device.  Outside stream
+// capture it is looked up again on every call (cheap once the module is
+// loaded), so a context that was reset and recreated, with the array at a new
+// address, is never handed a stale pointer; inside a capture the address
+// cached by an earlier call is used.
+cudaError_t scratch_address(cudaStream_t st, unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sample_scratch);
         if (e != cudaSuccess) return e;
@@ -71,7 +79,7 @@ extern "C" sbt_status sbt_sample_noalloc(const uint64_t *w, int64_t N, int64_t n
     }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    cudaError_t e = scratch_address(st, &base);
     if (e != cudaSuccess) {
         sbt::set_last_error(std::string("sbt_sample_noalloc: scratch address: ") + cudaGetErrorString(e));
         return SBT_E_CUDA;

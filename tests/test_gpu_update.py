@@ -228,16 +228,19 @@ def test_zero_entries_filled(sbt):
     lam, A, B, C0 = unit_factors(A, B, C[:20])
     A = A.copy()
     B = B.copy()
+    C0 = C0.copy()
     A[3, 1] = 0.0
     A[10, 2] = 0.0
     B[4, 0] = 0.0
+    C0[6, 2] = 0.0  # an old row of C: the mode-3 fill (every old slice is sampled at s_K = 1)
     ctx, ost = _pair(sbt, X, 20, 3, (lam, A, B, C0), prec="f64", s_I=1, s_J=1, s_K=1, r=2, fixed_iters=1,
                      max_iters=25)
     ost2, traces = O.update(ost, X[20:28])
     ctx.update(torch.from_numpy(X[20:28]).cuda())
     _check_update(ctx, ost2, traces, ftol=1e-7)
-    _, Ag, Bg, _ = ctx.factors()
-    assert Ag[3, 1] != 0.0 and Bg[4, 0] != 0.0
+    _, Ag, Bg, Cg = ctx.factors()
+    assert Ag[3, 1] != 0.0 and Bg[4, 0] != 0.0 and Cg[6, 2] != 0.0
+    assert abs(Cg[6, 2] - ost2.C[6, 2]) <= 1e-7 * abs(ost2.C[6, 2])
 
 
 def test_zero_slices_are_never_sampled(sbt):

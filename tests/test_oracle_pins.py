@@ -642,12 +642,18 @@ def test_update_zero_entries_filled_by_projection():
     st, X, (A, B, Cn, lam) = _planted_state(12, 10, 8, R, opts, Ktot=12, seed=5)
     st.A[3, 1] = 0.0
     st.B[4, 0] = 0.0
+    st.C[5, 1] = 0.0
     st2, _ = O.update(st, X[8:12])
     np.testing.assert_allclose(st2.A[3, 1], A[3, 1], rtol=1e-4)
     np.testing.assert_allclose(st2.B[4, 0], B[4, 0], rtol=1e-4)
+    # an old row of C (mode 3: every old slice is sampled at s_K = 1)
+    np.testing.assert_allclose(st2.C[5, 1], Cn[5, 1], rtol=1e-4)
     mask = np.ones_like(st.A, bool)
     mask[3, 1] = False
     assert np.array_equal(st2.A[mask], st.A[mask])
+    maskc = np.ones_like(st.C, bool)
+    maskc[5, 1] = False
+    assert np.array_equal(st2.C[:8][maskc], st.C[maskc])
 
 
 def test_update_lambda_modes():
@@ -720,3 +726,36 @@ def test_fp8_update_close_to_float64_update():
         fits[prec] = O.full_fit(st.X, st.lam, st.A, st.B, st.C)
     assert fits["f64"] > 0.85
     assert abs(fits["fp8"] - fits["f64"]) < 0.05
+
+
+def test_pool_oracle_equals_serial_update():
+    """The oracle with its repetitions in worker processes (the benchmark's
+    CPU baseline) gives the serial update's samples, matches and factors."""
+    from oracle.pool import PoolOracle
+    R = 3
+    opts = O.Options(s_I=2, s_J=2, s_K=2, r=4, tol=1e-7, max_iters=40, seed=6)
+    st, X, _ = _planted_state(30, 26, 20, R, opts, Ktot=32, seed=9)
+    st_s, tr_s = O.update(st, X[20:26])
+    st_s2, tr_s2 = O.update(st_s, X[26:32])
+    with PoolOracle(X.astype(np.float64), workers=2, threads=1) as po:
+        sp = po.state(20, st.lam, st.A, st.B, st.C, opts)
+        assert np.array_equal(sp.xa, st.xa) and np.array_equal(sp.xc, st.xc)
+        sp2, tr_p = po.update(sp, 6)
+        sp3, tr_p2 = po.update(sp2, 6)
+        f_pool = po.full_fit(sp3)
+        # a state rebuilt from the stored slices at K = 26 (marginals by chunks)
+        sq = po.state(26, st_s.lam, st_s.A, st_s.B, st_s.C, opts, K_shift=20, batch=1)
+        sq_xa, sq_xb, sq_xc, sq_S = sq.xa.copy(), sq.xb.copy(), sq.xc.copy(), sq.S
+        sp3 = O.State(X=np.array(sp3.X), A=sp3.A, B=sp3.B, C=sp3.C, lam=sp3.lam, S=sp3.S, xa=sp3.xa, xb=sp3.xb,
+                      xc=sp3.xc, batch=sp3.batch, opts=sp3.opts)
+        del sp, sp2, sq
+    for a, b in zip(tr_s + tr_s2, tr_p + tr_p2):
+        assert np.array_equal(a.Is, b.Is) and np.array_equal(a.Ks, b.Ks)
+        assert np.array_equal(a.match.perm, b.match.perm)
+        assert a.als.iters == b.als.iters
+    for u, v in ((st_s2.A, sp3.A), (st_s2.B, sp3.B), (st_s2.C, sp3.C), (st_s2.lam, sp3.lam)):
+        np.testing.assert_allclose(v, u, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(st_s2.xc, sp3.xc) and sp3.batch == 2
+    assert abs(f_pool - O.full_fit(st_s2.X, st_s2.lam, st_s2.A, st_s2.B, st_s2.C)) < 1e-12
+    assert sq_S == st_s.S and np.array_equal(sq_xa, st_s.xa) and np.array_equal(sq_xb, st_s.xb)
+    assert np.array_equal(sq_xc, st_s.xc)
