@@ -119,6 +119,20 @@ typedef struct {
                               the old factors at the sampled rows, A(I_s), B(J_s), C(K_s), with
                               the new slices' rows of C' zero; it then converges in a few
                               iterations and keeps the component order */
+    int32_t get_rank;      /* 1: quality control of Section 3.2 (Algorithm 2, GetRank) on every
+                              summary: for each candidate rank i = 1..R and trial t <
+                              get_rank_trials, a CP-ALS of the summary at rank i from Philox
+                              uniforms (counter (x, r | mode << 8 | rep << 12 | t << 20, batch, 3)),
+                              scored by its core consistency (sbt_core_consistency); R_new = the
+                              largest i whose best trial reaches get_rank_threshold (1 if none).
+                              The summary ALS then runs at rank R_new from the usual start, its
+                              components are matched to R_new distinct old components, and a new
+                              row of C averages each component over the repetitions that matched
+                              it (none: zero).  MTTKRP on the CUDA cores; SBT_PREC_FP8,
+                              refine_sweeps and COO contexts are rejected (SBT_E_INVALID).
+                              0 (default): every summary at rank R */
+    int32_t get_rank_trials;   /* GetRank decompositions per candidate rank (Algorithm 2's `it`); 0: 2 */
+    double get_rank_threshold; /* core consistency a candidate rank must reach; 0: 90 */
 } sbt_options;
 
 typedef struct {
@@ -129,7 +143,8 @@ typedef struct {
     int32_t iters[SBT_MAX_REPS];     /* ALS iterations per repetition */
     double fit[SBT_MAX_REPS];        /* summary fit at the last ALS iteration */
     double min_score[SBT_MAX_REPS];  /* smallest |G1|*|G2|*|G3| over matched pairs */
-    int32_t perm[SBT_MAX_REPS][SBT_MAX_RANK]; /* summary component -> old component */
+    int32_t perm[SBT_MAX_REPS][SBT_MAX_RANK]; /* summary component -> old component (-1 past rank[rep]) */
+    int32_t rank[SBT_MAX_REPS];      /* components of each summary: R, or R_new with get_rank */
 } sbt_update_stats;
 
 /* Library version string. */
@@ -248,7 +263,9 @@ sbt_status sbt_last_summary(const sbt_ctx *ctx, int32_t rep, double *out, int64_
                             int64_t dims[3]);
 
 /* Summary factors of repetition rep after the shared-row normalisation
- * (Alg. 1 step 6): lambda' (R), A' (n_I x R), B' (n_J x R), C' (Kp x R). */
+ * (Alg. 1 step 6): lambda' (R), A' (n_I x R), B' (n_J x R), C' (Kp x R).
+ * With get_rank the summary has rank[rep] components: columns beyond it
+ * (and their lambda') are zero. */
 sbt_status sbt_last_summary_factors(const sbt_ctx *ctx, int32_t rep, double *lambda,
                                     double *A, double *B, double *C);
 

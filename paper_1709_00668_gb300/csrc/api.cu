@@ -191,6 +191,8 @@ struct sbt_ctx {
     Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     Buf ymem;                           // mode-2 pass products for the mode-3 MTTKRP (mode3_pass 0)
+    Buf grscr, gcc, rnew;               // GetRank: CorConDia scratch, scores + status words, R_new per repetition
+    std::vector<int> last_rank;         // components of each summary of the last update
     Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
     // COO contexts (sbt_init_coo): nonzeros grouped by slice, and the summary workspace
     bool coo = false;
@@ -267,6 +269,9 @@ extern "C" sbt_status sbt_default_options(sbt_options *o) {
     o->max_batch = 0;
     o->cuda_stream = nullptr;
     o->check_every = 4;
+    o->get_rank = 0;
+    o->get_rank_trials = 2;
+    o->get_rank_threshold = 90.0;
     return SBT_OK;
 }
 
@@ -283,6 +288,11 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (o->mode3_pass != 0 && o->mode3_pass != 1) return fail(SBT_E_INVALID, "mode3_pass must be 0 or 1");
     if (o->als_groups < 0 || o->als_groups > SBT_MAX_REPS) return fail(SBT_E_INVALID, "als_groups out of [0, SBT_MAX_REPS]");
     if (o->warm_start != 0 && o->warm_start != 1) return fail(SBT_E_INVALID, "warm_start must be 0 or 1");
+    if (o->get_rank != 0 && o->get_rank != 1) return fail(SBT_E_INVALID, "get_rank must be 0 or 1");
+    if (o->get_rank_trials < 0 || o->get_rank_trials > 16) return fail(SBT_E_INVALID, "get_rank_trials out of [0, 16]");
+    if (!std::isfinite(o->get_rank_threshold)) return fail(SBT_E_INVALID, "get_rank_threshold must be finite");
+    if (o->get_rank && (o->prec == SBT_PREC_FP8 || o->refine_sweeps > 0))
+        return fail(SBT_E_INVALID, "get_rank takes float64, float32 or bfloat16 summaries without refinement");
     return SBT_OK;
 }
 
@@ -356,10 +366,10 @@ struct Sizer {
 static int als_elem(const sbt_ctx *c) { return c->elem == 3 ? 2 : c->elem; }
 
 static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], int ldj, int nK, int elem,
-                      int max_iters) {
+                      int max_iters, int rank = 0) {
     std::memset(&d, 0, sizeof(d));
     d.nrep = nrep;
-    d.R = c->R;
+    d.R = rank > 0 ? rank : c->R;
     d.n[0] = n[0];
     d.n[1] = n[1];
     d.n[2] = n[2];
@@ -369,10 +379,10 @@ static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.tol = c->opt.tol;
     d.max_iters = max_iters;
     d.fixed_iters = c->opt.fixed_iters;
-    d.pr = elem == 0 ? c->R : (c->R + 3) / 4 * 4;
+    d.pr = elem == 0 ? d.R : (d.R + 3) / 4 * 4;
     choose_tiles(d, c->num_sms);
     const int nmax = std::max(n[0], std::max(n[1], n[2]));
-    d.mrs = (long long)nmax * c->R;
+    d.mrs = (long long)nmax * d.R;
     d.prs = partial_elems(d);
     d.tchunks = (nmax + TAIL_ROWS - 1) / TAIL_ROWS;
 }
@@ -565,6 +575,7 @@ static AlsDesc group_desc(const AlsDesc &d, int rep0, int ng, size_t xbytes_per_
     const size_t tfs = esize_tf(d.elem);
     const long long r0 = rep0;
     s.nrep = ng;
+    s.rep0 = d.rep0 + rep0;
     if (d.X) s.X = (const char *)d.X + r0 * xbytes_per_rep;
     for (int m = 0; m < 3; ++m) s.U[m] = (char *)d.U[m] + r0 * d.n[m] * R * tfs;
     if (d.M) s.M = d.M + r0 * d.mrs;
@@ -1067,6 +1078,11 @@ static size_t update_part_bytes(const sbt_ctx *c, const UpdShape &u, bool bound)
         const int n[3] = {u.nI, u.nJ, Kp};
         als_shape(c, d, r, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
         best = std::max<size_t>(best, (size_t)r * d.prs * esize_tf(als_elem(c)));
+        if (c->opt.get_rank) {  // GetRank's final ALS runs one repetition at a time
+            AlsDesc d1;
+            als_shape(c, d1, 1, n, u.ldj, u.nK, als_elem(c), c->opt.max_iters);
+            best = std::max<size_t>(best, (size_t)d1.prs * esize_tf(als_elem(c)));
+        }
         if (u.tc) {
             tc_group_partials(c, d, als_group_count(c, r, true));
             best = std::max<size_t>(best, (size_t)r * d.prs * 4);
@@ -1098,6 +1114,16 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
         TRY(z.need(c->rowsq2, (size_t)r * u.Kp * u.nI * 8));
         TRY(z.need(c->iters_main, (size_t)r * 4));
     }
+    if (c->opt.get_rank) {
+        // CorConDia scratch of one candidate and the widened factors; scores
+        // and status words of every (repetition, rank, trial); R_new
+        const int T = c->opt.get_rank_trials > 0 ? c->opt.get_rank_trials : 2;
+        const size_t nd = core_consistency_scratch_doubles(u.Kp, u.nI, u.nJ, R) +
+                          (size_t)(u.nI + u.nJ + u.Kp) * R;
+        TRY(z.need(c->grscr, nd * 8));
+        TRY(z.need(c->gcc, (size_t)r * R * T * (8 + 4)));
+        TRY(z.need(c->rnew, (size_t)r * 4));
+    }
     const size_t pmax = (size_t)u.samp_stride;
     TRY(z.need(c->nu, (size_t)r * 3 * R * 8));
     TRY(z.need(c->cnew, (size_t)r * u.K_new * R * 8));
@@ -1122,6 +1148,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
             &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale, &c->ymem,
+            &c->grscr, &c->gcc, &c->rnew,
             &c->si, &c->sj, &c->sv, &c->sptr, &c->cin_i, &c->cin_j, &c->cin_k, &c->cin_v, &c->ccnt, &c->cfill,
             &c->cmax, &c->posI, &c->posJ, &c->gcnt, &c->goff, &c->gtot, &c->vmax, &c->fexp, &c->eii, &c->ejj,
             &c->ekk, &c->ev, &c->perm1, &c->perm2, &c->rp1, &c->rp2, &c->gc1, &c->gc2, &c->gf1, &c->gf2};
@@ -1209,7 +1236,8 @@ extern "C" sbt_status sbt_reserve(sbt_ctx *c, int64_t K_max, int64_t K_new_max) 
 // Steps 5 and 6 of an update (shared-row normalisation, matching, project
 // back, commit) and its statistics; shared by the dense and the COO updates.
 static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int K_new, int nI, int nJ, int nK,
-                               long long samp_stride, int ldj, bool refined, bool no_refine) {
+                               long long samp_stride, int ldj, bool refined, bool no_refine,
+                               const std::vector<int> *rnew = nullptr) {
     const int R = c->R, r = c->opt.r;
     // 5. normalise, match, project back; 6. commit
     const int pmax = (int)samp_stride;
@@ -1249,6 +1277,7 @@ static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int 
     m.dxb = c->dxb.as<unsigned long long>();
     m.xc_new = c->xc_new.as<unsigned long long>();
     m.status = c->status.as<DevStatus>();
+    m.rnew = rnew ? c->rnew.as<int>() : nullptr;
     CK(launch_match(m, c->stream));
     CK(launch_precommit(m, c->stream));
     CK(launch_commit(m, c->stream));
@@ -1297,7 +1326,11 @@ static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int 
     off += (size_t)r * 4;
     const int *pm = (const int *)(hb + off);
     if (no_refine) st.flags |= SBT_FLAG_NO_REFINE;
+    if (std::min(nI, std::min(nJ, nK)) < R) st.flags |= SBT_FLAG_SAMPLE_LT_RANK;
+    c->last_rank.assign(r, R);
+    if (rnew) c->last_rank = *rnew;
     for (int q = 0; q < r; ++q) {
+        st.rank[q] = c->last_rank[q];
         st.iters[q] = it[q];
         st.fit[q] = ft[q];
         st.min_score[q] = ms[q];
@@ -1311,6 +1344,110 @@ static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int 
     c->last_Knew = K_new;
     c->last_ldj = ldj;
     c->last_samp_stride = samp_stride;
+    return SBT_OK;
+}
+
+// The rank-dependent fields of a descriptor (tiles, partial and M strides,
+// tail chunks) for rank `rank`, its pointers kept.
+static void set_rank(const sbt_ctx *c, AlsDesc &d, int rank) {
+    AlsDesc t;
+    als_shape(c, t, d.nrep, d.n, d.ldj, d.nK, d.elem, d.max_iters, rank);
+    d.R = t.R;
+    d.pr = t.pr;
+    d.mrs = t.mrs;
+    d.prs = t.prs;
+    d.tchunks = t.tchunks;
+    d.spc = t.spc;
+    d.nks = t.nks;
+    d.nib = t.nib;
+    d.jc = t.jc;
+    d.rows_per = t.rows_per;
+    d.nrs = t.nrs;
+    d.cols = t.cols;
+    for (int m = 0; m < 3; ++m) d.P[m] = t.P[m];
+}
+
+// GetRank (Section 3.2, Algorithm 2) on the r summaries, then step 5 of
+// Algorithm 1 at each repetition's estimated rank.  For every trial t and
+// candidate rank i = 1..R: one batched CP-ALS of all r summaries at rank i
+// from trial t's Philox start (CUDA-core MTTKRP), then the core consistency
+// (float64) of every repetition's model.  R_new(rho) = the largest rank whose
+// best trial reaches the threshold (1 if none; a candidate whose factor Gram
+// is singular does not reach it).  The summary ALS of repetition rho then
+// runs alone at rank R_new(rho) from the usual start, its factors in the
+// repetition's n x R slot as rows of R_new(rho) values.
+static sbt_status get_rank_als(sbt_ctx *c, const UpdShape &u, const AlsDesc &d_full, std::vector<int> &rnew) {
+    const int R = c->R, r = c->opt.r;
+    const int T = c->opt.get_rank_trials > 0 ? c->opt.get_rank_trials : 2;
+    const double thr = c->opt.get_rank_threshold != 0.0 ? c->opt.get_rank_threshold : 90.0;
+    const int elem = als_elem(c);
+    const int n[3] = {u.nI, u.nJ, u.Kp};
+    const size_t xes = esize_elem(c->elem);
+    const size_t nslots = (size_t)r * R * T;
+    double *cc = c->gcc.as<double>();
+    int *cst = reinterpret_cast<int *>(cc + nslots);
+    CK(cudaMemsetAsync(cst, 0, nslots * 4, c->stream));
+    double *scr = c->grscr.as<double>();
+    const size_t nd = core_consistency_scratch_doubles(u.Kp, u.nI, u.nJ, R);
+    double *F64[3] = {scr + nd, scr + nd + (size_t)u.nI * R, scr + nd + (size_t)(u.nI + u.nJ) * R};
+    const int *samples = c->samples.as<int>();
+    const double *rowsq = c->rowsq.as<double>();
+    for (int t = 0; t < T; ++t) {
+        for (int i = 1; i <= R; ++i) {
+            AlsDesc dc;
+            als_shape(c, dc, r, n, u.ldj, u.nK, elem, c->opt.max_iters, i);
+            TRY(als_bind(c, dc, c->Xs.p, u.xrs));
+            WarmStart ws;
+            ws.trial = t;
+            CK(launch_als_prepare(dc, samples, u.samp_stride, (int)u.K_old, false, c->opt.seed, c->opt.stream_id,
+                                  c->batch, rowsq, c->stream, ws));
+            TRY(run_als(c, dc, c->opt.max_iters));
+            for (int rho = 0; rho < r; ++rho) {
+                const double *Fd[3];
+                for (int m = 0; m < 3; ++m) {
+                    const long long cnt = (long long)n[m] * i;
+                    if (elem == 0) {
+                        Fd[m] = (const double *)dc.U[m] + rho * cnt;
+                    } else {
+                        CK(launch_widen((const float *)dc.U[m] + rho * cnt, F64[m], cnt, c->stream));
+                        Fd[m] = F64[m];
+                    }
+                }
+                const size_t slot = ((size_t)rho * R + (i - 1)) * T + t;
+                CK(launch_core_consistency(elem, (const char *)c->Xs.p + (size_t)rho * u.xrs * xes, u.Kp, u.nI,
+                                           u.nJ, u.ldj, dc.lam + (size_t)rho * i, Fd[0], Fd[1], Fd[2], i, scr,
+                                           cst + slot, cc + slot, c->stream));
+            }
+        }
+    }
+    std::vector<double> h(nslots);
+    std::vector<int> hs(nslots);
+    CK(cudaMemcpyAsync(h.data(), cc, nslots * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hs.data(), cst, nslots * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    settle_als_counts(c);
+    rnew.assign(r, 1);
+    for (int rho = 0; rho < r; ++rho)
+        for (int i = 1; i <= R; ++i) {
+            double best = -INFINITY;
+            for (int t = 0; t < T; ++t) {
+                const size_t slot = ((size_t)rho * R + (i - 1)) * T + t;
+                if (!hs[slot] && std::isfinite(h[slot])) best = std::max(best, h[slot]);
+            }
+            if (best >= thr) rnew[rho] = i;
+        }
+    CK(cudaMemcpyAsync(c->rnew.p, rnew.data(), (size_t)r * 4, cudaMemcpyHostToDevice, c->stream));
+    // the summary ALS of each repetition at its rank (the partial sums are
+    // scratch of one run, so every run takes them from the start of the buffer)
+    for (int rho = 0; rho < r; ++rho) {
+        AlsDesc d1 = group_desc(d_full, rho, 1, (size_t)u.xrs * xes);
+        set_rank(c, d1, rnew[rho]);
+        d1.part = c->part.p;
+        CK(launch_als_prepare(d1, samples + (size_t)rho * 3 * u.samp_stride, u.samp_stride, (int)u.K_old, false,
+                              c->opt.seed, c->opt.stream_id, c->batch, rowsq + (size_t)rho * u.Kp * u.nI,
+                              c->stream, WarmStart{}));
+        TRY(run_als(c, d1, c->opt.max_iters));
+    }
     return SBT_OK;
 }
 
@@ -1333,6 +1470,8 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         TRY(size_update(c, u, false, z));
     }
     if (c->elem == 3 && !u.tc) return fail(SBT_E_INVALID, "float8 summaries need the tensor-core MTTKRP (R <= 32)");
+    if (c->opt.get_rank && (c->elem == 3 || c->opt.refine_sweeps > 0))
+        return fail(SBT_E_INVALID, "get_rank takes float64, float32 or bfloat16 summaries without refinement");
     const int nI = u.nI, nJ = u.nJ, nK = u.nK, Kp = u.Kp, ldj = u.ldj;
     const long long samp_stride = u.samp_stride, key_stride = u.key_stride, xrs = u.xrs;
     // 1. append + marginal deltas
@@ -1411,7 +1550,12 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     TRY(als_bind(c, d, c->Xs.p, xrs));
     // bfloat16 summaries: tensor-core MTTKRP over the summary and its transposed copy
     TcPlan &tc = c->tc;
-    tc.on = u.tc;
+    tc.on = u.tc && !c->opt.get_rank;
+    if (c->opt.get_rank) {  // Section 3.2: the rank of every summary first (Algorithm 2)
+        std::vector<int> rn;
+        TRY(get_rank_als(c, u, d, rn));
+        return match_commit(c, d, K_old, K_new, nI, nJ, nK, samp_stride, ldj, false, false, &rn);
+    }
     if (tc.on) {
         const int ldi = u.ldi;
         CK(make_summary_tmap(&tc.m1, c->Xs.p, nJ, nI, ldj, (long long)r * Kp, c->elem == 3));
@@ -1621,21 +1765,25 @@ extern "C" sbt_status sbt_last_summary_factors(const sbt_ctx *c, int32_t rep, do
     std::vector<double> nu(3 * R), ls(R);
     CK(cudaMemcpy(nu.data(), c->nu.as<double>() + (size_t)rep * 3 * R, 3 * R * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ls.data(), c->lam_s.as<double>() + (size_t)rep * R, R * 8, cudaMemcpyDeviceToHost));
+    // the repetition's n x R slot holds rows of Rs values (Rs < R with GetRank)
+    const int Rs = rep < (int)c->last_rank.size() ? c->last_rank[rep] : R;
     double *outs[3] = {A, B, C};
     for (int q = 0; q < 3; ++q) {
         if (!outs[q]) continue;
-        const size_t cnt = (size_t)n[q] * R;
+        const size_t slot = (size_t)n[q] * R, cnt = (size_t)n[q] * Rs;
+        std::vector<double> v(cnt);
         if (c->elem == 0) {
-            CK(cudaMemcpy(outs[q], c->U[q].as<double>() + (size_t)rep * cnt, cnt * 8, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(v.data(), c->U[q].as<double>() + (size_t)rep * slot, cnt * 8, cudaMemcpyDeviceToHost));
         } else {
             std::vector<float> f(cnt);
-            CK(cudaMemcpy(f.data(), c->U[q].as<float>() + (size_t)rep * cnt, cnt * 4, cudaMemcpyDeviceToHost));
-            for (size_t e = 0; e < cnt; ++e) outs[q][e] = f[e];
+            CK(cudaMemcpy(f.data(), c->U[q].as<float>() + (size_t)rep * slot, cnt * 4, cudaMemcpyDeviceToHost));
+            for (size_t e = 0; e < cnt; ++e) v[e] = f[e];
         }
-        for (size_t e = 0; e < cnt; ++e) outs[q][e] /= nu[q * R + e % R];
+        for (int x = 0; x < n[q]; ++x)
+            for (int a = 0; a < R; ++a) outs[q][(size_t)x * R + a] = a < Rs ? v[(size_t)x * Rs + a] / nu[q * R + a] : 0.0;
     }
     if (lambda)
-        for (int a = 0; a < R; ++a) lambda[a] = ls[a] * nu[a] * nu[R + a] * nu[2 * R + a];
+        for (int a = 0; a < R; ++a) lambda[a] = a < Rs ? ls[a] * nu[a] * nu[R + a] * nu[2 * R + a] : 0.0;
     return SBT_OK;
 }
 
@@ -1958,6 +2106,7 @@ extern "C" sbt_status sbt_init_coo_factors(const sbt_coo *X0, int32_t R, const d
 extern "C" sbt_status sbt_update_coo(sbt_ctx *c, const sbt_coo *X) {
     if (!c) return fail(SBT_E_INVALID, "null context");
     if (!c->coo) return fail(SBT_E_INVALID, "not a COO context (sbt_update takes dense slices)");
+    if (c->opt.get_rank) return fail(SBT_E_INVALID, "get_rank takes dense contexts");
     TRY(check_coo(X));
     if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
     DeviceGuard dg(c->device);
@@ -2308,7 +2457,8 @@ extern "C" sbt_status sbt_core_consistency(int32_t dtype, const void *X, int64_t
     double *out = (double *)(scr + 8), *scratch = out + 1;
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
     if (e == cudaSuccess)
-        e = launch_core_consistency(dtype == SBT_F64, X, K, I, J, ld, lambda, A, B, C, R, scratch, status, out, st);
+        e = launch_core_consistency(dtype == SBT_F64 ? 0 : 1, X, K, I, J, ld, lambda, A, B, C, R, scratch, status,
+                                    out, st);
     double h_out = 0.0;
     int h_status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_out, out, sizeof(double), cudaMemcpyDeviceToHost, st);

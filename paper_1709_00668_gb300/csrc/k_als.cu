@@ -1068,8 +1068,10 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
             else gx = (uint32_t)(x < d.nK ? S[x] : K_old + (x - d.nK));
             if (ws.F[0])  // warm: the old factor at the sampled row; new slices' rows zero
                 U[e] = (m < 2 || x < d.nK) ? (TF)ws.F[m][(long long)gx * R + r] : (TF)0;
+            else if (ws.trial >= 0)  // GetRank's trial start (Algorithm 2)
+                U[e] = (TF)init_value_trial(key, gx, r, m, rep + d.rep0, batch, ws.trial);
             else
-                U[e] = (TF)init_value(key, gx, r, m, rep, batch);
+                U[e] = (TF)init_value(key, gx, r, m, rep + d.rep0, batch);
         }
     }
     __syncthreads();

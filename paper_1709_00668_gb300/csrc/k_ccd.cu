@@ -20,6 +20,12 @@ namespace sbt {
 
 constexpr int CCD_THREADS = 256;
 
+// value of a summary element as float64 (bfloat16 widened exactly)
+__device__ __forceinline__ double ccd_value(double v) { return v; }
+__device__ __forceinline__ double ccd_value(float v) { return (double)v; }
+__device__ __forceinline__ double ccd_value(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+
 // F+ = (F^T F)^-1 F^T of F' = F diag(scale) (scale null: ones); F row-major n x R.
 // status bit 1: a pivot of the Gram was not positive (F' rank-deficient).
 __global__ void __launch_bounds__(CCD_THREADS) k_ccd_pinv(const double *F, long long n, int R, const double *scale,
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(CCD_THREADS) k_ccd_z(const T *X, long long K, 
 #pragma unroll
     for (int q = 0; q < 32; ++q) z[q] = 0.0;
     for (long long j = lane; j < J; j += 32) {
-        const double v = (double)x[j];
+        const double v = ccd_value(x[j]);
 #pragma unroll
         for (int q = 0; q < 32; ++q)
             if (q < R) z[q] = fma(v, PB[(long long)q * J + j], z[q]);
@@ -148,7 +154,19 @@ __global__ void __launch_bounds__(CCD_THREADS) k_ccd_final(const double *G, int 
     }
 }
 
-cudaError_t launch_core_consistency(int dtype_f64, const void *X, long long K, long long I, long long J, long long ld,
+// float32 factor rows widened to float64 (the GetRank candidates' factors)
+__global__ void k_ccd_widen(const float *in, double *out, long long n) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (double)in[e];
+}
+
+cudaError_t launch_widen(const float *in, double *out, long long n, cudaStream_t st) {
+    count_launches(1);
+    k_ccd_widen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_consistency(int elem, const void *X, long long K, long long I, long long J, long long ld,
                                     const double *lam, const double *A, const double *B, const double *C, int R,
                                     double *scratch, int *status, double *out, cudaStream_t st) {
     double *PA = scratch, *PB = PA + (size_t)R * I, *PC = PB + (size_t)R * J, *Z = PC + (size_t)R * K;
@@ -158,8 +176,9 @@ cudaError_t launch_core_consistency(int dtype_f64, const void *X, long long K, l
     k_ccd_pinv<<<1, CCD_THREADS, 0, st>>>(C, K, R, lam, PC, status);
     const long long rows = K * I;
     const unsigned zb = (unsigned)((rows + CCD_THREADS / 32 - 1) / (CCD_THREADS / 32));
-    if (dtype_f64) k_ccd_z<double><<<zb, CCD_THREADS, 0, st>>>((const double *)X, K, I, J, ld, PB, R, Z);
-    else k_ccd_z<float><<<zb, CCD_THREADS, 0, st>>>((const float *)X, K, I, J, ld, PB, R, Z);
+    if (elem == 0) k_ccd_z<double><<<zb, CCD_THREADS, 0, st>>>((const double *)X, K, I, J, ld, PB, R, Z);
+    else if (elem == 1) k_ccd_z<float><<<zb, CCD_THREADS, 0, st>>>((const float *)X, K, I, J, ld, PB, R, Z);
+    else k_ccd_z<__nv_bfloat16><<<zb, CCD_THREADS, 0, st>>>((const __nv_bfloat16 *)X, K, I, J, ld, PB, R, Z);
     const long long n1 = K * R * R;
     k_ccd_t1<<<(unsigned)((n1 + CCD_THREADS - 1) / CCD_THREADS), CCD_THREADS, 0, st>>>(Z, PA, K, I, R, T1);
     k_ccd_core<<<(R * R * R + CCD_THREADS - 1) / CCD_THREADS, CCD_THREADS, 0, st>>>(T1, PC, K, R, G);

@@ -6,39 +6,42 @@
 
 namespace sbt {
 
-// Maximum-weight perfect matching of an R x R score matrix (Hungarian method,
-// shortest augmenting paths with potentials; Kuhn 1955, Munkres 1957), single
-// thread.  perm[row] = column.  Ties resolve to the lower column index.
+// Maximum-weight assignment of an nr x nc score matrix, nr <= nc: every row
+// to a distinct column (Hungarian method, shortest augmenting paths with
+// potentials; Kuhn 1955, Munkres 1957), single thread.  perm[row] = column.
+// Ties resolve to the lower column index.  nr = nc is the perfect matching of
+// Lemma 1's square case; nr < nc is GetRank's R_new summary components
+// against R old ones.
 struct HungarianWork {
     double u[33], v[33], minv[33];
     int p[33], way[33];
     bool used[33];
 };
 
-__device__ void hungarian_max(const double *score, int ld, int R, int *perm, HungarianWork &w) {
+__device__ void hungarian_max(const double *score, int ld, int nr, int nc, int *perm, HungarianWork &w) {
     double *u = w.u, *v = w.v, *minv = w.minv;
     int *p = w.p, *way = w.way;
     bool *used = w.used;
-    for (int j = 0; j <= R; ++j) {
-        u[j] = 0.0;
+    for (int j = 0; j <= nc; ++j) {
         v[j] = 0.0;
         p[j] = 0;
         way[j] = 0;
     }
-    for (int i = 1; i <= R; ++i) {
+    for (int i = 0; i <= nr; ++i) u[i] = 0.0;
+    for (int i = 1; i <= nr; ++i) {
         p[0] = i;
         int j0 = 0;
-        for (int j = 0; j <= R; ++j) {
+        for (int j = 0; j <= nc; ++j) {
             minv[j] = INFINITY;
             used[j] = false;
         }
-        // each pass marks one more column used, so at most R passes
-        for (int guard = 0; guard <= R; ++guard) {
+        // each pass marks one more column used, so at most nc passes
+        for (int guard = 0; guard <= nc; ++guard) {
             used[j0] = true;
             const int i0 = p[j0];
             double delta = INFINITY;
             int j1 = 0;
-            for (int j = 1; j <= R; ++j) {
+            for (int j = 1; j <= nc; ++j) {
                 if (used[j]) continue;
                 double sc = score[(i0 - 1) * ld + (j - 1)];
                 if (!isfinite(sc)) sc = 0.0;
@@ -52,7 +55,7 @@ __device__ void hungarian_max(const double *score, int ld, int R, int *perm, Hun
                     j1 = j;
                 }
             }
-            for (int j = 0; j <= R; ++j) {
+            for (int j = 0; j <= nc; ++j) {
                 if (used[j]) {
                     u[p[j]] += delta;
                     v[j] -= delta;
@@ -64,27 +67,32 @@ __device__ void hungarian_max(const double *score, int ld, int R, int *perm, Hun
             j0 = j1;
             if (p[j0] == 0) break;
         }
-        for (int guard = 0; guard <= R && j0; ++guard) {
+        for (int guard = 0; guard <= nc && j0; ++guard) {
             const int j1 = way[j0];
             p[j0] = p[j1];
             j0 = j1;
         }
     }
-    // any column left unassigned is paired with the remaining rows in order
-    bool row_done[33];
-    for (int i = 0; i <= R; ++i) row_done[i] = false;
-    for (int j = 1; j <= R; ++j)
-        if (p[j] >= 1 && p[j] <= R && !row_done[p[j]]) row_done[p[j]] = true;
-        else p[j] = 0;
-    for (int j = 1; j <= R; ++j)
-        if (p[j] == 0)
-            for (int i = 1; i <= R; ++i)
-                if (!row_done[i]) {
-                    p[j] = i;
-                    row_done[i] = true;
+    // rows that no column took (cannot happen for finite scores) take the
+    // free columns in order
+    bool row_done[33], col_used[33];
+    for (int i = 0; i <= nr; ++i) row_done[i] = false;
+    for (int j = 0; j <= nc; ++j) col_used[j] = false;
+    for (int i = 0; i < nr; ++i) perm[i] = -1;
+    for (int j = 1; j <= nc; ++j)
+        if (p[j] >= 1 && p[j] <= nr && !row_done[p[j]]) {
+            row_done[p[j]] = true;
+            col_used[j] = true;
+            perm[p[j] - 1] = j - 1;
+        }
+    for (int i = 1; i <= nr; ++i)
+        if (!row_done[i])
+            for (int j = 1; j <= nc; ++j)
+                if (!col_used[j]) {
+                    col_used[j] = true;
+                    perm[i - 1] = j - 1;
                     break;
                 }
-    for (int j = 1; j <= R; ++j) perm[p[j] - 1] = j - 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -125,6 +133,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     using Anchor = typename Acc::Anchor;
     const int rep = blockIdx.x;
     const int R = m.R;
+    const int Rs = m.rnew ? m.rnew[rep] : R;  // summary components (GetRank: R_new <= R)
     const int Kp = m.nK + m.K_new;
     const int n[3] = {m.nI, m.nJ, Kp};
     const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
@@ -132,13 +141,14 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     constexpr int MATCH_TS = match_ts<TF>();
     __shared__ TF su[MATCH_TS * 32];
     __shared__ Anchor sa[MATCH_TS * 32];
-    __shared__ int perm[32];
+    __shared__ int perm[32], iperm[32];
     __shared__ int zflag;
     __shared__ HungarianWork hw;  // in shared memory rather than the thread's stack
     const TF *U[3];
     const int *S[3];
     const double *old[3] = {m.A, m.B, m.C};
     for (int q = 0; q < 3; ++q) {
+        // the repetition's n x R slot holds rows of Rs values
         U[q] = (const TF *)m.U[q] + (long long)rep * n[q] * R;
         S[q] = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
     }
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
             __syncthreads();
             for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
                 const int t = t0 + e / R, c = e % R;
-                su[e] = U[q][(long long)t * R + c];
+                su[e] = c < Rs ? U[q][(long long)t * Rs + c] : (TF)0;
                 sa[e] = Acc::anchor(old[q][(long long)S[q][t] * R + c]);
             }
             __syncthreads();
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
                 double s = sqrt(v);
                 if (s == 0.0) {
                     s = 1.0;
-                    zflag = 1;
+                    if (item - R * R < Rs) zflag = 1;  // columns past Rs are absent, not zero
                 }
                 nu[q][item - R * R] = s;
             } else {
@@ -200,25 +210,28 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int rp = 0; rp < R; ++rp) {
+        for (int rp = 0; rp < Rs; ++rp) {
             lsp[rp] = m.lam_s[rep * R + rp] * nu[0][rp] * nu[1][rp] * nu[2][rp];
             for (int r = 0; r < R; ++r)
                 score[rp * 32 + r] = fabs(gam[0][rp][r]) * fabs(gam[1][rp][r]) * fabs(gam[2][rp][r]);
         }
-        hungarian_max(score, 32, R, perm, hw);
+        hungarian_max(score, 32, Rs, R, perm, hw);
+        for (int r = 0; r < R; ++r) iperm[r] = -1;
         double mn = INFINITY;
-        for (int rp = 0; rp < R; ++rp) {
+        for (int rp = 0; rp < Rs; ++rp) {
             mn = fmin(mn, score[rp * 32 + perm[rp]]);
-            m.perm[rep * R + rp] = perm[rp];
+            iperm[perm[rp]] = rp;
         }
         m.min_score[rep] = mn;
+        for (int rp = 0; rp < R; ++rp) m.perm[rep * R + rp] = rp < Rs ? perm[rp] : -1;
         for (int q = 0; q < 3; ++q)
             for (int r = 0; r < R; ++r) m.nu[(rep * 3 + q) * R + r] = nu[q][r];
-        for (int rp = 0; rp < R; ++rp) {
-            const int r = perm[rp];
+        // the summary's estimate of lambda in the old scale; NaN: not matched
+        for (int r = 0; r < R; ++r) {
+            const int rp = iperm[r];
             const double den = Nn[0][r] * Nn[1][r] * Nn[2][r];
             m.lam_est[rep * R + r] =
-                den != 0.0 ? lsp[rp] * gam[0][rp][r] * gam[1][rp][r] * gam[2][rp][r] / den : 0.0;
+                rp < 0 ? NAN : (den != 0.0 ? lsp[rp] * gam[0][rp][r] * gam[1][rp][r] * gam[2][rp][r] / den : 0.0);
         }
         if (zflag) m.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
     }
@@ -226,30 +239,34 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     // least-squares scale of a summary column of mode q in the matched old
     // scale, per unit of the raw summary value
     if (threadIdx.x < 3 * R) {
-        const int q = threadIdx.x / R, rp = threadIdx.x % R, r = perm[rp];
-        double num = lsp[rp], den = m.lam[r];
-        for (int o = 0; o < 3; ++o)
-            if (o != q) {
-                num *= gam[o][rp][r];
-                den *= Nn[o][r];
-            }
-        scale[q][rp] = den != 0.0 ? num / den / nu[q][rp] : 0.0;
+        const int q = threadIdx.x / R, rp = threadIdx.x % R;
+        if (rp < Rs) {
+            const int r = perm[rp];
+            double num = lsp[rp], den = m.lam[r];
+            for (int o = 0; o < 3; ++o)
+                if (o != q) {
+                    num *= gam[o][rp][r];
+                    den *= Nn[o][r];
+                }
+            scale[q][rp] = den != 0.0 ? num / den / nu[q][rp] : 0.0;
+        }
     }
     __syncthreads();
-    // new rows of C (Alg. 1 step 9)
+    // new rows of C (Alg. 1 step 9); NaN in the columns no summary component matched
     double *cn = m.cnew + (long long)rep * m.K_new * R;
     for (int e = threadIdx.x; e < m.K_new * R; e += blockDim.x) {
-        const int k = e / R, rp = e % R;
-        cn[(long long)k * R + perm[rp]] = scale[2][rp] * (double)U[2][(long long)(m.nK + k) * R + rp];
+        const int k = e / R, r = e % R, rp = iperm[r];
+        cn[e] = rp < 0 ? NAN : scale[2][rp] * (double)U[2][(long long)(m.nK + k) * Rs + rp];
     }
     // zero-entry proposals (Alg. 1 step 8)
     for (int q = 0; q < 3; ++q) {
         double *pp = m.prop + ((long long)rep * 3 + q) * m.pmax * R;
         for (int e = threadIdx.x; e < nsh[q] * R; e += blockDim.x) {
-            const int t = e / R, rp = e % R, r = perm[rp];
+            const int t = e / R, r = e % R, rp = iperm[r];
             double val = NAN;
-            if (old[q][(long long)S[q][t] * R + r] == 0.0) val = scale[q][rp] * (double)U[q][(long long)t * R + rp];
-            pp[(long long)t * R + r] = val;
+            if (rp >= 0 && old[q][(long long)S[q][t] * R + r] == 0.0)
+                val = scale[q][rp] * (double)U[q][(long long)t * Rs + rp];
+            pp[e] = val;
         }
     }
 }
@@ -299,10 +316,19 @@ __global__ void k_commit(MergeDesc m) {
     const long long nC = (long long)m.K_new * R;
     const long long nA = (long long)m.I * R, nB = (long long)m.J * R, nCo = (long long)m.K_old * R;
     if (e < nC) {
+        // mean over the repetitions that matched the component (all of them
+        // without GetRank); none: zero
         const int k = (int)(e / R), r = (int)(e % R);
         double s = 0.0;
-        for (int q = 0; q < m.nrep; ++q) s += m.cnew[((long long)q * m.K_new + k) * R + r];
-        m.C[(long long)(m.K_old + k) * R + r] = s / m.nrep;
+        int c = 0;
+        for (int q = 0; q < m.nrep; ++q) {
+            const double v = m.cnew[((long long)q * m.K_new + k) * R + r];
+            if (!isnan(v)) {
+                s += v;
+                ++c;
+            }
+        }
+        m.C[(long long)(m.K_old + k) * R + r] = c ? s / c : 0.0;
         return;
     }
     e -= nC;
@@ -338,8 +364,15 @@ __global__ void k_commit(MergeDesc m) {
     if (e < R) {
         if (m.lambda_mode == 1) {
             double s = 0.0;
-            for (int rep = 0; rep < m.nrep; ++rep) s += m.lam_est[rep * R + e];
-            m.lam[e] = 0.5 * (m.lam[e] + s / m.nrep);
+            int c = 0;
+            for (int rep = 0; rep < m.nrep; ++rep) {
+                const double v = m.lam_est[rep * R + e];
+                if (!isnan(v)) {
+                    s += v;
+                    ++c;
+                }
+            }
+            if (c) m.lam[e] = 0.5 * (m.lam[e] + s / c);
         }
         return;
     }

@@ -124,6 +124,16 @@ __device__ __forceinline__ double init_value(uint2 key, uint32_t gx, int r, int 
     return (double)(o.x >> 8) * (1.0 / 16777216.0);
 }
 
+// Start value of GetRank's trial t (Section 3.2, Algorithm 2): counter
+// (global index, r | mode << 8 | rep << 12 | t << 20, batch, 3).
+__device__ __forceinline__ double init_value_trial(uint2 key, uint32_t gx, int r, int mode, int rep,
+                                                   uint32_t batch, int trial) {
+    uint4 c = make_uint4(gx, (uint32_t)r | ((uint32_t)mode << 8) | ((uint32_t)rep << 12) | ((uint32_t)trial << 20),
+                         batch, 3u);
+    uint4 o = philox4x32_10(c, key);
+    return (double)(o.x >> 8) * (1.0 / 16777216.0);
+}
+
 // ---------------------------------------------------------------------------
 // Reductions
 __device__ __forceinline__ float warp_sum(float v) {
@@ -335,6 +345,7 @@ struct AlsDesc {
     float *ymem;           // nullable: Y_kk = X_kk^T A of the mode-2 pass, [rep][n[2]][n[1]][pr]; the
                            // mode-3 MTTKRP is then M3(kk, r) = sum_j Y_kk(j, r) B(j, r) (k_mtt_memo)
     long long yrs;         // floats per repetition of ymem
+    int rep0;              // repetition index of the first repetition (Philox counters of the start)
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA
@@ -346,6 +357,7 @@ struct AlsDesc {
 // slices' rows of C' zero
 struct WarmStart {
     const double *F[3] = {nullptr, nullptr, nullptr};
+    int trial = -1;  // >= 0 (F null): GetRank's trial start, init_value_trial
 };
 
 // ---------------------------------------------------------------------------
@@ -385,13 +397,15 @@ cudaError_t set_als_kernel_attributes();
 cudaError_t set_tc_kernel_attributes();
 // V^-1 of `mode` for the float32 factor path (run beside the mode's MTTKRP)
 cudaError_t launch_xinv(const AlsDesc &d, int mode, cudaStream_t st);
-// CorConDia of a CP model (float64; X slice-major f64 when dtype_f64, else
-// f32); scratch: core_consistency_scratch_doubles(K, I, J, R) doubles; status
-// bit 1 when a factor's Gram is not positive definite; *out device double
-cudaError_t launch_core_consistency(int dtype_f64, const void *X, long long K, long long I, long long J, long long ld,
+// CorConDia of a CP model (float64; X slice-major, element kind elem: 0 f64,
+// 1 f32, 2 bf16); scratch: core_consistency_scratch_doubles(K, I, J, R)
+// doubles; status bit 1 when a factor's Gram is not positive definite; *out
+// device double
+cudaError_t launch_core_consistency(int elem, const void *X, long long K, long long I, long long J, long long ld,
                                     const double *lam, const double *A, const double *B, const double *C, int R,
                                     double *scratch, int *status, double *out, cudaStream_t st);
 size_t core_consistency_scratch_doubles(long long K, long long I, long long J, int R);
+cudaError_t launch_widen(const float *in, double *out, long long n, cudaStream_t st);
 
 // mode 3 after a memoised mode-2 pass: M3 from d.ymem and the new B as the
 // single partial of the mode-3 tail, and V^-1 of mode 3 (PDL launch)
@@ -479,6 +493,9 @@ struct MergeDesc {
     int lambda_mode;
     unsigned long long *xa, *xb, *xc, *dxa, *dxb, *xc_new;
     DevStatus *status;
+    const int *rnew;     // nullable: components of each summary (GetRank's R_new <= R), [rep];
+                         // summary factor rows then hold rnew[rep] values (stride rnew[rep]) in
+                         // the repetition's n x R slot
 };
 cudaError_t launch_match(const MergeDesc &m, cudaStream_t st);
 // overflow check of the marginal fold; sets ERR_RANGE before anything changes

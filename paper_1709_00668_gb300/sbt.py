@@ -77,7 +77,8 @@ class SbtOptions(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("check_every", ctypes.c_int32),
                 ("refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("mode3_pass", ctypes.c_int32), ("als_groups", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("get_rank", ctypes.c_int32),
+                ("get_rank_trials", ctypes.c_int32), ("get_rank_threshold", ctypes.c_double)]
 
 
 class SbtStats(ctypes.Structure):
@@ -87,7 +88,8 @@ class SbtStats(ctypes.Structure):
                 ("iters", ctypes.c_int32 * SBT_MAX_REPS),
                 ("fit", ctypes.c_double * SBT_MAX_REPS),
                 ("min_score", ctypes.c_double * SBT_MAX_REPS),
-                ("perm", (ctypes.c_int32 * SBT_MAX_RANK) * SBT_MAX_REPS)]
+                ("perm", (ctypes.c_int32 * SBT_MAX_RANK) * SBT_MAX_REPS),
+                ("rank", ctypes.c_int32 * SBT_MAX_REPS)]
 
 
 class SbtProfile(ctypes.Structure):
@@ -445,7 +447,7 @@ class SamBaTen:
         return {"K": st.K, "r": r, "R": R, "n_I": st.n_I, "n_J": st.n_J, "n_K": st.n_K,
                 "flags": st.flags, "iters": list(st.iters[:r]), "fit": list(st.fit[:r]),
                 "min_score": list(st.min_score[:r]),
-                "perm": [list(st.perm[q][:R]) for q in range(r)]}
+                "perm": [list(st.perm[q][:R]) for q in range(r)], "rank": list(st.rank[:r])}
 
     def profile_reset(self, timing: bool = True):
         _check(lib().sbt_profile_reset(self._h, 1 if timing else 0), "sbt_profile_reset")
