@@ -231,6 +231,78 @@ sbt_status sbt_init_coo_factors(const sbt_coo *X0, int32_t R, const double *lamb
  * sbt_last_samples and sbt_last_summary_factors apply to COO contexts too. */
 sbt_status sbt_update_coo(sbt_ctx *ctx, const sbt_coo *X_new);
 
+/* ---- order-N tensors ------------------------------------------------------
+ * Section 2.2: the problem and the method extend to tensors with any number
+ * of modes, one of which grows with time.  These calls run Algorithm 1 on a
+ * dense tensor with N = 3..SBT_NMODE_MAX modes: Eq. 1 marginals of every mode,
+ * each non-time mode and the old slices sampled by exponential keys (Philox
+ * counter (x, mode | rep << 4, batch, 1), mode = the factor's position below),
+ * the summary at the sampled indices plus the new slices, CP-ALS over all N
+ * modes (Philox start (x, r | mode << 8 | rep << 12, batch, 2); MTTKRP with the
+ * Khatri-Rao rows of the other N-1 factors formed on the fly; the Hadamard
+ * product of the other N-1 Grams solved by a float64 Cholesky factorisation;
+ * unit columns; the fit after the last mode), shared-row normalisation,
+ * Lemma 1 matching with the product of the N |cosine| matrices, and the new
+ * time rows projected back and averaged over the repetitions.  Zero-entry
+ * fills and lambda_mode are not applied (lambda is kept).
+ *
+ * Layout: time first, row-major: element (k, i_1, ..., i_{N-1}) of a tensor
+ * with dims = (K, I_1, ..., I_{N-1}) sits at
+ * data[((k * I_1 + i_1) * I_2 + i_2) ... * I_{N-1} + i_{N-1}].  Factors are in
+ * factor order: U[0..N-2] = the modes of I_1..I_{N-1} (I_m x R), U[N-1] = C
+ * (K x R), row-major float64.  Sampling factors: s_I for I_1 and for I_3 and
+ * later modes, s_J for I_2, s_K for time.  Options used: s_I, s_J, s_K, r, tol,
+ * max_iters, seed, stream_id, prec (SBT_PREC_F64 with a float64 tensor or
+ * SBT_PREC_F32 with a float32 one: the summary keeps the stored values; the
+ * float32 MTTKRP multiplies and adds in float32 within a lane, float64
+ * beyond), fixed_iters, K_capacity, cuda_stream, check_every; the others must
+ * be at their defaults (SBT_E_INVALID otherwise).  R <= SBT_MAX_RANK; the
+ * summary's last dimension I_{N-1} / s must fit the MTTKRP's shared-memory
+ * plan (I_{N-1} / s x 32 x 8 bytes <= 200 KB).  Every call returns a status. */
+#define SBT_NMODE_MAX 8
+
+typedef struct {
+    int32_t dtype;                  /* SBT_F64 or SBT_F32 */
+    int32_t on_device;              /* 1: device memory of the context's device */
+    int32_t N;                      /* modes, 3..SBT_NMODE_MAX */
+    int64_t dims[SBT_NMODE_MAX];    /* dims[0] = K (slices), dims[1..N-1] = I_1..I_{N-1} */
+    const void *data;
+} sbt_tensor_n;
+
+typedef struct sbt_nmode sbt_nmode; /* opaque; owned by the library */
+
+/* A context for the pre-existing decomposition lambda (R), U[0..N-1] (host
+ * float64, factor order, U[N-1] with K0 rows) of X0; X0, the factors and the
+ * marginals are kept on the device.  SBT_E_NONFINITE, SBT_E_SHAPE,
+ * SBT_E_INVALID, SBT_E_NOMEM, SBT_E_CUDA. */
+sbt_status sbt_nmode_init_factors(const sbt_tensor_n *X0, int32_t R, const double *lambda, const double *const *U,
+                                  const sbt_options *opt, sbt_nmode **out);
+
+/* Absorb K_new = X_new->dims[0] >= 1 new slices (the other dims as at init):
+ * Algorithm 1 once.  Transactional like sbt_update (non-finite values,
+ * marginal overflow: SBT_E_NONFINITE / SBT_E_RANGE, state unchanged).  One
+ * host synchronisation per ALS convergence poll and one at the end. */
+sbt_status sbt_nmode_update(sbt_nmode *c, const sbt_tensor_n *X_new);
+
+/* Copy the model to caller-owned host buffers (any may be NULL; U may hold
+ * NULL entries): lambda (R), U[m] (n_m x R, U[N-1] with K rows); *K_out = K. */
+sbt_status sbt_nmode_factors(const sbt_nmode *c, double *lambda, double *const *U, int64_t *K_out);
+
+/* 1 - ||X - X_hat||_F / ||X||_F over the whole resident tensor (Section 4.2). */
+sbt_status sbt_nmode_fit(sbt_nmode *c, double *fit);
+
+/* Statistics of the last update: n_I, n_J = the sample sizes of I_1 and I_2,
+ * n_K = of the old slices; iters, fit, min_score, perm per repetition. */
+sbt_status sbt_nmode_stats(const sbt_nmode *c, sbt_update_stats *st);
+
+/* Sampled indices of repetition rep in mode `mode` (factor order; N-1: the
+ * old slices), ascending; *n receives the count, at most cap written. */
+sbt_status sbt_nmode_last_samples(const sbt_nmode *c, int32_t rep, int32_t mode, int32_t *out, int64_t cap,
+                                  int64_t *n);
+
+/* Free the context.  NULL is a no-op. */
+void sbt_nmode_destroy(sbt_nmode *c);
+
 /* ---- device memory of a context ------------------------------------------
  * No counterpart in the paper: these let a caller (the server below) admit
  * work by a device-memory budget and keep allocation out of the update path. */

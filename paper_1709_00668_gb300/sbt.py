@@ -57,7 +57,10 @@ EXPORTS = [
     "sbt_server_default_options", "sbt_server_create", "sbt_server_open_stream", "sbt_server_submit",
     "sbt_server_wait", "sbt_server_stream_ctx", "sbt_server_close_stream", "sbt_server_stats",
     "sbt_server_stats_reset", "sbt_server_destroy",
+    "sbt_nmode_init_factors", "sbt_nmode_update", "sbt_nmode_factors", "sbt_nmode_fit", "sbt_nmode_stats",
+    "sbt_nmode_last_samples", "sbt_nmode_destroy",
 ]
+SBT_NMODE_MAX = 8
 SBT_SAMPLE_NOALLOC_MAX_N = 262144
 
 
@@ -65,6 +68,11 @@ class SbtTensor(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("on_device", ctypes.c_int32),
                 ("I", ctypes.c_int64), ("J", ctypes.c_int64), ("K", ctypes.c_int64),
                 ("data", ctypes.c_void_p)]
+
+
+class SbtTensorN(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("on_device", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * SBT_NMODE_MAX), ("data", ctypes.c_void_p)]
 
 
 class SbtOptions(ctypes.Structure):
@@ -194,9 +202,18 @@ def lib() -> ctypes.CDLL:
     L.sbt_server_stats_reset.argtypes = [P]
     L.sbt_server_destroy.argtypes = [P]
     L.sbt_server_destroy.restype = None
+    L.sbt_nmode_init_factors.argtypes = [ctypes.POINTER(SbtTensorN), I32, P, P, ctypes.POINTER(SbtOptions),
+                                         ctypes.POINTER(P)]
+    L.sbt_nmode_update.argtypes = [P, ctypes.POINTER(SbtTensorN)]
+    L.sbt_nmode_factors.argtypes = [P, P, P, ctypes.POINTER(I64)]
+    L.sbt_nmode_fit.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    L.sbt_nmode_stats.argtypes = [P, ctypes.POINTER(SbtStats)]
+    L.sbt_nmode_last_samples.argtypes = [P, I32, I32, P, I64, ctypes.POINTER(I64)]
+    L.sbt_nmode_destroy.argtypes = [P]
+    L.sbt_nmode_destroy.restype = None
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("sbt_version", "sbt_last_error", "sbt_destroy"):
+        if name not in ("sbt_version", "sbt_last_error", "sbt_destroy", "sbt_nmode_destroy"):
             f.restype = S
     _lib = L
     return L
@@ -487,6 +504,94 @@ class SamBaTen:
         _check(lib().sbt_last_summary_factors(self._h, rep, lam.ctypes.data, A.ctypes.data, B.ctypes.data,
                                               C.ctypes.data), "sbt_last_summary_factors")
         return lam, A, B, C
+
+
+def _tensor_n_desc(X, keep: list) -> SbtTensorN:
+    """SbtTensorN for an order-N torch tensor or numpy array, time first (K, I_1, ..., I_{N-1})."""
+    import torch
+    if isinstance(X, np.ndarray):
+        X = torch.from_numpy(np.ascontiguousarray(X))
+    if not (3 <= X.dim() <= SBT_NMODE_MAX):
+        raise ValueError("X must have 3..SBT_NMODE_MAX axes")
+    if X.dtype == torch.float64:
+        dt = SBT_F64
+    elif X.dtype == torch.float32:
+        dt = SBT_F32
+    else:
+        raise ValueError("X must be float32 or float64")
+    X = X.contiguous()
+    keep.append(X)
+    dims = (ctypes.c_int64 * SBT_NMODE_MAX)(*([int(v) for v in X.shape] + [0] * (SBT_NMODE_MAX - X.dim())))
+    return SbtTensorN(dt, 1 if X.is_cuda else 0, X.dim(), dims, ctypes.c_void_p(X.data_ptr()))
+
+
+class SamBaTenN:
+    """An order-N tensor stream (time first): the pre-existing decomposition
+    lambda, U = [U_1, ..., U_{N-1}, C] is given; sbt_nmode_* underneath."""
+
+    def __init__(self, X0, R: int, *, factors, **opts):
+        if "cuda_stream" not in opts:
+            opts["cuda_stream"] = _current_stream()
+        self.opts = sbt_default_options(**opts)
+        self.R = int(R)
+        keep: list = []
+        desc = _tensor_n_desc(X0, keep)
+        self.N = int(desc.N)
+        self.dims = [int(desc.dims[a]) for a in range(1, self.N)]
+        lam, U = factors
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        Us = [np.ascontiguousarray(np.asarray(u, dtype=np.float64)) for u in U]
+        ptrs = (ctypes.c_void_p * self.N)(*[u.ctypes.data for u in Us])
+        h = ctypes.c_void_p()
+        _check(lib().sbt_nmode_init_factors(ctypes.byref(desc), self.R, lam.ctypes.data, ptrs,
+                                            ctypes.byref(self.opts), ctypes.byref(h)), "sbt_nmode_init_factors")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sbt_nmode_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, X_new):
+        keep: list = []
+        desc = _tensor_n_desc(X_new, keep)
+        _check(lib().sbt_nmode_update(self._h, ctypes.byref(desc)), "sbt_nmode_update")
+
+    def factors(self):
+        K = ctypes.c_int64()
+        lib().sbt_nmode_factors(self._h, None, None, ctypes.byref(K))
+        lam = np.empty(self.R)
+        U = [np.empty((d, self.R)) for d in self.dims] + [np.empty((K.value, self.R))]
+        ptrs = (ctypes.c_void_p * self.N)(*[u.ctypes.data for u in U])
+        _check(lib().sbt_nmode_factors(self._h, lam.ctypes.data, ptrs, ctypes.byref(K)), "sbt_nmode_factors")
+        return lam, U
+
+    def fit(self) -> float:
+        f = ctypes.c_double()
+        _check(lib().sbt_nmode_fit(self._h, ctypes.byref(f)), "sbt_nmode_fit")
+        return f.value
+
+    def stats(self) -> dict:
+        st = SbtStats()
+        _check(lib().sbt_nmode_stats(self._h, ctypes.byref(st)), "sbt_nmode_stats")
+        r, R = st.r, st.R
+        return {"K": st.K, "r": r, "R": R, "n_I": st.n_I, "n_J": st.n_J, "n_K": st.n_K, "flags": st.flags,
+                "iters": list(st.iters[:r]), "fit": list(st.fit[:r]), "min_score": list(st.min_score[:r]),
+                "perm": [list(st.perm[q][:R]) for q in range(r)]}
+
+    def last_samples(self, rep: int, mode: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().sbt_nmode_last_samples(self._h, rep, mode, None, 0, ctypes.byref(n)), "sbt_nmode_last_samples")
+        out = np.empty(max(1, n.value), np.int32)
+        _check(lib().sbt_nmode_last_samples(self._h, rep, mode, out.ctypes.data, n.value, ctypes.byref(n)),
+               "sbt_nmode_last_samples")
+        return out[:n.value].copy()
 
 
 # module-level names of the C ABI --------------------------------------------

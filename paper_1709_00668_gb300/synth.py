@@ -180,3 +180,32 @@ def planted_sparse(I: int, J: int, K: int, R: int, *, support: int, coords: int,
             torch.float32)
     return SparsePlanted(k=k.to(torch.int32), i=i.to(torch.int32), j=j.to(torch.int32), v=v, A=A, B=B, C=C,
                          sigma=noise)
+
+
+@dataclass
+class PlantedN:
+    X: torch.Tensor          # (K, I_1, ..., I_{N-1}), time first, requested dtype
+    U: list                  # [U_1, ..., U_{N-1}, C] float64, planted (factor order)
+    sigma: float
+
+
+def planted_dense_n(dims, K: int, R: int, *, noise: float = 0.01, seed: int = 0,
+                    dtype=torch.float64, device="cpu") -> PlantedN:
+    """Planted rank-R order-N tensor, seeded: factors U_m ~ U[0, 1) i.i.d.
+    for the modes of `dims` = (I_1, ..., I_{N-1}) and for time (K rows);
+    X(k, i_1, ...) = sum_r prod_m U_m(i_m, r) + N(0, sigma^2), sigma = noise *
+    RMS of the noiseless tensor.  Time-first layout."""
+    dev = torch.device(device)
+    g = _gen(seed, dev)
+    U = [torch.rand(d, R, generator=g, device=dev, dtype=torch.float64) for d in dims]
+    C = torch.rand(K, R, generator=g, device=dev, dtype=torch.float64)
+    # noiseless X: outer products built up one mode at a time, time first
+    X = C
+    for u in U:
+        X = (X.unsqueeze(-2) * u.reshape((1,) * (X.dim() - 1) + u.shape))
+    X = X.sum(dim=-1)
+    rms = float(X.pow(2).mean().sqrt())
+    sigma = float(noise) * rms
+    if sigma > 0:
+        X = X + sigma * torch.randn(X.shape, generator=g, device=dev, dtype=torch.float64)
+    return PlantedN(X=X.to(dtype).contiguous(), U=U + [C], sigma=sigma)

@@ -169,3 +169,34 @@ def test_tile_table_host_logic(lib):
     assert lib.sbt_tile_table(7, None, 0, ctypes.byref(n)) == sbt.SBT_E_INVALID
     sbt.tile_table_clear()
     assert sbt.tile_table() == []
+
+
+def test_nmode_and_get_rank_arguments_rejected_without_gpu(lib):
+    """The order-N calls and the GetRank options check their arguments
+    before any device call."""
+    from paper_1709_00668_gb300 import sbt
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_double * 4096)()
+    dims = (ctypes.c_int64 * sbt.SBT_NMODE_MAX)(6, 5, 4, 3, 0, 0, 0, 0)
+    o = sbt.sbt_default_options(prec="f64")
+    lam = (ctypes.c_double * 2)(1.0, 1.0)
+    U = (ctypes.c_void_p * 4)(*([ctypes.cast(buf, ctypes.c_void_p)] * 4))
+    t2 = sbt.SbtTensorN(sbt.SBT_F64, 0, 2, dims, ctypes.cast(buf, ctypes.c_void_p))  # N below 3
+    assert lib.sbt_nmode_init_factors(ctypes.byref(t2), 2, lam, U, ctypes.byref(o), ctypes.byref(h)) == \
+        sbt.SBT_E_INVALID
+    t4 = sbt.SbtTensorN(sbt.SBT_F64, 0, 4, dims, ctypes.cast(buf, ctypes.c_void_p))
+    assert lib.sbt_nmode_init_factors(ctypes.byref(t4), 2, lam, None, ctypes.byref(o), ctypes.byref(h)) == \
+        sbt.SBT_E_INVALID
+    o32 = sbt.sbt_default_options(prec="f32")  # a float32 summary needs a float32 tensor
+    assert lib.sbt_nmode_init_factors(ctypes.byref(t4), 2, lam, U, ctypes.byref(o32), ctypes.byref(h)) == \
+        sbt.SBT_E_INVALID
+    ow = sbt.sbt_default_options(prec="f64", warm_start=1)
+    assert lib.sbt_nmode_init_factors(ctypes.byref(t4), 2, lam, U, ctypes.byref(ow), ctypes.byref(h)) == \
+        sbt.SBT_E_INVALID
+    assert lib.sbt_nmode_update(None, ctypes.byref(t4)) == sbt.SBT_E_INVALID
+    # GetRank: float8 summaries, refinement and out-of-range trial counts are rejected
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 4, 4, 4, ctypes.cast(buf, ctypes.c_void_p))
+    for kw in (dict(get_rank=1, prec="fp8"), dict(get_rank=1, prec="bf16", refine_sweeps=2),
+               dict(get_rank=2), dict(get_rank=1, get_rank_trials=17)):
+        og = sbt.sbt_default_options(**kw)
+        assert lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(og), ctypes.byref(h)) == sbt.SBT_E_INVALID
