@@ -133,6 +133,12 @@ typedef struct {
                               0 (default): every summary at rank R */
     int32_t get_rank_trials;   /* GetRank decompositions per candidate rank (Algorithm 2's `it`); 0: 2 */
     double get_rank_threshold; /* core consistency a candidate rank must reach; 0: 90 */
+    int32_t fp64_tail;     /* SBT_PREC_F32 / BF16 / FP8: 1 runs the R x R work of every ALS step in
+                              float64 -- the Hadamard product of the Grams, its Cholesky factorisation
+                              and the solve U = M V^-1, the column norms, the Grams and the fit --
+                              one CTA per repetition, after the MTTKRP partials are summed in float64;
+                              0 (default): double-float (~44 bits) on the float32 pipes, V^-1 beside
+                              the MTTKRP pass */
 } sbt_options;
 
 typedef struct {

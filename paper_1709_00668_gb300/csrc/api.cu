@@ -289,6 +289,7 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (o->als_groups < 0 || o->als_groups > SBT_MAX_REPS) return fail(SBT_E_INVALID, "als_groups out of [0, SBT_MAX_REPS]");
     if (o->warm_start != 0 && o->warm_start != 1) return fail(SBT_E_INVALID, "warm_start must be 0 or 1");
     if (o->get_rank != 0 && o->get_rank != 1) return fail(SBT_E_INVALID, "get_rank must be 0 or 1");
+    if (o->fp64_tail != 0 && o->fp64_tail != 1) return fail(SBT_E_INVALID, "fp64_tail must be 0 or 1");
     if (o->get_rank_trials < 0 || o->get_rank_trials > 16) return fail(SBT_E_INVALID, "get_rank_trials out of [0, 16]");
     if (!std::isfinite(o->get_rank_threshold)) return fail(SBT_E_INVALID, "get_rank_threshold must be finite");
     if (o->get_rank && (o->prec == SBT_PREC_FP8 || o->refine_sweeps > 0))
@@ -379,6 +380,7 @@ static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.tol = c->opt.tol;
     d.max_iters = max_iters;
     d.fixed_iters = c->opt.fixed_iters;
+    d.tail64 = elem != 0 && c->opt.fp64_tail ? 1 : 0;
     d.pr = elem == 0 ? d.R : (d.R + 3) / 4 * 4;
     choose_tiles(d, c->num_sms);
     const int nmax = std::max(n[0], std::max(n[1], n[2]));
@@ -678,7 +680,7 @@ static cudaError_t launch_iterations(sbt_ctx *c, const std::vector<AlsPlan> &pla
                 cudaEvent_t join = g == 0 ? c->ev_join : c->grt[g - 1].join;
                 // V^-1 beside the pass; a memoised mode 3 has no pass over the
                 // summary, and k_mtt_memo forms its inverse
-                const bool xinv = d.xinv && !(mode == 2 && d.ymem);
+                const bool xinv = d.xinv && !(mode == 2 && d.ymem) && !d.tail64;
                 if (xinv) {
                     e = cudaEventRecord(fork, st);
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);

@@ -248,16 +248,19 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
 
 // ---------------------------------------------------------------------------
 // Fixed-order reduction of the partials: M[rep][e] = sum_p part[rep][p][e]
+// M(x, r) = sum of the P partials in order; partials [rep][P][n][pr] (row
+// stride pr >= R), M [rep][n][R]
 template <typename TF>
-__global__ void k_reduce(const TF *part, long long prs, int P, long long cnt, double *M, long long mrs,
+__global__ void k_reduce(const TF *part, long long prs, int P, int n, int R, int pr, double *M, long long mrs,
                          const int *conv) {
     const int rep = blockIdx.y;
     if (conv[rep]) return;
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= cnt) return;
-    const TF *p = part + rep * prs + e;
+    if (e >= (long long)n * R) return;
+    const long long x = e / R, r = e % R;
+    const TF *p = part + rep * prs + x * pr + r;
     double s = 0.0;
-    for (int q = 0; q < P; ++q) s += (double)p[(long long)q * cnt];
+    for (int q = 0; q < P; ++q) s += (double)p[(long long)q * n * pr];
     M[rep * mrs + e] = s;
 }
 
@@ -995,10 +998,12 @@ __global__ void __launch_bounds__(MEMO_THREADS) k_mtt_memo(AlsDesc d) {
     const int R = d.R, nj = d.n[1], pr = d.pr;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x == 0) {
-        __shared__ DF W[32 * 64];
-        int reg = 0;
-        cta_inverse_df(d.Gf + (long long)rep * 3 * R * R, R, 2, d.xinv + (long long)rep * 2048, &reg, W);
-        if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
+        if (!d.tail64) {  // the float64 tail solves with its own Cholesky factorisation
+            __shared__ DF W[32 * 64];
+            int reg = 0;
+            cta_inverse_df(d.Gf + (long long)rep * 3 * R * R, R, 2, d.xinv + (long long)rep * 2048, &reg, W);
+            if (threadIdx.x == 0 && reg) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
+        }
         return;
     }
     const int kk = blockIdx.x - 1;
@@ -1087,7 +1092,7 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
                 ++r;
             }
             int s = r + rem;
-            if (d.Gf) {
+            if (d.Gf && !d.tail64) {
                 // float32 factors: exact products, double-float sums
                 DF a{0.f, 0.f};
                 for (int x = lane; x < n; x += 32)
@@ -1279,9 +1284,11 @@ static cudaError_t reduce_dispatch(const AlsDesc &d, int mode, cudaStream_t st) 
     const long long cnt = (long long)d.n[mode] * d.R;
     dim3 grid((unsigned)((cnt + 255) / 256), d.nrep);
     if (d.elem == 0)
-        k_reduce<double><<<grid, 256, 0, st>>>((const double *)d.part, d.prs, P, cnt, d.M, d.mrs, d.conv);
+        k_reduce<double><<<grid, 256, 0, st>>>((const double *)d.part, d.prs, P, d.n[mode], d.R, d.pr, d.M, d.mrs,
+                                               d.conv);
     else
-        k_reduce<float><<<grid, 256, 0, st>>>((const float *)d.part, d.prs, P, cnt, d.M, d.mrs, d.conv);
+        k_reduce<float><<<grid, 256, 0, st>>>((const float *)d.part, d.prs, P, d.n[mode], d.R, d.pr, d.M, d.mrs,
+                                              d.conv);
     return cudaGetLastError();
 }
 
@@ -1305,7 +1312,7 @@ cudaError_t launch_store_m(const AlsDesc &d, int mode, void *Mout, cudaStream_t 
 }
 
 cudaError_t launch_reduce_tail(const AlsDesc &d, int mode, cudaStream_t st) {
-    if (d.elem != 0) {
+    if (d.elem != 0 && !d.tail64) {
         // float32 factors: row kernel (partial reduction fused) + finish kernel
         const int RP = rp_of(d.R);
         cudaLaunchConfig_t cfg = {};

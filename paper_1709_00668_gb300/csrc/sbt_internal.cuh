@@ -346,6 +346,8 @@ struct AlsDesc {
                            // mode-3 MTTKRP is then M3(kk, r) = sum_j Y_kk(j, r) B(j, r) (k_mtt_memo)
     long long yrs;         // floats per repetition of ymem
     int rep0;              // repetition index of the first repetition (Philox counters of the start)
+    int tail64;            // float32 factor path with the float64 tail (k_reduce + k_tail): Grams in G,
+                           // no V^-1 beside the passes
     // tile choices
     int spc, nks, nib, jc; // row kernel: slices per CTA, slice splits, row blocks, column chunk
     long long rows_per;    // column kernel: rows per CTA

@@ -86,7 +86,8 @@ class SbtOptions(ctypes.Structure):
                 ("refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("mode3_pass", ctypes.c_int32), ("als_groups", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("get_rank", ctypes.c_int32),
-                ("get_rank_trials", ctypes.c_int32), ("get_rank_threshold", ctypes.c_double)]
+                ("get_rank_trials", ctypes.c_int32), ("get_rank_threshold", ctypes.c_double),
+                ("fp64_tail", ctypes.c_int32)]
 
 
 class SbtStats(ctypes.Structure):
