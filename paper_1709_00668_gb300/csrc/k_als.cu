@@ -1375,9 +1375,13 @@ static cudaError_t raise_smem_limits() {
 template <int RP>
 static cudaError_t tail_attributes() {
     const int smem = (int)tail_smem_bytes<RP>();
+    const cudaFuncAttribute co = cudaFuncAttributePreferredSharedMemoryCarveout;
     cudaError_t e = cudaFuncSetAttribute(k_tail_rows<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    // the largest carveout, like the tensor-core MTTKRP they alternate with
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, false>, co, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tail_rows<RP, true>, co, cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -1395,6 +1399,10 @@ cudaError_t set_als_kernel_attributes() {
     if (e == cudaSuccess) e = tail_attributes<8>();
     if (e == cudaSuccess) e = tail_attributes<16>();
     if (e == cudaSuccess) e = tail_attributes<32>();
+    const cudaFuncAttribute co = cudaFuncAttributePreferredSharedMemoryCarveout;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xinv, co, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_memo<16>, co, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_memo<32>, co, cudaSharedmemCarveoutMaxShared);
     return e;
 }
 

@@ -220,6 +220,11 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     // kernel just before; it is read again after the wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (p.conv[rep]) return;
+    if (threadIdx.x == 0) {
+        // fetch the tensor maps while the barriers and tensor memory are set up
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+        if (p.split) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap_lo) : "memory");
+    }
     const int pb = blockIdx.x % p.npb, ks = blockIdx.x / p.npb;
     const int k0 = ks * p.spc, k1 = min(p.Kp, k0 + p.spc);
     const int nsl = k1 - k0;
@@ -248,17 +253,27 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         }
         sh->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (p.br < TC_M) {
-        // TMA fills rows [0, br) of a stage; rows [br, 128) stay zero (whole
-        // 8-row swizzle atoms), so the M = 128 products add nothing there
-        const int zb = (TC_M - p.br) * 128 / 16;  // 16-byte words per stage
-        for (int e = threadIdx.x; e < S * zb; e += blockDim.x) {
-            const int st = e / zb, w = e % zb;
-            reinterpret_cast<uint4 *>(ring + (size_t)st * TC_BOX_BYTES + (size_t)p.br * 128)[w] = make_uint4(0, 0, 0, 0);
-        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // the producer (thread 0, which initialised the barriers) issues its
+    // first S boxes at once: every stage starts empty, so they need no wait,
+    // and they fly while tensor memory and the B operand are set up
+    const int nkb2 = p.nkb * (1 + p.split);
+    const int nbox = nsl * nkb2;
+    const int pre = min(S, nbox);
+    const uint64_t pol = l2_evict_first_policy();
+    auto issue_box = [&](int b, int stage) {
+        const int t = b / nkb2, kb2 = b % nkb2;
+        const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
+        mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
+        tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * KE, pb * p.br,
+                    rep * p.Kp + k0 + t, &sh->full[stage], pol);
+    };
+    if (threadIdx.x == 0)
+        for (int b = 0; b < pre; ++b) issue_box(b, b);
+    // TMA fills rows [0, br) of a stage; rows [br, 128) keep whatever the
+    // shared memory held.  Row i of an M = 128 product depends on row i of A
+    // only, so those rows reach accumulator rows the epilogue never reads.
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
                      "r"(2 * TS));
@@ -278,6 +293,15 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
         // epilogue weights C(kk, :) (times the slice scale for float8)
         const float *F = p.F + rep * p.frs;
         const int t = threadIdx.x - 32;
+        // the epilogue weights' first round (up to 320 entries) is loaded
+        // with the factor, so the two L2 round trips overlap
+        const float *W = p.W + rep * p.wrs;
+        float w0[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = t + u * 160, tt = e / RH, r = e % RH;
+            w0[u] = (p.epi == 0 && e < nsl * RH && r < R) ? W[(long long)(k0 + tt) * R + r] : 0.f;
+        }
         // two contraction indices per thread and round, all loads of a round
         // in flight before the conversions
         for (int j0 = t; j0 < p.nkb * KE; j0 += 2 * 160) {
@@ -329,13 +353,12 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             }
         }
         if (p.epi == 0) {
-            const float *W = p.W + rep * p.wrs;
             for (int e0 = t; e0 < nsl * RH; e0 += 2 * 160) {
                 float w[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int e = e0 + u * 160, tt = e / RH, r = e % RH;
-                    w[u] = (e < nsl * RH && r < R) ? W[(long long)(k0 + tt) * R + r] : 0.f;
+                    w[u] = e0 == t ? w0[u] : ((e < nsl * RH && r < R) ? W[(long long)(k0 + tt) * R + r] : 0.f);
                     if (FP8 && e < nsl * RH) w[u] *= p.sscale[(long long)rep * p.Kp + k0 + tt];
                 }
 #pragma unroll
@@ -349,24 +372,18 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
 
     if (warp == 0) {
         if (lane == 0) {
-            // producer
-            int stage = 0;
-            uint32_t phase = 0;
-            int issued = 0;
-            const int nkb2 = p.nkb * (1 + p.split);
-            const uint64_t pol = l2_evict_first_policy();
-            for (int t = 0; t < nsl && !*abort_flag; ++t) {
-                for (int kb2 = 0; kb2 < nkb2; ++kb2) {
-                    const int kb = kb2 < p.nkb ? kb2 : kb2 - p.nkb;
-                    if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
-                    mbar_expect_tx(&sh->full[stage], (uint32_t)p.br * 128u);
-                    tma_load_3d(ring + (size_t)stage * TC_BOX_BYTES, kb2 < p.nkb ? &tmap : &tmap_lo, kb * KE,
-                                pb * p.br, rep * p.Kp + k0 + t, &sh->full[stage], pol);
-                    ++issued;
-                    if (++stage == S) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
+            // producer: the boxes after the first S, each into the stage the
+            // MMA released
+            int stage = pre % S;
+            uint32_t phase = pre == S ? 1u : 0u;
+            int issued = pre;
+            for (int b = pre; b < nbox && !*abort_flag; ++b) {
+                if (!tc_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+                issue_box(b, stage);
+                ++issued;
+                if (++stage == S) {
+                    stage = 0;
+                    phase ^= 1u;
                 }
             }
             if (*abort_flag) {
@@ -490,7 +507,7 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             } else {
 #pragma unroll
                 for (int r = 0; r < RH; ++r) {
-                    float v = warp_sum(z[r] * arow[r]);
+                    float v = warp_sum(valid ? z[r] * arow[r] : 0.f);  // rows past the tile hold no data
                     if (lane == 0) sh->red[quarter][r] = v;
                 }
                 epi_bar();
@@ -744,12 +761,22 @@ cudaError_t launch_mttkrp_tc(const CUtensorMap &tmap, const CUtensorMap *tmap_lo
 
 // Raise the dynamic shared-memory limit of the tensor-core kernels once,
 // outside any stream capture.
+template <int N, bool FP8>
+static cudaError_t tc_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<N, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // the largest shared-memory carveout, as for the tails around it, so that
+    // the SM is not reconfigured at every kernel boundary of the ALS chain
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mtt_tc<N, FP8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 cudaError_t set_tc_kernel_attributes() {
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_mtt_tc<48, false>, a, 200 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<64, false>, a, 200 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<48, true>, a, 200 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mtt_tc<96, true>, a, 200 * 1024);
+    cudaError_t e = tc_attributes<48, false>();
+    if (e == cudaSuccess) e = tc_attributes<64, false>();
+    if (e == cudaSuccess) e = tc_attributes<48, true>();
+    if (e == cudaSuccess) e = tc_attributes<96, true>();
     return e;
 }
 
