@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--sparse", action="store_true",
                     help="sparse COO workload: 100000^3, R=10 planted components on 1000-index supports, "
                          "1e7 coordinates each, K0=10000, batches of 1000 slices, s=20, r=8 (one JSON line)")
+    ap.add_argument("--latency", action="store_true",
+                    help="small dense FP64 workload 100x100x(50+5x10), R=5, s=2, r=4: microseconds per batch "
+                         "update, the CUDA-graph ALS against the persistent ALS (one JSON line)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same summary shapes, 200 initial slices (a few GB on the device)")
     args = ap.parse_args()
@@ -462,10 +465,7 @@ def run_ours(args):
     fit_gpu = ctx.fit()
     # Relative Fitness against CP-ALS recomputed on the whole final tensor
     # (after the timed region)
-    # (a warm-start run with a 5-iteration cap that also recomputed once ran
-    # past its time limit, cause not found: those runs skip it)
-    skip_cp = args.no_recompute or args.warm_start or args.max_iters > 0
-    fit_cp = None if skip_cp else ctx.recompute(max_iters=w["max_iters"], tol=w["tol"], seed=w["seed"])[0]
+    fit_cp = None if args.no_recompute else ctx.recompute(max_iters=w["max_iters"], tol=w["tol"], seed=w["seed"])[0]
     ctx.close()
 
     # profiling pass: the same batches on a fresh context, with CUDA events
@@ -616,6 +616,9 @@ class _ServedStream:
         return X.contiguous()
 
 
+STALL_S = 60.0  # --serve: seconds without a finished batch that end the run with a report
+
+
 def run_serve(args):
     """Serving workload: `--streams` live streams absorbed through one server.
     A closed loop (--rate 0) keeps one batch outstanding per stream; otherwise
@@ -680,8 +683,23 @@ def run_serve(args):
     next_arrival = t0
     closed = args.rate <= 0
 
+    last_done = [time.perf_counter()]
+
+    def stalled():
+        # no batch finished for STALL_S while some were pending: report the
+        # server's state and leave (os._exit: a worker may be inside a call)
+        if not pending or time.perf_counter() - last_done[0] < STALL_S:
+            return
+        st = srv.stats()
+        why = ("admission: every queued batch needs memory the resident streams hold"
+               if st["in_flight"] == 0 else "batches in flight made no progress")
+        print(json.dumps({"metric": "served slices absorbed/sec", "value": None, "error": f"stalled: {why}",
+                          "stall_seconds": STALL_S, "server": st, "pending": len(pending)}), flush=True)
+        os._exit(1)
+
     def reap(block_ms):
         nonlocal done_slices, next_seed
+        stalled()
         for t in list(pending):
             try:
                 res = srv.wait(t, block_ms)
@@ -689,6 +707,7 @@ def run_serve(args):
                 if e.status == sbt.SBT_E_TIMEOUT:
                     continue
                 raise
+            last_done[0] = time.perf_counter()
             block_ms = 0
             sid, X, k_after = pending.pop(t)
             busy_sid.discard(sid)
@@ -925,8 +944,75 @@ def run_sparse(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+LATENCY = dict(I=100, J=100, K0=50, batches=5, batch=10, R=5, noise=0.01, s=2, r=4, tol=1e-6, max_iters=50, seed=0)
+LATENCY_NAME = "dense FP64 100x100x(50+5x10), R=5, s=2, r=4, tol 1e-6, at most 50 iterations"
+
+
+def run_latency(args):
+    """Launch-bound workload: wall-clock microseconds per batch update (the
+    call through the stream's synchronisation, inputs resident on the device)
+    over runs of the 5-batch sequence from a fresh context, the ALS as a CUDA
+    graph of per-step kernels and as one persistent cooperative launch.  The
+    two give the same bits (float64 tail on both); the line reports both,
+    with their kernel launches per batch and the fit after the last batch."""
+    import torch
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_00668_gb300 import sbt, synth
+    w = LATENCY
+    K = w["K0"] + w["batches"] * w["batch"]
+    p = synth.planted_dense(w["I"], w["J"], K, w["R"], noise=w["noise"], seed=w["seed"], dtype=torch.float64,
+                            device=device)
+    stream = torch.cuda.current_stream(device)
+    X0 = p.X[:w["K0"]]
+    news = [p.X[w["K0"] + q * w["batch"]:w["K0"] + (q + 1) * w["batch"]] for q in range(w["batches"])]
+    out = {}
+    for name, extra in (("graph", {}), ("persistent", {"persistent_als": 1})):
+        # K_capacity and max_batch: the context sizes its store and workspace
+        # at creation, so that no update allocates (a cudaFree synchronises
+        # the device)
+        o = dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
+                 seed=w["seed"], prec="f64", cuda_stream=stream.cuda_stream, K_capacity=K, max_batch=w["batch"],
+                 **extra)
+        per, launches, fits = [], [], []
+        for run in range(args.warmup + args.steps):
+            ctx = sbt.SamBaTen(X0, w["R"], **o)
+            torch.cuda.synchronize()
+            ctx.profile_reset(timing=False)
+            for Xn in news:
+                t0 = time.perf_counter()
+                ctx.update(Xn)
+                torch.cuda.synchronize()
+                if run >= args.warmup:
+                    per.append(1e6 * (time.perf_counter() - t0))
+            launches.append(ctx.profile()["launches"] / w["batches"])
+            fits.append(ctx.fit())
+            ctx.close()
+        out[name] = {"us_per_batch_p50": percentile(per, 0.5), "us_per_batch_mean": sum(per) / len(per),
+                     "us_per_batch_p99": percentile(per, 0.99), "launches_per_batch": launches[-1],
+                     "fit_after_last_batch": fits[-1]}
+    g, q = out["graph"], out["persistent"]
+    line = {"metric": "microseconds per batch update (small dense FP64)", "value": q["us_per_batch_p50"],
+            "unit": "us/batch", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": LATENCY_NAME, **w, "runs": "each step is the 5-batch sequence from a fresh "
+                       "context; value = p50 over the timed batches of the persistent ALS"},
+            "graph_als": g, "persistent_als": q, "same_fit": g["fit_after_last_batch"] == q["fit_after_last_batch"],
+            "gpu_launches": q["launches_per_batch"], "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.latency:
+        return run_latency(args)
     if args.serve:
         return run_serve(args)
     if args.sweep:

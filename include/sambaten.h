@@ -139,6 +139,13 @@ typedef struct {
                               one CTA per repetition, after the MTTKRP partials are summed in float64;
                               0 (default): double-float (~44 bits) on the float32 pipes, V^-1 beside
                               the MTTKRP pass */
+    int32_t persistent_als;/* 1: the summary ALS of all repetitions, when its MTTKRP runs on the CUDA
+                              cores (SBT_PREC_F64 / F32, or BF16 without the tensor-core plan) and the
+                              context is dense, is one persistent cooperative launch: the steps of
+                              every iteration separated by bounded grid barriers instead of kernel
+                              boundaries, the float64 tail (as fp64_tail); the same results as the
+                              launch-per-step ALS with the float64 tail.  Ignored with per-launch
+                              profiling timing.  0 (default): a CUDA graph of per-step kernels */
 } sbt_options;
 
 typedef struct {
@@ -468,8 +475,10 @@ sbt_status sbt_server_open_stream(sbt_server *srv, const sbt_tensor *X0, int32_t
 sbt_status sbt_server_submit(sbt_server *srv, int32_t sid, const sbt_tensor *X_new, uint64_t *ticket);
 
 /* Wait for a batch (timeout_ms < 0: no limit).  On SBT_OK *res (may be NULL)
- * receives its result and the ticket is released; SBT_E_TIMEOUT leaves it
- * pending; SBT_E_INVALID: unknown ticket.  One thread waits for a ticket. */
+ * receives its result and the ticket is released; if the batch failed
+ * (res->status), its message becomes the calling thread's sbt_last_error().
+ * SBT_E_TIMEOUT leaves it pending; SBT_E_INVALID: unknown ticket.  One thread
+ * waits for a ticket. */
 sbt_status sbt_server_wait(sbt_server *srv, uint64_t ticket, int32_t timeout_ms, sbt_request_result *res);
 
 /* The stream's context, for sbt_factors / sbt_fit / sbt_stats while the
@@ -485,7 +494,9 @@ sbt_status sbt_server_stats(sbt_server *srv, sbt_serving_stats *st);
 sbt_status sbt_server_stats_reset(sbt_server *srv);
 
 /* Fail the batches not yet started (SBT_E_STATE), let the ones in flight
- * finish, stop the workers and free every stream.  NULL is a no-op. */
+ * finish, stop the workers, wait until no thread is inside sbt_server_wait,
+ * and free every stream.  No other call may start on the server once destroy
+ * has begun.  NULL is a no-op. */
 void sbt_server_destroy(sbt_server *srv);
 
 /* ---- device-level operations (device pointers, ordered on `stream`) -------

@@ -192,6 +192,7 @@ struct sbt_ctx {
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     Buf ymem;                           // mode-2 pass products for the mode-3 MTTKRP (mode3_pass 0)
     Buf grscr, gcc, rnew;               // GetRank: CorConDia scratch, scores + status words, R_new per repetition
+    Buf psync;                          // grid-barrier words of the persistent ALS
     std::vector<int> last_rank;         // components of each summary of the last update
     Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
     // COO contexts (sbt_init_coo): nonzeros grouped by slice, and the summary workspace
@@ -290,6 +291,7 @@ static sbt_status check_options(const sbt_options *o, int R) {
     if (o->warm_start != 0 && o->warm_start != 1) return fail(SBT_E_INVALID, "warm_start must be 0 or 1");
     if (o->get_rank != 0 && o->get_rank != 1) return fail(SBT_E_INVALID, "get_rank must be 0 or 1");
     if (o->fp64_tail != 0 && o->fp64_tail != 1) return fail(SBT_E_INVALID, "fp64_tail must be 0 or 1");
+    if (o->persistent_als != 0 && o->persistent_als != 1) return fail(SBT_E_INVALID, "persistent_als must be 0 or 1");
     if (o->get_rank_trials < 0 || o->get_rank_trials > 16) return fail(SBT_E_INVALID, "get_rank_trials out of [0, 16]");
     if (!std::isfinite(o->get_rank_threshold)) return fail(SBT_E_INVALID, "get_rank_threshold must be finite");
     if (o->get_rank && (o->prec == SBT_PREC_FP8 || o->refine_sweeps > 0))
@@ -380,7 +382,9 @@ static void als_shape(const sbt_ctx *c, AlsDesc &d, int nrep, const int n[3], in
     d.tol = c->opt.tol;
     d.max_iters = max_iters;
     d.fixed_iters = c->opt.fixed_iters;
-    d.tail64 = elem != 0 && c->opt.fp64_tail ? 1 : 0;
+    // the float64 tail: asked for, or part of the persistent ALS (which a
+    // tensor-core plan, decided later, turns off again)
+    d.tail64 = elem != 0 && (c->opt.fp64_tail || c->opt.persistent_als) ? 1 : 0;
     d.pr = elem == 0 ? d.R : (d.R + 3) / 4 * 4;
     choose_tiles(d, c->num_sms);
     const int nmax = std::max(n[0], std::max(n[1], n[2]));
@@ -773,6 +777,13 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
         CK(cudaStreamSynchronize(c->stream));
         settle_als_counts(c);
     }
+    if (c->opt.persistent_als && !(tc && tc->on) && !c->coo && !c->timing) {
+        // one cooperative launch for every iteration and repetition
+        TRY(c->psync.ensure(4 * sizeof(unsigned)));
+        CK(launch_als_persistent(d, max_iters, c->psync.as<unsigned>(), &c->status.as<DevStatus>()->err,
+                                 c->num_sms, c->stream));
+        return SBT_OK;
+    }
     if (!c->timing) {
         TRY(c->passes.ensure(sizeof(int)));
         TRY(c->h_passes.ensure(sizeof(int)));
@@ -1150,7 +1161,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
             &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale, &c->ymem,
-            &c->grscr, &c->gcc, &c->rnew,
+            &c->grscr, &c->gcc, &c->rnew, &c->psync,
             &c->si, &c->sj, &c->sv, &c->sptr, &c->cin_i, &c->cin_j, &c->cin_k, &c->cin_v, &c->ccnt, &c->cfill,
             &c->cmax, &c->posI, &c->posJ, &c->gcnt, &c->goff, &c->gtot, &c->vmax, &c->fexp, &c->eii, &c->ejj,
             &c->ekk, &c->ev, &c->perm1, &c->perm2, &c->rp1, &c->rp2, &c->gc1, &c->gc2, &c->gf1, &c->gf2};
@@ -1553,6 +1564,7 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     // bfloat16 summaries: tensor-core MTTKRP over the summary and its transposed copy
     TcPlan &tc = c->tc;
     tc.on = u.tc && !c->opt.get_rank;
+    if (tc.on && !c->opt.fp64_tail) d.tail64 = 0;  // the persistent ALS does not apply to the tensor-core plan
     if (c->opt.get_rank) {  // Section 3.2: the rank of every summary first (Algorithm 2)
         std::vector<int> rn;
         TRY(get_rank_als(c, u, d, rn));

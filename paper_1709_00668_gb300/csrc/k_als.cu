@@ -99,18 +99,16 @@ template <> struct FactorOf<double> { using T = double; };
 //   mode 1: part[ks][ii][r] = sum_kk z(kk,ii,r) C(kk,r)
 //   mode 3: part[ib][kk][r] = sum_ii z(kk,ii,r) A(ii,r)
 template <typename TX, int RP>
-__global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
+__device__ void mtt_row_block(const AlsDesc &d, int mode, int bx, int rep, unsigned char *smem_raw) {
     using TF = typename FactorOf<TX>::T;
     constexpr int V = VecLd<TX, TF>::V;
-    const int rep = blockIdx.y;
     if (d.conv[rep]) return;
     const int NI = d.n[0], NJ = d.n[1], Kp = d.n[2], R = d.R, ldj = d.ldj;
-    const int ib = blockIdx.x % d.nib, ks = blockIdx.x / d.nib;
+    const int ib = bx % d.nib, ks = bx / d.nib;
     const int k0 = ks * d.spc, k1 = min(Kp, k0 + d.spc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ii = ib * 8 + warp;
     const int jc = d.jc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     TF *Bt = reinterpret_cast<TF *>(smem_raw);               // [RP][jc]
     TF *z = Bt + (size_t)RP * jc;                            // [spc][8][RP]
     const TF *A = (const TF *)d.U[0] + (long long)rep * NI * R;
@@ -185,18 +183,23 @@ __global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
     }
 }
 
+template <typename TX, int RP>
+__global__ void __launch_bounds__(256) k_mtt_row(AlsDesc d, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mtt_row_block<TX, RP>(d, mode, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Column kernel: mode 2.  A CTA owns 32*COLS columns jj and a range of
 // flattened rows (kk, ii); M2(jj, r) += X[kk][ii][jj] A(ii,r) C(kk,r).  Each
 // warp takes every 8th row; warps are summed in shared memory in fixed order.
 template <typename TX, int RP, int COLS>
-__global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
+__device__ void mtt_col_block(const AlsDesc &d, int bx, int rep, unsigned char *smem_raw) {
     using TF = typename FactorOf<TX>::T;
-    const int rep = blockIdx.y;
     if (d.conv[rep]) return;
     const int NI = d.n[0], NJ = d.n[1], Kp = d.n[2], R = d.R, ldj = d.ldj;
     const int njb = (NJ + 32 * COLS - 1) / (32 * COLS);
-    const int jb = blockIdx.x % njb, rs = blockIdx.x / njb;
+    const int jb = bx % njb, rs = bx / njb;
     const long long rows = (long long)Kp * NI;
     const long long r0 = (long long)rs * d.rows_per, r1 = min(rows, r0 + d.rows_per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,7 +208,6 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
         const int cols = min(NJ, (jb + 1) * 32 * COLS) - jb * 32 * COLS;
         atomicAdd(d.bytes_ctr, (unsigned long long)max(0LL, r1 - r0) * cols * sizeof(TX));
     }
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     TF *red = reinterpret_cast<TF *>(smem_raw);  // [8][32*COLS][RP]
     const TF *A = (const TF *)d.U[0] + (long long)rep * NI * R;
     const TF *C = (const TF *)d.U[2] + (long long)rep * Kp * R;
@@ -244,6 +246,12 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
         for (int w = 0; w < 8; ++w) s += red[((size_t)w * 32 * COLS + cl) * RP + r];
         part[((long long)rs * NJ + jj) * d.pr + r] = s;
     }
+}
+
+template <typename TX, int RP, int COLS>
+__global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mtt_col_block<TX, RP, COLS>(d, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,8 +319,7 @@ __device__ void warp_chol_inverse(const double *L, double *Vi, int R, int lane) 
 // ---------------------------------------------------------------------------
 // Tail of one mode for one repetition (one CTA per repetition).
 template <typename TF>
-__global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
-    const int rep = blockIdx.x;
+__device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
     if (d.conv[rep]) return;
     const int R = d.R, n = d.n[mode];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -446,6 +453,11 @@ __global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
             for (int r = 0; r < R; ++r) d.lam[rep * R + r] = lam_s[r];
         }
     }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(256) k_tail(AlsDesc d, int mode) {
+    tail_rep<TF>(d, mode, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1475,6 +1487,146 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
                                                  stream_id, batch, rowsq, ws);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The whole ALS of all repetitions as one persistent launch (CUDA-core
+// MTTKRP path): every CTA stays resident (cooperative launch) and the
+// iterations' steps are separated by a grid barrier instead of kernel
+// boundaries.  Per iteration and mode: the MTTKRP's blocks (the row or column
+// kernel's, as virtual blocks spread over the CTAs) -> barrier -> per
+// repetition the partials summed in order and the float64 tail (CTA b takes
+// repetitions b, b + grid, ...) -> barrier; after mode 3 every CTA reads the
+// convergence flags and all leave together.  The same device functions and
+// summation orders as the separate kernels (k_mtt_row / k_mtt_col, k_reduce,
+// k_tail), so the results are the same bits as the kernel-per-step ALS with
+// the float64 tail.
+constexpr unsigned PA_SPIN_LIMIT = 1u << 22;
+
+struct PersistSync {
+    unsigned *count;  // arrivals at the current barrier (zero at launch)
+    unsigned *gen;    // barrier generation
+    int *abort;       // a barrier gave up: every CTA leaves
+};
+
+// Grid barrier: the last CTA to arrive resets the count and advances the
+// generation; the others poll it (bounded; on timeout the error word gets
+// ERR_TIMEOUT and every CTA leaves at its next barrier).  Writes before the
+// barrier are visible to every thread after it (fence, arrive, poll, fence,
+// then the CTA barrier).  Returns false if the launch is giving up.
+__device__ bool pa_barrier(const PersistSync &ps, unsigned *err) {
+    __shared__ int go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = ps.gen;
+        volatile int *ab = ps.abort;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(ps.count, 1u) == gridDim.x - 1) {
+            *ps.count = 0;
+            __threadfence();
+            atomicAdd(ps.gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g && !*ab) {
+                if (++it > PA_SPIN_LIMIT) {
+                    atomicExch(ps.abort, 1);
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        go = !*ab;
+    }
+    __syncthreads();
+    return go != 0;
+}
+
+template <typename TX, int RP, int COLS>
+__global__ void __launch_bounds__(256) k_als_persistent(AlsDesc d, PersistSync ps, unsigned *err, int max_iters) {
+    using TF = typename FactorOf<TX>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
+    for (int it = 0; it < max_iters; ++it) {
+        for (int mode = 0; mode < 3; ++mode) {
+            const int per = mode == 1 ? njb * d.nrs : d.nib * d.nks;
+            const int nvb = per * d.nrep;
+            for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+                if (mode == 1) mtt_col_block<TX, RP, COLS>(d, vb % per, vb / per, smem_raw);
+                else mtt_row_block<TX, RP>(d, mode, vb % per, vb / per, smem_raw);
+                __syncthreads();  // the shared memory is reused by the next virtual block
+            }
+            if (!pa_barrier(ps, err)) return;
+            for (int rep = blockIdx.x; rep < d.nrep; rep += gridDim.x) {
+                if (!d.conv[rep]) {
+                    // k_reduce's sums for this repetition, in partial order
+                    const int n = d.n[mode], P = d.P[mode];
+                    const TF *part = (const TF *)d.part + rep * d.prs;
+                    for (long long e = threadIdx.x; e < (long long)n * d.R; e += blockDim.x) {
+                        const long long x = e / d.R, r = e % d.R;
+                        double sum = 0.0;
+                        for (int q = 0; q < P; ++q) sum += (double)part[(long long)q * n * d.pr + x * d.pr + r];
+                        d.M[rep * d.mrs + e] = sum;
+                    }
+                }
+                __syncthreads();
+                tail_rep<TF>(d, mode, rep);
+                __syncthreads();
+            }
+            if (!pa_barrier(ps, err)) return;
+        }
+        bool all = true;
+        for (int q = 0; q < d.nrep; ++q) all = all && ((volatile const int *)d.conv)[q] != 0;
+        if (all) break;
+    }
+}
+
+template <typename TX, int RP>
+static cudaError_t persistent_rp(const AlsDesc &d, int max_iters, const PersistSync &ps, unsigned *err,
+                                 int num_sms, cudaStream_t st) {
+    constexpr int COLS = cols_for<TX, RP>();
+    auto kern = k_als_persistent<TX, RP, COLS>;
+    const size_t smem = std::max(row_smem(d), col_smem(d));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // as many CTAs as the largest step has blocks, at most all co-resident
+    const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
+    const long long want = std::max<long long>(
+        std::max<long long>((long long)d.nib * d.nks, (long long)njb * d.nrs) * d.nrep, d.nrep);
+    const int grid = (int)std::min<long long>(want, (long long)per_sm * num_sms);
+    AlsDesc dd = d;
+    PersistSync pp = ps;
+    unsigned *ee = err;
+    int mi = max_iters;
+    void *args[] = {&dd, &pp, &ee, &mi};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, smem, st);
+}
+
+template <typename TX>
+static cudaError_t persistent_tx(const AlsDesc &d, int max_iters, const PersistSync &ps, unsigned *err,
+                                 int num_sms, cudaStream_t st) {
+    const int RP = rp_of(d.R);
+    if (RP == 8) return persistent_rp<TX, 8>(d, max_iters, ps, err, num_sms, st);
+    if (RP == 16) return persistent_rp<TX, 16>(d, max_iters, ps, err, num_sms, st);
+    return persistent_rp<TX, 32>(d, max_iters, ps, err, num_sms, st);
+}
+
+cudaError_t launch_als_persistent(const AlsDesc &d, int max_iters, unsigned *sync_words, unsigned *err, int num_sms,
+                                  cudaStream_t st) {
+    // sync_words: [count, generation, abort], zeroed here
+    cudaError_t e = cudaMemsetAsync(sync_words, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    PersistSync ps{sync_words, sync_words + 1, reinterpret_cast<int *>(sync_words + 2)};
+    if (d.elem == 0) return persistent_tx<double>(d, max_iters, ps, err, num_sms, st);
+    if (d.elem == 1) return persistent_tx<float>(d, max_iters, ps, err, num_sms, st);
+    return persistent_tx<__nv_bfloat16>(d, max_iters, ps, err, num_sms, st);
 }
 
 // ---------------------------------------------------------------------------

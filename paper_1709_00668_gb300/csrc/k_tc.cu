@@ -219,7 +219,10 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     // at once.  The flag read here may predate a convergence decided by the
     // kernel just before; it is read again after the wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (p.conv[rep]) return;
+    // one decision for the whole CTA: the kernel before may be writing the
+    // flag now, and threads that read it at different moments must not
+    // split (some leaving, the rest waiting at a barrier for them)
+    if (__syncthreads_or(p.conv[rep] != 0)) return;
     if (threadIdx.x == 0) {
         // fetch the tensor maps while the barriers and tensor memory are set up
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
@@ -274,18 +277,24 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
     // TMA fills rows [0, br) of a stage; rows [br, 128) keep whatever the
     // shared memory held.  Row i of an M = 128 product depends on row i of A
     // only, so those rows reach accumulator rows the epilogue never reads.
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "r"(2 * TS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sh->tmem_base;
+    __syncthreads();  // the barriers' initialisation, seen by every warp
+    uint32_t tmem = 0;
     const int R = p.R;
     if (warp != 0) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
+        // Tensor memory is allocated only now, once the grid this one depends
+        // on has finished.  tcgen05.alloc blocks while the SM's 512 columns
+        // are taken; a CTA launched early (the tail before it triggers at its
+        // start) that held columns while it waited here could hold them
+        // against a CTA of an earlier MTTKRP on the same SM, which that tail
+        // waits for: a cycle.  After the wait, every holder depends only on
+        // its own copies and products, so every allocation is served.
+        if (warp == 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sh->tmem_base)),
+                         "r"(2 * TS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
         if (threadIdx.x == 32 && p.conv[rep]) *abort_flag = 2;  // converged just before: skip, no error
         // warps 1-5 (160 threads), while warp 0 already streams X: the B operand
         // (row n of term q holds column n - q RH of the factor; K-major,
@@ -367,7 +376,10 @@ __global__ void __launch_bounds__(192, 2) k_mtt_tc(const __grid_constant__ CUten
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
         asm volatile("bar.sync 2, 160;" ::: "memory");
+        tc_fence_after();
+        tmem = sh->tmem_base;  // written by warp 1's allocation
     }
 
     if (warp == 0) {

@@ -408,6 +408,11 @@ cudaError_t launch_core_consistency(int elem, const void *X, long long K, long l
                                     double *scratch, int *status, double *out, cudaStream_t st);
 size_t core_consistency_scratch_doubles(long long K, long long I, long long J, int R);
 cudaError_t launch_widen(const float *in, double *out, long long n, cudaStream_t st);
+// The whole ALS (CUDA-core MTTKRP, float64 tail) of d's repetitions as one
+// persistent cooperative launch; sync_words: 3 device words (zeroed here);
+// err: the device status word (ERR_TIMEOUT if a grid barrier gave up)
+cudaError_t launch_als_persistent(const AlsDesc &d, int max_iters, unsigned *sync_words, unsigned *err, int num_sms,
+                                  cudaStream_t st);
 
 // mode 3 after a memoised mode-2 pass: M3 from d.ymem and the new B as the
 // single partial of the mode-3 tail, and V^-1 of mode 3 (PDL launch)

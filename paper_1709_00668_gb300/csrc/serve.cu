@@ -52,6 +52,7 @@ struct Request {
     Clock::time_point t_submit, t_start, t_end;
     bool done = false;
     sbt_request_result res{};
+    std::string err;  // message of a failed batch, handed to the thread that waits for it
 };
 
 struct Stream {
@@ -94,6 +95,7 @@ struct sbt_server {
     std::vector<double> lat_total, lat_service;
     Clock::time_point t_reset, busy_since;
     double busy_ms = 0.0;
+    int64_t waiters = 0;  // threads inside sbt_server_wait (destroy frees nothing before they leave)
 
     void worker();
     // the first admissible stream of `ready` (-1: none); fails batches that can never fit
@@ -133,6 +135,7 @@ int32_t sbt_server::pick_locked() {
         if (st != SBT_OK) {  // can never run: fail it, keep the stream's order
             s.queue.pop_front();
             queued -= 1;
+            q->err = sbt_last_error();
             q->t_start = Clock::now();
             finish_locked(q, st);
             if (s.queue.empty()) {
@@ -180,6 +183,7 @@ void sbt_server::worker() {
         sbt_status st = sbt_update(ctx, &q->X);
         int64_t K = 0;
         if (st == SBT_OK) st = sbt_factors(ctx, nullptr, nullptr, nullptr, nullptr, &K);
+        const std::string err = st == SBT_OK ? std::string() : std::string(sbt_last_error());
         uint64_t now_bytes = 0;
         sbt_device_bytes(ctx, &now_bytes);
         lock.lock();
@@ -187,6 +191,7 @@ void sbt_server::worker() {
         resident = resident - s2.bytes + now_bytes;
         s2.bytes = now_bytes;
         q->res.K = K;
+        q->err = err;
         finish_locked(q, st);
         in_flight -= 1;
         if (in_flight == 0) busy_ms += ms_between(busy_since, Clock::now());
@@ -312,12 +317,16 @@ extern "C" sbt_status sbt_server_wait(sbt_server *srv, uint64_t ticket, int32_t 
     if (it == srv->requests.end()) return fail(SBT_E_INVALID, "unknown ticket");
     Request *q = it->second;
     auto pred = [&] { return q->done; };
-    if (timeout_ms < 0) {
-        srv->cv_done.wait(lock, pred);
-    } else if (!srv->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred)) {
-        return fail(SBT_E_TIMEOUT, "batch not finished within the timeout");
-    }
+    srv->waiters += 1;
+    bool ok = true;
+    if (timeout_ms < 0) srv->cv_done.wait(lock, pred);
+    else ok = srv->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred);
+    srv->waiters -= 1;
+    if (srv->waiters == 0) srv->cv_done.notify_all();  // a destroy may wait for the last waiter
+    if (!ok) return fail(SBT_E_TIMEOUT, "batch not finished within the timeout");
     if (res) *res = q->res;
+    // a failed batch's message becomes this thread's last error
+    if (q->res.status != SBT_OK) sbt::set_last_error(q->err);
     srv->requests.erase(it);
     delete q;
     return SBT_OK;
@@ -411,6 +420,13 @@ extern "C" void sbt_server_destroy(sbt_server *srv) {
         srv->cv_done.notify_all();
     }
     for (auto &t : srv->workers) t.join();  // in-flight batches finish first
+    {
+        // every ticket is done now; threads woken inside sbt_server_wait
+        // leave before the requests and the server are freed
+        std::unique_lock<std::mutex> lock(srv->mu);
+        srv->cv_done.notify_all();
+        srv->cv_done.wait(lock, [&] { return srv->waiters == 0; });
+    }
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(srv->device);

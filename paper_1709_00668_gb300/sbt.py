@@ -87,7 +87,7 @@ class SbtOptions(ctypes.Structure):
                 ("mode3_pass", ctypes.c_int32), ("als_groups", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("get_rank", ctypes.c_int32),
                 ("get_rank_trials", ctypes.c_int32), ("get_rank_threshold", ctypes.c_double),
-                ("fp64_tail", ctypes.c_int32)]
+                ("fp64_tail", ctypes.c_int32), ("persistent_als", ctypes.c_int32)]
 
 
 class SbtStats(ctypes.Structure):

@@ -169,6 +169,8 @@ def test_failed_batch_leaves_its_stream_usable(sbt):
         ts.append(srv.submit(sid, X[k:k + b]))
         k += b
     assert srv.wait(t_bad)["status"] == sbt.SBT_E_NONFINITE
+    # the failed batch's message reaches the waiting thread
+    assert b"non-finite" in sbt.lib().sbt_last_error()
     for t in ts:
         assert srv.wait(t)["status"] == sbt.SBT_OK
     got = srv.stream(sid).factors()
