@@ -366,6 +366,11 @@ typedef struct {
     double mttkrp_bytes;     /* algorithmic bytes of the passes: each summary element of every
                                 repetition still iterating read once per pass */
     int64_t mttkrp_passes;   /* timed passes (mttkrp_ms covers these) */
+    double mttkrp_busy_ms;   /* device time during which at least one timed MTTKRP launch ran: the
+                                union of the launches' event intervals (a group's pass that overlaps
+                                the other group's next pass is not counted twice) */
+    double mttkrp_launch_ms; /* sum of the timed launches' own durations (concurrent launches of
+                                the groups each counted in full) */
 } sbt_profile;
 
 /* Zero the counters; timing = 1 also brackets every MTTKRP launch of this

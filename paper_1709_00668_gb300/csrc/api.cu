@@ -219,7 +219,7 @@ struct sbt_ctx {
     int pass_iters = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
-    double mtt_ms = 0.0;
+    double mtt_ms = 0.0, mtt_busy_ms = 0.0, mtt_launch_ms = 0.0;
     long long launch_base = 0, updates = 0, mtt_launches = 0, mtt_passes = 0;
     int mtt_per_iter = 3;  // MTTKRP launches per ALS iteration of the last loop (2 with the memoised mode 3)
     ~sbt_ctx() {
@@ -818,7 +818,28 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
         if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS (timed): ") + cudaGetErrorString(e));
         // a pass (one launch per group, concurrent on the groups' streams)
         // lasts from the earliest start to the latest end, taken relative
-        // to the first start event of the batch
+        // to the first start event of the body; the busy time is the union
+        // of all the body's launch intervals
+        std::vector<std::pair<float, float>> iv;
+        for (int q = 0; q < nslots; ++q) {
+            if ((q / ngr) % 3 == 2 && d.ymem) continue;
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, c->gev[0].first, c->gev[q].first) == cudaSuccess &&
+                cudaEventElapsedTime(&b, c->gev[0].first, c->gev[q].second) == cudaSuccess)
+                iv.emplace_back(a, b);
+        }
+        std::sort(iv.begin(), iv.end());
+        for (size_t q = 0; q < iv.size();) {
+            float lo = iv[q].first, hi = iv[q].second;
+            c->mtt_launch_ms += iv[q].second - iv[q].first;
+            size_t u = q + 1;
+            for (; u < iv.size() && iv[u].first <= hi; ++u) {
+                hi = std::max(hi, iv[u].second);
+                c->mtt_launch_ms += iv[u].second - iv[u].first;
+            }
+            c->mtt_busy_ms += hi - lo;
+            q = u;
+        }
         for (int q0 = 0; q0 < nslots; q0 += ngr) {
             if ((q0 / ngr) % 3 == 2 && d.ymem) continue;
             float t0 = 0.f, t1 = 0.f;
@@ -1810,6 +1831,8 @@ extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     CK(cudaStreamSynchronize(c->stream));
     c->timing = timing != 0;
     c->mtt_ms = 0.0;
+    c->mtt_busy_ms = 0.0;
+    c->mtt_launch_ms = 0.0;
     c->launch_base = launch_count();
     c->updates = 0;
     c->mtt_launches = 0;
@@ -1831,6 +1854,8 @@ extern "C" sbt_status sbt_profile_read(sbt_ctx *c, sbt_profile *out) {
     out->mttkrp_ms = ms;
     out->mttkrp_bytes = (double)bytes;
     out->mttkrp_passes = c->mtt_passes;
+    out->mttkrp_busy_ms = c->mtt_busy_ms;
+    out->mttkrp_launch_ms = c->mtt_launch_ms;
     return SBT_OK;
 }
 

@@ -104,7 +104,8 @@ class SbtStats(ctypes.Structure):
 class SbtProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("mttkrp_launches", ctypes.c_int64), ("mttkrp_ms", ctypes.c_double),
-                ("mttkrp_bytes", ctypes.c_double), ("mttkrp_passes", ctypes.c_int64)]
+                ("mttkrp_bytes", ctypes.c_double), ("mttkrp_passes", ctypes.c_int64),
+                ("mttkrp_busy_ms", ctypes.c_double), ("mttkrp_launch_ms", ctypes.c_double)]
 
 
 class SbtCoo(ctypes.Structure):
@@ -474,7 +475,8 @@ class SamBaTen:
         p = SbtProfile()
         _check(lib().sbt_profile_read(self._h, ctypes.byref(p)), "sbt_profile_read")
         return {"launches": p.launches, "updates": p.updates, "mttkrp_launches": p.mttkrp_launches,
-                "mttkrp_ms": p.mttkrp_ms, "mttkrp_bytes": p.mttkrp_bytes, "mttkrp_passes": p.mttkrp_passes}
+                "mttkrp_ms": p.mttkrp_ms, "mttkrp_bytes": p.mttkrp_bytes, "mttkrp_passes": p.mttkrp_passes,
+                "mttkrp_busy_ms": p.mttkrp_busy_ms, "mttkrp_launch_ms": p.mttkrp_launch_ms}
 
     def last_samples(self, rep: int, mode: int) -> np.ndarray:
         n = ctypes.c_int64()
