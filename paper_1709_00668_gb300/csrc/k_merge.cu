@@ -121,13 +121,19 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         gam[q][rp][r] /= nu[q][rp] * Nn[q][r];
     }
     __syncthreads();
+    // the scores (one entry per thread) and the summary's lambda in its own scale
+    for (int e = threadIdx.x; e < Rs * R; e += blockDim.x) {
+        const int rp = e / R, r = e % R;
+        score[rp * 32 + r] = fabs(gam[0][rp][r]) * fabs(gam[1][rp][r]) * fabs(gam[2][rp][r]);
+    }
+    if (threadIdx.x < Rs) {
+        const int rp = threadIdx.x;
+        lsp[rp] = m.lam_s[rep * R + rp] * nu[0][rp] * nu[1][rp] * nu[2][rp];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) hungarian_max_warp(score, 32, Rs, R, perm, hw, threadIdx.x);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int rp = 0; rp < Rs; ++rp) {
-            lsp[rp] = m.lam_s[rep * R + rp] * nu[0][rp] * nu[1][rp] * nu[2][rp];
-            for (int r = 0; r < R; ++r)
-                score[rp * 32 + r] = fabs(gam[0][rp][r]) * fabs(gam[1][rp][r]) * fabs(gam[2][rp][r]);
-        }
-        hungarian_max(score, 32, Rs, R, perm, hw);
         for (int r = 0; r < R; ++r) iperm[r] = -1;
         double mn = INFINITY;
         for (int rp = 0; rp < Rs; ++rp) {

@@ -613,14 +613,16 @@ __global__ void __launch_bounds__(NM_THREADS) k_nm_match(NmMerge g) {
         gam(m, rp, r) /= nu[m][rp] * (Nn[m][r] == 0.0 ? 1.0 : Nn[m][r]);
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int rp = e / R, r = e % R;
+        double sc = 1.0;
+        for (int m = 0; m < N; ++m) sc *= fabs(gam(m, rp, r));
+        score[rp * 32 + r] = sc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) hungarian_max_warp(score, 32, R, R, perm, hw, threadIdx.x);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int rp = 0; rp < R; ++rp)
-            for (int r = 0; r < R; ++r) {
-                double sc = 1.0;
-                for (int m = 0; m < N; ++m) sc *= fabs(gam(m, rp, r));
-                score[rp * 32 + r] = sc;
-            }
-        hungarian_max(score, 32, R, R, perm, hw);
         double mn = INFINITY;
         for (int rp = 0; rp < R; ++rp) {
             mn = fmin(mn, score[rp * 32 + perm[rp]]);

@@ -6,93 +6,132 @@
 
 namespace sbt {
 
-// Maximum-weight assignment of an nr x nc score matrix, nr <= nc: every row
-// to a distinct column (Hungarian method, shortest augmenting paths with
-// potentials; Kuhn 1955, Munkres 1957), single thread.  perm[row] = column.
-// Ties resolve to the lower column index.  nr = nc is the perfect matching of
+// Maximum-weight assignment of an nr x nc score matrix, nr <= nc <= 32:
+// every row to a distinct column (Hungarian method, shortest augmenting
+// paths with potentials; Kuhn 1955, Munkres 1957).  perm[row] = column.  Ties
+// resolve to the lower column index.  nr = nc is the perfect matching of
 // Lemma 1's square case; nr < nc is GetRank's R_new summary components
 // against R old ones.
+//
+// One warp: lane c owns column c + 1 (its potential v, its slack minv, its
+// "used" mark, its row p and its predecessor way); column 0 is the method's
+// virtual column.  Each pass of a row is one step of the warp: every free
+// column updates its slack from the row just reached, the warp takes the
+// smallest slack (first column on ties) by shuffles, and every column
+// updates its potential or slack by that amount.  Per entry these are the
+// operations, in the order, of the textbook single-thread loop, so the
+// result is the same; only the loop over columns runs across the lanes.  The
+// float64 chain a row waits for is one pass per column reached instead of
+// one pass times nc (float64 is a slow, long-latency unit on this GPU).
+// Call from all 32 lanes of one converged warp; w in shared memory.
 struct HungarianWork {
-    double u[33], v[33], minv[33];
+    double u[33];  // row potentials (row 0 unused)
     int p[33], way[33];
-    bool used[33];
 };
 
-__device__ inline void hungarian_max(const double *score, int ld, int nr, int nc, int *perm, HungarianWork &w) {
-    double *u = w.u, *v = w.v, *minv = w.minv;
+__device__ inline void hungarian_max_warp(const double *score, int ld, int nr, int nc, int *perm, HungarianWork &w,
+                                          int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    double *u = w.u;
     int *p = w.p, *way = w.way;
-    bool *used = w.used;
-    for (int j = 0; j <= nc; ++j) {
-        v[j] = 0.0;
-        p[j] = 0;
-        way[j] = 0;
-    }
-    for (int i = 0; i <= nr; ++i) u[i] = 0.0;
+    const int j = lane + 1;
+    const bool col = j <= nc;
+    double vj = 0.0, minv = INFINITY;
+    int pj = 0, wayj = 0;
+    for (int i = lane; i <= nr; i += 32) u[i] = 0.0;
+    __syncwarp();
     for (int i = 1; i <= nr; ++i) {
-        p[0] = i;
+        const int p0 = i;  // the virtual column holds the row being placed
         int j0 = 0;
-        for (int j = 0; j <= nc; ++j) {
-            minv[j] = INFINITY;
-            used[j] = false;
-        }
+        bool used = false;
+        minv = INFINITY;
         // each pass marks one more column used, so at most nc passes
         for (int guard = 0; guard <= nc; ++guard) {
-            used[j0] = true;
-            const int i0 = p[j0];
-            double delta = INFINITY;
-            int j1 = 0;
-            for (int j = 1; j <= nc; ++j) {
-                if (used[j]) continue;
+            if (j0 == j) used = true;
+            const int i0 = j0 == 0 ? p0 : __shfl_sync(FULL, pj, j0 - 1);
+            const double ui0 = u[i0];
+            double cand = INFINITY;
+            if (col && !used) {
                 double sc = score[(i0 - 1) * ld + (j - 1)];
                 if (!isfinite(sc)) sc = 0.0;
-                const double cur = -sc - u[i0] - v[j];
-                if (cur < minv[j]) {
-                    minv[j] = cur;
-                    way[j] = j0;
+                const double cur = -sc - ui0 - vj;
+                if (cur < minv) {
+                    minv = cur;
+                    wayj = j0;
                 }
-                if (minv[j] < delta) {
-                    delta = minv[j];
-                    j1 = j;
+                cand = minv;
+            }
+            // the smallest slack strictly below +inf, the first column on ties
+            double dv = cand < INFINITY ? cand : INFINITY;
+            int dj = cand < INFINITY ? j : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ov = __shfl_xor_sync(FULL, dv, o);
+                const int oj = __shfl_xor_sync(FULL, dj, o);
+                if (ov < dv || (ov == dv && oj < dj)) {
+                    dv = ov;
+                    dj = oj;
                 }
             }
-            for (int j = 0; j <= nc; ++j) {
-                if (used[j]) {
-                    u[p[j]] += delta;
-                    v[j] -= delta;
+            const double delta = dv;
+            const int j1 = dj == 0x7fffffff ? 0 : dj;
+            __syncwarp();  // every lane has read u[i0]
+            // used columns hold distinct rows (and the virtual column the row
+            // being placed), so no two lanes update the same potential
+            if (col) {
+                if (used) {
+                    u[pj] += delta;
+                    vj -= delta;
                 } else {
-                    minv[j] -= delta;
+                    minv -= delta;
                 }
             }
+            if (lane == 0) u[p0] += delta;
+            __syncwarp();
             if (j1 == 0) break;  // no free column reachable (cannot happen for finite scores)
             j0 = j1;
-            if (p[j0] == 0) break;
+            if (__shfl_sync(FULL, pj, j0 - 1) == 0) break;
         }
-        for (int guard = 0; guard <= nc && j0; ++guard) {
-            const int j1 = way[j0];
-            p[j0] = p[j1];
-            j0 = j1;
+        // augment along the predecessors, from the free column reached back
+        // to the virtual one
+        if (col) {
+            p[j] = pj;
+            way[j] = wayj;
         }
+        if (lane == 0) p[0] = p0;
+        __syncwarp();
+        if (lane == 0)
+            for (int guard = 0; guard <= nc && j0; ++guard) {
+                const int j1 = way[j0];
+                p[j0] = p[j1];
+                j0 = j1;
+            }
+        __syncwarp();
+        if (col) pj = p[j];
     }
-    // rows that no column took (cannot happen for finite scores) take the
-    // free columns in order
-    bool row_done[33], col_used[33];
-    for (int i = 0; i <= nr; ++i) row_done[i] = false;
-    for (int j = 0; j <= nc; ++j) col_used[j] = false;
-    for (int i = 0; i < nr; ++i) perm[i] = -1;
-    for (int j = 1; j <= nc; ++j)
-        if (p[j] >= 1 && p[j] <= nr && !row_done[p[j]]) {
-            row_done[p[j]] = true;
-            col_used[j] = true;
-            perm[p[j] - 1] = j - 1;
-        }
-    for (int i = 1; i <= nr; ++i)
-        if (!row_done[i])
-            for (int j = 1; j <= nc; ++j)
-                if (!col_used[j]) {
-                    col_used[j] = true;
-                    perm[i - 1] = j - 1;
-                    break;
-                }
+    if (lane == 0) {
+        // rows that no column took (cannot happen for finite scores) take
+        // the free columns in order
+        bool row_done[33], col_used[33];
+        for (int i = 0; i <= nr; ++i) row_done[i] = false;
+        for (int c = 0; c <= nc; ++c) col_used[c] = false;
+        for (int i = 0; i < nr; ++i) perm[i] = -1;
+        for (int c = 1; c <= nc; ++c)
+            if (p[c] >= 1 && p[c] <= nr && !row_done[p[c]]) {
+                row_done[p[c]] = true;
+                col_used[c] = true;
+                perm[p[c] - 1] = c - 1;
+            }
+        for (int i = 1; i <= nr; ++i)
+            if (!row_done[i])
+                for (int c = 1; c <= nc; ++c)
+                    if (!col_used[c]) {
+                        col_used[c] = true;
+                        perm[i - 1] = c - 1;
+                        break;
+                    }
+    }
+    __syncwarp();
 }
 
 }  // namespace sbt
