@@ -76,6 +76,8 @@ def parse():
                     help="ALS iteration cap of every update (0: the workload's 50)")
     ap.add_argument("--warm-start", action="store_true",
                     help="start every summary ALS from the old factors at the sampled rows (default: random start)")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="ALS iterations per device-side loop body (library option check_every; 0: default)")
     ap.add_argument("--als-groups", type=int, default=0,
                     help="groups the repetitions' ALS runs in (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true",
@@ -108,7 +110,8 @@ def parse():
         WORKLOAD["K0"] = 200
     if args.max_iters > 0:
         WORKLOAD["max_iters"] = args.max_iters
-    global MODE3_PASS, ALS_GROUPS, WARM_START
+    global MODE3_PASS, ALS_GROUPS, WARM_START, CHECK_EVERY
+    CHECK_EVERY = args.check_every
     MODE3_PASS = int(args.mode3_pass)
     ALS_GROUPS = args.als_groups
     WARM_START = int(args.warm_start)
@@ -229,6 +232,7 @@ def make_data(steps: int, warmup: int, device):
 MODE3_PASS = 0
 ALS_GROUPS = 0
 WARM_START = 0
+CHECK_EVERY = 0
 
 
 def opts_for(prec: str, stream, nb: int):
@@ -237,7 +241,7 @@ def opts_for(prec: str, stream, nb: int):
     return dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
                 max_iters_init=50, seed=w["seed"], prec=prec, cuda_stream=stream,
                 K_capacity=w["K0"] + nb * w["batch"], mode3_pass=MODE3_PASS, als_groups=ALS_GROUPS,
-                warm_start=WARM_START)
+                warm_start=WARM_START, check_every=CHECK_EVERY)
 
 
 def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
@@ -575,6 +579,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {**workload_config(args), "prec": args.prec, "autotuned_tiles": bool(args.autotune),
                        "mode3_pass": bool(MODE3_PASS), "als_groups": ALS_GROUPS or "default",
+                       "check_every": CHECK_EVERY or "default",
                        "warm_start": bool(WARM_START), "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": percentile(per, 0.5), "p99": percentile(per, 0.99)},
             "fit": {"full_tensor_fit_after_steps": fit_gpu,

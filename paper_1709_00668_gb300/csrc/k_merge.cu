@@ -133,27 +133,25 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     __syncthreads();
     if (threadIdx.x < 32) hungarian_max_warp(score, 32, Rs, R, perm, hw, threadIdx.x);
     __syncthreads();
+    if (threadIdx.x < R) iperm[threadIdx.x] = -1;
+    __syncthreads();
+    if (threadIdx.x < Rs) iperm[perm[threadIdx.x]] = threadIdx.x;
+    if (threadIdx.x < R) m.perm[rep * R + threadIdx.x] = threadIdx.x < Rs ? perm[threadIdx.x] : -1;
+    for (int e = threadIdx.x; e < 3 * R; e += blockDim.x) m.nu[rep * 3 * R + e] = nu[e / R][e % R];
     if (threadIdx.x == 0) {
-        for (int r = 0; r < R; ++r) iperm[r] = -1;
         double mn = INFINITY;
-        for (int rp = 0; rp < Rs; ++rp) {
-            mn = fmin(mn, score[rp * 32 + perm[rp]]);
-            iperm[perm[rp]] = rp;
-        }
+        for (int rp = 0; rp < Rs; ++rp) mn = fmin(mn, score[rp * 32 + perm[rp]]);
         m.min_score[rep] = mn;
-        for (int rp = 0; rp < R; ++rp) m.perm[rep * R + rp] = rp < Rs ? perm[rp] : -1;
-        for (int q = 0; q < 3; ++q)
-            for (int r = 0; r < R; ++r) m.nu[(rep * 3 + q) * R + r] = nu[q][r];
-        // the summary's estimate of lambda in the old scale; NaN: not matched
-        for (int r = 0; r < R; ++r) {
-            const int rp = iperm[r];
-            const double den = Nn[0][r] * Nn[1][r] * Nn[2][r];
-            m.lam_est[rep * R + r] =
-                rp < 0 ? NAN : (den != 0.0 ? lsp[rp] * gam[0][rp][r] * gam[1][rp][r] * gam[2][rp][r] / den : 0.0);
-        }
         if (zflag) m.flags[rep] |= SBT_FLAG_ZERO_COLUMN_DEV;
     }
     __syncthreads();
+    // the summary's estimate of lambda in the old scale; NaN: not matched
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x, rp = iperm[r];
+        const double den = Nn[0][r] * Nn[1][r] * Nn[2][r];
+        m.lam_est[rep * R + r] =
+            rp < 0 ? NAN : (den != 0.0 ? lsp[rp] * gam[0][rp][r] * gam[1][rp][r] * gam[2][rp][r] / den : 0.0);
+    }
     // least-squares scale of a summary column of mode q in the matched old
     // scale, per unit of the raw summary value
     if (threadIdx.x < 3 * R) {

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(APPEND_THREADS) k_append(const T *Xin, long lo
     const bool vec = vec_ok && jc + V <= J;
     // rows in groups of AU: the loads of a group are issued before any of
     // its rows is processed (several vectors in flight per thread)
-    constexpr int AU = 8;
+    constexpr int AU = 4;
     for (int t0 = 0; t0 < rows; t0 += AU) {
         T xs[AU][V];
 #pragma unroll

@@ -24,6 +24,13 @@ namespace sbt {
 // float64 chain a row waits for is one pass per column reached instead of
 // one pass times nc (float64 is a slow, long-latency unit on this GPU).
 // Call from all 32 lanes of one converged warp; w in shared memory.
+// Order-preserving map of a non-NaN double to an unsigned 64-bit key
+// (negative values: all bits flipped; others: the sign bit set).
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 struct HungarianWork {
     double u[33];  // row potentials (row 0 unused)
     int p[33], way[33];
@@ -61,20 +68,24 @@ __device__ inline void hungarian_max_warp(const double *score, int ld, int nr, i
                 }
                 cand = minv;
             }
-            // the smallest slack strictly below +inf, the first column on ties
-            double dv = cand < INFINITY ? cand : INFINITY;
-            int dj = cand < INFINITY ? j : 0x7fffffff;
+            // the smallest slack strictly below +inf, the first column on
+            // ties: compared as order-preserving 64-bit keys (integer pipes;
+            // -0 taken as +0 so that equal values give equal keys)
+            const bool fin = cand < INFINITY;
+            const double cz = cand == 0.0 ? 0.0 : cand;
+            unsigned long long key = fin ? order_key(cz) : ~0ull;
+            int dj = fin ? j : 0x7fffffff;
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
-                const double ov = __shfl_xor_sync(FULL, dv, o);
+                const unsigned long long ok = __shfl_xor_sync(FULL, key, o);
                 const int oj = __shfl_xor_sync(FULL, dj, o);
-                if (ov < dv || (ov == dv && oj < dj)) {
-                    dv = ov;
+                if (ok < key || (ok == key && oj < dj)) {
+                    key = ok;
                     dj = oj;
                 }
             }
-            const double delta = dv;
             const int j1 = dj == 0x7fffffff ? 0 : dj;
+            const double delta = j1 == 0 ? INFINITY : __shfl_sync(FULL, cand, j1 - 1);
             __syncwarp();  // every lane has read u[i0]
             // used columns hold distinct rows (and the virtual column the row
             // being placed), so no two lanes update the same potential
