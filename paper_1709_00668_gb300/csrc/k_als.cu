@@ -256,6 +256,23 @@ __global__ void __launch_bounds__(256) k_mtt_col(AlsDesc d) {
 
 // ---------------------------------------------------------------------------
 // Fixed-order reduction of the partials: M[rep][e] = sum_p part[rep][p][e]
+
+// sum_{q < P} p[q * stride] in q order, in float64, eight loads in flight
+template <typename TF>
+__device__ __forceinline__ double sum_partials(const TF *p, int P, long long stride) {
+    double s = 0.0;
+    int q = 0;
+    for (; q + 8 <= P; q += 8) {
+        TF v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p[(long long)(q + u) * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
+    for (; q < P; ++q) s += (double)p[(long long)q * stride];
+    return s;
+}
+
 // M(x, r) = sum of the P partials in order; partials [rep][P][n][pr] (row
 // stride pr >= R), M [rep][n][R]
 template <typename TF>
@@ -266,10 +283,7 @@ __global__ void k_reduce(const TF *part, long long prs, int P, int n, int R, int
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * R) return;
     const long long x = e / R, r = e % R;
-    const TF *p = part + rep * prs + x * pr + r;
-    double s = 0.0;
-    for (int q = 0; q < P; ++q) s += (double)p[(long long)q * n * pr];
-    M[rep * mrs + e] = s;
+    M[rep * mrs + e] = sum_partials(part + rep * prs + x * pr + r, P, (long long)n * pr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1062,6 +1076,24 @@ __global__ void __launch_bounds__(MEMO_THREADS) k_mtt_memo(AlsDesc d) {
     }
 }
 
+// Sum of the thread's entries q[t], q[t + blockDim.x], ... in that order,
+// eight loads in flight before their additions (the order, and so the
+// result, of a plain strided loop).
+__device__ __forceinline__ double sum_strided(const double *q, long long n) {
+    double a = 0.0;
+    long long e = threadIdx.x;
+    const long long step = blockDim.x;
+    for (; e + 7 * step < n; e += 8 * step) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = q[e + u * step];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a += v[u];
+    }
+    for (; e < n; e += step) a += q[e];
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // Start values, Grams and ||X_s||^2 (one CTA per repetition)
 template <typename TF>
@@ -1129,8 +1161,7 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
     __shared__ double red[256];
     const long long rows = d.rq_rows ? d.rq_rows : (long long)d.n[2] * d.n[0];
     const double *rq = rowsq + rep * rows;
-    double a = 0.0;
-    for (long long e = threadIdx.x; e < rows; e += blockDim.x) a += rq[e];
+    const double a = sum_strided(rq, rows);
     red[threadIdx.x] = a;
     __syncthreads();
     for (int s = 128; s; s >>= 1) {
@@ -1160,8 +1191,7 @@ __global__ void __launch_bounds__(256) k_refine_start(AlsDesc d, const double *r
     __shared__ double red[256];
     const long long rows = (long long)d.n[2] * d.n[0];
     const double *rq = rowsq2 + rep * rows;
-    double a = 0.0;
-    for (long long e = threadIdx.x; e < rows; e += blockDim.x) a += rq[e];
+    const double a = sum_strided(rq, rows);
     red[threadIdx.x] = a;
     __syncthreads();
     for (int s = 128; s; s >>= 1) {
@@ -1201,6 +1231,10 @@ void choose_tiles(AlsDesc &d, int num_sms) {
     long long nks = target / std::max(1LL, (long long)d.nib * d.nrep);
     nks = std::max(1LL, std::min<long long>(nks, Kp));
     int spc = (int)((Kp + nks - 1) / nks);
+    // small summaries: at least ~1024 elements per warp and 64 rows per
+    // column block, so that the partial sums the reduction adds one by one
+    // stay few (split finer, each block would do almost nothing)
+    spc = std::max(spc, (1024 + NJ - 1) / NJ);
     spc = std::max(1, std::min(spc, 32));
     d.spc = spc;
     d.nks = (Kp + spc - 1) / spc;
@@ -1220,7 +1254,7 @@ void choose_tiles(AlsDesc &d, int num_sms) {
     const long long rows = (long long)Kp * NI;
     long long nrs = target / std::max(1LL, (long long)njb * d.nrep);
     nrs = std::max(1LL, std::min(nrs, rows));
-    d.rows_per = (rows + nrs - 1) / nrs;
+    d.rows_per = std::max<long long>((rows + nrs - 1) / nrs, std::min<long long>(64, rows));
     d.nrs = (int)((rows + d.rows_per - 1) / d.rows_per);
     d.P[0] = d.nks;
     d.P[1] = d.nrs;
@@ -1566,9 +1600,7 @@ __global__ void __launch_bounds__(256) k_als_persistent(AlsDesc d, PersistSync p
                     const TF *part = (const TF *)d.part + rep * d.prs;
                     for (long long e = threadIdx.x; e < (long long)n * d.R; e += blockDim.x) {
                         const long long x = e / d.R, r = e % d.R;
-                        double sum = 0.0;
-                        for (int q = 0; q < P; ++q) sum += (double)part[(long long)q * n * d.pr + x * d.pr + r];
-                        d.M[rep * d.mrs + e] = sum;
+                        d.M[rep * d.mrs + e] = sum_partials(part + x * d.pr + r, P, (long long)n * d.pr);
                     }
                 }
                 __syncthreads();
