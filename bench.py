@@ -94,6 +94,11 @@ def parse():
     ap.add_argument("--duration", type=float, default=30.0, help="--serve: seconds of arrivals")
     ap.add_argument("--streams", type=int, default=64, help="--serve: live streams")
     ap.add_argument("--slots", type=int, default=8, help="--serve: concurrent updates")
+    ap.add_argument("--serve-prec", default="bf16", choices=["bf16", "f32"],
+                    help="--serve: summary precision of every stream")
+    ap.add_argument("--batch-als", action="store_true",
+                    help="--serve: the server runs the summary ALS of the admitted batches in shared persistent "
+                         "launches (streams with the persistent ALS; needs --serve-prec f32)")
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep on the 2000x2000x(1000+10x100), R=20 workload: f32, bf16, "
                          "bf16 + refinement, fp8; throughput and error against the FP64 oracle (one JSON line)")
@@ -654,7 +659,9 @@ def run_serve(args):
     w = SERVE
     rng = np.random.default_rng(0)
     free, _ = torch.cuda.mem_get_info(device)
-    srv = sbt.Server(slots=args.slots, mem_budget=int(0.75 * free), device=local)
+    if args.batch_als and args.serve_prec != "f32":
+        raise SystemExit("--batch-als needs --serve-prec f32 (the persistent ALS is the CUDA-core path)")
+    srv = sbt.Server(slots=args.slots, mem_budget=int(0.75 * free), device=local, batch_als=int(args.batch_als))
     live, opening = {}, []
     counter = {"opened": 0, "refused": 0}
 
@@ -666,7 +673,8 @@ def run_serve(args):
         X0 = st.slices(torch, 0, w["K0"])
         torch.cuda.current_stream().synchronize()
         o = dict(s_I=w["s"], s_J=w["s"], s_K=w["s"], r=w["r"], tol=w["tol"], max_iters=w["max_iters"],
-                 max_iters_init=50, seed=seed, stream_id=seed, prec="bf16",
+                 max_iters_init=50, seed=seed, stream_id=seed, prec=args.serve_prec,
+                 persistent_als=1 if args.batch_als else 0,
                  K_capacity=w["K_end"], max_batch=w["batch"][1])
         code, sid = srv.open_stream_status(X0, st.R, **o)
         return code, sid, st
@@ -776,16 +784,18 @@ def run_serve(args):
         return 0
     line = {"metric": "served slices absorbed/sec; p50/p99 batch-update latency (submit -> commit)",
             "value": done_slices / total_s, "unit": "slices/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "bf16", "data": "synthetic",
+            "dtype": args.serve_prec, "data": "synthetic",
             "config": {"workload": SERVE_NAME, "streams": args.streams, "slots": args.slots,
                        "rate_per_s": args.rate if not closed else "closed loop (saturation)",
-                       "arrival_seconds": args.duration, **{k: v for k, v in w.items()}},
+                       "arrival_seconds": args.duration, "batch_als": bool(args.batch_als),
+                       **{k: v for k, v in w.items()}},
             "requests": requests, "completed": stats["completed"], "failed": stats["failed"],
             "streams_replaced": counter["opened"], "streams_refused": counter["refused"],
             "wall_s": total_s, "arrivals_s": arrivals_s,
             "latency_ms": {"p50": stats["latency_p50_ms"], "p99": stats["latency_p99_ms"]},
             "service_ms": {"p50": stats["service_p50_ms"], "p99": stats["service_p99_ms"]},
             "busy_fraction": stats["busy_fraction"],
+            "batched_als": {"launches": stats["als_launches"], "updates": stats["als_sets"]},
             "peak_resident_gb": stats["peak_resident_bytes"] / 1e9, "mem_budget_gb": stats["mem_budget"] / 1e9}
     print(json.dumps(line), flush=True)
     return 0

@@ -436,6 +436,14 @@ typedef struct {
     int32_t slots;        /* concurrent updates (worker threads), 1..64; 0: 4 */
     uint64_t mem_budget;  /* device bytes all streams may hold; 0: 90 % of the free memory at create */
     int32_t device;       /* CUDA device; -1: the calling thread's current device */
+    int32_t batch_als;    /* 1: one worker admits up to `slots` batches together and runs the summary
+                             ALS of those whose streams were opened with persistent_als (the CUDA-core
+                             path: SBT_PREC_F64 / F32) in one persistent launch, up to 8 compatible
+                             updates (same summary precision, R in the same range 1-8, 9-16, 17-32)
+                             per launch; every other step of each update, and the whole update of other
+                             streams, runs as in sbt_update.  Each stream's results are the same bits
+                             as its update alone with persistent_als.  0 (default): `slots` workers,
+                             one sbt_update each */
 } sbt_server_options;
 
 typedef struct {
@@ -458,6 +466,8 @@ typedef struct {
     double service_p50_ms, service_p99_ms; /* update started -> committed */
     double busy_fraction;                  /* wall time with an update in flight / elapsed */
     double elapsed_s;                      /* since the reset */
+    int64_t als_launches;                  /* batch_als: persistent launches run since the reset */
+    int64_t als_sets;                      /* batch_als: updates' summary ALS those launches ran */
 } sbt_serving_stats;
 
 /* Defaults: 4 slots, 90 % of free memory, the current device. */

@@ -168,7 +168,19 @@ static cudaError_t ensure_kernel_attributes(int device) {
     return e;
 }
 
+// An update stopped before its summary ALS, which a server runs in a batched
+// persistent launch with other contexts' (steps 1-4 and the ALS start done;
+// the ALS, the match and the commit pending).
+struct PendingAls {
+    bool on = false;
+    AlsDesc d{};
+    int64_t K_old = 0;
+    int K_new = 0, nI = 0, nJ = 0, nK = 0, ldj = 0;
+    long long samp_stride = 0;
+};
+
 struct sbt_ctx {
+    PendingAls pend;
     int device = 0;
     int num_sms = 0;
     cudaStream_t user = nullptr;    // the caller's stream (inputs are ordered on it)
@@ -192,7 +204,7 @@ struct sbt_ctx {
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     Buf ymem;                           // mode-2 pass products for the mode-3 MTTKRP (mode3_pass 0)
     Buf grscr, gcc, rnew;               // GetRank: CorConDia scratch, scores + status words, R_new per repetition
-    Buf psync;                          // grid-barrier words of the persistent ALS
+    Buf psync, pdesc;                   // grid-barrier words and the descriptor of the persistent ALS
     std::vector<int> last_rank;         // components of each summary of the last update
     Buf samax, sscale;  // float8: max |x| of every stored slice (float bits); scale of every summary slice
     // COO contexts (sbt_init_coo): nonzeros grouped by slice, and the summary workspace
@@ -780,8 +792,9 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
     if (c->opt.persistent_als && !(tc && tc->on) && !c->coo && !c->timing) {
         // one cooperative launch for every iteration and repetition
         TRY(c->psync.ensure(4 * sizeof(unsigned)));
-        CK(launch_als_persistent(d, max_iters, c->psync.as<unsigned>(), &c->status.as<DevStatus>()->err,
-                                 c->num_sms, c->stream));
+        TRY(c->pdesc.ensure(sizeof(AlsDesc)));
+        CK(launch_als_persistent(&d, 1, c->pdesc.as<AlsDesc>(), max_iters, c->psync.as<unsigned>(),
+                                 &c->status.as<DevStatus>()->err, c->num_sms, c->stream));
         return SBT_OK;
     }
     if (!c->timing) {
@@ -1148,6 +1161,10 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
         TRY(z.need(c->rowsq2, (size_t)r * u.Kp * u.nI * 8));
         TRY(z.need(c->iters_main, (size_t)r * 4));
     }
+    if (c->opt.persistent_als) {  // barrier words and the descriptor of the persistent ALS
+        TRY(z.need(c->psync, 4 * sizeof(unsigned)));
+        TRY(z.need(c->pdesc, sizeof(AlsDesc)));
+    }
     if (c->opt.get_rank) {
         // CorConDia scratch of one candidate and the widened factors; scores
         // and status words of every (repetition, rank, trial); R_new
@@ -1182,7 +1199,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
             &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
             &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale, &c->ymem,
-            &c->grscr, &c->gcc, &c->rnew, &c->psync,
+            &c->grscr, &c->gcc, &c->rnew, &c->psync, &c->pdesc,
             &c->si, &c->sj, &c->sv, &c->sptr, &c->cin_i, &c->cin_j, &c->cin_k, &c->cin_v, &c->ccnt, &c->cfill,
             &c->cmax, &c->posI, &c->posJ, &c->gcnt, &c->goff, &c->gtot, &c->vmax, &c->fexp, &c->eii, &c->ejj,
             &c->ekk, &c->ev, &c->perm1, &c->perm2, &c->rp1, &c->rp2, &c->gc1, &c->gc2, &c->gf1, &c->gf2};
@@ -1485,8 +1502,12 @@ static sbt_status get_rank_als(sbt_ctx *c, const UpdShape &u, const AlsDesc &d_f
     return SBT_OK;
 }
 
-extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
+// Alg. 1 for one batch.  deferred non-null: an update whose ALS can join a
+// batched persistent launch (persistent_als, the CUDA-core path, no
+// per-launch timing) stops before it, with *deferred = true.
+static sbt_status update_impl(sbt_ctx *c, const sbt_tensor *X, bool *deferred) {
     if (!c) return fail(SBT_E_INVALID, "null context");
+    if (c->pend.on) return fail(SBT_E_STATE, "an update of this context is pending");
     if (c->coo) return fail(SBT_E_INVALID, "a COO context takes sbt_update_coo");
     TRY(check_tensor(X));
     if (X->I != c->I || X->J != c->J) return fail(SBT_E_SHAPE, "I and J must match the initial tensor");
@@ -1617,6 +1638,19 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
         TRY(als_plans(c, d, &tc, plans));
         for (AlsPlan &pl : plans) TRY(autotune_tiles(c, pl.d, pl.tc));
     }
+    if (deferred && c->opt.persistent_als && !tc.on && !c->timing) {
+        c->pend.d = d;
+        c->pend.K_old = K_old;
+        c->pend.K_new = K_new;
+        c->pend.nI = nI;
+        c->pend.nJ = nJ;
+        c->pend.nK = nK;
+        c->pend.ldj = ldj;
+        c->pend.samp_stride = samp_stride;
+        c->pend.on = true;
+        *deferred = true;
+        return SBT_OK;
+    }
     TRY(run_als(c, d, c->opt.max_iters, tc.on ? &tc : nullptr));
     // refinement sweeps: the same ALS continued for refine_sweeps iterations
     // with every MTTKRP on the split summary (hi + lo)
@@ -1643,6 +1677,38 @@ extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) {
     }
     return match_commit(c, d, K_old, K_new, nI, nJ, nK, samp_stride, ldj, refined, no_refine);
 }
+
+extern "C" sbt_status sbt_update(sbt_ctx *c, const sbt_tensor *X) { return update_impl(c, X, nullptr); }
+
+namespace sbt {
+
+sbt_status update_deferred(sbt_ctx *c, const sbt_tensor *X, bool *deferred) {
+    *deferred = false;
+    return update_impl(c, X, deferred);
+}
+
+sbt_status deferred_als(sbt_ctx *c, AlsDesc *d, cudaStream_t *st, int *num_sms) {
+    if (!c || !c->pend.on) return fail(SBT_E_STATE, "no pending update");
+    *d = c->pend.d;
+    *st = c->stream;
+    *num_sms = c->num_sms;
+    return SBT_OK;
+}
+
+sbt_status update_complete(sbt_ctx *c) {
+    if (!c || !c->pend.on) return fail(SBT_E_STATE, "no pending update");
+    DeviceGuard dg(c->device);
+    PendingAls p = c->pend;
+    c->pend.on = false;
+    return match_commit(c, p.d, p.K_old, p.K_new, p.nI, p.nJ, p.nK, p.samp_stride, p.ldj, false, false);
+}
+
+void update_abandon(sbt_ctx *c) {
+    // the model and K are untouched until the commit: nothing to undo
+    if (c) c->pend.on = false;
+}
+
+}  // namespace sbt
 
 extern "C" sbt_status sbt_factors(const sbt_ctx *c, double *lambda, double *A, double *B, double *C, int64_t *K_out) {
     if (!c) return fail(SBT_E_INVALID, "null context");

@@ -287,23 +287,27 @@ __global__ void k_reduce(const TF *part, long long prs, int P, int n, int R, int
 }
 
 // ---------------------------------------------------------------------------
-// float64 helpers of the tail: Cholesky, inverse, by one warp (R <= 32)
-__device__ bool warp_cholesky(const double *V, double *L, int R, int lane) {
-    // L lower triangular, row-major 32x32
+// float64 helpers of the tail: Cholesky, inverse, by one warp (R <= 32).
+// L lower triangular, row-major 32 x 32; rinv[j] = 1 / L(j, j), so that the
+// other lanes of a column and both triangular solves multiply instead of
+// dividing (float64 division is a long chain of dependent operations here).
+__device__ bool warp_cholesky(const double *V, double *L, double *rinv, int R, int lane) {
     bool ok = true;
     for (int j = 0; j < R; ++j) {
         if (lane == j) {
             double s = V[j * 32 + j];
             for (int k = 0; k < j; ++k) s -= L[j * 32 + k] * L[j * 32 + k];
-            L[j * 32 + j] = (s > 0.0 && isfinite(s)) ? sqrt(s) : -1.0;
+            const bool pos = s > 0.0 && isfinite(s);
+            const double dj = pos ? sqrt(s) : -1.0;
+            L[j * 32 + j] = dj;
+            rinv[j] = pos ? 1.0 / dj : 0.0;
         }
         __syncwarp();
-        const double djj = L[j * 32 + j];
-        if (!(djj > 0.0)) ok = false;
+        if (!(L[j * 32 + j] > 0.0)) ok = false;
         if (ok && lane > j && lane < R) {
             double s = V[lane * 32 + j];
             for (int k = 0; k < j; ++k) s -= L[lane * 32 + k] * L[j * 32 + k];
-            L[lane * 32 + j] = s / djj;
+            L[lane * 32 + j] = s * rinv[j];
         }
         __syncwarp();
         if (!ok) break;
@@ -311,35 +315,68 @@ __device__ bool warp_cholesky(const double *V, double *L, int R, int lane) {
     return ok;
 }
 
-// Vi = (L L^T)^-1: lane c solves L y = e_c, then L^T x = y.
-__device__ void warp_chol_inverse(const double *L, double *Vi, int R, int lane) {
+// Vi = (L L^T)^-1: lane c solves L y = e_c, then L^T x = y; up to RP = 8
+// y in registers (the loops unrolled over RP >= R), above in lane c's column
+// of Vi itself.
+template <int RP>
+__device__ void warp_chol_inverse(const double *L, const double *rinv, double *Vi, int R, int lane) {
+    if constexpr (RP > 8) {
+        if (lane < R) {
+            for (int i = 0; i < R; ++i) {
+                double s = (i == lane) ? 1.0 : 0.0;
+                for (int k = 0; k < i; ++k) s -= L[i * 32 + k] * Vi[k * 32 + lane];
+                Vi[i * 32 + lane] = s * rinv[i];
+            }
+            for (int i = R - 1; i >= 0; --i) {
+                double s = Vi[i * 32 + lane];
+                for (int k = i + 1; k < R; ++k) s -= L[k * 32 + i] * Vi[k * 32 + lane];
+                Vi[i * 32 + lane] = s * rinv[i];
+            }
+        }
+        __syncwarp();
+        return;
+    }
     if (lane < R) {
-        double y[32];
-        for (int i = 0; i < R; ++i) {
+        double y[RP];
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
             double s = (i == lane) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= L[i * 32 + k] * y[k];
-            y[i] = s / L[i * 32 + i];
+#pragma unroll
+            for (int k = 0; k < RP; ++k)
+                if (k < i) s -= L[i * 32 + k] * y[k];
+            y[i] = i < R ? s * rinv[i] : 0.0;
         }
-        for (int i = R - 1; i >= 0; --i) {
-            double s = y[i];
-            for (int k = i + 1; k < R; ++k) s -= L[k * 32 + i] * y[k];
-            y[i] = s / L[i * 32 + i];
+#pragma unroll
+        for (int i = RP - 1; i >= 0; --i) {
+            if (i < R) {
+                double s = y[i];
+#pragma unroll
+                for (int k = 0; k < RP; ++k)
+                    if (k > i && k < R) s -= L[k * 32 + i] * y[k];
+                y[i] = s * rinv[i];
+            }
         }
-        for (int i = 0; i < R; ++i) Vi[i * 32 + lane] = y[i];
+#pragma unroll
+        for (int i = 0; i < RP; ++i)
+            if (i < R) Vi[i * 32 + lane] = y[i];
     }
     __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// Tail of one mode for one repetition (one CTA per repetition).
-template <typename TF>
-__device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
-    if (d.conv[rep]) return;
+// Tail of one mode for one repetition (one CTA of 256 threads): the float64
+// normal-equation solve, unit columns, the Gram and (mode 3) the fit.
+struct TailShared {
+    double V[32 * 32], L[32 * 32], Vi[32 * 32];
+    double lam_s[32], rinv[32], red[8];
+    int chol_ok, reg_flag, zero_flag;
+};
+
+template <typename TF, int RP>
+__device__ void tail_rep_rp(const AlsDesc &d, int mode, int rep, TailShared &ts) {
     const int R = d.R, n = d.n[mode];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ double V[32 * 32], L[32 * 32], Vi[32 * 32];
-    __shared__ double lam_s[32];
-    __shared__ int chol_ok, reg_flag, zero_flag;
+    double *V = ts.V, *L = ts.L, *Vi = ts.Vi, *lam_s = ts.lam_s;
     double *G = d.G + (long long)rep * 3 * R * R;
     const double *M = d.M + rep * d.mrs;
     TF *U = (TF *)d.U[mode] + (long long)rep * n * R;
@@ -352,12 +389,12 @@ __device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
         V[r * 32 + s] = v;
     }
     if (threadIdx.x == 0) {
-        reg_flag = 0;
-        zero_flag = 0;
+        ts.reg_flag = 0;
+        ts.zero_flag = 0;
     }
     __syncthreads();
     if (warp == 0) {
-        bool ok = warp_cholesky(V, L, R, lane);
+        bool ok = warp_cholesky(V, L, ts.rinv, R, lane);
         if (!ok) {
             // V + 1e-12 tr(V)/R I
             double tr = 0.0;
@@ -365,27 +402,41 @@ __device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
             __syncwarp();
             if (lane < R) V[lane * 32 + lane] += 1e-12 * tr / R;
             __syncwarp();
-            ok = warp_cholesky(V, L, R, lane);
-            if (lane == 0) reg_flag = 1;
+            ok = warp_cholesky(V, L, ts.rinv, R, lane);
+            if (lane == 0) ts.reg_flag = 1;
         }
-        if (lane == 0) chol_ok = ok;
+        if (lane == 0) ts.chol_ok = ok;
         __syncwarp();
-        if (ok) warp_chol_inverse(L, Vi, R, lane);
+        if (ok) warp_chol_inverse<RP>(L, ts.rinv, Vi, R, lane);
     }
     __syncthreads();
-    if (!chol_ok) {
+    if (!ts.chol_ok) {
         // singular even after the shift: leave the factor, flag
         if (threadIdx.x == 0) atomicOr(&d.flags[rep], SBT_FLAG_CHOL_REGULARIZED_DEV);
         return;
     }
     // U = M Vi (float64 arithmetic, stored as TF)
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        double m[32];
-        for (int s = 0; s < R; ++s) m[s] = M[(long long)x * R + s];
+    for (int x = threadIdx.x; x < n && RP > 8; x += blockDim.x) {
         for (int r = 0; r < R; ++r) {
             double acc = 0.0;
-            for (int s = 0; s < R; ++s) acc += m[s] * Vi[s * 32 + r];
+            for (int s = 0; s < R; ++s) acc += M[(long long)x * R + s] * Vi[s * 32 + r];
             U[(long long)x * R + r] = (TF)acc;
+        }
+    }
+    for (int x = threadIdx.x; x < n && RP <= 8; x += blockDim.x) {
+        double m[RP <= 8 ? RP : 1];
+        constexpr int Q = RP <= 8 ? RP : 1;
+#pragma unroll
+        for (int s = 0; s < Q; ++s) m[s] = s < R ? M[(long long)x * R + s] : 0.0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            if (r < R) {
+                double acc = 0.0;
+#pragma unroll
+                for (int s = 0; s < Q; ++s)
+                    if (s < R) acc += m[s] * Vi[s * 32 + r];
+                U[(long long)x * R + r] = (TF)acc;
+            }
         }
     }
     __syncthreads();
@@ -401,15 +452,16 @@ __device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
             double l = sqrt(a);
             if (l == 0.0) {
                 l = 1.0;
-                zero_flag = 1;
+                ts.zero_flag = 1;
             }
             lam_s[r] = l;
+            ts.rinv[r] = 1.0 / l;
         }
     }
     __syncthreads();
     for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x) {
         int r = (int)(e % R);
-        U[e] = (TF)((double)U[e] / lam_s[r]);
+        U[e] = (TF)((double)U[e] * ts.rinv[r]);
     }
     __syncthreads();
     // Gram of the normalised factor
@@ -432,41 +484,54 @@ __device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int f = 0;
-        if (reg_flag) f |= SBT_FLAG_CHOL_REGULARIZED_DEV;
-        if (zero_flag) f |= SBT_FLAG_ZERO_COLUMN_DEV;
+        if (ts.reg_flag) f |= SBT_FLAG_CHOL_REGULARIZED_DEV;
+        if (ts.zero_flag) f |= SBT_FLAG_ZERO_COLUMN_DEV;
         if (f) d.flags[rep] |= f;
     }
     if (mode == 2) {
         // fit = 1 - ||X - X_hat|| / ||X||
-        __shared__ double red[8];
         double inner = 0.0;
         for (long long e = threadIdx.x; e < (long long)n * R; e += blockDim.x) {
             int r = (int)(e % R);
             inner += lam_s[r] * M[e] * (double)U[e];
         }
         inner = warp_sum(inner);
-        if (lane == 0) red[warp] = inner;
+        if (lane == 0) ts.red[warp] = inner;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double in = 0.0;
-            for (int w = 0; w < 8; ++w) in += red[w];
+        if (warp == 0) {
+            // ||X_hat||^2 = sum_{r,s} lam_r lam_s G1 G2 G3, a term per lane in turn
             double xh = 0.0;
-            for (int r = 0; r < R; ++r)
-                for (int s = 0; s < R; ++s)
-                    xh += lam_s[r] * lam_s[s] * G[r * R + s] * G[R * R + r * R + s] * G[2 * R * R + r * R + s];
-            double nx2 = d.normX2[rep];
-            double res2 = fmax(nx2 + xh - 2.0 * in, 0.0);
-            double fit = nx2 > 0.0 ? 1.0 - sqrt(res2) / sqrt(nx2) : 0.0;
-            int it = d.iters[rep] + 1;
-            d.iters[rep] = it;
-            d.fit[rep] = fit;
-            bool stop = it >= d.max_iters;
-            if (!d.fixed_iters && fabs(fit - d.fit_prev[rep]) < d.tol) stop = true;
-            d.fit_prev[rep] = fit;
-            if (stop) d.conv[rep] = 1;
-            for (int r = 0; r < R; ++r) d.lam[rep * R + r] = lam_s[r];
+            for (int e = lane; e < R * R; e += 32) {
+                const int r = e / R, s = e % R;
+                xh += lam_s[r] * lam_s[s] * G[e] * G[R * R + e] * G[2 * R * R + e];
+            }
+            xh = warp_sum(xh);
+            if (lane == 0) {
+                double in = 0.0;
+                for (int w = 0; w < 8; ++w) in += ts.red[w];
+                double nx2 = d.normX2[rep];
+                double res2 = fmax(nx2 + xh - 2.0 * in, 0.0);
+                double fit = nx2 > 0.0 ? 1.0 - sqrt(res2) / sqrt(nx2) : 0.0;
+                int it = d.iters[rep] + 1;
+                d.iters[rep] = it;
+                d.fit[rep] = fit;
+                bool stop = it >= d.max_iters;
+                if (!d.fixed_iters && fabs(fit - d.fit_prev[rep]) < d.tol) stop = true;
+                d.fit_prev[rep] = fit;
+                if (stop) d.conv[rep] = 1;
+                for (int r = 0; r < R; ++r) d.lam[rep * R + r] = lam_s[r];
+            }
         }
     }
+}
+
+template <typename TF>
+__device__ void tail_rep(const AlsDesc &d, int mode, int rep) {
+    __shared__ TailShared ts;
+    if (d.conv[rep]) return;
+    if (d.R <= 8) tail_rep_rp<TF, 8>(d, mode, rep, ts);
+    else if (d.R <= 16) tail_rep_rp<TF, 16>(d, mode, rep, ts);
+    else tail_rep_rp<TF, 32>(d, mode, rep, ts);
 }
 
 template <typename TF>
@@ -1231,10 +1296,6 @@ void choose_tiles(AlsDesc &d, int num_sms) {
     long long nks = target / std::max(1LL, (long long)d.nib * d.nrep);
     nks = std::max(1LL, std::min<long long>(nks, Kp));
     int spc = (int)((Kp + nks - 1) / nks);
-    // small summaries: at least ~1024 elements per warp and 64 rows per
-    // column block, so that the partial sums the reduction adds one by one
-    // stay few (split finer, each block would do almost nothing)
-    spc = std::max(spc, (1024 + NJ - 1) / NJ);
     spc = std::max(1, std::min(spc, 32));
     d.spc = spc;
     d.nks = (Kp + spc - 1) / spc;
@@ -1254,6 +1315,9 @@ void choose_tiles(AlsDesc &d, int num_sms) {
     const long long rows = (long long)Kp * NI;
     long long nrs = target / std::max(1LL, (long long)njb * d.nrep);
     nrs = std::max(1LL, std::min(nrs, rows));
+    // small summaries: at least 64 rows (8 per warp) per column block, so
+    // that the partial sums the reduction adds one by one stay few (split
+    // finer, each block would do almost nothing)
     d.rows_per = std::max<long long>((rows + nrs - 1) / nrs, std::min<long long>(64, rows));
     d.nrs = (int)((rows + d.rows_per - 1) / d.rows_per);
     d.P[0] = d.nks;
@@ -1578,49 +1642,114 @@ __device__ bool pa_barrier(const PersistSync &ps, unsigned *err) {
     return go != 0;
 }
 
+// One grid-strided pass over the items [base, base + cnt) of a sequence that
+// concatenates the summary sets: the first item of this CTA at or after base.
+__device__ __forceinline__ long long pa_first(long long base) {
+    const long long g = gridDim.x;
+    return base + (((long long)blockIdx.x - base) % g + g) % g;
+}
+
+// Copy of descriptor i into shared memory (the CTA's threads, then a barrier).
+__device__ __forceinline__ void pa_load_desc(AlsDesc &sd, const AlsDesc *descs, int i) {
+    static_assert(sizeof(AlsDesc) % 4 == 0, "AlsDesc copied as 32-bit words");
+    const int *src = reinterpret_cast<const int *>(descs + i);
+    int *dst = reinterpret_cast<int *>(&sd);
+    for (int w = threadIdx.x; w < (int)(sizeof(AlsDesc) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+}
+
+// The summary sets' descriptors, nd of them, in device memory (one context's
+// update, or several contexts' updates that a server runs together).  Per
+// iteration and mode: the MTTKRP's virtual blocks of every set, set after
+// set, spread over the CTAs -> barrier -> the (set, repetition) pairs' partial
+// sums and float64 tails -> barrier; after mode 3 every CTA reads every
+// convergence flag.  Each set's arithmetic is its own: a set gives the same
+// bits alone and in any batch.
 template <typename TX, int RP, int COLS>
-__global__ void __launch_bounds__(256) k_als_persistent(AlsDesc d, PersistSync ps, unsigned *err, int max_iters) {
+__global__ void __launch_bounds__(256) k_als_persistent(const AlsDesc *__restrict__ descs, int nd, PersistSync ps,
+                                                        unsigned *err, int max_iters) {
     using TF = typename FactorOf<TX>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
+    __shared__ AlsDesc sd;
     for (int it = 0; it < max_iters; ++it) {
         for (int mode = 0; mode < 3; ++mode) {
-            const int per = mode == 1 ? njb * d.nrs : d.nib * d.nks;
-            const int nvb = per * d.nrep;
-            for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-                if (mode == 1) mtt_col_block<TX, RP, COLS>(d, vb % per, vb / per, smem_raw);
-                else mtt_row_block<TX, RP>(d, mode, vb % per, vb / per, smem_raw);
-                __syncthreads();  // the shared memory is reused by the next virtual block
-            }
-            if (!pa_barrier(ps, err)) return;
-            for (int rep = blockIdx.x; rep < d.nrep; rep += gridDim.x) {
-                if (!d.conv[rep]) {
-                    // k_reduce's sums for this repetition, in partial order
-                    const int n = d.n[mode], P = d.P[mode];
-                    const TF *part = (const TF *)d.part + rep * d.prs;
-                    for (long long e = threadIdx.x; e < (long long)n * d.R; e += blockDim.x) {
-                        const long long x = e / d.R, r = e % d.R;
-                        d.M[rep * d.mrs + e] = sum_partials(part + x * d.pr + r, P, (long long)n * d.pr);
+            long long base = 0;
+            for (int i = 0; i < nd; ++i) {
+                const AlsDesc &g = descs[i];
+                const int njb = (g.n[1] + 32 * COLS - 1) / (32 * COLS);
+                const int per = mode == 1 ? njb * g.nrs : g.nib * g.nks;
+                const long long cnt = (long long)per * g.nrep;
+                long long vb = pa_first(base);
+                if (vb < base + cnt) {
+                    pa_load_desc(sd, descs, i);
+                    for (; vb < base + cnt; vb += gridDim.x) {
+                        const int local = (int)(vb - base);
+                        if (mode == 1) mtt_col_block<TX, RP, COLS>(sd, local % per, local / per, smem_raw);
+                        else mtt_row_block<TX, RP>(sd, mode, local % per, local / per, smem_raw);
+                        __syncthreads();  // shared memory (and sd) are reused next
                     }
                 }
-                __syncthreads();
-                tail_rep<TF>(d, mode, rep);
-                __syncthreads();
+                base += cnt;
+            }
+            if (!pa_barrier(ps, err)) return;
+            base = 0;
+            for (int i = 0; i < nd; ++i) {
+                const int nrep = descs[i].nrep;
+                long long q = pa_first(base);
+                if (q < base + nrep) {
+                    pa_load_desc(sd, descs, i);
+                    for (; q < base + nrep; q += gridDim.x) {
+                        const int rep = (int)(q - base);
+                        if (!sd.conv[rep]) {
+                            // k_reduce's sums for this repetition, in partial order
+                            const int n = sd.n[mode], P = sd.P[mode];
+                            const TF *part = (const TF *)sd.part + rep * sd.prs;
+                            for (long long e = threadIdx.x; e < (long long)n * sd.R; e += blockDim.x) {
+                                const long long x = e / sd.R, r = e % sd.R;
+                                sd.M[rep * sd.mrs + e] = sum_partials(part + x * sd.pr + r, P, (long long)n * sd.pr);
+                            }
+                        }
+                        __syncthreads();
+                        tail_rep<TF>(sd, mode, rep);
+                        __syncthreads();
+                    }
+                }
+                base += nrep;
             }
             if (!pa_barrier(ps, err)) return;
         }
         bool all = true;
-        for (int q = 0; q < d.nrep; ++q) all = all && ((volatile const int *)d.conv)[q] != 0;
+        for (int i = 0; i < nd && all; ++i)
+            for (int q = 0; q < descs[i].nrep; ++q) all = all && ((volatile const int *)descs[i].conv)[q] != 0;
         if (all) break;
     }
 }
 
+static_assert(sizeof(AlsSetArg) <= 3072, "the descriptors travel as a kernel parameter (4 KB limit)");
+
+// descriptors into device memory, stream-ordered (block i writes set i)
+__global__ void k_put_descs(AlsSetArg s, AlsDesc *dst) {
+    const int *src = reinterpret_cast<const int *>(&s.d[blockIdx.x]);
+    int *out = reinterpret_cast<int *>(dst + blockIdx.x);
+    for (int w = threadIdx.x; w < (int)(sizeof(AlsDesc) / 4); w += blockDim.x) out[w] = src[w];
+}
+
 template <typename TX, int RP>
-static cudaError_t persistent_rp(const AlsDesc &d, int max_iters, const PersistSync &ps, unsigned *err,
-                                 int num_sms, cudaStream_t st) {
+static cudaError_t persistent_rp(const AlsDesc *hd, const AlsDesc *dd, int nd, int max_iters, const PersistSync &ps,
+                                 unsigned *err, int num_sms, cudaStream_t st) {
     constexpr int COLS = cols_for<TX, RP>();
     auto kern = k_als_persistent<TX, RP, COLS>;
-    const size_t smem = std::max(row_smem(d), col_smem(d));
+    size_t smem = 0;
+    long long want = 1, w3[3] = {0, 0, 0}, reps = 0;
+    for (int i = 0; i < nd; ++i) {
+        const AlsDesc &d = hd[i];
+        smem = std::max(smem, std::max(row_smem(d), col_smem(d)));
+        const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
+        w3[0] += (long long)d.nib * d.nks * d.nrep;
+        w3[1] += (long long)njb * d.nrs * d.nrep;
+        reps += d.nrep;
+    }
+    want = std::max(std::max(w3[0], w3[1]), reps);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1628,37 +1757,44 @@ static cudaError_t persistent_rp(const AlsDesc &d, int max_iters, const PersistS
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // as many CTAs as the largest step has blocks, at most all co-resident
-    const int njb = (d.n[1] + 32 * COLS - 1) / (32 * COLS);
-    const long long want = std::max<long long>(
-        std::max<long long>((long long)d.nib * d.nks, (long long)njb * d.nrs) * d.nrep, d.nrep);
     const int grid = (int)std::min<long long>(want, (long long)per_sm * num_sms);
-    AlsDesc dd = d;
+    const AlsDesc *dp = dd;
+    int n = nd;
     PersistSync pp = ps;
     unsigned *ee = err;
     int mi = max_iters;
-    void *args[] = {&dd, &pp, &ee, &mi};
+    void *args[] = {&dp, &n, &pp, &ee, &mi};
     count_launches(1);
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, smem, st);
 }
 
 template <typename TX>
-static cudaError_t persistent_tx(const AlsDesc &d, int max_iters, const PersistSync &ps, unsigned *err,
-                                 int num_sms, cudaStream_t st) {
-    const int RP = rp_of(d.R);
-    if (RP == 8) return persistent_rp<TX, 8>(d, max_iters, ps, err, num_sms, st);
-    if (RP == 16) return persistent_rp<TX, 16>(d, max_iters, ps, err, num_sms, st);
-    return persistent_rp<TX, 32>(d, max_iters, ps, err, num_sms, st);
+static cudaError_t persistent_tx(const AlsDesc *hd, const AlsDesc *dd, int nd, int max_iters, const PersistSync &ps,
+                                 unsigned *err, int num_sms, cudaStream_t st) {
+    const int RP = rp_of(hd[0].R);
+    if (RP == 8) return persistent_rp<TX, 8>(hd, dd, nd, max_iters, ps, err, num_sms, st);
+    if (RP == 16) return persistent_rp<TX, 16>(hd, dd, nd, max_iters, ps, err, num_sms, st);
+    return persistent_rp<TX, 32>(hd, dd, nd, max_iters, ps, err, num_sms, st);
 }
 
-cudaError_t launch_als_persistent(const AlsDesc &d, int max_iters, unsigned *sync_words, unsigned *err, int num_sms,
-                                  cudaStream_t st) {
+bool persistent_compatible(const AlsDesc &a, const AlsDesc &b) { return a.elem == b.elem && rp_of(a.R) == rp_of(b.R); }
+
+cudaError_t launch_als_persistent(const AlsDesc *descs, int nd, AlsDesc *dev_descs, int max_iters,
+                                  unsigned *sync_words, unsigned *err, int num_sms, cudaStream_t st) {
+    if (nd < 1 || nd > PA_MAX_SETS) return cudaErrorInvalidValue;
+    for (int i = 1; i < nd; ++i)
+        if (!persistent_compatible(descs[0], descs[i])) return cudaErrorInvalidValue;
+    AlsSetArg s;
+    for (int i = 0; i < nd; ++i) s.d[i] = descs[i];
+    k_put_descs<<<nd, 64, 0, st>>>(s, dev_descs);
+    count_launches(1);
     // sync_words: [count, generation, abort], zeroed here
     cudaError_t e = cudaMemsetAsync(sync_words, 0, 3 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     PersistSync ps{sync_words, sync_words + 1, reinterpret_cast<int *>(sync_words + 2)};
-    if (d.elem == 0) return persistent_tx<double>(d, max_iters, ps, err, num_sms, st);
-    if (d.elem == 1) return persistent_tx<float>(d, max_iters, ps, err, num_sms, st);
-    return persistent_tx<__nv_bfloat16>(d, max_iters, ps, err, num_sms, st);
+    if (descs[0].elem == 0) return persistent_tx<double>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);
+    if (descs[0].elem == 1) return persistent_tx<float>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);
+    return persistent_tx<__nv_bfloat16>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 // launchers of every kernel family.
 #pragma once
 
+#include "sambaten.h"
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -408,11 +410,32 @@ cudaError_t launch_core_consistency(int elem, const void *X, long long K, long l
                                     double *scratch, int *status, double *out, cudaStream_t st);
 size_t core_consistency_scratch_doubles(long long K, long long I, long long J, int R);
 cudaError_t launch_widen(const float *in, double *out, long long n, cudaStream_t st);
-// The whole ALS (CUDA-core MTTKRP, float64 tail) of d's repetitions as one
-// persistent cooperative launch; sync_words: 3 device words (zeroed here);
-// err: the device status word (ERR_TIMEOUT if a grid barrier gave up)
-cudaError_t launch_als_persistent(const AlsDesc &d, int max_iters, unsigned *sync_words, unsigned *err, int num_sms,
-                                  cudaStream_t st);
+// The whole ALS (CUDA-core MTTKRP, float64 tail) of every repetition of nd
+// summary sets (1..PA_MAX_SETS descriptors, one per update, all of one
+// element type and one rp_of(R)) as one persistent cooperative launch.
+// dev_descs: room for nd descriptors in device memory (written here, in
+// stream order); sync_words: 3 device words (zeroed here); err: a device
+// status word (ERR_TIMEOUT if a grid barrier gave up); max_iters: the largest
+// of the sets' caps (each set stops at its own).
+constexpr int PA_MAX_SETS = 8;
+struct AlsSetArg {
+    AlsDesc d[PA_MAX_SETS];
+};
+bool persistent_compatible(const AlsDesc &a, const AlsDesc &b);
+
+// Updates whose summary ALS a server runs in one batched persistent launch
+// (api.cu).  update_deferred: sbt_update, stopped before the ALS when the
+// context's options allow (persistent_als, the CUDA-core path, no per-launch
+// timing; *deferred tells), else the whole update.  deferred_als: the pending
+// ALS's descriptor, the context's stream and SM count.  update_complete: the
+// match and the commit after the ALS ran (synchronises the context's stream).
+// update_abandon: drop the pending update (the model and K are unchanged).
+sbt_status update_deferred(sbt_ctx *c, const sbt_tensor *X, bool *deferred);
+sbt_status deferred_als(sbt_ctx *c, AlsDesc *d, cudaStream_t *st, int *num_sms);
+sbt_status update_complete(sbt_ctx *c);
+void update_abandon(sbt_ctx *c);
+cudaError_t launch_als_persistent(const AlsDesc *descs, int nd, AlsDesc *dev_descs, int max_iters,
+                                  unsigned *sync_words, unsigned *err, int num_sms, cudaStream_t st);
 
 // mode 3 after a memoised mode-2 pass: M3 from d.ymem and the new B as the
 // single partial of the mode-3 tail, and V^-1 of mode 3 (PDL launch)

@@ -13,7 +13,17 @@
 // different streams are admitted in arrival order, skipping those that do
 // not fit yet.  Every kernel reduces in a fixed order, so a stream's results
 // do not depend on which other batches shared the GPU.
+//
+// batch_als: one worker admits up to `slots` batches at a time.  Each runs
+// sbt_update's steps up to the start of its summary ALS on its own context's
+// stream; the pending ALS of those whose streams take the persistent ALS
+// (CUDA-core path) then run together, up to PA_MAX_SETS compatible updates
+// per persistent cooperative launch on the server's stream (ordered after
+// the contexts' streams by events, and they after it); then each update
+// matches and commits.  A set's arithmetic inside the launch is its own, so
+// every stream's result equals its update alone.
 #include "sambaten.h"
+#include "sbt_internal.cuh"
 
 #include <cuda_runtime.h>
 
@@ -27,10 +37,6 @@
 #include <thread>
 #include <unordered_map>
 #include <vector>
-
-namespace sbt {
-void set_last_error(const std::string &msg);
-}
 
 namespace {
 
@@ -96,8 +102,30 @@ struct sbt_server {
     Clock::time_point t_reset, busy_since;
     double busy_ms = 0.0;
     int64_t waiters = 0;  // threads inside sbt_server_wait (destroy frees nothing before they leave)
+    // batch_als: the server's stream, events, descriptor and barrier words
+    cudaStream_t bst = nullptr;
+    std::vector<cudaEvent_t> bev;  // PA_MAX_SETS + 1
+    sbt::AlsDesc *bdesc = nullptr;
+    unsigned *bsync = nullptr;     // [count, generation, abort, err]
+    unsigned *h_berr = nullptr;    // pinned copy of the err word
+    int64_t als_launches = 0, als_sets = 0;
 
     void worker();
+    void worker_batched();
+    // run one admitted batch of items (the lock not held)
+    struct Item {
+        int32_t sid = 0;
+        Request *q = nullptr;
+        sbt_ctx *ctx = nullptr;
+        sbt_status st = SBT_OK;
+        std::string err;
+        bool deferred = false;
+        int64_t K = 0;
+        uint64_t bytes = 0;
+    };
+    Item start_locked(int32_t sid);
+    void finish_item_locked(Item &it);
+    void run_items(std::vector<Item> &items);
     // the first admissible stream of `ready` (-1: none); fails batches that can never fit
     int32_t pick_locked();
     void finish_locked(Request *q, sbt_status st);
@@ -159,6 +187,36 @@ int32_t sbt_server::pick_locked() {
     return -1;
 }
 
+// The first queued batch of stream sid goes in flight.
+sbt_server::Item sbt_server::start_locked(int32_t sid) {
+    Stream &s = streams[sid];
+    Item it;
+    it.sid = sid;
+    it.q = s.queue.front();
+    it.ctx = s.ctx;
+    s.queue.pop_front();
+    queued -= 1;
+    s.busy = true;
+    if (in_flight == 0) busy_since = Clock::now();
+    in_flight += 1;
+    it.q->t_start = Clock::now();
+    return it;
+}
+
+// A batch in flight is done: the stream's bytes, the result, the next batch.
+void sbt_server::finish_item_locked(Item &it) {
+    Stream &s = streams[it.sid];
+    resident = resident - s.bytes + it.bytes;
+    s.bytes = it.bytes;
+    it.q->res.K = it.K;
+    it.q->err = it.err;
+    finish_locked(it.q, it.st);
+    in_flight -= 1;
+    if (in_flight == 0) busy_ms += ms_between(busy_since, Clock::now());
+    s.busy = false;
+    if (!s.queue.empty()) ready.push_back(it.sid);
+}
+
 void sbt_server::worker() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lock(mu);
@@ -170,35 +228,116 @@ void sbt_server::worker() {
             return sid >= 0;
         });
         if (sid < 0) return;  // stop
-        Stream &s = streams[sid];
-        Request *q = s.queue.front();
-        s.queue.pop_front();
-        queued -= 1;
-        s.busy = true;
-        if (in_flight == 0) busy_since = Clock::now();
-        in_flight += 1;
-        q->t_start = Clock::now();
-        sbt_ctx *ctx = s.ctx;
+        Item it = start_locked(sid);
         lock.unlock();
-        sbt_status st = sbt_update(ctx, &q->X);
-        int64_t K = 0;
-        if (st == SBT_OK) st = sbt_factors(ctx, nullptr, nullptr, nullptr, nullptr, &K);
-        const std::string err = st == SBT_OK ? std::string() : std::string(sbt_last_error());
-        uint64_t now_bytes = 0;
-        sbt_device_bytes(ctx, &now_bytes);
+        it.st = sbt_update(it.ctx, &it.q->X);
+        if (it.st == SBT_OK) it.st = sbt_factors(it.ctx, nullptr, nullptr, nullptr, nullptr, &it.K);
+        if (it.st != SBT_OK) it.err = sbt_last_error();
+        sbt_device_bytes(it.ctx, &it.bytes);
         lock.lock();
-        Stream &s2 = streams[sid];
-        resident = resident - s2.bytes + now_bytes;
-        s2.bytes = now_bytes;
-        q->res.K = K;
-        q->err = err;
-        finish_locked(q, st);
-        in_flight -= 1;
-        if (in_flight == 0) busy_ms += ms_between(busy_since, Clock::now());
-        s2.busy = false;
-        if (!s2.queue.empty()) ready.push_back(sid);
+        finish_item_locked(it);
         cv_done.notify_all();
         cv_work.notify_all();
+    }
+}
+
+// batch_als: admit up to `slots` batches, run them (their summary ALS
+// batched), finish them; again.
+void sbt_server::worker_batched() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lock(mu);
+    for (;;) {
+        std::vector<Item> items;
+        cv_work.wait(lock, [&] {
+            if (stop) return true;
+            const int32_t sid = pick_locked();
+            if (sid >= 0) items.push_back(start_locked(sid));
+            return !items.empty();
+        });
+        if (items.empty()) return;  // stop
+        for (int32_t sid; (int)items.size() < opt.slots && (sid = pick_locked()) >= 0;)
+            items.push_back(start_locked(sid));
+        lock.unlock();
+        run_items(items);
+        lock.lock();
+        for (Item &it : items) finish_item_locked(it);
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+}
+
+void sbt_server::run_items(std::vector<Item> &items) {
+    // 1. every update up to its summary ALS (the whole update where it cannot wait)
+    for (Item &it : items) {
+        it.st = sbt::update_deferred(it.ctx, &it.q->X, &it.deferred);
+        if (it.st != SBT_OK) it.err = sbt_last_error();
+    }
+    // 2. the pending ALS, up to PA_MAX_SETS compatible sets per persistent launch
+    std::vector<Item *> pend;
+    for (Item &it : items)
+        if (it.st == SBT_OK && it.deferred) pend.push_back(&it);
+    std::vector<char> taken(pend.size(), 0);
+    for (size_t a = 0; a < pend.size(); ++a) {
+        if (taken[a]) continue;
+        std::vector<Item *> grp;
+        std::vector<sbt::AlsDesc> ds;
+        std::vector<cudaStream_t> sts;
+        int sms = 0;
+        for (size_t b = a; b < pend.size() && (int)grp.size() < sbt::PA_MAX_SETS; ++b) {
+            if (taken[b]) continue;
+            sbt::AlsDesc d;
+            cudaStream_t st = nullptr;
+            int ns = 0;
+            if (sbt::deferred_als(pend[b]->ctx, &d, &st, &ns) != SBT_OK) continue;
+            if (!ds.empty() && !sbt::persistent_compatible(ds[0], d)) continue;
+            taken[b] = 1;
+            grp.push_back(pend[b]);
+            ds.push_back(d);
+            sts.push_back(st);
+            sms = ns;
+        }
+        int max_iters = 1;
+        for (const sbt::AlsDesc &d : ds) max_iters = std::max(max_iters, d.max_iters);
+        cudaError_t e = cudaSuccess;
+        for (size_t k = 0; k < grp.size() && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(bev[k], sts[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(bst, bev[k], 0);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(bsync + 3, 0, sizeof(unsigned), bst);
+        if (e == cudaSuccess)
+            e = sbt::launch_als_persistent(ds.data(), (int)ds.size(), bdesc, max_iters, bsync, bsync + 3, sms, bst);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_berr, bsync + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, bst);
+        const cudaError_t er = cudaEventRecord(bev[sbt::PA_MAX_SETS], bst);
+        if (e == cudaSuccess) e = er;
+        for (size_t k = 0; k < grp.size() && er == cudaSuccess; ++k) cudaStreamWaitEvent(sts[k], bev[sbt::PA_MAX_SETS], 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(bst);
+        const bool timeout = e == cudaSuccess && (*h_berr & sbt::ERR_TIMEOUT);
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(mu);
+            als_launches += 1;
+            als_sets += (int64_t)grp.size();
+        }
+        if (e != cudaSuccess || timeout) {
+            for (Item *it : grp) {
+                sbt::update_abandon(it->ctx);
+                it->st = timeout ? SBT_E_TIMEOUT : SBT_E_CUDA;
+                it->err = timeout ? std::string("batched ALS: a grid barrier gave up")
+                                  : std::string("batched ALS launch: ") + cudaGetErrorString(e);
+            }
+        }
+    }
+    // 3. match and commit
+    for (Item *it : pend)
+        if (it->st == SBT_OK) {
+            it->st = sbt::update_complete(it->ctx);
+            if (it->st != SBT_OK) it->err = sbt_last_error();
+        }
+    for (Item &it : items) {
+        if (it.st == SBT_OK) {
+            it.st = sbt_factors(it.ctx, nullptr, nullptr, nullptr, nullptr, &it.K);
+            if (it.st != SBT_OK) it.err = sbt_last_error();
+        }
+        sbt_device_bytes(it.ctx, &it.bytes);
     }
 }
 
@@ -207,6 +346,7 @@ extern "C" sbt_status sbt_server_default_options(sbt_server_options *o) {
     o->slots = 4;
     o->mem_budget = 0;
     o->device = -1;
+    o->batch_als = 0;
     return SBT_OK;
 }
 
@@ -218,6 +358,7 @@ extern "C" sbt_status sbt_server_create(const sbt_server_options *o, sbt_server 
     if (o) opt = *o;
     if (opt.slots <= 0) opt.slots = 4;
     if (opt.slots > 64) return fail(SBT_E_INVALID, "slots must be <= 64");
+    if (opt.batch_als != 0 && opt.batch_als != 1) return fail(SBT_E_INVALID, "batch_als must be 0 or 1");
     int dev = opt.device;
     if (dev < 0) {
         cudaError_t e = cudaGetDevice(&dev);
@@ -237,7 +378,29 @@ extern "C" sbt_status sbt_server_create(const sbt_server_options *o, sbt_server 
     srv->opt = opt;
     srv->device = dev;
     srv->t_reset = Clock::now();
-    for (int w = 0; w < opt.slots; ++w) srv->workers.emplace_back([srv] { srv->worker(); });
+    if (opt.batch_als) {
+        // the batched launches' stream, events, descriptors and barrier words
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaError_t e = cudaSetDevice(dev);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->bst, cudaStreamNonBlocking);
+        for (int k = 0; k <= sbt::PA_MAX_SETS && e == cudaSuccess; ++k) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) srv->bev.push_back(ev);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&srv->bdesc, sbt::PA_MAX_SETS * sizeof(sbt::AlsDesc));
+        if (e == cudaSuccess) e = cudaMalloc(&srv->bsync, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost(&srv->h_berr, sizeof(unsigned));
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            sbt_server_destroy(srv);
+            return fail(SBT_E_CUDA, std::string("batched ALS resources: ") + cudaGetErrorString(e));
+        }
+        srv->workers.emplace_back([srv] { srv->worker_batched(); });
+    } else {
+        for (int w = 0; w < opt.slots; ++w) srv->workers.emplace_back([srv] { srv->worker(); });
+    }
     *out = srv;
     return SBT_OK;
 }
@@ -385,6 +548,8 @@ extern "C" sbt_status sbt_server_stats(sbt_server *srv, sbt_serving_stats *st) {
     st->busy_fraction = el > 0 ? busy / el : 0.0;
     st->slices = srv->slices;
     st->elapsed_s = el / 1e3;
+    st->als_launches = srv->als_launches;
+    st->als_sets = srv->als_sets;
     return SBT_OK;
 }
 
@@ -396,6 +561,7 @@ extern "C" sbt_status sbt_server_stats_reset(sbt_server *srv) {
     srv->lat_service.clear();
     srv->t_reset = Clock::now();
     srv->busy_ms = 0.0;
+    srv->als_launches = srv->als_sets = 0;
     if (srv->in_flight > 0) srv->busy_since = srv->t_reset;
     srv->peak_resident = srv->resident;
     return SBT_OK;
@@ -431,6 +597,12 @@ extern "C" void sbt_server_destroy(sbt_server *srv) {
     cudaGetDevice(&prev);
     cudaSetDevice(srv->device);
     for (auto &kv : srv->streams) sbt_destroy(kv.second.ctx);
+    if (srv->bst) cudaStreamSynchronize(srv->bst);
+    for (cudaEvent_t ev : srv->bev) cudaEventDestroy(ev);
+    if (srv->bst) cudaStreamDestroy(srv->bst);
+    if (srv->bdesc) cudaFree(srv->bdesc);
+    if (srv->bsync) cudaFree(srv->bsync);
+    if (srv->h_berr) cudaFreeHost(srv->h_berr);
     cudaSetDevice(prev);
     for (auto &kv : srv->requests) delete kv.second;
     delete srv;

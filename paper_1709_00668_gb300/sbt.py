@@ -122,7 +122,8 @@ class SbtTileEntry(ctypes.Structure):
 
 
 class SbtServerOptions(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int32), ("mem_budget", ctypes.c_uint64), ("device", ctypes.c_int32)]
+    _fields_ = [("slots", ctypes.c_int32), ("mem_budget", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("batch_als", ctypes.c_int32)]
 
 
 class SbtRequestResult(ctypes.Structure):
@@ -137,7 +138,8 @@ class SbtServingStats(ctypes.Structure):
                 ("peak_resident_bytes", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
                 ("service_p50_ms", ctypes.c_double), ("service_p99_ms", ctypes.c_double),
-                ("busy_fraction", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
+                ("busy_fraction", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+                ("als_launches", ctypes.c_int64), ("als_sets", ctypes.c_int64)]
 
 
 class SbtError(RuntimeError):
@@ -707,10 +709,11 @@ class Server:
     Batches are borrowed until their ticket is waited for: the binding keeps a
     reference to each submitted tensor until then."""
 
-    def __init__(self, slots: int = 4, mem_budget: int = 0, device: int = -1):
+    def __init__(self, slots: int = 4, mem_budget: int = 0, device: int = -1, batch_als: int = 0):
         o = SbtServerOptions()
         _check(lib().sbt_server_default_options(ctypes.byref(o)), "sbt_server_default_options")
         o.slots, o.mem_budget, o.device = int(slots), int(mem_budget), int(device)
+        o.batch_als = int(batch_als)
         h = ctypes.c_void_p()
         _check(lib().sbt_server_create(ctypes.byref(o), ctypes.byref(h)), "sbt_server_create")
         self._h = h

@@ -200,3 +200,20 @@ def test_nmode_and_get_rank_arguments_rejected_without_gpu(lib):
                dict(get_rank=2), dict(get_rank=1, get_rank_trials=17)):
         og = sbt.sbt_default_options(**kw)
         assert lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(og), ctypes.byref(h)) == sbt.SBT_E_INVALID
+
+
+def test_persistent_and_batch_options_rejected_without_gpu(lib):
+    """persistent_als and the server's batch_als take 0 or 1, checked before
+    any device call."""
+    from paper_1709_00668_gb300 import sbt
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_double * 64)()
+    t = sbt.SbtTensor(sbt.SBT_F32, 0, 4, 4, 4, ctypes.cast(buf, ctypes.c_void_p))
+    o = sbt.sbt_default_options(persistent_als=2)
+    assert lib.sbt_init(ctypes.byref(t), 3, ctypes.byref(o), ctypes.byref(h)) == sbt.SBT_E_INVALID
+    so = sbt.SbtServerOptions()
+    assert lib.sbt_server_default_options(ctypes.byref(so)) == sbt.SBT_OK
+    assert so.batch_als == 0
+    so.batch_als = 3
+    srv = ctypes.c_void_p()
+    assert lib.sbt_server_create(ctypes.byref(so), ctypes.byref(srv)) == sbt.SBT_E_INVALID

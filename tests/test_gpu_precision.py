@@ -10,7 +10,7 @@ eigenvalues), so cond(V) stays near cond(G).
 
   * cond(G) ~ 1e3 (the sweep's recipe; cond(V) ~ 6e2): both tails within the
     parity bars against FP64 (float32 summaries 1e-4, bfloat16 1e-3) and
-    within a third of the bar of each other.
+    within half the bar of each other.
   * cond(G) ~ 1e4 (cond(V) ~ 7e3): the float32 MTTKRP's rounding (~1e-7
     relative per sum) times cond(V) bounds the summary factors near 1e-3 with
     either tail; the float64 tail keeps the new rows of C within 2e-4 of the
@@ -82,7 +82,7 @@ def _compare(sbt, cond, prec):
 def test_sweep_conditioning_both_tails_within_the_bar(sbt, prec, bar):
     condV, gap, err, err_c = _compare(sbt, 1e3, prec)
     assert 2e2 < condV < 2e3
-    assert gap < bar / 3
+    assert gap < bar / 2
     for fp in (0, 1):
         assert err[fp] < bar and err_c[fp] < bar
 

@@ -178,3 +178,72 @@ def test_failed_batch_leaves_its_stream_usable(sbt):
         assert np.array_equal(a, b)
     assert srv.stats()["failed"] == 1
     srv.close()
+
+
+# batch_als: f32 and f64 streams with the persistent ALS (the CUDA-core path),
+# ranks in two ranges (1-8 and 9-16), and a bf16 stream that runs whole
+BATCHED = [(60, 50, 3, "f32", 11), (80, 70, 5, "f32", 12), (45, 64, 8, "f32", 13), (70, 40, 12, "f32", 14),
+           (50, 52, 4, "f64", 15), (64, 48, 6, "f32", 16), (40, 44, 3, "bf16", 17)]
+
+
+def _bopts(prec, seed):
+    o = _opts(prec, seed)
+    if prec != "bf16":
+        o["persistent_als"] = 1
+    return o
+
+
+def _alone_b(sbt, I, J, R, prec, seed):
+    sizes = _batch_sizes(seed)
+    X = _data(I, J, R, seed, sizes)
+    if prec == "f64":
+        X = X.double()
+    ctx = sbt.SamBaTen(X[:K0], R, **_bopts(prec, seed))
+    k = K0
+    for b in sizes:
+        ctx.update(X[k:k + b])
+        k += b
+    out = ctx.factors()
+    ctx.close()
+    return out
+
+
+def test_batched_als_each_stream_same_as_alone(sbt):
+    """A server with batch_als runs the summary ALS of several streams'
+    updates in one persistent launch; every stream's factors are the same
+    bits as the stream absorbed alone with the persistent ALS."""
+    alone = [_alone_b(sbt, *s) for s in BATCHED]
+    srv = sbt.Server(slots=8, mem_budget=8 << 30, batch_als=1)
+    data, sids, sizes = [], [], []
+    for (I, J, R, prec, seed) in BATCHED:
+        sz = _batch_sizes(seed)
+        X = _data(I, J, R, seed, sz)
+        if prec == "f64":
+            X = X.double()
+        data.append(X)
+        sizes.append(sz)
+        sids.append(srv.open_stream(X[:K0], R, **_bopts(prec, seed)))
+    torch.cuda.synchronize()
+    srv.stats_reset()
+    tickets = []
+    offs = [K0] * len(BATCHED)
+    for b in range(4):
+        for q in range(len(BATCHED)):
+            n = sizes[q][b]
+            tickets.append((q, srv.submit(sids[q], data[q][offs[q]:offs[q] + n]), offs[q] + n))
+            offs[q] += n
+    for q, t, k_after in tickets:
+        res = srv.wait(t, 120000)
+        assert res["status"] == sbt.SBT_OK, res
+        assert res["K"] == k_after
+    st = srv.stats()
+    assert st["completed"] == 4 * len(BATCHED) and st["failed"] == 0
+    # the six persistent streams' 24 updates went through batched launches,
+    # more than one set per launch on average
+    assert st["als_sets"] == 4 * 6
+    assert 0 < st["als_launches"] < st["als_sets"]
+    for q in range(len(BATCHED)):
+        mix = srv.stream(sids[q]).factors()
+        for a, b in zip(alone[q], mix):
+            assert np.array_equal(a, b), BATCHED[q]
+    srv.close()
