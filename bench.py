@@ -108,6 +108,9 @@ def parse():
     ap.add_argument("--latency", action="store_true",
                     help="small dense FP64 workload 100x100x(50+5x10), R=5, s=2, r=4: microseconds per batch "
                          "update, the CUDA-graph ALS against the persistent ALS (one JSON line)")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="--latency: launch the graph arm's ALS kernels directly (per-launch events) so that a "
+                         "profiler lists them; its times are then not the graph's")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same summary shapes, 200 initial slices (a few GB on the device)")
     args = ap.parse_args()
@@ -1010,7 +1013,9 @@ def run_latency(args):
         for run in range(args.warmup + args.steps):
             ctx = sbt.SamBaTen(X0, w["R"], **o)
             torch.cuda.synchronize()
-            ctx.profile_reset(timing=False)
+            # --launch-list: per-launch timing on, so that the graph arm's ALS
+            # kernels run as direct launches a profiler can list (not for timing)
+            ctx.profile_reset(timing=bool(args.launch_list) and name == "graph")
             for Xn in news:
                 t0 = time.perf_counter()
                 ctx.update(Xn)
