@@ -1160,7 +1160,9 @@ __device__ __forceinline__ double sum_strided(const double *q, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// Start values, Grams and ||X_s||^2 (one CTA per repetition)
+// Start values, Grams and ||X_s||^2: grid (repetitions, 4); CTA (rep, m < 3)
+// starts mode m's factor and its Gram, CTA (rep, 3) takes ||X_s||^2 and the
+// per-repetition words
 template <typename TF>
 __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, long long samp_stride,
                                                  int K_old, int identity, uint64_t seed,
@@ -1170,7 +1172,8 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
     const int R = d.R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint2 key = philox_key(seed, stream_id);
-    for (int m = 0; m < 3; ++m) {
+    const int m = blockIdx.y;
+    if (m < 3) {
         const int n = d.n[m];
         TF *U = (TF *)d.U[m] + (long long)rep * n * R;
         const int *S = samples ? samples + (long long)(rep * 3 + m) * samp_stride : nullptr;
@@ -1187,13 +1190,9 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
             else
                 U[e] = (TF)init_value(key, gx, r, m, rep + d.rep0, batch);
         }
-    }
-    __syncthreads();
-    double *G = d.G + (long long)rep * 3 * R * R;
-    const int npairs = R * (R + 1) / 2;
-    for (int m = 0; m < 3; ++m) {
-        const int n = d.n[m];
-        const TF *U = (const TF *)d.U[m] + (long long)rep * n * R;
+        __syncthreads();
+        double *G = d.G + (long long)rep * 3 * R * R;
+        const int npairs = R * (R + 1) / 2;
         for (int pq = warp; pq < npairs; pq += 8) {
             int r = 0, rem = pq;
             while (rem >= R - r) {
@@ -1221,6 +1220,7 @@ __global__ void __launch_bounds__(256) k_prepare(AlsDesc d, const int *samples, 
                 }
             }
         }
+        return;
     }
     // ||X_s||^2 from the row sums, fixed order
     __shared__ double red[256];
@@ -1578,10 +1578,10 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
                                bool identity, uint64_t seed, uint32_t stream_id, uint32_t batch,
                                const double *rowsq, cudaStream_t st, const WarmStart &ws) {
     if (d.elem == 0)
-        k_prepare<double><<<d.nrep, 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
+        k_prepare<double><<<dim3(d.nrep, 4), 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
                                                   stream_id, batch, rowsq, ws);
     else
-        k_prepare<float><<<d.nrep, 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
+        k_prepare<float><<<dim3(d.nrep, 4), 256, 0, st>>>(d, samples, samp_stride, K_old, identity ? 1 : 0, seed,
                                                  stream_id, batch, rowsq, ws);
     count_launches(1);
     return cudaGetLastError();

@@ -69,13 +69,35 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     // per mode over the shared rows: U'(:,r')^T anchor(:,r), |U'(:,r')|^2, |anchor(:,r)|^2
     for (int q = 0; q < 3; ++q) {
         Acc acc[MATCH_ITEMS];
-        for (int t0 = 0; t0 < nsh[q]; t0 += MATCH_TS) {
-            const int rows = min(MATCH_TS, nsh[q] - t0);
+        // tiles of as many rows as R columns fill (the staged rows are packed
+        // by R): few global round trips per mode; each item still adds the
+        // rows in order
+        const int TR = (MATCH_TS * 32) / R;
+        for (int t0 = 0; t0 < nsh[q]; t0 += TR) {
+            const int rows = min(TR, nsh[q] - t0);
             __syncthreads();
-            for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
-                const int t = t0 + e / R, c = e % R;
-                su[e] = c < Rs ? U[q][(long long)t * Rs + c] : (TF)0;
-                sa[e] = Acc::anchor(old[q][(long long)S[q][t] * R + c]);
+            // four entries per thread and round: the sampled indices, then
+            // the anchor rows, all loads of a round in flight together
+            for (int e0 = threadIdx.x; e0 < rows * R; e0 += 4 * blockDim.x) {
+                int row[4];
+                TF uv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < rows * R) {
+                        const int t = t0 + e / R, c = e % R;
+                        row[u] = S[q][t];
+                        uv[u] = c < Rs ? U[q][(long long)t * Rs + c] : (TF)0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < rows * R) {
+                        su[e] = uv[u];
+                        sa[e] = Acc::anchor(old[q][(long long)row[u] * R + e % R]);
+                    }
+                }
             }
             __syncthreads();
 #pragma unroll
