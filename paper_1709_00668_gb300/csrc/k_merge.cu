@@ -196,15 +196,36 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         const int k = e / R, r = e % R, rp = iperm[r];
         cn[e] = rp < 0 ? NAN : scale[2][rp] * (double)U[2][(long long)(m.nK + k) * Rs + rp];
     }
-    // zero-entry proposals (Alg. 1 step 8)
-    for (int q = 0; q < 3; ++q) {
-        double *pp = m.prop + ((long long)rep * 3 + q) * m.pmax * R;
-        for (int e = threadIdx.x; e < nsh[q] * R; e += blockDim.x) {
-            const int t = e / R, r = e % R, rp = iperm[r];
+    // zero-entry proposals (Alg. 1 step 8): the three modes' entries as one
+    // sequence, four per thread and round, the sampled indices and then the
+    // old and summary values of a round in flight together
+    const int tot0 = nsh[0] * R, tot01 = tot0 + nsh[1] * R, tot = tot01 + nsh[2] * R;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * blockDim.x) {
+        int qv[4], ev[4], row[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int g = e0 + u * blockDim.x;
+            qv[u] = g < tot0 ? 0 : (g < tot01 ? 1 : 2);
+            ev[u] = g - (qv[u] == 0 ? 0 : (qv[u] == 1 ? tot0 : tot01));
+            row[u] = g < tot ? S[qv[u]][ev[u] / R] : 0;
+        }
+        double ov[4], uv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int g = e0 + u * blockDim.x;
+            const int q = qv[u], t = ev[u] / R, r = ev[u] % R;
+            const int rp = g < tot ? iperm[r] : -1;
+            ov[u] = rp >= 0 ? old[q][(long long)row[u] * R + r] : 1.0;
+            uv[u] = rp >= 0 ? (double)U[q][(long long)t * Rs + rp] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int g = e0 + u * blockDim.x;
+            if (g >= tot) continue;
+            const int q = qv[u], r = ev[u] % R, rp = iperm[r];
             double val = NAN;
-            if (rp >= 0 && old[q][(long long)S[q][t] * R + r] == 0.0)
-                val = scale[q][rp] * (double)U[q][(long long)t * Rs + rp];
-            pp[e] = val;
+            if (rp >= 0 && ov[u] == 0.0) val = scale[q][rp] * uv[u];
+            m.prop[((long long)rep * 3 + q) * m.pmax * R + ev[u]] = val;
         }
     }
 }
