@@ -262,7 +262,7 @@ def time_updates(ctx, batches, torch, stream, *, host=False, read_back=False):
         ctx.update(b)
         if read_back:
             lam, A, B, C = ctx.factors()
-            d2h += C.nbytes + lam.nbytes
+            d2h += lam.nbytes + A.nbytes + B.nbytes + C.nbytes
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0

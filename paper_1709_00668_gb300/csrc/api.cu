@@ -336,8 +336,11 @@ static sbt_status append_slices(sbt_ctx *c, const sbt_tensor *X, int64_t K0, uns
     const void *src = X->data;
     int ldin = c->J;
     if (!X->on_device) {
-        CK(cudaMemcpy2DAsync(dst, (size_t)c->lds * es, X->data, (size_t)c->J * es, (size_t)c->J * es,
-                             (size_t)X->K * c->I, cudaMemcpyHostToDevice, c->stream));
+        if (c->lds == c->J)  // rows already at the store's pitch: one contiguous copy
+            CK(cudaMemcpyAsync(dst, X->data, (size_t)X->K * c->I * c->J * es, cudaMemcpyHostToDevice, c->stream));
+        else
+            CK(cudaMemcpy2DAsync(dst, (size_t)c->lds * es, X->data, (size_t)c->J * es, (size_t)c->J * es,
+                                 (size_t)X->K * c->I, cudaMemcpyHostToDevice, c->stream));
         src = dst;
         ldin = c->lds;
     }

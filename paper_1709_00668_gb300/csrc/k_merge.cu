@@ -20,6 +20,7 @@ template <> struct MatchAcc<double> {
     __device__ __forceinline__ void add_prod(double u, Anchor a) { v = fma(u, a, v); }
     __device__ __forceinline__ void add_sq(double u) { v = fma(u, u, v); }
     __device__ __forceinline__ void add_sq_anchor(Anchor a) { v = fma(a, a, v); }
+    __device__ __forceinline__ void merge(const MatchAcc &o) { v += o.v; }
     __device__ __forceinline__ double value() const { return v; }
 };
 template <> struct MatchAcc<float> {
@@ -29,6 +30,7 @@ template <> struct MatchAcc<float> {
     __device__ __forceinline__ void add_prod(float u, Anchor a) { v = df_fma(v, DF{u, 0.f}, a); }
     __device__ __forceinline__ void add_sq(float u) { v = df_add_sq(v, u); }
     __device__ __forceinline__ void add_sq_anchor(Anchor a) { v = df_fma(v, a, a); }
+    __device__ __forceinline__ void merge(const MatchAcc &o) { v = df_add(v, o.v); }
     __device__ __forceinline__ double value() const { return df_value(v); }
 };
 
@@ -66,6 +68,12 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     }
     if (threadIdx.x == 0) zflag = 0;
     const int nitems = R * R + 2 * R;
+    // few items (small R): `split` threads per item, each over the rows
+    // t = part (mod split); the parts are merged in order 0..split-1
+    const int split = nitems <= 64 ? 4 : (nitems <= 128 ? 2 : 1);
+    const int part = threadIdx.x % split;
+    static_assert(sizeof(TF) * MATCH_TS * 32 >= 256 * sizeof(Acc), "the merge reuses the staging buffer");
+    Acc *parts = reinterpret_cast<Acc *>(su);  // free between a mode's last tile and the next mode's first
     // per mode over the shared rows: U'(:,r')^T anchor(:,r), |U'(:,r')|^2, |anchor(:,r)|^2
     for (int q = 0; q < 3; ++q) {
         Acc acc[MATCH_ITEMS];
@@ -100,26 +108,35 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
                 }
             }
             __syncthreads();
+            // this thread's first row of the tile among rows = part (mod split)
+            const int tb = ((part - t0) % split + split) % split;
 #pragma unroll
             for (int u = 0; u < MATCH_ITEMS; ++u) {
-                const int item = threadIdx.x + u * 256;
-                if (item >= nitems) break;
+                const int item = (threadIdx.x + u * 256) / split;
+                if (item >= nitems || (split > 1 && u > 0)) break;
                 if (item < R * R) {
                     const int rp = item / R, r = item % R;
-                    for (int t = 0; t < rows; ++t) acc[u].add_prod(su[t * R + rp], sa[t * R + r]);
+                    for (int t = tb; t < rows; t += split) acc[u].add_prod(su[t * R + rp], sa[t * R + r]);
                 } else if (item < R * R + R) {
                     const int rp = item - R * R;
-                    for (int t = 0; t < rows; ++t) acc[u].add_sq(su[t * R + rp]);
+                    for (int t = tb; t < rows; t += split) acc[u].add_sq(su[t * R + rp]);
                 } else {
                     const int r = item - R * R - R;
-                    for (int t = 0; t < rows; ++t) acc[u].add_sq_anchor(sa[t * R + r]);
+                    for (int t = tb; t < rows; t += split) acc[u].add_sq_anchor(sa[t * R + r]);
                 }
             }
         }
+        if (split > 1) {
+            __syncthreads();
+            parts[threadIdx.x] = acc[0];
+            __syncthreads();
+            if (part == 0 && threadIdx.x / split < nitems)
+                for (int k = 1; k < split; ++k) acc[0].merge(parts[threadIdx.x + k]);
+        }
 #pragma unroll
         for (int u = 0; u < MATCH_ITEMS; ++u) {
-            const int item = threadIdx.x + u * 256;
-            if (item >= nitems) break;
+            const int item = (threadIdx.x + u * 256) / split;
+            if (item >= nitems || (split > 1 && (u > 0 || part != 0))) break;
             const double v = acc[u].value();
             if (item < R * R) {
                 gam[q][item / R][item % R] = v;  // the dot product; divided by the norms below
