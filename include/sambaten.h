@@ -19,7 +19,9 @@
  *   - Factor matrices are row-major n x R doubles: U[x * R + r].
  *   - Input buffers are borrowed for the duration of the call and copied; the
  *     caller keeps ownership.  on_device = 1 means the pointer is device memory
- *     of the context's device, ordered on the context's CUDA stream.
+ *     of the context's device, ordered on the context's CUDA stream.  Host
+ *     input in page-locked (pinned) memory is read by the device in place
+ *     during the call; pageable host input is copied first.
  *   - Output buffers are caller-owned host memory unless stated otherwise.
  *   - R <= SBT_MAX_RANK, r <= SBT_MAX_REPS.
  *   - Everything computes on the GPU; there is no CPU fallback.  A missing

@@ -336,13 +336,29 @@ static sbt_status append_slices(sbt_ctx *c, const sbt_tensor *X, int64_t K0, uns
     const void *src = X->data;
     int ldin = c->J;
     if (!X->on_device) {
-        if (c->lds == c->J)  // rows already at the store's pitch: one contiguous copy
-            CK(cudaMemcpyAsync(dst, X->data, (size_t)X->K * c->I * c->J * es, cudaMemcpyHostToDevice, c->stream));
-        else
-            CK(cudaMemcpy2DAsync(dst, (size_t)c->lds * es, X->data, (size_t)c->J * es, (size_t)c->J * es,
-                                 (size_t)X->K * c->I, cudaMemcpyHostToDevice, c->stream));
-        src = dst;
-        ldin = c->lds;
+        // page-locked host memory is mapped into the device's address space:
+        // the append kernel then reads the batch over the host link and
+        // writes the store in the same pass (no separate copy, no second
+        // read of the copied slices); pageable memory is copied first
+        cudaPointerAttributes pa;
+        const void *mapped = nullptr;
+        if (cudaPointerGetAttributes(&pa, X->data) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
+        } else {
+            cudaGetLastError();  // an unregistered pointer is not an error here
+        }
+        if (mapped) {
+            src = mapped;
+        } else {
+            if (c->lds == c->J)  // rows already at the store's pitch: one contiguous copy
+                CK(cudaMemcpyAsync(dst, X->data, (size_t)X->K * c->I * c->J * es, cudaMemcpyHostToDevice,
+                                   c->stream));
+            else
+                CK(cudaMemcpy2DAsync(dst, (size_t)c->lds * es, X->data, (size_t)c->J * es, (size_t)c->J * es,
+                                     (size_t)X->K * c->I, cudaMemcpyHostToDevice, c->stream));
+            src = dst;
+            ldin = c->lds;
+        }
     }
     CK(launch_append(src, c->sdtype, X->K, c->I, c->J, ldin, dst, c->lds, c->S, ma, mb, mc,
                      c->samax.p ? c->samax.as<unsigned>() + K0 : nullptr, c->status.as<DevStatus>(), c->stream));

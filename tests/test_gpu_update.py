@@ -293,10 +293,14 @@ def test_host_input_equals_device_input(sbt):
     fac = unit_factors(A, B, C[:20])
     c1, _ = _pair(sbt, X, 20, 3, fac, fixed_iters=1, max_iters=5)
     c2, _ = _pair(sbt, X, 20, 3, fac, fixed_iters=1, max_iters=5)
+    c3, _ = _pair(sbt, X, 20, 3, fac, fixed_iters=1, max_iters=5)
     c1.update(torch.from_numpy(X[20:26]).cuda())
-    c2.update(X[20:26])
-    for a, b in zip(c1.factors(), c2.factors()):
-        assert np.array_equal(a, b)
+    c2.update(X[20:26])                                  # pageable host memory: copied first
+    c3.update(torch.from_numpy(X[20:26]).pin_memory())   # page-locked: read by the append kernel in place
+    for c in (c2, c3):
+        for a, b in zip(c1.factors(), c.factors()):
+            assert np.array_equal(a, b)
+        assert c.K == 26
 
 
 def test_store_grows_past_capacity(sbt):
