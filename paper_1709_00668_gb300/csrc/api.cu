@@ -810,7 +810,7 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
     }
     if (c->opt.persistent_als && !(tc && tc->on) && !c->coo && !c->timing) {
         // one cooperative launch for every iteration and repetition
-        TRY(c->psync.ensure(4 * sizeof(unsigned)));
+        TRY(c->psync.ensure(PA_SYNC_WORDS * sizeof(unsigned)));
         TRY(c->pdesc.ensure(sizeof(AlsDesc)));
         CK(launch_als_persistent(&d, 1, c->pdesc.as<AlsDesc>(), max_iters, c->psync.as<unsigned>(),
                                  &c->status.as<DevStatus>()->err, c->num_sms, c->stream));
@@ -1181,7 +1181,7 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
         TRY(z.need(c->iters_main, (size_t)r * 4));
     }
     if (c->opt.persistent_als) {  // barrier words and the descriptor of the persistent ALS
-        TRY(z.need(c->psync, 4 * sizeof(unsigned)));
+        TRY(z.need(c->psync, PA_SYNC_WORDS * sizeof(unsigned)));
         TRY(z.need(c->pdesc, sizeof(AlsDesc)));
     }
     if (c->opt.get_rank) {

@@ -1602,33 +1602,48 @@ cudaError_t launch_als_prepare(const AlsDesc &d, const int *samples, long long s
 constexpr unsigned PA_SPIN_LIMIT = 1u << 22;
 
 struct PersistSync {
-    unsigned *count;  // arrivals at the current barrier (zero at launch)
-    unsigned *gen;    // barrier generation
-    int *abort;       // a barrier gave up: every CTA leaves
+    unsigned *words;  // PA_SYNC_WORDS, zero at launch: [0] groups arrived, [1] generation, [2] abort,
+                      // [32 (1 + g)] arrivals of CTA group g (a 128-byte line each)
 };
 
-// Grid barrier: the last CTA to arrive resets the count and advances the
-// generation; the others poll it (bounded; on timeout the error word gets
-// ERR_TIMEOUT and every CTA leaves at its next barrier).  Writes before the
-// barrier are visible to every thread after it (fence, arrive, poll, fence,
-// then the CTA barrier).  Returns false if the launch is giving up.
+// Grid barrier in two levels: the CTAs arrive on PA_GROUPS counters (CTA b
+// on counter b mod groups), the last of a group on the top counter, and the
+// last group's CTA resets it and advances the generation, which the others
+// poll (bounded; on timeout the error word gets ERR_TIMEOUT and every CTA
+// leaves at its next barrier).  Each counter sees at most ~grid / groups
+// contending atomics instead of grid.  Writes before the barrier are visible
+// to every thread after it (fence, arrive, poll, fence, then the CTA
+// barrier; every counter is reset before the arrival that follows it).
+// Returns false if the launch is giving up.
 __device__ bool pa_barrier(const PersistSync &ps, unsigned *err) {
     __shared__ int go;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = ps.gen;
-        volatile int *ab = ps.abort;
+        unsigned *w = ps.words;
+        volatile unsigned *gen = w + 1;
+        volatile int *ab = reinterpret_cast<volatile int *>(w + 2);
+        const unsigned ng = min(gridDim.x, (unsigned)PA_GROUPS);
+        const unsigned grp = blockIdx.x % ng;
+        const unsigned gsize = gridDim.x / ng + (grp < gridDim.x % ng ? 1u : 0u);
+        unsigned *gc = w + 32 * (1 + grp);
         const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(ps.count, 1u) == gridDim.x - 1) {
-            *ps.count = 0;
+        bool flip = false;
+        if (atomicAdd(gc, 1u) == gsize - 1) {  // the last of its group
+            *gc = 0;
             __threadfence();
-            atomicAdd(ps.gen, 1u);
-        } else {
+            if (atomicAdd(w, 1u) == ng - 1) {  // the last group
+                *w = 0;
+                __threadfence();
+                atomicAdd(w + 1, 1u);
+                flip = true;
+            }
+        }
+        if (!flip) {
             unsigned it = 0;
             while (*gen == g && !*ab) {
                 if (++it > PA_SPIN_LIMIT) {
-                    atomicExch(ps.abort, 1);
+                    atomicExch(reinterpret_cast<int *>(w + 2), 1);
                     atomicOr(err, ERR_TIMEOUT);
                     break;
                 }
@@ -1788,10 +1803,10 @@ cudaError_t launch_als_persistent(const AlsDesc *descs, int nd, AlsDesc *dev_des
     for (int i = 0; i < nd; ++i) s.d[i] = descs[i];
     k_put_descs<<<nd, 64, 0, st>>>(s, dev_descs);
     count_launches(1);
-    // sync_words: [count, generation, abort], zeroed here
-    cudaError_t e = cudaMemsetAsync(sync_words, 0, 3 * sizeof(unsigned), st);
+    // sync_words: PA_SYNC_WORDS, zeroed here
+    cudaError_t e = cudaMemsetAsync(sync_words, 0, PA_SYNC_WORDS * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    PersistSync ps{sync_words, sync_words + 1, reinterpret_cast<int *>(sync_words + 2)};
+    PersistSync ps{sync_words};
     if (descs[0].elem == 0) return persistent_tx<double>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);
     if (descs[0].elem == 1) return persistent_tx<float>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);
     return persistent_tx<__nv_bfloat16>(descs, dev_descs, nd, max_iters, ps, err, num_sms, st);

@@ -414,10 +414,12 @@ cudaError_t launch_widen(const float *in, double *out, long long n, cudaStream_t
 // summary sets (1..PA_MAX_SETS descriptors, one per update, all of one
 // element type and one rp_of(R)) as one persistent cooperative launch.
 // dev_descs: room for nd descriptors in device memory (written here, in
-// stream order); sync_words: 3 device words (zeroed here); err: a device
+// stream order); sync_words: PA_SYNC_WORDS device words (zeroed here); err: a device
 // status word (ERR_TIMEOUT if a grid barrier gave up); max_iters: the largest
 // of the sets' caps (each set stops at its own).
 constexpr int PA_MAX_SETS = 8;
+constexpr int PA_GROUPS = 16;                        // arrival counters of the grid barrier
+constexpr int PA_SYNC_WORDS = 32 * (1 + PA_GROUPS);  // one 128-byte line each, and the top line
 struct AlsSetArg {
     AlsDesc d[PA_MAX_SETS];
 };

@@ -106,7 +106,7 @@ struct sbt_server {
     cudaStream_t bst = nullptr;
     std::vector<cudaEvent_t> bev;  // PA_MAX_SETS + 1
     sbt::AlsDesc *bdesc = nullptr;
-    unsigned *bsync = nullptr;     // [count, generation, abort, err]
+    unsigned *bsync = nullptr;     // the grid barrier's words, then the err word
     unsigned *h_berr = nullptr;    // pinned copy of the err word
     int64_t als_launches = 0, als_sets = 0;
 
@@ -303,10 +303,11 @@ void sbt_server::run_items(std::vector<Item> &items) {
             e = cudaEventRecord(bev[k], sts[k]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(bst, bev[k], 0);
         }
-        if (e == cudaSuccess) e = cudaMemsetAsync(bsync + 3, 0, sizeof(unsigned), bst);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bsync + sbt::PA_SYNC_WORDS, 0, sizeof(unsigned), bst);
         if (e == cudaSuccess)
-            e = sbt::launch_als_persistent(ds.data(), (int)ds.size(), bdesc, max_iters, bsync, bsync + 3, sms, bst);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_berr, bsync + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, bst);
+            e = sbt::launch_als_persistent(ds.data(), (int)ds.size(), bdesc, max_iters, bsync, bsync + sbt::PA_SYNC_WORDS,
+                                           sms, bst);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_berr, bsync + sbt::PA_SYNC_WORDS, sizeof(unsigned), cudaMemcpyDeviceToHost, bst);
         const cudaError_t er = cudaEventRecord(bev[sbt::PA_MAX_SETS], bst);
         if (e == cudaSuccess) e = er;
         for (size_t k = 0; k < grp.size() && er == cudaSuccess; ++k) cudaStreamWaitEvent(sts[k], bev[sbt::PA_MAX_SETS], 0);
@@ -390,7 +391,7 @@ extern "C" sbt_status sbt_server_create(const sbt_server_options *o, sbt_server 
             if (e == cudaSuccess) srv->bev.push_back(ev);
         }
         if (e == cudaSuccess) e = cudaMalloc(&srv->bdesc, sbt::PA_MAX_SETS * sizeof(sbt::AlsDesc));
-        if (e == cudaSuccess) e = cudaMalloc(&srv->bsync, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(&srv->bsync, (sbt::PA_SYNC_WORDS + 1) * sizeof(unsigned));
         if (e == cudaSuccess) e = cudaMallocHost(&srv->h_berr, sizeof(unsigned));
         cudaSetDevice(prev);
         if (e != cudaSuccess) {
