@@ -247,3 +247,38 @@ def test_batched_als_each_stream_same_as_alone(sbt):
         for a, b in zip(alone[q], mix):
             assert np.array_equal(a, b), BATCHED[q]
     srv.close()
+
+
+def test_batched_als_failed_batch_leaves_the_others(sbt):
+    """batch_als: a batch with a non-finite value fails alone (SBT_E_NONFINITE);
+    the other updates admitted with it, and the failing stream's later
+    batches, give the same bits as each stream absorbed alone."""
+    picks = [BATCHED[0], BATCHED[1], BATCHED[4]]
+    alone = [_alone_b(sbt, *s) for s in picks]
+    srv = sbt.Server(slots=8, mem_budget=8 << 30, batch_als=1)
+    data, sids, sizes = [], [], []
+    for (I, J, R, prec, seed) in picks:
+        sz = _batch_sizes(seed)
+        X = _data(I, J, R, seed, sz)
+        if prec == "f64":
+            X = X.double()
+        data.append(X)
+        sizes.append(sz)
+        sids.append(srv.open_stream(X[:K0], R, **_bopts(prec, seed)))
+    bad = data[0][K0:K0 + 3].clone()
+    bad[1, 2, 3] = float("nan")
+    torch.cuda.synchronize()
+    t_bad = srv.submit(sids[0], bad)
+    tickets, offs = [], [K0] * len(picks)
+    for b in range(4):
+        for q in range(len(picks)):
+            n = sizes[q][b]
+            tickets.append(srv.submit(sids[q], data[q][offs[q]:offs[q] + n]))
+            offs[q] += n
+    assert srv.wait(t_bad)["status"] == sbt.SBT_E_NONFINITE
+    for t in tickets:
+        assert srv.wait(t)["status"] == sbt.SBT_OK
+    for q in range(len(picks)):
+        for a, b in zip(alone[q], srv.stream(sids[q]).factors()):
+            assert np.array_equal(a, b), picks[q]
+    srv.close()
