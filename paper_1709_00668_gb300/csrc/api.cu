@@ -200,7 +200,7 @@ struct sbt_ctx {
     HBuf h_status, h_poll, h_stats;
     // workspace
     Buf samples, khi, klo, Xs, rowsq, U[3], M, part, G, lam_s, fit, fit_prev, normX2, iters, conv, flags;
-    Buf nu, cnew, prop, lam_est, perm, min_score, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
+    Buf nu, cnew, prop, lam_est, perm, min_score, mdots, fitscr, staging, Xt, tpart, xinv, tail_cnt, Gf, dfs;
     Buf Xlo, Xtlo, rowsq2, iters_main;  // refinement: lo parts of the split summary
     Buf ymem;                           // mode-2 pass products for the mode-3 MTTKRP (mode3_pass 0)
     Buf grscr, gcc, rnew;               // GetRank: CorConDia scratch, scores + status words, R_new per repetition
@@ -1201,6 +1201,7 @@ static sbt_status size_update(sbt_ctx *c, const UpdShape &u, bool bound, Sizer &
     TRY(z.need(c->lam_est, (size_t)r * R * 8));
     TRY(z.need(c->perm, (size_t)r * R * 4));
     TRY(z.need(c->min_score, (size_t)r * 8));
+    TRY(z.need(c->mdots, (size_t)r * 3 * (32 * 32 + 64) * 8));
     if (z.dry && u.K_old + u.K_new > c->Kcap) {
         const int64_t ncap = std::max<int64_t>(u.K_old + u.K_new, c->Kcap * 2);
         TRY(z.need(c->store, (size_t)ncap * c->I * c->lds * esize_store(c->sdtype)));
@@ -1215,7 +1216,7 @@ static std::vector<Buf *> ctx_bufs(sbt_ctx *c) {
     return {&c->store, &c->A, &c->B, &c->C, &c->lam, &c->xa, &c->xb, &c->xc, &c->dxa, &c->dxb, &c->xc_new,
             &c->status, &c->samples, &c->khi, &c->klo, &c->Xs, &c->rowsq, &c->U[0], &c->U[1], &c->U[2], &c->M,
             &c->part, &c->G, &c->lam_s, &c->fit, &c->fit_prev, &c->normX2, &c->iters, &c->conv, &c->flags,
-            &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->fitscr, &c->staging,
+            &c->nu, &c->cnew, &c->prop, &c->lam_est, &c->perm, &c->min_score, &c->mdots, &c->fitscr, &c->staging,
             &c->Xt, &c->tpart, &c->xinv, &c->tail_cnt, &c->Gf, &c->dfs, &c->prof_bytes, &c->passes,
             &c->Xlo, &c->Xtlo, &c->rowsq2, &c->iters_main, &c->samax, &c->sscale, &c->ymem,
             &c->grscr, &c->gcc, &c->rnew, &c->psync, &c->pdesc,
@@ -1338,6 +1339,7 @@ static sbt_status match_commit(sbt_ctx *c, const AlsDesc &d, int64_t K_old, int 
     m.lam_est = c->lam_est.as<double>();
     m.perm = c->perm.as<int>();
     m.min_score = c->min_score.as<double>();
+    m.dots = c->mdots.as<double>();
     m.flags = c->flags.as<int>();
     m.lambda_mode = c->opt.lambda_mode;
     m.xa = c->xa.as<unsigned long long>();
@@ -2379,6 +2381,7 @@ extern "C" sbt_status sbt_update_coo(sbt_ctx *c, const sbt_coo *X) {
     TRY(c->lam_est.ensure((size_t)r * R * 8));
     TRY(c->perm.ensure((size_t)r * R * 4));
     TRY(c->min_score.ensure((size_t)r * 8));
+    TRY(c->mdots.ensure((size_t)r * 3 * (32 * 32 + 64) * 8));
     const int64_t nnz_in = X->nnz;
     TRY(match_commit(c, d, K_old, K_new, nI, nJ, nK, samp_stride, 0, false, false));
     c->nnz += nnz_in;

@@ -38,35 +38,31 @@ template <> struct MatchAcc<float> {
 // stays within 48 KB of static shared memory with 16)
 template <typename TF> constexpr int match_ts() { return sizeof(TF) == 8 ? 16 : 32; }
 constexpr int MATCH_ITEMS = (32 * 32 + 2 * 32 + 255) / 256;      // accumulators per thread
+constexpr int MATCH_SLOTS = 32 * 32 + 2 * 32;                     // per-mode sums of a repetition
 
-// One CTA per repetition: shared-row norms (Alg. 1 step 6), cosines and the
-// matching (Lemma 1, Alg. 1 step 7), project back (steps 8-9).
+// The per-mode sums of k_match (one CTA per repetition and mode): over the
+// shared rows, U'(:,r')^T anchor(:,r), |U'(:,r')|^2 and |anchor(:,r)|^2,
+// each item's rows added in order; m.dots[rep][mode][item].
 template <typename TF>
-__global__ void __launch_bounds__(256) k_match(MergeDesc m) {
+__global__ void __launch_bounds__(256) k_match_dots(MergeDesc m) {
     using Acc = MatchAcc<TF>;
     using Anchor = typename Acc::Anchor;
     const int rep = blockIdx.x;
     const int R = m.R;
-    const int Rs = m.rnew ? m.rnew[rep] : R;  // summary components (GetRank: R_new <= R)
+    const int Rs = m.rnew ? m.rnew[rep] : R;
     const int Kp = m.nK + m.K_new;
     const int n[3] = {m.nI, m.nJ, Kp};
-    const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
-    __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32], scale[3][32];
+    const int nsh[3] = {m.nI, m.nJ, m.nK};
     constexpr int MATCH_TS = match_ts<TF>();
     __shared__ TF su[MATCH_TS * 32];
     __shared__ Anchor sa[MATCH_TS * 32];
-    __shared__ int perm[32], iperm[32];
-    __shared__ int zflag;
-    __shared__ HungarianWork hw;  // in shared memory rather than the thread's stack
     const TF *U[3];
     const int *S[3];
     const double *old[3] = {m.A, m.B, m.C};
     for (int q = 0; q < 3; ++q) {
-        // the repetition's n x R slot holds rows of Rs values
         U[q] = (const TF *)m.U[q] + (long long)rep * n[q] * R;
         S[q] = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
     }
-    if (threadIdx.x == 0) zflag = 0;
     const int nitems = R * R + 2 * R;
     // few items (small R): `split` threads per item, each over the rows
     // t = part (mod split); the parts are merged in order 0..split-1
@@ -75,7 +71,8 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
     static_assert(sizeof(TF) * MATCH_TS * 32 >= 256 * sizeof(Acc), "the merge reuses the staging buffer");
     Acc *parts = reinterpret_cast<Acc *>(su);  // free between a mode's last tile and the next mode's first
     // per mode over the shared rows: U'(:,r')^T anchor(:,r), |U'(:,r')|^2, |anchor(:,r)|^2
-    for (int q = 0; q < 3; ++q) {
+    {
+        const int q = blockIdx.y;
         Acc acc[MATCH_ITEMS];
         // tiles of as many rows as R columns fill (the staged rows are packed
         // by R): few global round trips per mode; each item still adds the
@@ -137,20 +134,51 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
         for (int u = 0; u < MATCH_ITEMS; ++u) {
             const int item = (threadIdx.x + u * 256) / split;
             if (item >= nitems || (split > 1 && (u > 0 || part != 0))) break;
-            const double v = acc[u].value();
-            if (item < R * R) {
-                gam[q][item / R][item % R] = v;  // the dot product; divided by the norms below
-            } else if (item < R * R + R) {
-                double s = sqrt(v);
-                if (s == 0.0) {
-                    s = 1.0;
-                    if (item - R * R < Rs) zflag = 1;  // columns past Rs are absent, not zero
-                }
-                nu[q][item - R * R] = s;
-            } else {
-                const double s = sqrt(v);
-                Nn[q][item - R * R - R] = s == 0.0 ? 1.0 : s;
+            m.dots[((long long)rep * 3 + q) * MATCH_SLOTS + item] = acc[u].value();
+        }
+    }
+}
+
+// One CTA per repetition: shared-row norms (Alg. 1 step 6), cosines and the
+// matching (Lemma 1, Alg. 1 step 7), project back (steps 8-9).
+template <typename TF>
+__global__ void __launch_bounds__(256) k_match(MergeDesc m) {
+    const int rep = blockIdx.x;
+    const int R = m.R;
+    const int Rs = m.rnew ? m.rnew[rep] : R;  // summary components (GetRank: R_new <= R)
+    const int Kp = m.nK + m.K_new;
+    const int n[3] = {m.nI, m.nJ, Kp};
+    const int nsh[3] = {m.nI, m.nJ, m.nK};  // shared rows per mode
+    __shared__ double nu[3][32], Nn[3][32], gam[3][32][32], score[32 * 32], lsp[32], scale[3][32];
+    __shared__ int perm[32], iperm[32];
+    __shared__ int zflag;
+    __shared__ HungarianWork hw;  // in shared memory rather than the thread's stack
+    const TF *U[3];
+    const int *S[3];
+    const double *old[3] = {m.A, m.B, m.C};
+    for (int q = 0; q < 3; ++q) {
+        // the repetition's n x R slot holds rows of Rs values
+        U[q] = (const TF *)m.U[q] + (long long)rep * n[q] * R;
+        S[q] = m.samples + (long long)(rep * 3 + q) * m.samp_stride;
+    }
+    if (threadIdx.x == 0) zflag = 0;
+    const int nitems = R * R + 2 * R;
+    // the per-mode sums (k_match_dots): dot products, then norms
+    for (int e = threadIdx.x; e < 3 * nitems; e += blockDim.x) {
+        const int q = e / nitems, item = e % nitems;
+        const double v = m.dots[((long long)rep * 3 + q) * MATCH_SLOTS + item];
+        if (item < R * R) {
+            gam[q][item / R][item % R] = v;  // the dot product; divided by the norms below
+        } else if (item < R * R + R) {
+            double s = sqrt(v);
+            if (s == 0.0) {
+                s = 1.0;
+                if (item - R * R < Rs) zflag = 1;  // columns past Rs are absent, not zero
             }
+            nu[q][item - R * R] = s;
+        } else {
+            const double s = sqrt(v);
+            Nn[q][item - R * R - R] = s == 0.0 ? 1.0 : s;
         }
     }
     __syncthreads();
@@ -248,9 +276,14 @@ __global__ void __launch_bounds__(256) k_match(MergeDesc m) {
 }
 
 cudaError_t launch_match(const MergeDesc &m, cudaStream_t st) {
-    count_launches(1);
-    if (m.elem == 0) k_match<double><<<m.nrep, 256, 0, st>>>(m);
-    else k_match<float><<<m.nrep, 256, 0, st>>>(m);
+    count_launches(2);
+    if (m.elem == 0) {
+        k_match_dots<double><<<dim3(m.nrep, 3), 256, 0, st>>>(m);
+        k_match<double><<<m.nrep, 256, 0, st>>>(m);
+    } else {
+        k_match_dots<float><<<dim3(m.nrep, 3), 256, 0, st>>>(m);
+        k_match<float><<<m.nrep, 256, 0, st>>>(m);
+    }
     return cudaGetLastError();
 }
 

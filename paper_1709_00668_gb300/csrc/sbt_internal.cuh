@@ -521,6 +521,7 @@ struct MergeDesc {
     double *lam_est;     // [rep][R]
     int *perm;           // [rep][R]
     double *min_score;   // [rep]
+    double *dots;        // [rep][3][32 * 32 + 64] per-mode sums of the matching (dot products, norms)
     int *flags;          // [rep]
     int lambda_mode;
     unsigned long long *xa, *xb, *xc, *dxa, *dxb, *xc_new;
