@@ -1015,7 +1015,7 @@ def run_latency(args):
             torch.cuda.synchronize()
             # --launch-list: per-launch timing on, so that the graph arm's ALS
             # kernels run as direct launches a profiler can list (not for timing)
-            ctx.profile_reset(timing=bool(args.launch_list) and name == "graph")
+            ctx.profile_reset(timing=bool(args.launch_list) and name == "graph", direct=True)
             for Xn in news:
                 t0 = time.perf_counter()
                 ctx.update(Xn)

@@ -375,10 +375,15 @@ typedef struct {
                                 the groups each counted in full) */
 } sbt_profile;
 
-/* Zero the counters; timing = 1 also brackets every MTTKRP launch of this
- * context with CUDA events on the stream it runs on (the ALS then runs its
- * kernels directly, polling convergence from the host, rather than as one
- * graph: leave it off for throughput). */
+/* Zero the counters.  timing != 0 also brackets every MTTKRP launch of this
+ * context with CUDA events on the stream it runs on; the ALS then runs in
+ * chunks of check_every iterations, polling convergence from the host after
+ * each, rather than as one graph with a device-side loop (leave it off for
+ * throughput).  timing = 1: each chunk is one launch of a graph of its
+ * kernels and events, captured once per ALS, so that no event interval holds
+ * host submission time; timing = 2: the chunk's kernels launched one by one
+ * (visible to tools that trace kernel launches, intervals may include
+ * submission gaps).  Other values: SBT_E_INVALID. */
 sbt_status sbt_profile_reset(sbt_ctx *ctx, int32_t timing);
 
 /* Read the counters (synchronises the context's stream). */

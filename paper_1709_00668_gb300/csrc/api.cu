@@ -229,7 +229,7 @@ struct sbt_ctx {
     bool passes_pending = false;
     long long launches_per_pass = 0;
     int pass_iters = 0;
-    bool timing = false;
+    int timing = 0;  // 0 off; 1 events, each chunk of iterations as a graph; 2 events, direct launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // MTTKRP timing slots of the ALS graph
     double mtt_ms = 0.0, mtt_busy_ms = 0.0, mtt_launch_ms = 0.0;
     long long launch_base = 0, updates = 0, mtt_launches = 0, mtt_passes = 0;
@@ -694,10 +694,14 @@ static sbt_status ensure_group_rt(sbt_ctx *c, int G) {
 // The kernels of G ALS iterations: group 0 on the library's stream, group g
 // on its own stream, forked from and joined back to the library's stream.
 // Per mode and group: V^-1 on the group's side stream beside its MTTKRP
-// pass, then the tail.  With timing, CUDA events bracket every MTTKRP launch
-// on the stream it runs on (slots from 0).
-static cudaError_t launch_iterations(sbt_ctx *c, const std::vector<AlsPlan> &plans, int G, bool timed) {
+// pass, then the tail.  With timed != 0, CUDA events bracket every MTTKRP
+// launch on the stream it runs on (slots from 0); timed == 2 records them as
+// event nodes of the graph being captured.
+static cudaError_t launch_iterations(sbt_ctx *c, const std::vector<AlsPlan> &plans, int G, int timed) {
     cudaError_t e = cudaSuccess;
+    auto record = [timed](cudaEvent_t ev, cudaStream_t s) {
+        return timed == 2 ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+    };
     const int ng = (int)plans.size();
     if (ng > 1) {
         e = cudaEventRecord(c->ev_groups, c->stream);
@@ -723,9 +727,9 @@ static cudaError_t launch_iterations(sbt_ctx *c, const std::vector<AlsPlan> &pla
                     if (e == cudaSuccess) e = cudaEventRecord(join, side);
                 }
                 const bool pass = !(mode == 2 && d.ymem);  // a memoised mode 3 launches no pass
-                if (e == cudaSuccess && timed && pass) e = cudaEventRecord(c->gev[slot].first, st);
+                if (e == cudaSuccess && timed && pass) e = record(c->gev[slot].first, st);
                 if (e == cudaSuccess) e = mttkrp_mode(c, d, tc, mode, st);
-                if (e == cudaSuccess && timed && pass) e = cudaEventRecord(c->gev[slot].second, st);
+                if (e == cudaSuccess && timed && pass) e = record(c->gev[slot].second, st);
                 if (e == cudaSuccess && xinv) e = cudaStreamWaitEvent(st, join, 0);
                 if (e == cudaSuccess) e = launch_reduce_tail(d, mode, st);
             }
@@ -760,7 +764,7 @@ static sbt_status build_als_loop(sbt_ctx *c, const AlsDesc &d, const std::vector
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t el = launch_iterations(c, plans, G, false);
+            cudaError_t el = launch_iterations(c, plans, G, 0);
             if (el == cudaSuccess)
                 el = launch_als_continue(h, d.conv, d.nrep, c->passes.as<int>(), max_passes, c->stream);
             cudaGraph_t got = nullptr;
@@ -789,10 +793,12 @@ static void settle_als_counts(sbt_ctx *c) {
 // Run ALS iterations until every repetition has converged or max_iters.
 // Throughput path: one graph launch of the device-side loop; the pass count
 // is read back with the caller's next synchronisation.  Timing path (CUDA
-// events around every MTTKRP launch): the same kernels issued directly on the
-// streams, convergence polled every check_every iterations.  Kernels of
-// converged repetitions exit at once, so iterations past convergence cost
-// only their launches.
+// events around every MTTKRP launch): the same kernels in chunks of
+// check_every iterations, convergence polled from the host after each chunk;
+// a chunk is one launch of a graph captured once (timing 1: the kernels and
+// events run back to back, so no interval holds host submission time) or its
+// kernels issued one by one (timing 2).  Kernels of converged repetitions
+// exit at once, so iterations past convergence cost only their launches.
 static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcPlan *tc = nullptr) {
     const int every = c->opt.check_every > 0 ? c->opt.check_every : 4;
     const int G = std::max(1, std::min(every, max_iters));
@@ -840,8 +846,36 @@ static sbt_status run_als(sbt_ctx *c, const AlsDesc &d, int max_iters, const TcP
         CK(cudaEventCreate(&b));
         c->gev.emplace_back(a, b);
     }
+    struct ExecGuard {
+        cudaGraphExec_t x = nullptr;
+        ~ExecGuard() {
+            if (x) cudaGraphExecDestroy(x);
+        }
+    } chunk;
+    long long chunk_launches = 0;
+    if (c->timing == 1) {
+        cudaGraph_t graph = nullptr;
+        const long long base = launch_count();
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = launch_iterations(c, plans, G, 2);
+            e = cudaStreamEndCapture(c->stream, &graph);
+            if (el != cudaSuccess) e = el;
+        }
+        chunk_launches = launch_count() - base;
+        count_launches(-(int)chunk_launches);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&chunk.x, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(SBT_E_CUDA, std::string("ALS (timed) graph: ") + cudaGetErrorString(e));
+    }
     for (int k = 0; k < nl; ++k) {
-        cudaError_t e = launch_iterations(c, plans, G, true);
+        cudaError_t e = cudaSuccess;
+        if (chunk.x) {
+            e = cudaGraphLaunch(chunk.x, c->stream);
+            count_launches((int)chunk_launches);
+        } else {
+            e = launch_iterations(c, plans, G, 1);
+        }
         c->mtt_launches += (long long)c->mtt_per_iter * G;
         const bool poll = (k == nl - 1) || !c->opt.fixed_iters;
         if (e == cudaSuccess && poll)
@@ -1916,7 +1950,8 @@ extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     settle_als_counts(c);
     CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->timing = timing != 0;
+    if (timing < 0 || timing > 2) return fail(SBT_E_INVALID, "timing must be 0, 1 or 2");
+    c->timing = timing;
     c->mtt_ms = 0.0;
     c->mtt_busy_ms = 0.0;
     c->mtt_launch_ms = 0.0;

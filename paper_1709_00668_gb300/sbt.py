@@ -470,8 +470,11 @@ class SamBaTen:
                 "min_score": list(st.min_score[:r]),
                 "perm": [list(st.perm[q][:R]) for q in range(r)], "rank": list(st.rank[:r])}
 
-    def profile_reset(self, timing: bool = True):
-        _check(lib().sbt_profile_reset(self._h, 1 if timing else 0), "sbt_profile_reset")
+    def profile_reset(self, timing: bool = True, direct: bool = False):
+        """timing: CUDA events around every MTTKRP launch; direct: the ALS
+        kernels launched one by one instead of as graph chunks."""
+        mode = 0 if not timing else (2 if direct else 1)
+        _check(lib().sbt_profile_reset(self._h, mode), "sbt_profile_reset")
 
     def profile(self) -> dict:
         p = SbtProfile()

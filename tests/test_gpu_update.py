@@ -410,17 +410,19 @@ def test_marginals_of_extreme_magnitudes_sample_like_oracle(sbt):
 
 def test_device_loop_equals_directly_launched_iterations(sbt):
     """The ALS as one graph with a device-side WHILE loop (throughput path)
-    gives bit-identical results to the same kernels launched one by one with
-    host polling (timing path), with fixed iterations and with the tolerance
-    stop, and reports the passes it ran."""
+    gives bit-identical results to the same kernels in chunks with host
+    polling (timing path: each chunk a captured graph, or its kernels launched
+    one by one), with fixed iterations and with the tolerance stop, and
+    reports the passes it ran."""
     X, A, B, C = planted(64, 48, 46, 4, dtype=torch.float32, seed=16)
     fac = unit_factors(A, B, C[:30])
-    for kw in (dict(fixed_iters=1, max_iters=7), dict(fixed_iters=0, max_iters=40, tol=1e-3)):
+    for kw, direct in ((dict(fixed_iters=1, max_iters=7), False), (dict(fixed_iters=0, max_iters=40, tol=1e-3), False),
+                       (dict(fixed_iters=0, max_iters=40, tol=1e-3), True)):
         for prec in ("bf16", "f32"):
             c_loop, _ = _pair(sbt, X, 30, 4, fac, prec=prec, r=3, **kw)
             c_timed, _ = _pair(sbt, X, 30, 4, fac, prec=prec, r=3, **kw)
             c_loop.profile_reset(timing=False)
-            c_timed.profile_reset(timing=True)
+            c_timed.profile_reset(timing=True, direct=direct)
             for k0 in (30, 38):
                 c_loop.update(torch.from_numpy(X[k0:k0 + 8]).cuda())
                 c_timed.update(torch.from_numpy(X[k0:k0 + 8]).cuda())
