@@ -559,7 +559,8 @@ def run_ours(args):
                 "passes": prof["mttkrp_passes"], "launches": prof["mttkrp_launches"],
                 "mttkrp_share_of_step": busy / (1e3 * secs_prof) if secs_prof > 0 else None,
                 "measured_in": "profiling pass over the same steps: CUDA events around each MTTKRP launch on "
-                               "the stream it runs on; achieved = the passes' algorithmic bytes / the union of "
+                               "the stream it runs on, each chunk of check_every ALS iterations one graph launch "
+                               "of its kernels and events; achieved = the passes' algorithmic bytes / the union of "
                                "the launches' intervals (busy time); avg_pass_span_us = first start to last "
                                "end of each pass's launches; "
                                f"{1e3 * secs_prof / args.steps:.2f} ms per step there",
