@@ -1945,12 +1945,12 @@ extern "C" sbt_status sbt_last_summary_factors(const sbt_ctx *c, int32_t rep, do
 
 extern "C" sbt_status sbt_profile_reset(sbt_ctx *c, int32_t timing) {
     if (!c) return fail(SBT_E_INVALID, "null context");
+    if (timing < 0 || timing > 2) return fail(SBT_E_INVALID, "timing must be 0, 1 or 2");
     DeviceGuard dg(c->device);
     CK(cudaStreamSynchronize(c->stream));
     settle_als_counts(c);
     CK(cudaMemsetAsync(c->prof_bytes.p, 0, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (timing < 0 || timing > 2) return fail(SBT_E_INVALID, "timing must be 0, 1 or 2");
     c->timing = timing;
     c->mtt_ms = 0.0;
     c->mtt_busy_ms = 0.0;

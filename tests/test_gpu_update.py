@@ -408,6 +408,16 @@ def test_marginals_of_extreme_magnitudes_sample_like_oracle(sbt):
         assert np.array_equal(ctx.last_samples(rep, 2), t.Ks)
 
 
+def test_profile_reset_rejects_unknown_timing_modes(sbt):
+    X, A, B, C = planted(40, 32, 30, 3, dtype=torch.float32, seed=21)
+    fac = unit_factors(A, B, C[:24])
+    ctx, _ = _pair(sbt, X, 24, 3, fac, prec="bf16", r=2, fixed_iters=1, max_iters=3)
+    for mode in (-1, 3):
+        assert sbt.lib().sbt_profile_reset(ctx._h, mode) == sbt.SBT_E_INVALID
+    for mode in (0, 1, 2):
+        assert sbt.lib().sbt_profile_reset(ctx._h, mode) == sbt.SBT_OK
+
+
 def test_device_loop_equals_directly_launched_iterations(sbt):
     """The ALS as one graph with a device-side WHILE loop (throughput path)
     gives bit-identical results to the same kernels in chunks with host
